@@ -1,0 +1,64 @@
+"""Seeded input generators: code constructions and the PRNG (no GPU)."""
+import numpy as np
+import pytest
+
+from paper_2406_18655_gb300 import inputs as I
+
+
+def test_splitmix_xoshiro_published_values():
+    # splitmix64 from state 0 yields 0xE220A8397B1DCDAF first (Vigna's reference output).
+    g = I.Xoshiro256ss.__new__(I.Xoshiro256ss)
+    x = np.array([0], dtype=np.uint64) + I._GOLDEN
+    z = x
+    z = (z ^ (z >> np.uint64(30))) * I._SM_M1
+    z = (z ^ (z >> np.uint64(27))) * I._SM_M2
+    z = z ^ (z >> np.uint64(31))
+    assert int(z[0]) == 0xE220A8397B1DCDAF
+    # xoshiro256** state update: with s = (1, 2, 3, 4) the first output is rotl(2*5, 7)*9 = 11520
+    g.s0, g.s1, g.s2, g.s3 = (np.array([v], dtype=np.uint64) for v in (1, 2, 3, 4))
+    assert int(g.next_u64()[0]) == 11520
+    assert int(g.next_u64()[0]) == 0  # s1 becomes 0 after the first update: rotl(0)*9 = 0
+
+
+def test_streams_are_reproducible_by_shot():
+    p = np.full(50, 0.2)
+    a = I.sample_errors(11, 40, p)
+    b = I.sample_errors(11, 10, p, first_shot=30)
+    assert np.array_equal(a[30:], b)
+    assert 0.1 < a.mean() < 0.3
+
+
+@pytest.mark.parametrize("fn,n", [(I.bb72, 72), (I.bb144, 144), (I.bb288, 288)])
+def test_bb_codes(fn, n):
+    hx, hz = fn()
+    assert hx.shape == (n // 2, n) and hz.shape == (n // 2, n)
+    assert np.all(hx.sum(0) == 3) and np.all(hx.sum(1) == 6)
+    assert not np.any((hx.astype(int) @ hz.T.astype(int)) % 2)
+
+
+def test_hgp_instance():
+    h = I.random_regular_ldpc(48, 64, 3, 4, 2406)
+    assert np.all(h.sum(0) == 3) and np.all(h.sum(1) == 4)
+    ov = h.astype(int) @ h.T.astype(int)
+    np.fill_diagonal(ov, 0)
+    assert ov.max() <= 1  # no two rows share two columns: girth >= 6
+    hx, hz = I.hgp(h)
+    assert hx.shape == (3072, 6400)
+    assert np.all(hx.sum(1) == 7)
+    assert sorted(set(hx.sum(0).tolist())) == [3, 4]
+    assert not np.any((hx.astype(int) @ hz.T.astype(int)) % 2)
+
+
+def test_space_time_structure():
+    hx, _ = I.bb72()
+    d = 6
+    st = I.space_time(hx, d)
+    assert st.shape == ((d + 1) * 36, d * (72 + 36))
+    assert st.sum() == d * (3 * 72 + 2 * 36)
+    # measurement faults flip the same detector in two consecutive blocks
+    col = st[:, 72]
+    assert col.sum() == 2 and col[0] == 1 and col[36] == 1
+    e = np.zeros((1, st.shape[1]), np.uint8)
+    e[0, 5] = 1                      # data fault of round 0
+    e[0, 108 + 5] = 1                # the same data fault again in round 1
+    assert not np.any(I.space_time_data_residual(e, 72, 36, d))
