@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 BP + LSD decoder.
+
+Workload (one step = one batch): the [[144,12,12]] bivariate bicycle code, H_X (72 x 144),
+i.i.d. bit flips with p = 0.05, 10^6 seeded synthetic shots resident in HBM, min-sum BP
+(alpha = 0.625, at most 50 iterations, per-shot early exit) then LSD-0 on every shot BP
+does not solve.  L2 is flushed (256 MiB write) between timed steps.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank decodes its own 10^6 shots (weak scaling; shots are
+independent, so there is no collective on the data path) and the step time is the max
+over ranks.  ``--impl reference`` times the CPU oracle (the only reference this project
+has) on the host cores, on a bounded sample of the same workload.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "shots/s + p99 latency: BB[[144,12,12]] BP+LSD vs learned+LSD at equal LER"
+UNIT = "shots/s"
+# Algorithmic work of min-sum BP per edge per executed iteration: abs, two-minimum
+# tracking, sign parity, select, scaling multiply, sign apply, the variable-side add
+# and subtract, and the hard-decision parity (about ten integer / FP32 operations).
+OPS_PER_EDGE_ITER = 10
+L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes per launch of bp_kernel on this workload from the committed ncu capture
+# (profiles/bp_kernel_bb144_p005.md); None when the kernel has changed since.
+BP_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--shots", type=int, default=1_000_000)
+    ap.add_argument("--p", type=float, default=0.05)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--order", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=20240601)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2406_18655_gb300 import inputs as I
+    hx, hz = I.bb144()
+    return hx, hz
+
+
+def config(args, hx):
+    return {
+        "workload": f"BB[[144,12,12]] H_X {hx.shape[0]}x{hx.shape[1]}, i.i.d. p={args.p}, "
+                    f"{args.shots} shots/step, min-sum BP {args.iters} it (alpha 0.625, early exit)"
+                    f" + LSD-{args.order}",
+        "code": "BB[[144,12,12]] (l=12, m=6, A=x^3+y+y^2, B=y^3+x+x^2)",
+        "shots_per_step": args.shots,
+        "p": args.p,
+        "bp_iters": args.iters,
+        "lsd_order": args.order,
+        "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, hx, probs, s, budget_s):
+    """The CPU oracle (BP in its FP32 mirror, then LSD) on a bounded sample of the shots."""
+    import oracle
+    cores = os.cpu_count() or 1
+    cal = min(4000, s.shape[0])
+    t0 = time.perf_counter()
+    oracle.decode(hx, probs, s[:cal], args.iters, lsd_order=args.order, precision=1, nthreads=0)
+    dt = time.perf_counter() - t0
+    n_s = int(min(s.shape[0], max(cal, cal * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.decode(hx, probs, s[:n_s], args.iters, lsd_order=args.order, precision=1, nthreads=0)
+    dt = time.perf_counter() - t0
+    return {"value": n_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_s} of the step's {args.shots} shots ({dt:.1f} s, "
+                      f"std::thread over shots, {cores} threads)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2406_18655_gb300 import inputs as I
+    import oracle
+    hx, _ = workload(args)
+    probs = np.full(hx.shape[1], args.p, np.float32).astype(np.float64)
+    # each step: a bounded sample of the workload, sized so K + W steps stay within minutes
+    sample = min(args.shots, 20000)
+    e = I.sample_errors(args.seed, sample, probs)
+    s = I.syndromes(hx, e)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.decode(hx, probs, s, args.iters, lsd_order=args.order, precision=1, nthreads=0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.decode(hx, probs, s, args.iters, lsd_order=args.order, precision=1, nthreads=0)
+        times.append(time.perf_counter() - t0)
+    value = sample / float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(args, hx),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} shots of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.evaluate import LogicalChecker
+    from paper_2406_18655_gb300.lsd import Decoder
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    hx, hz = workload(args)
+    m, n = hx.shape
+    probs = np.full(n, args.p, np.float32)
+    e = I.sample_errors(args.seed, args.shots, probs.astype(np.float64),
+                        first_shot=rank * args.shots)
+    s = I.syndromes(hx, e)
+    stream = torch.cuda.current_stream()
+    dec = Decoder(hx, probs, args.iters, args.order, bp_lanes=args.lanes, stream=stream)
+    s_dev = torch.from_numpy(s).cuda()
+    corr = torch.empty((args.shots, n), dtype=torch.uint8, device="cuda")
+    status = torch.empty(args.shots, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        dec.decode(s_dev, corr, status)
+    barrier()
+
+    step_ms, bp_ms, lsd_ms, iters_sum, conv_sum, lsd_sum = [], [], [], 0, 0, 0
+    kappa_max = nu_max = 0
+    launches0 = dec.kernel_launches()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            barrier()
+            start.record(stream)
+            dec.decode(s_dev, corr, status)
+            end.record(stream)
+            end.synchronize()
+            step_ms.append(start.elapsed_time(end))
+            st = dec.stats()
+            bp_ms.append(st["ms_bp"])
+            lsd_ms.append(st["ms_lsd"])
+            iters_sum += st["bp_iterations"]
+            conv_sum += st["bp_converged"]
+            lsd_sum += st["lsd_shots"]
+            kappa_max = max(kappa_max, st["kappa_max"])
+            nu_max = max(nu_max, st["nu_max"])
+    launches = dec.kernel_launches() - launches0
+    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    ms_per_step = float(total.item()) / args.steps
+    value = world * args.shots / (ms_per_step / 1000.0)
+
+    # logical error rate of the last step's corrections (evaluation, outside the timing)
+    checker = LogicalChecker(hz)
+    fails = checker.failures(torch.from_numpy(e).cuda(), corr)
+    ler = float(fails.float().mean().item())
+
+    # end to end through the host-buffer C-ABI call (H2D + decode + D2H each step)
+    e2e = None
+    if not args.no_e2e:
+        s_pin = torch.from_numpy(s).pin_memory()
+        c_pin = torch.empty((args.shots, n), dtype=torch.uint8).pin_memory()
+        st_pin = torch.empty(args.shots, dtype=torch.uint8).pin_memory()
+        for _ in range(max(args.warmup, 1)):
+            dec.decode_host(s_pin, c_pin, st_pin)
+        barrier()
+        t_e2e = []
+        for _ in range(args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            dec.decode_host(s_pin, c_pin, st_pin)
+            t_e2e.append(time.perf_counter() - t0)
+        tot = torch.tensor([sum(t_e2e)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.shots / (float(tot.item()) / args.steps), "unit": UNIT,
+               "h2d_bytes_per_step": int(args.shots * m),
+               "d2h_bytes_per_step": int(args.shots * (n + 1))}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    E = int(hx.sum())
+    bp_ms_avg = float(np.mean(bp_ms))
+    iters_per_step = iters_sum / args.steps
+    achieved = OPS_PER_EDGE_ITER * E * iters_per_step / (bp_ms_avg / 1000.0) / 1e12
+    alu_peak = sms * 128 * sm_max_mhz * 1e6 / 1e12  # FP32/INT32 lanes x max SM clock
+    roofline = {"bound": "alu", "kernel": "bp_kernel", "achieved": achieved, "peak": alu_peak,
+                "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": BP_TRAFFIC_BYTES,
+                "peak_source": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_max_mhz:.0f} MHz "
+                               "(max SM clock of MEASURED_PEAKS.json)",
+                "ops_per_unit": f"{OPS_PER_EDGE_ITER} ops per edge-iteration, {E} edges, "
+                                f"{iters_per_step:.0f} shot-iterations per launch"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(args, hx),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99)),
+                       "what": "batch latency of one step (10^6 shots, device-resident)"},
+        "ler": ler,
+        "bp_converged_frac": conv_sum / (args.steps * args.shots),
+        "lsd_frac": lsd_sum / (args.steps * args.shots),
+        "mean_bp_iters": iters_per_step / args.shots,
+        "kappa_max": kappa_max, "nu_max": nu_max,
+        "kernel_ms": {"bp_kernel": bp_ms_avg, "lsd_kernel": float(np.mean(lsd_ms))},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "learned": None,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, hx, probs.astype(np.float64), s,
+                                            args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

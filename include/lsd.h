@@ -1,0 +1,183 @@
+/*
+ * lsd.h -- C ABI of the GB300 (sm_103a) BP + localized statistics decoding library.
+ *
+ * The library decodes batches of syndromes of one binary check matrix H (m detectors x
+ * n faults).  For each shot it runs min-sum belief propagation (BP) over the Tanner
+ * graph of H and, when BP's hard decision does not satisfy the syndrome, the localized
+ * statistics decoder (LSD) on BP's posterior log-likelihood ratios.  Everything after
+ * lsd_create runs in the library's own CUDA kernels on the caller's stream; there is no
+ * CPU fallback.
+ *
+ * The decoding problem (arXiv 2406.18655, Sec. 2.1): given s in F_2^m, find e_hat in
+ * F_2^n with H e_hat = s, guided by soft information lambda in R^n in log-likelihood
+ * ratio form (lower lambda = more likely faulty, Sec. 4.1).  LSD (Alg. 1, Sec. 4.1)
+ * factorizes this into independent local problems on clusters grown in order of
+ * reliability, validated and solved by on-the-fly GF(2) elimination (Sec. 4.2), and
+ * returns the union of the local solutions (Eq. 2).  BP is the pre-decoder of Sec. 4.3:
+ * min-sum, flooding ("parallel") schedule, scaling alpha = 0.625.  LSD-mu (App. D) adds
+ * mu growth steps per cluster followed by local exhaustive OSD of order mu.
+ *
+ * Conventions used by every entry point
+ *   - Return value: LSD_OK (0) or a negative LSD_ERR_* code.  lsd_status_string()
+ *     names it.  On an error no output is guaranteed to be written.
+ *   - "device" pointers are CUDA device (or managed) memory of the current device,
+ *     "host" pointers are ordinary host memory.  The caller owns every pointer it
+ *     passes; the library never frees or retains them after the call returns.
+ *   - All device work of a call is enqueued on the decoder's stream (lsd_options.stream)
+ *     and is complete only after that stream is synchronized, except where an entry
+ *     point says it synchronizes.
+ *   - One decoder must not be used from two host threads at the same time, and calls on
+ *     one decoder must not overlap on the GPU (they share the decoder's workspace); the
+ *     library enqueues them in order on one stream, which guarantees this.  Separate
+ *     decoders are independent.
+ *   - Layouts are row-major and shot-major in the sense "one contiguous row per shot":
+ *     syndromes [shots][m] bytes, corrections [shots][n] bytes, LLRs [shots][n] float32.
+ *     Bytes hold 0 or 1; any nonzero syndrome byte counts as 1.
+ */
+#ifndef LSD_GB300_H
+#define LSD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define LSD_OK 0
+#define LSD_ERR_INVALID_ARG (-1) /* bad size, pointer, index, duplicate entry or option */
+#define LSD_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define LSD_ERR_OOM (-3)         /* device allocation failed */
+#define LSD_ERR_ADMISSION (-4)   /* the work does not fit in lsd_options.mem_budget */
+#define LSD_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define LSD_ERR_UNSUPPORTED (-6) /* matrix shape beyond this build's kernel limits */
+
+/* ---- per-shot status bytes ---- */
+#define LSD_SHOT_OK_BP 1      /* BP's hard decision satisfied the syndrome */
+#define LSD_SHOT_OK_LSD 2     /* LSD produced the correction */
+#define LSD_SHOT_UNSOLVABLE 3 /* s is not in image(H): some cluster exhausted its component */
+
+typedef struct lsd_decoder lsd_decoder; /* opaque; owns device copies of H, priors, workspace */
+
+/* Options.  A zero-initialised struct (or NULL) selects every default. */
+typedef struct lsd_options {
+  float ms_scaling;       /* min-sum scaling alpha of the check message; 0 -> 0.625 (Sec. 4.3) */
+  int32_t bp_method;      /* 0 = min-sum (default); 1 = sum-product (tanh rule) */
+  int32_t no_early_exit;  /* 0 = a shot stops BP once H e_hat = s (default); 1 = run all iterations */
+  int32_t single_cluster; /* 1 = LSD seeds one cluster holding every detector; it then equals OSD-0 */
+  int32_t bp_lanes;       /* threads cooperating on one shot in BP: 0 = auto, else 8, 16 or 32 */
+  int32_t lsd_warps;      /* warps per CTA of the LSD kernel: 0 = auto, else 1..16 */
+  int32_t reserved[2];    /* must be zero */
+  size_t mem_budget;      /* device bytes the decoder may hold (H, priors, workspace); 0 = no limit */
+  void* stream;           /* cudaStream_t used for all work; NULL = the legacy default stream */
+} lsd_options;
+
+/* Batch summary, filled only when a non-NULL pointer is passed (the call then synchronizes). */
+typedef struct lsd_stats {
+  int64_t shots;         /* shots in the call */
+  int64_t bp_converged;  /* shots whose BP hard decision satisfied s */
+  int64_t lsd_shots;     /* shots handed to LSD */
+  int64_t unsolvable;    /* shots with status LSD_SHOT_UNSOLVABLE */
+  int64_t bp_iterations; /* BP iterations summed over shots */
+  int64_t lsd_steps;     /* LSD growth steps summed over LSD shots */
+  int32_t kappa_max;     /* largest final cluster (columns) of any shot (App. A's kappa) */
+  int32_t nu_max;        /* most final clusters in one shot (App. A's nu) */
+  float ms_bp;           /* device time of the BP kernel, CUDA events on the decoder stream */
+  float ms_lsd;          /* device time of the LSD kernel */
+} lsd_stats;
+
+/*
+ * lsd_create -- build a decoder for H and the i.i.d. channel probabilities.
+ *   out            receives the decoder (host pointer to a handle).
+ *   m, n           H is m x n (detectors x faults); 1 <= m, 1 <= n.
+ *   nnz, rows,cols host COO list of the ones of H, any order; an out-of-range index or a
+ *                  repeated (row, col) pair is LSD_ERR_INVALID_ARG.
+ *   channel_probs  host, n values in (0, 1): fault probabilities p_j.  The priors
+ *                  lambda_j = ln((1-p_j)/p_j) (Sec. 4.1's LLR form) are computed on the
+ *                  device in double and rounded to float32.
+ *   bp_iters       maximum BP iterations, >= 0 (0 = LSD on the priors alone).
+ *   lsd_order      mu of LSD-mu (App. D), 0..12; 0 = LSD-0.
+ *   opt            nullable; see lsd_options.
+ * The decoder copies H and the priors to the device; the caller's arrays may be freed
+ * after the call.  Synchronizes its stream before returning.
+ */
+int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
+               const int32_t* cols, const float* channel_probs, int32_t bp_iters,
+               int32_t lsd_order, const lsd_options* opt);
+
+/*
+ * lsd_decode_batch -- BP then LSD on `shots` syndromes (App. C.4: LSD runs only when BP
+ * does not converge).  Asynchronous unless stats != NULL.
+ *   syndromes    device, [shots][m] bytes.
+ *   corrections  device, [shots][n] bytes, written for every shot; H e_hat = s for every
+ *                shot whose status is 1 or 2.
+ *   status       device, [shots] bytes (LSD_SHOT_*), nullable.
+ *   posteriors   device, [shots][n] float32 BP posteriors of the last iteration run, nullable.
+ *   stats        host, nullable; filled after the call's work completes.
+ */
+int lsd_decode_batch(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
+                     uint8_t* corrections, uint8_t* status, float* posteriors, lsd_stats* stats);
+
+/*
+ * lsd_decode_batch_host -- lsd_decode_batch with HOST buffers: copies the syndromes to
+ * the decoder's device staging buffers, decodes, copies the corrections (and status)
+ * back, and synchronizes.  Pinned host memory makes the copies asynchronous DMA.
+ *   syndromes    host, [shots][m] bytes.   corrections host, [shots][n] bytes.
+ *   status       host, [shots] bytes, nullable.   stats host, nullable.
+ */
+int lsd_decode_batch_host(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
+                          uint8_t* corrections, uint8_t* status, lsd_stats* stats);
+
+/*
+ * lsd_bp_batch -- BP only (the pre-decoder of Sec. 4.3), for inspection and tests.
+ *   syndromes   device [shots][m] bytes.
+ *   posteriors  device [shots][n] float32: Lambda of the last iteration run.
+ *   converged   device [shots] bytes, nullable: 1 if the hard decision [Lambda < 0]
+ *               satisfied s after that iteration.
+ *   iterations  device [shots] int32, nullable: iterations run.
+ */
+int lsd_bp_batch(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes, float* posteriors,
+                 uint8_t* converged, int32_t* iterations);
+
+/*
+ * lsd_postprocess_batch -- LSD only (Alg. 1 plus LSD-mu when lsd_order > 0) on given soft
+ * information, for every shot (no BP, no convergence test).
+ *   llrs         device [shots][n] float32 soft information (lower = more likely faulty);
+ *                ties are broken toward the lower column index.
+ *   syndromes    device [shots][m] bytes.
+ *   corrections  device [shots][n] bytes.
+ *   status       device [shots] bytes, nullable (LSD_SHOT_OK_LSD or LSD_SHOT_UNSOLVABLE).
+ *   shot_info    device [shots][3] int32, nullable: (nu, kappa, growth steps of LSD-0).
+ */
+int lsd_postprocess_batch(lsd_decoder* dec, int64_t shots, const float* llrs,
+                          const uint8_t* syndromes, uint8_t* corrections, uint8_t* status,
+                          int32_t* shot_info);
+
+/*
+ * lsd_get_stats -- counters and kernel event times of the decoder's most recent
+ * lsd_decode_batch / lsd_bp_batch / lsd_postprocess_batch call (stats: host, required).
+ * Synchronizes the decoder's stream.  Counts of a call are complete only once that call's
+ * work has finished, which this synchronization guarantees.
+ */
+int lsd_get_stats(lsd_decoder* dec, lsd_stats* stats);
+
+/* lsd_get_priors -- copy the n float32 priors lambda_j to host memory; synchronizes. */
+int lsd_get_priors(lsd_decoder* dec, float* priors);
+
+/* lsd_workspace_bytes -- device bytes the decoder currently holds (H, priors, workspace). */
+int lsd_workspace_bytes(const lsd_decoder* dec, size_t* bytes);
+
+/* lsd_kernel_launches -- number of kernels the decoder has launched so far. */
+int lsd_kernel_launches(const lsd_decoder* dec, int64_t* count);
+
+/* lsd_destroy -- free the decoder and its device memory; NULL is a no-op.  Synchronizes. */
+int lsd_destroy(lsd_decoder* dec);
+
+/* lsd_status_string -- static description of a return code or per-shot status. */
+const char* lsd_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSD_GB300_H */

@@ -1,0 +1,462 @@
+// Host side of the C ABI declared in include/lsd.h: decoder construction, device
+// memory, launches.  No decoding arithmetic runs on the host.
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "lsd_internal.cuh"
+
+using namespace lsdgb;
+
+struct lsd_decoder {
+  int m = 0, n = 0, E = 0;
+  int bp_iters = 0, order = 0;
+  lsd_options opt{};
+  float alpha = 0.625f;
+  cudaStream_t st = nullptr;
+  DevGraph g{};
+  // owned device memory
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  DevCounters* d_ctr = nullptr;
+  DevCounters* h_ctr = nullptr;  // pinned
+  int32_t* d_queue = nullptr;
+  float* d_queue_llr = nullptr;
+  size_t cap_shots = 0;
+  uint8_t* d_stage = nullptr;  // host-buffer entry point: syndromes | corrections | status
+  size_t stage_cap = 0;
+  // launch shapes
+  int bp_lanes = 32, bp_grid = 0, bp_block = 0;
+  size_t bp_smem = 0;
+  bool lsd_ok = false;
+  int lsd_warps = 0, lsd_grid = 0, lsd_W = 0;
+  size_t lsd_smem = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  long long launches = 0;
+  int64_t last_shots = 0;
+  int last_kind = 0;  // 0 none, 1 decode, 2 bp only, 3 lsd only
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return LSD_ERR_OOM;
+  return LSD_ERR_CUDA;
+}
+
+// Device allocation charged to the decoder (and to its memory budget).
+int dev_alloc(lsd_decoder* d, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (d->opt.mem_budget && d->bytes + bytes > d->opt.mem_budget) return LSD_ERR_ADMISSION;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  d->allocs.push_back(*p);
+  d->bytes += bytes;
+  return LSD_OK;
+}
+
+void dev_free(lsd_decoder* d, void* p, size_t bytes) {
+  if (!p) return;
+  auto it = std::find(d->allocs.begin(), d->allocs.end(), p);
+  if (it != d->allocs.end()) d->allocs.erase(it);
+  cudaFree(p);
+  d->bytes -= bytes;
+}
+
+template <typename T>
+int upload(lsd_decoder* d, T** dst, const std::vector<T>& src) {
+  int rc = dev_alloc(d, reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                  cudaMemcpyHostToDevice, d->st);
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+// Queue and LLR buffer for `shots` unconverged shots.
+int ensure_workspace(lsd_decoder* d, int64_t shots) {
+  if ((size_t)shots <= d->cap_shots) return LSD_OK;
+  cudaError_t e = cudaStreamSynchronize(d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  dev_free(d, d->d_queue, d->cap_shots * sizeof(int32_t));
+  dev_free(d, d->d_queue_llr, d->cap_shots * (size_t)d->n * sizeof(float));
+  d->d_queue = nullptr;
+  d->d_queue_llr = nullptr;
+  d->cap_shots = 0;
+  int rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_queue), (size_t)shots * sizeof(int32_t));
+  if (rc) return rc;
+  rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_queue_llr),
+                 (size_t)shots * (size_t)d->n * sizeof(float));
+  if (rc) {
+    dev_free(d, d->d_queue, (size_t)shots * sizeof(int32_t));
+    d->d_queue = nullptr;
+    return rc;
+  }
+  d->cap_shots = (size_t)shots;
+  return LSD_OK;
+}
+
+int reset_counters(lsd_decoder* d) {
+  cudaError_t e = cudaMemsetAsync(d->d_ctr, 0, sizeof(DevCounters), d->st);
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+BPArgs bp_args(lsd_decoder* d, int64_t shots, const uint8_t* syn) {
+  BPArgs a{};
+  a.g = d->g;
+  a.shots = shots;
+  a.syndromes = syn;
+  a.iters = d->bp_iters;
+  a.alpha = d->alpha;
+  a.method = d->opt.bp_method;
+  a.early_exit = d->opt.no_early_exit ? 0 : 1;
+  a.ctr = d->d_ctr;
+  return a;
+}
+
+int fill_stats(lsd_decoder* d, int64_t shots, lsd_stats* stats, bool timed_lsd) {
+  cudaError_t e = cudaMemcpyAsync(d->h_ctr, d->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                  d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::memset(stats, 0, sizeof(*stats));
+  stats->shots = shots;
+  stats->bp_converged = (int64_t)d->h_ctr->bp_converged;
+  stats->lsd_shots = (int64_t)d->h_ctr->lsd_count;
+  stats->unsolvable = (int64_t)d->h_ctr->unsolvable;
+  stats->bp_iterations = (int64_t)d->h_ctr->bp_iterations;
+  stats->lsd_steps = (int64_t)d->h_ctr->lsd_steps;
+  stats->kappa_max = d->h_ctr->kappa_max;
+  stats->nu_max = d->h_ctr->nu_max;
+  float ms = 0.f;
+  if (d->last_kind != 3 && cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]) == cudaSuccess)
+    stats->ms_bp = ms;
+  if (timed_lsd && d->last_kind != 2 && cudaEventElapsedTime(&ms, d->ev[1], d->ev[2]) == cudaSuccess)
+    stats->ms_lsd = ms;
+  cudaGetLastError();
+  return LSD_OK;
+}
+
+bool valid_lanes(int l) { return l == 0 || l == 8 || l == 16 || l == 32; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lsd_status_string(int code) {
+  switch (code) {
+    case LSD_OK: return "ok";
+    case LSD_ERR_INVALID_ARG: return "invalid argument";
+    case LSD_ERR_CUDA: return "CUDA error";
+    case LSD_ERR_OOM: return "out of device memory";
+    case LSD_ERR_ADMISSION: return "work does not fit in the memory budget";
+    case LSD_ERR_TIMEOUT: return "device wait timed out";
+    case LSD_ERR_UNSUPPORTED: return "matrix shape beyond the kernel limits";
+    case LSD_SHOT_OK_BP: return "shot decoded by BP";
+    case LSD_SHOT_OK_LSD: return "shot decoded by LSD";
+    case LSD_SHOT_UNSOLVABLE: return "syndrome not in the image of H";
+    default: return "unknown code";
+  }
+}
+
+int lsd_destroy(lsd_decoder* d) {
+  if (!d) return LSD_OK;
+  if (d->st || d->allocs.size()) cudaStreamSynchronize(d->st);
+  for (void* p : d->allocs) cudaFree(p);
+  if (d->h_ctr) cudaFreeHost(d->h_ctr);
+  for (auto& e : d->ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete d;
+  return LSD_OK;
+}
+
+int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
+               const int32_t* cols, const float* channel_probs, int32_t bp_iters,
+               int32_t lsd_order, const lsd_options* opt) {
+  if (!out) return LSD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (m < 1 || n < 1 || nnz < 0 || (nnz > 0 && (!rows || !cols)) || !channel_probs ||
+      bp_iters < 0 || lsd_order < 0 || lsd_order > kMaxOrder)
+    return LSD_ERR_INVALID_ARG;
+  lsd_options o{};
+  if (opt) o = *opt;
+  if (o.bp_method < 0 || o.bp_method > 1 || !valid_lanes(o.bp_lanes) || o.lsd_warps < 0 ||
+      o.lsd_warps > 16 || o.reserved[0] || o.reserved[1] || o.ms_scaling < 0.f)
+    return LSD_ERR_INVALID_ARG;
+  for (int j = 0; j < n; ++j)
+    if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
+  // Tanner graph: edges sorted by (row, column); duplicates are an error
+  std::vector<std::pair<int, int>> e((size_t)nnz);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (rows[k] < 0 || rows[k] >= m || cols[k] < 0 || cols[k] >= n) return LSD_ERR_INVALID_ARG;
+    e[(size_t)k] = {rows[k], cols[k]};
+  }
+  std::sort(e.begin(), e.end());
+  for (size_t k = 1; k < e.size(); ++k)
+    if (e[k] == e[k - 1]) return LSD_ERR_INVALID_ARG;
+  const int E = (int)e.size();
+  if (E >= 65536 || n >= 65536 || m >= 65536) return LSD_ERR_UNSUPPORTED;
+  std::vector<int32_t> chk_ptr(m + 1, 0), var_ptr(n + 1, 0);
+  std::vector<uint16_t> chk_var(E), var_edge(E), var_chk(E);
+  for (auto& p : e) {
+    chk_ptr[p.first + 1]++;
+    var_ptr[p.second + 1]++;
+  }
+  int max_row = 0, max_col = 0;
+  for (int i = 0; i < m; ++i) max_row = std::max(max_row, chk_ptr[i + 1]);
+  for (int j = 0; j < n; ++j) max_col = std::max(max_col, var_ptr[j + 1]);
+  if (max_row > kMaxRowDeg) return LSD_ERR_UNSUPPORTED;
+  for (int i = 0; i < m; ++i) chk_ptr[i + 1] += chk_ptr[i];
+  for (int j = 0; j < n; ++j) var_ptr[j + 1] += var_ptr[j];
+  std::vector<int32_t> vfill(var_ptr.begin(), var_ptr.end() - 1);
+  for (int k = 0; k < E; ++k) {  // edge k is (row e[k].first, column e[k].second)
+    chk_var[k] = (uint16_t)e[k].second;
+    const int slot = vfill[e[k].second]++;  // rows arrive in ascending order per column
+    var_edge[slot] = (uint16_t)k;
+    var_chk[slot] = (uint16_t)e[k].first;
+  }
+
+  lsd_decoder* d = new (std::nothrow) lsd_decoder();
+  if (!d) return LSD_ERR_OOM;
+  d->m = m;
+  d->n = n;
+  d->E = E;
+  d->bp_iters = bp_iters;
+  d->order = lsd_order;
+  d->opt = o;
+  d->alpha = o.ms_scaling > 0.f ? o.ms_scaling : 0.625f;
+  d->st = static_cast<cudaStream_t>(o.stream);
+  int rc = LSD_OK;
+  int32_t *d_chk_ptr = nullptr, *d_var_ptr = nullptr;
+  uint16_t *d_chk_var = nullptr, *d_var_edge = nullptr, *d_var_chk = nullptr;
+  float *d_prior = nullptr, *d_probs = nullptr;
+  long long* d_wfix = nullptr;
+  std::vector<float> probs(channel_probs, channel_probs + n);
+  if ((rc = upload(d, &d_chk_ptr, chk_ptr)) || (rc = upload(d, &d_var_ptr, var_ptr)) ||
+      (rc = upload(d, &d_chk_var, chk_var)) || (rc = upload(d, &d_var_edge, var_edge)) ||
+      (rc = upload(d, &d_var_chk, var_chk)) || (rc = upload(d, &d_probs, probs)) ||
+      (rc = dev_alloc(d, reinterpret_cast<void**>(&d_prior), (size_t)n * sizeof(float))) ||
+      (rc = dev_alloc(d, reinterpret_cast<void**>(&d_wfix), (size_t)n * sizeof(long long))) ||
+      (rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_ctr), sizeof(DevCounters)))) {
+    lsd_destroy(d);
+    return rc;
+  }
+  if (cudaMallocHost(reinterpret_cast<void**>(&d->h_ctr), sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    lsd_destroy(d);
+    return LSD_ERR_OOM;
+  }
+  for (auto& ev : d->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      lsd_destroy(d);
+      return LSD_ERR_CUDA;
+    }
+  DevGraph& g = d->g;
+  g.m = m;
+  g.n = n;
+  g.E = E;
+  g.max_row_deg = max_row;
+  g.max_col_deg = max_col;
+  g.chk_ptr = d_chk_ptr;
+  g.chk_var = d_chk_var;
+  g.var_ptr = d_var_ptr;
+  g.var_edge = d_var_edge;
+  g.var_chk = d_var_chk;
+  g.prior = d_prior;
+  g.wfix = d_wfix;
+  cudaError_t ce = launch_priors(d_probs, d_prior, d_wfix, n, d->st);
+  d->launches++;
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(d->st);
+  if (ce != cudaSuccess) {
+    lsd_destroy(d);
+    return cuda_fail(ce);
+  }
+  d->bp_lanes = o.bp_lanes ? o.bp_lanes : 32;
+  ce = bp_config(g, d->bp_lanes, o.bp_method, &d->bp_grid, &d->bp_block, &d->bp_smem);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    lsd_destroy(d);
+    return LSD_ERR_UNSUPPORTED;
+  }
+  ce = lsd_config(g, lsd_order, o.lsd_warps, &d->lsd_warps, &d->lsd_grid, &d->lsd_smem, &d->lsd_W);
+  if (ce == cudaSuccess) {
+    d->lsd_ok = true;
+  } else {
+    cudaGetLastError();  // BP still works; LSD entry points report LSD_ERR_UNSUPPORTED
+  }
+  *out = d;
+  return LSD_OK;
+}
+
+int lsd_decode_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
+                     uint8_t* corrections, uint8_t* status, float* posteriors, lsd_stats* stats) {
+  if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) {
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+    }
+    return LSD_OK;
+  }
+  if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  int rc = ensure_workspace(d, shots);
+  if (rc) return rc;
+  if ((rc = reset_counters(d))) return rc;
+  BPArgs a = bp_args(d, shots, syndromes);
+  a.corrections = corrections;
+  a.status = status;
+  a.posteriors = posteriors;
+  a.queue = d->d_queue;
+  a.queue_llr = d->d_queue_llr;
+  cudaEventRecord(d->ev[0], d->st);
+  cudaError_t e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[1], d->st);
+  LSDArgs l{};
+  l.g = d->g;
+  l.count_from_ctr = 1;
+  l.queue = d->d_queue;
+  l.llr = d->d_queue_llr;
+  l.llr_by_item = 1;
+  l.syndromes = syndromes;
+  l.corrections = corrections;
+  l.status = status;
+  l.order = d->order;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = d->d_ctr;
+  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[2], d->st);
+  d->last_shots = shots;
+  d->last_kind = 1;
+  if (stats) return fill_stats(d, shots, stats, true);
+  return LSD_OK;
+}
+
+int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
+                          uint8_t* corrections, uint8_t* status, lsd_stats* stats) {
+  if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return lsd_decode_batch(d, 0, nullptr, nullptr, nullptr, nullptr, stats);
+  if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  const size_t need = (size_t)shots * ((size_t)d->m + (size_t)d->n + 1);
+  if (need > d->stage_cap) {
+    cudaError_t e = cudaStreamSynchronize(d->st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dev_free(d, d->d_stage, d->stage_cap);
+    d->d_stage = nullptr;
+    d->stage_cap = 0;
+    int rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_stage), need);
+    if (rc) return rc;
+    d->stage_cap = need;
+  }
+  uint8_t* dsyn = d->d_stage;
+  uint8_t* dcor = dsyn + (size_t)shots * d->m;
+  uint8_t* dst = dcor + (size_t)shots * d->n;
+  cudaError_t e = cudaMemcpyAsync(dsyn, syndromes, (size_t)shots * d->m, cudaMemcpyHostToDevice,
+                                  d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int rc = lsd_decode_batch(d, shots, dsyn, dcor, dst, nullptr, nullptr);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(corrections, dcor, (size_t)shots * d->n, cudaMemcpyDeviceToHost, d->st);
+  if (e == cudaSuccess && status)
+    e = cudaMemcpyAsync(status, dst, (size_t)shots, cudaMemcpyDeviceToHost, d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (stats) return fill_stats(d, shots, stats, true);
+  e = cudaStreamSynchronize(d->st);
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_bp_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes, float* posteriors,
+                 uint8_t* converged, int32_t* iterations) {
+  if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return LSD_OK;
+  if (!syndromes || !posteriors) return LSD_ERR_INVALID_ARG;
+  int rc = reset_counters(d);
+  if (rc) return rc;
+  BPArgs a = bp_args(d, shots, syndromes);
+  a.posteriors = posteriors;
+  a.converged_out = converged;
+  a.iters_out = iterations;
+  cudaEventRecord(d->ev[0], d->st);
+  cudaError_t e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[1], d->st);
+  d->last_shots = shots;
+  d->last_kind = 2;
+  return LSD_OK;
+}
+
+int lsd_postprocess_batch(lsd_decoder* d, int64_t shots, const float* llrs,
+                          const uint8_t* syndromes, uint8_t* corrections, uint8_t* status,
+                          int32_t* shot_info) {
+  if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return LSD_OK;
+  if (!llrs || !syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  int rc = reset_counters(d);
+  if (rc) return rc;
+  LSDArgs l{};
+  l.g = d->g;
+  l.count = shots;
+  l.count_from_ctr = 0;
+  l.queue = nullptr;
+  l.llr = llrs;
+  l.llr_by_item = 0;
+  l.syndromes = syndromes;
+  l.corrections = corrections;
+  l.status = status;
+  l.shot_info = shot_info;
+  l.order = d->order;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = d->d_ctr;
+  cudaEventRecord(d->ev[1], d->st);
+  cudaError_t e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[2], d->st);
+  d->last_shots = shots;
+  d->last_kind = 3;
+  return LSD_OK;
+}
+
+int lsd_get_stats(lsd_decoder* d, lsd_stats* stats) {
+  if (!d || !stats) return LSD_ERR_INVALID_ARG;
+  if (d->last_kind == 0) {
+    std::memset(stats, 0, sizeof(*stats));
+    return LSD_OK;
+  }
+  return fill_stats(d, d->last_shots, stats, true);
+}
+
+int lsd_get_priors(lsd_decoder* d, float* priors) {
+  if (!d || !priors) return LSD_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(priors, d->g.prior, (size_t)d->n * sizeof(float),
+                                  cudaMemcpyDeviceToHost, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_workspace_bytes(const lsd_decoder* d, size_t* bytes) {
+  if (!d || !bytes) return LSD_ERR_INVALID_ARG;
+  *bytes = d->bytes;
+  return LSD_OK;
+}
+
+int lsd_kernel_launches(const lsd_decoder* d, int64_t* count) {
+  if (!d || !count) return LSD_ERR_INVALID_ARG;
+  *count = d->launches;
+  return LSD_OK;
+}
+
+}  // extern "C"

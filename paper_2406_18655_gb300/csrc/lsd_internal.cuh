@@ -1,0 +1,93 @@
+// Internal declarations shared by the kernels and the host API of liblsd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsd.h"
+
+namespace lsdgb {
+
+// Device copy of the Tanner graph of H.
+//   Edges are numbered in check-major order: edge e = (chk_ptr[i] + k) is the k-th
+//   one of row i, columns ascending.  var_edge lists, for each column j, its edges in
+//   ascending row order; var_chk the matching rows.
+struct DevGraph {
+  int32_t m, n, E;
+  int32_t max_row_deg, max_col_deg;
+  const int32_t* chk_ptr;   // [m+1]
+  const uint16_t* chk_var;  // [E]  column of edge e
+  const int32_t* var_ptr;   // [n+1]
+  const uint16_t* var_edge; // [E]  edges of column j (ascending row)
+  const uint16_t* var_chk;  // [E]  rows of column j (ascending)
+  const float* prior;       // [n]  lambda_j (float32)
+  const long long* wfix;    // [n]  2^-32 fixed point of lambda_j, LSD-mu costs
+};
+
+// Counters accumulated by the kernels of one call (reset per call).
+struct DevCounters {
+  unsigned long long next_shot;     // BP work queue head
+  unsigned long long lsd_count;     // unconverged shots appended by BP
+  unsigned long long lsd_next;      // LSD work queue head
+  unsigned long long bp_converged;
+  unsigned long long bp_iterations;
+  unsigned long long unsolvable;
+  unsigned long long lsd_steps;
+  int kappa_max;
+  int nu_max;
+  int timeout_flag;
+  int pad;
+};
+
+struct BPArgs {
+  DevGraph g;
+  long long shots;
+  const uint8_t* syndromes;  // [shots][m]
+  int iters;
+  float alpha;
+  int method;                // 0 min-sum, 1 sum-product
+  int early_exit;
+  // decode mode outputs
+  uint8_t* corrections;      // [shots][n] nullable (written for converged shots)
+  uint8_t* status;           // [shots] nullable
+  float* posteriors;         // [shots][n] nullable
+  uint8_t* converged_out;    // [shots] nullable
+  int32_t* iters_out;        // [shots] nullable
+  int32_t* queue;            // [shots] unconverged shot ids, nullable (BP-only mode)
+  float* queue_llr;          // [shots][n] LLRs of queued shots (row = queue slot)
+  DevCounters* ctr;
+};
+
+struct LSDArgs {
+  DevGraph g;
+  long long count;            // number of work items when count_from_ctr == 0
+  int count_from_ctr;         // 1: work items = ctr->lsd_count (appended by BP)
+  const int32_t* queue;       // work item -> shot id; NULL = identity
+  const float* llr;           // [items or shots][n]
+  int llr_by_item;            // 1: LLR row = work item, 0: LLR row = shot id
+  const uint8_t* syndromes;   // [shots][m]
+  uint8_t* corrections;       // [shots][n]
+  uint8_t* status;            // [shots] nullable
+  int32_t* shot_info;         // [shots][3] nullable
+  int order;                  // LSD-mu order
+  int single_cluster;
+  DevCounters* ctr;
+};
+
+// Launch helpers (return a cudaError_t).
+cudaError_t launch_priors(const float* probs, float* prior, long long* wfix, int n,
+                          cudaStream_t st);
+cudaError_t launch_bp(const BPArgs& a, int lanes, int grid, int block, size_t smem,
+                      cudaStream_t st);
+cudaError_t bp_config(const DevGraph& g, int lanes, int method, int* grid, int* block,
+                      size_t* smem);
+cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaStream_t st);
+cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
+                       size_t* smem, int* words);
+
+// Limits of this build's kernels.
+constexpr int kMaxLsdWords = 16;    // LSD: m <= 32 * kMaxLsdWords detectors per shot
+constexpr int kMaxRowDeg = 32;      // BP: check degree (sign bits in one word)
+constexpr int kMaxOrder = 12;       // LSD-mu order
+
+}  // namespace lsdgb

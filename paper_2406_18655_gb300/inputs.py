@@ -243,8 +243,17 @@ def sample_errors(seed: int, shots: int, probs, first_shot: int = 0) -> np.ndarr
 
 
 def syndromes(h: np.ndarray, errors: np.ndarray) -> np.ndarray:
-    """s = H e (mod 2) for each row of ``errors``; uint8 [shots][m]."""
-    return ((errors.astype(np.int32) @ h.T.astype(np.int32)) & 1).astype(np.uint8)
+    """s = H e (mod 2) for each row of ``errors``; uint8 [shots][m].
+
+    Computed as a float32 product (exact: every count is below 2^24), in chunks.
+    """
+    ht = h.T.astype(np.float32)
+    out = np.empty((errors.shape[0], h.shape[0]), dtype=np.uint8)
+    step = 1 << 16
+    for a in range(0, errors.shape[0], step):
+        prod = errors[a:a + step].astype(np.float32) @ ht
+        out[a:a + step] = (prod.astype(np.int64) & 1).astype(np.uint8)
+    return out
 
 
 def coo(h: np.ndarray):

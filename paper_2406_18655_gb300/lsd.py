@@ -1,0 +1,267 @@
+"""Python binding of liblsd (include/lsd.h): argument marshalling only.
+
+Every decoding step runs in the library's CUDA kernels.  PyTorch provides the device
+memory and the stream; numpy arrays are accepted for host-side inputs.  If the
+compiled library is missing this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblsd.so")
+
+LSD_OK = 0
+LSD_ERR_INVALID_ARG = -1
+LSD_ERR_CUDA = -2
+LSD_ERR_OOM = -3
+LSD_ERR_ADMISSION = -4
+LSD_ERR_TIMEOUT = -5
+LSD_ERR_UNSUPPORTED = -6
+SHOT_OK_BP = 1
+SHOT_OK_LSD = 2
+SHOT_UNSOLVABLE = 3
+
+# Every entry point declared in include/lsd.h.
+EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_batch",
+           "lsd_postprocess_batch", "lsd_get_stats", "lsd_get_priors", "lsd_workspace_bytes",
+           "lsd_kernel_launches", "lsd_destroy", "lsd_status_string")
+
+
+class LsdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("ms_scaling", C.c_float), ("bp_method", C.c_int32),
+                ("no_early_exit", C.c_int32), ("single_cluster", C.c_int32),
+                ("bp_lanes", C.c_int32), ("lsd_warps", C.c_int32),
+                ("reserved", C.c_int32 * 2), ("mem_budget", C.c_size_t),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("shots", C.c_int64), ("bp_converged", C.c_int64), ("lsd_shots", C.c_int64),
+                ("unsolvable", C.c_int64), ("bp_iterations", C.c_int64),
+                ("lsd_steps", C.c_int64), ("kappa_max", C.c_int32), ("nu_max", C.c_int32),
+                ("ms_bp", C.c_float), ("ms_lsd", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load liblsd.so (built in-tree by ``paper_2406_18655_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.lsd_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int64, P, P, P, C.c_int32,
+                             C.c_int32, C.POINTER(Options)]
+    L.lsd_decode_batch.argtypes = [P, C.c_int64, P, P, P, P, C.POINTER(Stats)]
+    L.lsd_decode_batch_host.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
+    L.lsd_bp_batch.argtypes = [P, C.c_int64, P, P, P, P]
+    L.lsd_postprocess_batch.argtypes = [P, C.c_int64, P, P, P, P, P]
+    L.lsd_get_stats.argtypes = [P, C.POINTER(Stats)]
+    L.lsd_get_priors.argtypes = [P, P]
+    L.lsd_workspace_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+    L.lsd_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
+    L.lsd_destroy.argtypes = [P]
+    L.lsd_status_string.argtypes = [C.c_int]
+    L.lsd_status_string.restype = C.c_char_p
+    for name in EXPORTS:
+        getattr(L, name).restype = C.c_int if name != "lsd_status_string" else C.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().lsd_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != LSD_OK:
+        raise LsdError(code, what)
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev_tensor(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+    return t
+
+
+class Decoder:
+    """BP + LSD decoder of one check matrix (``lsd_create``).
+
+    ``h`` is a dense 0/1 matrix (numpy or torch, m x n).  ``stream`` is a
+    ``torch.cuda.Stream`` (default: the current stream at construction); all work of
+    this decoder runs on it.
+    """
+
+    def __init__(self, h, channel_probs, bp_iters: int, lsd_order: int = 0, *,
+                 ms_scaling: float = 0.0, bp_method: int = 0, no_early_exit: bool = False,
+                 single_cluster: bool = False, bp_lanes: int = 0, lsd_warps: int = 0,
+                 mem_budget: int = 0, stream=None):
+        import torch
+        h = np.asarray(h.cpu() if isinstance(h, torch.Tensor) else h, dtype=np.uint8)
+        self.m, self.n = h.shape
+        rows, cols = np.nonzero(h)
+        rows = np.ascontiguousarray(rows, np.int32)
+        cols = np.ascontiguousarray(cols, np.int32)
+        p = np.asarray(channel_probs, dtype=np.float32)
+        if p.ndim == 0:
+            p = np.full(self.n, float(p), np.float32)
+        p = np.ascontiguousarray(p)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt = Options()
+        opt.ms_scaling = ms_scaling
+        opt.bp_method = bp_method
+        opt.no_early_exit = int(no_early_exit)
+        opt.single_cluster = int(single_cluster)
+        opt.bp_lanes = bp_lanes
+        opt.lsd_warps = lsd_warps
+        opt.mem_budget = mem_budget
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        self._opt = opt
+        handle = C.c_void_p()
+        _check(lib().lsd_create(C.byref(handle), self.m, self.n, rows.size,
+                                rows.ctypes.data_as(C.c_void_p), cols.ctypes.data_as(C.c_void_p),
+                                p.ctypes.data_as(C.c_void_p), bp_iters, lsd_order, C.byref(opt)),
+               "lsd_create")
+        self._h = handle
+        self.bp_iters = bp_iters
+        self.lsd_order = lsd_order
+
+    # -- lifetime ---------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lsd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -----------------------------------------------------------------
+    def decode(self, syndromes, corrections=None, status=None, posteriors=None,
+               want_stats: bool = False):
+        """BP then LSD on device syndromes [shots][m] (uint8).  Returns (corrections, status[, stats])."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.m), "syndromes")
+        dev = syndromes.device
+        if corrections is None:
+            corrections = torch.empty((shots, self.n), dtype=torch.uint8, device=dev)
+        if status is None:
+            status = torch.empty(shots, dtype=torch.uint8, device=dev)
+        _dev_tensor(corrections, torch.uint8, (shots, self.n), "corrections")
+        _dev_tensor(status, torch.uint8, (shots,), "status")
+        if posteriors is not None:
+            _dev_tensor(posteriors, torch.float32, (shots, self.n), "posteriors")
+        st = Stats() if want_stats else None
+        _check(lib().lsd_decode_batch(self._h, shots, _ptr(syndromes), _ptr(corrections),
+                                      _ptr(status), _ptr(posteriors),
+                                      C.byref(st) if st is not None else None),
+               "lsd_decode_batch")
+        if want_stats:
+            return corrections, status, st.as_dict()
+        return corrections, status
+
+    def decode_host(self, syndromes, corrections=None, status=None, want_stats: bool = False):
+        """Host-buffer entry point: syndromes and outputs in host memory (numpy or CPU tensors)."""
+        s = syndromes
+        shots = s.shape[0]
+        if corrections is None:
+            corrections = np.empty((shots, self.n), np.uint8)
+        if status is None:
+            status = np.empty(shots, np.uint8)
+
+        def hp(a, shape, name):
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+                    raise ValueError(f"{name} must be a contiguous CPU tensor of shape {shape}")
+                return C.c_void_p(a.data_ptr())
+            if a.dtype != np.uint8 or not a.flags.c_contiguous or a.shape != tuple(shape):
+                raise ValueError(f"{name} must be a contiguous uint8 array of shape {shape}")
+            return a.ctypes.data_as(C.c_void_p)
+
+        st = Stats() if want_stats else None
+        _check(lib().lsd_decode_batch_host(self._h, shots, hp(s, (shots, self.m), "syndromes"),
+                                           hp(corrections, (shots, self.n), "corrections"),
+                                           hp(status, (shots,), "status"),
+                                           C.byref(st) if st is not None else None),
+               "lsd_decode_batch_host")
+        if want_stats:
+            return corrections, status, st.as_dict()
+        return corrections, status
+
+    def bp(self, syndromes):
+        """BP only.  Returns (posteriors [shots][n] f32, converged [shots] u8, iterations [shots] i32)."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.m), "syndromes")
+        dev = syndromes.device
+        post = torch.empty((shots, self.n), dtype=torch.float32, device=dev)
+        conv = torch.empty(shots, dtype=torch.uint8, device=dev)
+        iters = torch.empty(shots, dtype=torch.int32, device=dev)
+        _check(lib().lsd_bp_batch(self._h, shots, _ptr(syndromes), _ptr(post), _ptr(conv),
+                                  _ptr(iters)), "lsd_bp_batch")
+        return post, conv, iters
+
+    def postprocess(self, llrs, syndromes):
+        """LSD only on device soft information.  Returns (corrections, status, info[nu, kappa, steps])."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.m), "syndromes")
+        _dev_tensor(llrs, torch.float32, (shots, self.n), "llrs")
+        dev = syndromes.device
+        corr = torch.empty((shots, self.n), dtype=torch.uint8, device=dev)
+        status = torch.empty(shots, dtype=torch.uint8, device=dev)
+        info = torch.empty((shots, 3), dtype=torch.int32, device=dev)
+        _check(lib().lsd_postprocess_batch(self._h, shots, _ptr(llrs), _ptr(syndromes),
+                                           _ptr(corr), _ptr(status), _ptr(info)),
+               "lsd_postprocess_batch")
+        return corr, status, info
+
+    def stats(self) -> dict:
+        """Counters and kernel times of the last call (synchronizes the decoder's stream)."""
+        st = Stats()
+        _check(lib().lsd_get_stats(self._h, C.byref(st)), "lsd_get_stats")
+        return st.as_dict()
+
+    def priors(self):
+        out = np.empty(self.n, np.float32)
+        _check(lib().lsd_get_priors(self._h, out.ctypes.data_as(C.c_void_p)), "lsd_get_priors")
+        return out
+
+    def workspace_bytes(self) -> int:
+        v = C.c_size_t()
+        _check(lib().lsd_workspace_bytes(self._h, C.byref(v)), "lsd_workspace_bytes")
+        return v.value
+
+    def kernel_launches(self) -> int:
+        v = C.c_int64()
+        _check(lib().lsd_kernel_launches(self._h, C.byref(v)), "lsd_kernel_launches")
+        return v.value

@@ -1,0 +1,255 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Bars (the oracle's FP32 mirror rounds every BP operation in the kernel's order):
+  * BP posteriors: |dLLR| <= 1e-4 * max(1, |LLR|), and in practice bit-identical;
+    iteration counts and convergence flags identical.
+  * LSD given identical soft information: corrections, status, nu, kappa and step
+    counts bit-exact.
+  * End to end BP + LSD: corrections identical; logical error rates within 2 sigma.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_18655_gb300 import inputs as I
+from tests.gpu_cases import code, logicals_hz, sample
+
+pytestmark = pytest.mark.gpu
+
+BP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def L():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_18655_gb300 import build
+    build.build()
+    from paper_2406_18655_gb300 import lsd
+    lsd.lib()
+    return lsd
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def f64(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def test_priors_bit_exact(L):
+    p = np.array([0.5, 0.25, 0.1, 0.05, 0.01, 1e-3, 1e-5, 0.3, 0.45, 0.999], np.float32)
+    h = np.eye(p.size, dtype=np.uint8)
+    d = L.Decoder(h, p, 1)
+    got = d.priors()
+    exp = oracle.priors(f64(p), precision=1).astype(np.float32)
+    assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+@pytest.mark.parametrize("name,p,iters,shots", [
+    ("bb72", 0.05, 30, 4000), ("bb144", 0.02, 50, 3000), ("bb144", 0.08, 50, 3000),
+    ("bb288", 0.04, 50, 1500), ("st_bb72_d6", 0.01, 50, 1500), ("rep_boundary", 0.1, 20, 2000)])
+def test_bp_matches_oracle(L, lanes, name, p, iters, shots):
+    h, probs, e, s = sample(name, p, shots, seed=1000 + int(p * 1000) + lanes)
+    d = L.Decoder(h, probs, iters, bp_lanes=lanes)
+    post, conv, it = d.bp(dev(s))
+    torch.cuda.synchronize()
+    llr, hard, used, convo = oracle.bp(h, f64(probs), s, iters, precision=1)
+    assert np.array_equal(it.cpu().numpy(), used)
+    assert np.array_equal(conv.cpu().numpy(), convo)
+    g = post.cpu().numpy().astype(np.float64)
+    rel = np.abs(g - llr) / np.maximum(1.0, np.abs(llr))
+    assert rel.max() <= BP_TOL
+    assert np.array_equal(g, llr)
+
+
+def test_bp_no_early_exit_and_zero_iterations(L):
+    h, probs, e, s = sample("bb72", 0.04, 500, seed=5)
+    d = L.Decoder(h, probs, 15, no_early_exit=True)
+    post, conv, it = d.bp(dev(s))
+    llr, hard, used, convo = oracle.bp(h, f64(probs), s, 15, early_exit=0, precision=1)
+    assert np.all(it.cpu().numpy() == 15)
+    assert np.array_equal(conv.cpu().numpy(), convo)
+    assert np.array_equal(post.cpu().numpy().astype(np.float64), llr)
+    d0 = L.Decoder(h, probs, 0)
+    post0, conv0, it0 = d0.bp(dev(s))
+    assert np.all(it0.cpu().numpy() == 0) and not conv0.cpu().numpy().any()
+    assert np.array_equal(post0.cpu().numpy(), np.broadcast_to(d0.priors(), post0.shape))
+
+
+def test_sum_product_exact_on_trees(L):
+    """Sum-product (FP32 on the GPU) reproduces exact tree marginals within the BP tolerance."""
+    for seed in range(6):
+        h = I.random_tree_tanner(seed, 10 + seed)
+        n = h.shape[1]
+        g = I.Xoshiro256ss(1000 + seed, np.arange(n + h.shape[0], dtype=np.uint64))
+        u = g.uniform()
+        p = (0.02 + 0.43 * u[:n]).astype(np.float32)
+        s = (u[n:] < 0.5).astype(np.uint8)[None]
+        xs = ((np.arange(2 ** n)[:, None] >> np.arange(n)[None, :]) & 1)
+        ok = np.all((xs @ h.T.astype(np.int64)) % 2 == s[0], axis=1)
+        xs = xs[ok]
+        pd = f64(p)
+        w = np.exp(xs @ np.log(pd) + (1 - xs) @ np.log(1 - pd))
+        exact = np.array([np.log(w[xs[:, j] == 0].sum() / w[xs[:, j] == 1].sum()) for j in range(n)])
+        d = L.Decoder(h, p, 2 * n, bp_method=1, no_early_exit=True)
+        post, conv, it = d.bp(dev(s))
+        got = post.cpu().numpy()[0].astype(np.float64)
+        assert (np.abs(got - exact) / np.maximum(1.0, np.abs(exact))).max() <= BP_TOL
+
+
+def _rounded_llrs(shape, seed):
+    g = I.Xoshiro256ss(seed, np.arange(int(np.prod(shape)), dtype=np.uint64))
+    return np.round(g.uniform() * 5 - 0.5, 1).astype(np.float32).reshape(shape)
+
+
+@pytest.mark.parametrize("name,p,order,single,soft", [
+    ("bb72", 0.05, 0, False, "bp"), ("bb72", 0.1, 0, False, "ties"),
+    ("bb144", 0.04, 0, False, "bp"), ("bb144", 0.1, 0, False, "bp"),
+    ("bb144", 0.06, 0, False, "ties"), ("bb288", 0.05, 0, False, "bp"),
+    ("st_bb72_d6", 0.02, 0, False, "bp"), ("rep_boundary", 0.15, 0, False, "ties"),
+    ("bb72", 0.05, 0, True, "bp"), ("bb144", 0.05, 0, True, "ties"),
+    ("bb72", 0.08, 6, False, "bp"), ("bb144", 0.06, 6, False, "bp"),
+    ("bb144", 0.06, 10, False, "ties"), ("bb72", 0.05, 1, False, "bp")])
+def test_lsd_bit_exact_given_identical_soft_information(L, name, p, order, single, soft):
+    h, probs, e, s = sample(name, p, 1500, seed=77 + order + int(100 * p))
+    if soft == "bp":
+        llr, *_ = oracle.bp(h, f64(probs), s, 30, precision=1)
+        llr = llr.astype(np.float32)
+    else:
+        llr = _rounded_llrs((s.shape[0], h.shape[1]), 5 + order)
+    d = L.Decoder(h, probs, 30, order, single_cluster=single)
+    corr, st, info = d.postprocess(dev(llr), dev(s))
+    torch.cuda.synchronize()
+    r = oracle.lsd(h, s, llr.astype(np.float64), order=order, probs=f64(probs),
+                   single_cluster=single)
+    assert np.array_equal(st.cpu().numpy(), r["status"])
+    assert np.array_equal(corr.cpu().numpy(), r["corrections"])
+    info = info.cpu().numpy()
+    assert np.array_equal(info[:, 0], r["nu"])
+    assert np.array_equal(info[:, 1], r["kappa"])
+    assert np.array_equal(info[:, 2], r["steps"])
+
+
+def test_single_cluster_equals_osd0(L):
+    h, probs, e, s = sample("bb144", 0.05, 200, seed=9)
+    llr, *_ = oracle.bp(h, f64(probs), s, 20, precision=1)
+    llr = llr.astype(np.float32)
+    d = L.Decoder(h, probs, 20, single_cluster=True)
+    corr, st, info = d.postprocess(dev(llr), dev(s))
+    corr = corr.cpu().numpy()
+    for k in range(s.shape[0]):
+        ok, out = oracle.osd0(h, s[k], llr[k].astype(np.float64))
+        assert ok and np.array_equal(corr[k], out)
+
+
+@pytest.mark.parametrize("name,p,iters,order", [
+    ("bb72", 0.05, 30, 0), ("bb144", 0.05, 50, 0), ("bb144", 0.08, 50, 6),
+    ("bb288", 0.06, 50, 0), ("st_bb72_d6", 0.02, 50, 0)])
+def test_decode_matches_oracle(L, name, p, iters, order):
+    h, probs, e, s = sample(name, p, 4000, seed=300 + iters + order)
+    d = L.Decoder(h, probs, iters, order)
+    corr, st, stats = d.decode(dev(s), want_stats=True)
+    o = oracle.decode(h, f64(probs), s, iters, lsd_order=order, precision=1)
+    corr = corr.cpu().numpy()
+    st = st.cpu().numpy()
+    assert np.array_equal(st, o["status"])
+    assert np.array_equal(corr, o["corrections"])
+    assert np.array_equal((corr.astype(np.int64) @ h.T) % 2, s)
+    assert stats["bp_converged"] == int((o["status"] == 1).sum())
+    assert stats["lsd_shots"] == int((o["status"] != 1).sum())
+    assert stats["bp_iterations"] == int(o["bp_iters"].sum())
+    assert stats["kappa_max"] == int(o["kappa"].max())
+
+
+def test_logical_error_rate_within_two_sigma(L):
+    name, p = "bb144", 0.06
+    h, probs, e, s = sample(name, p, 20000, seed=4242)
+    d = L.Decoder(h, probs, 50)
+    corr, st = d.decode(dev(s))
+    gpu_fail = oracle.logical_failures(logicals_hz(name), e ^ corr.cpu().numpy())
+    o = oracle.decode(h, f64(probs), s, 50, precision=1)
+    orc_fail = oracle.logical_failures(logicals_hz(name), e ^ o["corrections"])
+    n = s.shape[0]
+    pg, po = gpu_fail.mean(), orc_fail.mean()
+    sigma = np.sqrt(max(po * (1 - po), 1.0 / n) / n)
+    assert abs(pg - po) <= 2 * sigma
+    assert np.array_equal(gpu_fail, orc_fail)
+
+
+def test_edge_cases(L):
+    h, probs, e, s = sample("bb72", 0.05, 64, seed=1)
+    d = L.Decoder(h, probs, 30)
+    # empty batch
+    c0, st0 = d.decode(dev(np.zeros((0, h.shape[0]), np.uint8)))
+    assert c0.shape == (0, h.shape[1])
+    # zero syndromes: BP converges after one iteration with the zero correction
+    z = np.zeros((5, h.shape[0]), np.uint8)
+    cz, stz = d.decode(dev(z))
+    assert not cz.cpu().numpy().any() and np.all(stz.cpu().numpy() == 1)
+    post, conv, it = d.bp(dev(z))
+    assert np.all(it.cpu().numpy() == 1)
+    # a single shot
+    c1, st1 = d.decode(dev(s[:1]))
+    o = oracle.decode(h, f64(probs), s[:1], 30, precision=1)
+    assert np.array_equal(c1.cpu().numpy(), o["corrections"])
+    # unsolvable syndrome: duplicated rows, syndrome differs on them
+    hu = np.array([[1, 1, 0, 0], [1, 1, 0, 0], [0, 1, 1, 0], [0, 0, 1, 1]], np.uint8)
+    su = np.array([[1, 0, 0, 0]], np.uint8)
+    du = L.Decoder(hu, np.full(4, 0.1, np.float32), 10)
+    cu, stu = du.decode(dev(su))
+    assert stu.cpu().numpy()[0] == L.SHOT_UNSOLVABLE and not cu.cpu().numpy().any()
+    ro = oracle.lsd(hu, su, np.full((1, 4), 2.0), order=0)
+    assert ro["status"][0] == 3
+    # ragged: a batch that is not a multiple of anything
+    h2, probs2, e2, s2 = sample("bb144", 0.05, 1237, seed=8)
+    d2 = L.Decoder(h2, probs2, 50)
+    c2, _ = d2.decode(dev(s2))
+    o2 = oracle.decode(h2, f64(probs2), s2, 50, precision=1)
+    assert np.array_equal(c2.cpu().numpy(), o2["corrections"])
+
+
+def test_host_buffer_entry_point(L):
+    h, probs, e, s = sample("bb144", 0.06, 3000, seed=12)
+    d = L.Decoder(h, probs, 50)
+    c_dev, st_dev = d.decode(dev(s))
+    c_host, st_host = d.decode_host(np.ascontiguousarray(s))
+    assert np.array_equal(c_host, c_dev.cpu().numpy())
+    assert np.array_equal(st_host, st_dev.cpu().numpy())
+    pinned = torch.from_numpy(s).pin_memory()
+    out = torch.empty((s.shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+    stt = torch.empty(s.shape[0], dtype=torch.uint8).pin_memory()
+    d.decode_host(pinned, out, stt)
+    assert np.array_equal(out.numpy(), c_host)
+
+
+def test_memory_budget_admission(L):
+    h, probs, e, s = sample("bb144", 0.05, 10, seed=3)
+    with pytest.raises(L.LsdError) as ei:
+        L.Decoder(h, probs, 50, mem_budget=1024)
+    assert ei.value.code == L.LSD_ERR_ADMISSION
+    d = L.Decoder(h, probs, 50, mem_budget=2 << 20)
+    with pytest.raises(L.LsdError) as ei:
+        d.decode(dev(np.zeros((100000, h.shape[0]), np.uint8)))
+    assert ei.value.code == L.LSD_ERR_ADMISSION
+
+
+def test_full_size_bb144_million_shots(L):
+    """The benchmark workload (BB144, p = 0.05, 10^6 shots, 50 iterations) in the
+    benchmark's launch configuration: every correction satisfies H e = s, and a sample of
+    shots matches the oracle exactly."""
+    shots = 1_000_000
+    h, probs, e, s = sample("bb144", 0.05, shots, seed=20240601)
+    d = L.Decoder(h, probs, 50)
+    sd = dev(s)
+    corr, st, stats = d.decode(sd, want_stats=True)
+    ht = torch.from_numpy(h.T.astype(np.float32)).cuda()
+    syn = torch.remainder(corr.float() @ ht, 2).to(torch.uint8)
+    assert torch.equal(syn, sd)
+    assert stats["unsolvable"] == 0
+    idx = np.sort(np.random.default_rng(0).choice(shots, 3000, replace=False))
+    o = oracle.decode(h, f64(probs), s[idx], 50, precision=1)
+    assert np.array_equal(corr.cpu().numpy()[idx], o["corrections"])
+    assert np.array_equal(st.cpu().numpy()[idx], o["status"])
