@@ -162,6 +162,41 @@ int lsd_postprocess_batch(lsd_decoder* dec, int64_t shots, const float* llrs,
  */
 int lsd_get_stats(lsd_decoder* dec, lsd_stats* stats);
 
+/*
+ * lsd_decode_batch_static -- lsd_decode_batch for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of the same BP + LSD
+ * path, with identical results.
+ *
+ * Who needs it: code that must not call cudaMalloc at decode time -- for example a
+ * real-time decoding loop that runs with a fixed device-memory footprint reserved at
+ * start-up (cudaMalloc can block on an implicit device synchronization and its latency is
+ * unbounded), or a host process whose free device memory is already held by another
+ * allocator (a framework's caching allocator), where a further cudaMalloc fails or
+ * fragments.  lsd_decode_batch may grow the decoder's workspace with cudaMalloc when a
+ * batch is larger than any before; this entry point never allocates or frees anything.
+ *
+ * Its scratch (the work-queue counters, the queue of unconverged shots and their LLR rows)
+ * lives in one file-scope device array of LSD_STATIC_SCRATCH_BYTES bytes inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ *   dec          a decoder from lsd_create (H and the priors are already on the device).
+ *   shots        0 <= shots, and 256 + shots * 4 (rounded up to 256) + shots * n * 4 must
+ *                not exceed LSD_STATIC_SCRATCH_BYTES (BB[[144,12,12]]: up to 14,462 shots
+ *                per call); a larger batch returns LSD_ERR_ADMISSION and touches nothing.
+ *   syndromes    device [shots][m] bytes.  corrections device [shots][n] bytes.
+ *   status       device [shots] bytes, nullable.
+ * Behaviour:
+ *   - The first call on a device looks up the array's device address on that device (the
+ *     current one); make that first call before any stream capture.  Later calls reuse it.
+ *   - Every call, on every decoder, shares the one array; each call clears the counters it
+ *     needs at its start.  Calls that overlap on the GPU (different streams, decoders or
+ *     threads without ordering between them) race on the array and give wrong results:
+ *     order them on one stream or synchronize between them.
+ *   - Asynchronous on the decoder's stream, like lsd_decode_batch.
+ */
+#define LSD_STATIC_SCRATCH_BYTES ((size_t)8 << 20)
+int lsd_decode_batch_static(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
+                            uint8_t* corrections, uint8_t* status);
+
 /* lsd_get_priors -- copy the n float32 priors lambda_j to host memory; synchronizes. */
 int lsd_get_priors(lsd_decoder* dec, float* priors);
 

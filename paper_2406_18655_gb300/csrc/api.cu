@@ -4,6 +4,7 @@
 #include <climits>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -460,3 +461,87 @@ int lsd_kernel_launches(const lsd_decoder* d, int64_t* count) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free decode (lsd_decode_batch_static).  The scratch of the BP and LSD kernels
+// (counters, queue, LLR rows) comes from one file-scope device array instead of the
+// decoder's workspace.  Its device address is looked up once per device, on that device.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[LSD_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxStaticDevices = 64;
+
+struct StaticScratchSlot {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+  void* ptr = nullptr;
+};
+
+StaticScratchSlot g_static_slots[kMaxStaticDevices];
+
+// Device address of g_static_scratch on the current device (first use: the lookup).
+int static_scratch(void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxStaticDevices) return LSD_ERR_UNSUPPORTED;
+  StaticScratchSlot& slot = g_static_slots[dev];
+  std::call_once(slot.once, [&slot]() {
+    slot.err = cudaGetSymbolAddress(&slot.ptr, g_static_scratch);
+  });
+  if (slot.err != cudaSuccess || !slot.ptr) return cuda_fail(slot.err);
+  *ptr = slot.ptr;
+  return LSD_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int lsd_decode_batch_static(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
+                                       uint8_t* corrections, uint8_t* status) {
+  if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return LSD_OK;
+  if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  const size_t ctr_bytes = round256(sizeof(DevCounters));
+  const size_t queue_bytes = round256((size_t)shots * sizeof(int32_t));
+  const size_t llr_bytes = (size_t)shots * (size_t)d->n * sizeof(float);
+  if (ctr_bytes + queue_bytes + llr_bytes > LSD_STATIC_SCRATCH_BYTES) return LSD_ERR_ADMISSION;
+  void* base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc) return rc;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  DevCounters* ctr = reinterpret_cast<DevCounters*>(p);
+  int32_t* queue = reinterpret_cast<int32_t*>(p + ctr_bytes);
+  float* queue_llr = reinterpret_cast<float*>(p + ctr_bytes + queue_bytes);
+  // the array keeps the previous call's contents: the counters must start at zero
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(DevCounters), d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  BPArgs a = bp_args(d, shots, syndromes);
+  a.ctr = ctr;
+  a.corrections = corrections;
+  a.status = status;
+  a.queue = queue;
+  a.queue_llr = queue_llr;
+  e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  LSDArgs l{};
+  l.g = d->g;
+  l.count_from_ctr = 1;
+  l.queue = queue;
+  l.llr = queue_llr;
+  l.llr_by_item = 1;
+  l.syndromes = syndromes;
+  l.corrections = corrections;
+  l.status = status;
+  l.order = d->order;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = ctr;
+  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}

@@ -27,7 +27,8 @@ SHOT_UNSOLVABLE = 3
 # Every entry point declared in include/lsd.h.
 EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_batch",
            "lsd_postprocess_batch", "lsd_get_stats", "lsd_get_priors", "lsd_workspace_bytes",
-           "lsd_kernel_launches", "lsd_destroy", "lsd_status_string")
+           "lsd_kernel_launches", "lsd_destroy", "lsd_status_string",
+           "lsd_decode_batch_static")
 
 
 class LsdError(RuntimeError):
@@ -77,6 +78,7 @@ def lib():
     L.lsd_workspace_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
     L.lsd_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_destroy.argtypes = [P]
+    L.lsd_decode_batch_static.argtypes = [P, C.c_int64, P, P, P]
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
