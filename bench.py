@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--bp-kernel", type=int, default=0, help="0 auto, 1 generic, 2 register")
+    ap.add_argument("--lsd-warps", type=int, default=0)
     ap.add_argument("--seed", type=int, default=20240601)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -211,7 +213,8 @@ def run_ours(args):
                         first_shot=rank * args.shots)
     s = I.syndromes(hx, e)
     stream = torch.cuda.current_stream()
-    dec = Decoder(hx, probs, args.iters, args.order, bp_lanes=args.lanes, stream=stream)
+    dec = Decoder(hx, probs, args.iters, args.order, bp_lanes=args.lanes,
+                  bp_kernel=args.bp_kernel, lsd_warps=args.lsd_warps, stream=stream)
     s_dev = torch.from_numpy(s).cuda()
     corr = torch.empty((args.shots, n), dtype=torch.uint8, device="cuda")
     status = torch.empty(args.shots, dtype=torch.uint8, device="cuda")

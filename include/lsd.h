@@ -68,7 +68,9 @@ typedef struct lsd_options {
   int32_t single_cluster; /* 1 = LSD seeds one cluster holding every detector; it then equals OSD-0 */
   int32_t bp_lanes;       /* threads cooperating on one shot in BP: 0 = auto, else 8, 16 or 32 */
   int32_t lsd_warps;      /* warps per CTA of the LSD kernel: 0 = auto, else 1..16 */
-  int32_t reserved[2];    /* must be zero */
+  int32_t bp_kernel;      /* BP kernel: 0 = auto, 1 = generic (graph in shared memory),
+                             2 = register-resident graph tables (min-sum, small codes) */
+  int32_t reserved[1];    /* must be zero */
   size_t mem_budget;      /* device bytes the decoder may hold (H, priors, workspace); 0 = no limit */
   void* stream;           /* cudaStream_t used for all work; NULL = the legacy default stream */
 } lsd_options;

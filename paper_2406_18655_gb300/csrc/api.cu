@@ -31,7 +31,7 @@ struct lsd_decoder {
   uint8_t* d_stage = nullptr;  // host-buffer entry point: syndromes | corrections | status
   size_t stage_cap = 0;
   // launch shapes
-  int bp_lanes = 32, bp_grid = 0, bp_block = 0;
+  int bp_variant = -1, bp_grid = 0, bp_block = 0;
   size_t bp_smem = 0;
   bool lsd_ok = false;
   int lsd_warps = 0, lsd_grid = 0, lsd_W = 0;
@@ -190,7 +190,8 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   lsd_options o{};
   if (opt) o = *opt;
   if (o.bp_method < 0 || o.bp_method > 1 || !valid_lanes(o.bp_lanes) || o.lsd_warps < 0 ||
-      o.lsd_warps > 16 || o.reserved[0] || o.reserved[1] || o.ms_scaling < 0.f)
+      o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 2 || o.reserved[0] ||
+      o.ms_scaling < 0.f)
     return LSD_ERR_INVALID_ARG;
   for (int j = 0; j < n; ++j)
     if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
@@ -211,9 +212,15 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
     chk_ptr[p.first + 1]++;
     var_ptr[p.second + 1]++;
   }
-  int max_row = 0, max_col = 0;
-  for (int i = 0; i < m; ++i) max_row = std::max(max_row, chk_ptr[i + 1]);
-  for (int j = 0; j < n; ++j) max_col = std::max(max_col, var_ptr[j + 1]);
+  int max_row = 0, max_col = 0, min_row = INT_MAX, min_col = INT_MAX;
+  for (int i = 0; i < m; ++i) {
+    max_row = std::max(max_row, chk_ptr[i + 1]);
+    min_row = std::min(min_row, chk_ptr[i + 1]);
+  }
+  for (int j = 0; j < n; ++j) {
+    max_col = std::max(max_col, var_ptr[j + 1]);
+    min_col = std::min(min_col, var_ptr[j + 1]);
+  }
   if (max_row > kMaxRowDeg) return LSD_ERR_UNSUPPORTED;
   for (int i = 0; i < m; ++i) chk_ptr[i + 1] += chk_ptr[i];
   for (int j = 0; j < n; ++j) var_ptr[j + 1] += var_ptr[j];
@@ -266,6 +273,8 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   g.E = E;
   g.max_row_deg = max_row;
   g.max_col_deg = max_col;
+  g.min_row_deg = min_row;
+  g.min_col_deg = min_col;
   g.chk_ptr = d_chk_ptr;
   g.chk_var = d_chk_var;
   g.var_ptr = d_var_ptr;
@@ -280,8 +289,9 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
     lsd_destroy(d);
     return cuda_fail(ce);
   }
-  d->bp_lanes = o.bp_lanes ? o.bp_lanes : 32;
-  ce = bp_config(g, d->bp_lanes, o.bp_method, &d->bp_grid, &d->bp_block, &d->bp_smem);
+  d->bp_variant = -1;
+  ce = bp_config(g, o.bp_lanes, o.bp_method, o.bp_kernel, &d->bp_variant, &d->bp_grid,
+                 &d->bp_block, &d->bp_smem);
   if (ce != cudaSuccess) {
     cudaGetLastError();
     lsd_destroy(d);
@@ -318,7 +328,7 @@ int lsd_decode_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
   a.queue = d->d_queue;
   a.queue_llr = d->d_queue_llr;
   cudaEventRecord(d->ev[0], d->st);
-  cudaError_t e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  cudaError_t e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   cudaEventRecord(d->ev[1], d->st);
@@ -389,7 +399,7 @@ int lsd_bp_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes, float*
   a.converged_out = converged;
   a.iters_out = iterations;
   cudaEventRecord(d->ev[0], d->st);
-  cudaError_t e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  cudaError_t e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   cudaEventRecord(d->ev[1], d->st);
@@ -526,7 +536,7 @@ extern "C" int lsd_decode_batch_static(lsd_decoder* d, int64_t shots, const uint
   a.status = status;
   a.queue = queue;
   a.queue_llr = queue_llr;
-  e = launch_bp(a, d->bp_lanes, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   LSDArgs l{};

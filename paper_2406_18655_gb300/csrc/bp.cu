@@ -33,6 +33,9 @@ __host__ __device__ inline size_t bp_graph_bytes(int m, int n, int E) {
 __host__ __device__ inline size_t bp_group_bytes(int m, int n, int E) {
   return align16((size_t)E * 4 + (size_t)n * 4 + (size_t)m);
 }
+__host__ __device__ inline size_t bp_reg_group_bytes(int n, int E) {
+  return align16((size_t)E * 4 + (size_t)n * 4);
+}
 
 __global__ void priors_kernel(const float* __restrict__ probs, float* __restrict__ prior,
                               long long* __restrict__ wfix, int n) {
@@ -214,6 +217,212 @@ __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
   }
 }
 
+// Min-sum on a regular Tanner graph (every check of degree DC, every variable of degree
+// DV) with the per-lane graph tables in registers.  A group of G lanes owns a shot; lane l
+// owns checks l, l+G, ... (at most CPL) and variables l, l+G, ... (at most VPL).  Check i's
+// edges are i*DC .. i*DC+DC-1 (CSR order), so only the column indices of the lane's checks
+// and the edge slots of its variables are kept, two 16-bit indices per register.  Loops
+// are unrolled over the compile-time degrees; r[E], Lam[n] and the priors live in shared
+// memory as the exchange between the two phases.  Same operations in the same order as
+// bp_kernel<G, 0>, so the results are identical.
+template <int G, int CPL, int DC, int VPL, int DV>
+__global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const int lane = threadIdx.x & (G - 1);
+  const int group = threadIdx.x / G;
+  const unsigned gmask = group_mask<G>();
+  const int leader = (threadIdx.x & 31) & ~(G - 1);
+  float* s_prior = reinterpret_cast<float*>(smem);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s_prior[j] = a.g.prior[j];
+  __syncthreads();
+  float* r = reinterpret_cast<float*>(smem + align16((size_t)n * 4) +
+                                      (size_t)group * bp_reg_group_bytes(n, E));
+  float* Lam = r + E;
+  const float alpha = a.alpha;
+
+  // ---- the lane's graph tables: column indices of its checks, edge slots of its variables
+  uint32_t cv[CPL][(DC + 1) / 2];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int i = lane + G * c;
+#pragma unroll
+    for (int k = 0; k < (DC + 1) / 2; ++k) cv[c][k] = 0;
+    if (i < m) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) cv[c][k >> 1] |= (uint32_t)a.g.chk_var[i * DC + k] << (16 * (k & 1));
+    }
+  }
+  uint32_t ve[VPL][(DV + 1) / 2];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int j = lane + G * v;
+#pragma unroll
+    for (int k = 0; k < (DV + 1) / 2; ++k) ve[v][k] = 0;
+    if (j < n) {
+#pragma unroll
+      for (int k = 0; k < DV; ++k) ve[v][k >> 1] |= (uint32_t)a.g.var_edge[j * DV + k] << (16 * (k & 1));
+    }
+  }
+
+  unsigned long long my_iters = 0, my_conv = 0;
+  for (;;) {
+    unsigned long long shot_u = 0;
+    if (lane == 0) shot_u = atomicAdd(&a.ctr->next_shot, 1ULL);
+    shot_u = __shfl_sync(gmask, shot_u, leader);
+    if (shot_u >= (unsigned long long)a.shots) break;
+    const long long shot = (long long)shot_u;
+
+    const uint8_t* sp = a.syndromes + shot * m;
+    unsigned sbits = 0;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int i = lane + G * c;
+      if (i < m) {
+        if (sp[i]) sbits |= 1u << c;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      const int j = lane + G * v;
+      if (j < n) Lam[j] = s_prior[j];
+    }
+    __syncwarp(gmask);
+
+    int t = 0;
+    bool conv = false;
+    for (;;) {
+      const bool msgs = t < a.iters;
+      unsigned unsat = 0;
+      // ---- check phase: parity of [Lam^(t) < 0] and messages r^(t+1) ----
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int i = lane + G * c;
+        if (i >= m) continue;
+        const unsigned si = (sbits >> c) & 1u;
+        unsigned hp = si, sgn = si, negs = 0;
+        float min1 = kBig, min2 = kBig;
+        int idx = 0;
+        float* rc = r + i * DC;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+          const int j = (cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff;
+          const float L = Lam[j];
+          hp ^= (L < 0.f) ? 1u : 0u;
+          const float q = __fsub_rn(L, rc[k]);
+          const float aq = fabsf(q);
+          const unsigned ng = (q < 0.f) ? 1u : 0u;
+          sgn ^= ng;
+          negs |= ng << k;
+          const bool lt1 = aq < min1;
+          min2 = lt1 ? min1 : fminf(min2, aq);
+          min1 = lt1 ? aq : min1;
+          idx = lt1 ? k : idx;
+        }
+        unsat |= hp;
+        if (msgs) {
+          const float m1 = __fmul_rn(alpha, min1), m2 = __fmul_rn(alpha, min2);
+#pragma unroll
+          for (int k = 0; k < DC; ++k) {
+            const float mag = (k == idx) ? m2 : m1;
+            rc[k] = ((sgn ^ (negs >> k)) & 1u) ? -mag : mag;
+          }
+        }
+      }
+      if (t > 0) {
+        conv = !__any_sync(gmask, unsat != 0);
+        if (conv && a.early_exit) break;
+      }
+      if (!msgs) break;
+      __syncwarp(gmask);
+      // ---- variable phase: Lam^(t+1) ----
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int j = lane + G * v;
+        if (j >= n) continue;
+        float L = s_prior[j];
+#pragma unroll
+        for (int k = 0; k < DV; ++k) L = __fadd_rn(L, r[(ve[v][k >> 1] >> (16 * (k & 1))) & 0xffff]);
+        Lam[j] = L;
+      }
+      __syncwarp(gmask);
+      ++t;
+    }
+
+    // ---- outputs (each lane writes its own variables) ----
+    if (a.posteriors) {
+      float* po = a.posteriors + shot * n;
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int j = lane + G * v;
+        if (j < n) po[j] = Lam[j];
+      }
+    }
+    if (lane == 0) {
+      if (a.converged_out) a.converged_out[shot] = conv ? 1 : 0;
+      if (a.iters_out) a.iters_out[shot] = t;
+    }
+    my_iters += (lane == 0) ? (unsigned long long)t : 0ull;
+    my_conv += (lane == 0 && conv) ? 1ull : 0ull;
+    if (a.queue) {
+      if (conv) {
+        uint8_t* co = a.corrections + shot * n;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const int j = lane + G * v;
+          if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+        }
+        if (lane == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
+      } else {
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
+        slot = __shfl_sync(gmask, slot, leader);
+        if (lane == 0) a.queue[slot] = (int32_t)shot;
+        float* lo = a.queue_llr + (long long)slot * n;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const int j = lane + G * v;
+          if (j < n) lo[j] = Lam[j];
+        }
+      }
+    }
+    __syncwarp(gmask);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    my_iters += __shfl_down_sync(0xffffffffu, my_iters, off);
+    my_conv += __shfl_down_sync(0xffffffffu, my_conv, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (my_iters) atomicAdd(&a.ctr->bp_iterations, my_iters);
+    if (my_conv) atomicAdd(&a.ctr->bp_converged, my_conv);
+  }
+}
+
+// Shapes of bp_reg_kernel: (G, CPL, DC, VPL, DV).
+struct RegShape {
+  int G, cpl, dc, vpl, dv;
+  const void* fn;
+};
+
+#define LSD_REG_SHAPE(G, C, DCx, V, DVx) {G, C, DCx, V, DVx, (const void*)bp_reg_kernel<G, C, DCx, V, DVx>}
+const RegShape kRegShapes[] = {
+    LSD_REG_SHAPE(16, 3, 6, 5, 3),   // m <= 48,  n <= 80   (BB [[72,12,6]])
+    LSD_REG_SHAPE(32, 3, 6, 5, 3),   // m <= 96,  n <= 160  (BB [[144,12,12]])
+    LSD_REG_SHAPE(16, 5, 6, 9, 3),   // m <= 80,  n <= 144  (BB [[144,12,12]])
+    LSD_REG_SHAPE(32, 5, 6, 9, 3),   // m <= 160, n <= 288  (BB [[288,12,18]])
+    LSD_REG_SHAPE(8, 5, 6, 9, 3),    // m <= 40,  n <= 72   (BB [[72,12,6]])
+};
+#undef LSD_REG_SHAPE
+constexpr int kNumRegShapes = sizeof(kRegShapes) / sizeof(kRegShapes[0]);
+
+bool reg_shape_fits(const RegShape& s, const DevGraph& g) {
+  // regular graphs only: every row has degree dc and every column degree dv
+  return g.m <= s.G * s.cpl && g.n <= s.G * s.vpl && g.max_row_deg == s.dc &&
+         g.min_row_deg == s.dc && g.max_col_deg == s.dv && g.min_col_deg == s.dv;
+}
+
 }  // namespace
 
 cudaError_t launch_priors(const float* probs, float* prior, long long* wfix, int n,
@@ -222,48 +431,97 @@ cudaError_t launch_priors(const float* probs, float* prior, long long* wfix, int
   return cudaGetLastError();
 }
 
-cudaError_t bp_config(const DevGraph& g, int lanes, int method, int* grid, int* block,
-                      size_t* smem) {
+// Variant ids: 0..2 generic min-sum with G = 8, 16, 32; 3..5 generic sum-product;
+// 6 + i register-resident min-sum shape kRegShapes[i].
+namespace {
+const void* generic_fn(int v) {
+  switch (v) {
+    case 0: return (const void*)bp_kernel<8, 0>;
+    case 1: return (const void*)bp_kernel<16, 0>;
+    case 2: return (const void*)bp_kernel<32, 0>;
+    case 3: return (const void*)bp_kernel<8, 1>;
+    case 4: return (const void*)bp_kernel<16, 1>;
+    default: return (const void*)bp_kernel<32, 1>;
+  }
+}
+int lanes_of(int variant) {
+  if (variant >= 6) return kRegShapes[variant - 6].G;
+  return variant % 3 == 0 ? 8 : variant % 3 == 1 ? 16 : 32;
+}
+}  // namespace
+
+int bp_num_variants() { return 6 + kNumRegShapes; }
+
+cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
+                      int* grid, int* block, size_t* smem) {
   int dev = 0, sms = 0, max_smem = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t gb = bp_graph_bytes(g.m, g.n, g.E), grp = bp_group_bytes(g.m, g.n, g.E);
-  int b = 256;
-  while (b > lanes && gb + (size_t)(b / lanes) * grp > (size_t)max_smem) b /= 2;
-  if (gb + (size_t)(b / lanes) * grp > (size_t)max_smem) return cudaErrorInvalidValue;
-  *block = b;
-  *smem = gb + (size_t)(b / lanes) * grp;
-  int per_sm = 0;
-  const void* fns[6] = {(const void*)bp_kernel<8, 0>,  (const void*)bp_kernel<16, 0>,
-                        (const void*)bp_kernel<32, 0>, (const void*)bp_kernel<8, 1>,
-                        (const void*)bp_kernel<16, 1>, (const void*)bp_kernel<32, 1>};
-  // the limit is a property of the function, shared by every decoder: allow the maximum
-  for (const void* f : fns) {
-    err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (err != cudaSuccess) return err;
+  // choose the variant: a register-resident shape for min-sum when one fits (the one that
+  // wastes the fewest lane slots), else the generic kernel
+  int v = -1;
+  if (*variant >= 0) {
+    v = *variant;
+    if (v >= bp_num_variants()) return cudaErrorInvalidValue;
+    if (v >= 6 && (method != 0 || !reg_shape_fits(kRegShapes[v - 6], g))) return cudaErrorInvalidValue;
+    if (v < 6 && (v >= 3) != (method != 0)) return cudaErrorInvalidValue;
+  } else {
+    if (method == 0 && kind != 1) {
+      // least work per lane first (fewer registers, shorter per-shot latency), then the
+      // fewest idle lane slots
+      long best_lane = -1, best_slots = -1;
+      for (int i = 0; i < kNumRegShapes; ++i) {
+        const RegShape& sh = kRegShapes[i];
+        if (!reg_shape_fits(sh, g) || (lanes && sh.G != lanes)) continue;
+        const long per_lane = (long)sh.cpl * sh.dc + (long)sh.vpl * sh.dv;
+        const long slots = (long)sh.G * per_lane;
+        if (best_lane < 0 || per_lane < best_lane || (per_lane == best_lane && slots < best_slots)) {
+          best_lane = per_lane;
+          best_slots = slots;
+          v = 6 + i;
+        }
+      }
+    }
+    if (v < 0) {
+      if (kind == 2) return cudaErrorInvalidValue;
+      const int l = lanes ? lanes : 32;
+      v = (l == 8 ? 0 : l == 16 ? 1 : 2) + (method ? 3 : 0);
+    }
   }
-  const void* fn = fns[(lanes == 8 ? 0 : lanes == 16 ? 1 : 2) + (method ? 3 : 0)];
+  const int G = lanes_of(v);
+  size_t gb, grp;
+  if (v >= 6) {
+    gb = align16((size_t)g.n * 4);
+    grp = bp_reg_group_bytes(g.n, g.E);
+  } else {
+    gb = bp_graph_bytes(g.m, g.n, g.E);
+    grp = bp_group_bytes(g.m, g.n, g.E);
+  }
+  int b = 256;
+  while (b > G && gb + (size_t)(b / G) * grp > (size_t)max_smem) b /= 2;
+  if (gb + (size_t)(b / G) * grp > (size_t)max_smem) return cudaErrorInvalidValue;
+  *block = b;
+  *smem = gb + (size_t)(b / G) * grp;
+  const void* fn = v >= 6 ? kRegShapes[v - 6].fn : generic_fn(v);
+  // the limit is a property of the function, shared by every decoder: allow the maximum
+  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b, *smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidValue;
   *grid = per_sm * sms;
+  *variant = v;
   return cudaSuccess;
 }
 
-cudaError_t launch_bp(const BPArgs& a, int lanes, int grid, int block, size_t smem,
+cudaError_t launch_bp(const BPArgs& a, int variant, int grid, int block, size_t smem,
                       cudaStream_t st) {
-  const int sel = (lanes == 8 ? 0 : lanes == 16 ? 1 : 2) + (a.method ? 3 : 0);
-  switch (sel) {
-    case 0: bp_kernel<8, 0><<<grid, block, smem, st>>>(a); break;
-    case 1: bp_kernel<16, 0><<<grid, block, smem, st>>>(a); break;
-    case 2: bp_kernel<32, 0><<<grid, block, smem, st>>>(a); break;
-    case 3: bp_kernel<8, 1><<<grid, block, smem, st>>>(a); break;
-    case 4: bp_kernel<16, 1><<<grid, block, smem, st>>>(a); break;
-    default: bp_kernel<32, 1><<<grid, block, smem, st>>>(a); break;
-  }
-  return cudaGetLastError();
+  const void* fn = variant >= 6 ? kRegShapes[variant - 6].fn : generic_fn(variant);
+  void* args[] = {const_cast<BPArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
 }  // namespace lsdgb

@@ -4,29 +4,34 @@
 // One warp owns one shot; a persistent grid pulls shots from a device work queue (the
 // unconverged shots BP appended, or every shot for lsd_postprocess_batch).
 //
-// Per-shot state in shared memory (m detectors, n faults, W = ceil(m/32) words):
-//   dlab[m]    cluster label of each detector (-1: in no cluster).  Labels are the
-//              seed detectors (one cluster per flipped detector, Alg. 1 init).
+// Per-shot state in shared memory (m detectors, n faults, W = ceil(m/32), Wn = ceil(n/32)):
+//   rank[n], fat[n] the reliability order: the shot's (LLR, index) keys are sorted once
+//              (bitonic sort) and every later comparison is a comparison of 16-bit ranks.
+//   dlab[m]    cluster label of each detector (-1: in no cluster).  Labels are the seed
+//              detectors (one cluster per flipped detector, Alg. 1 init).
 //   parent[m]  union-find forest over labels; a merge links the larger root under the
-//              smaller one with a CAS (Alg. 2's parallel_union), so a cluster's root is
-//              its smallest seed.
-//   flab[n]    fault state: -2 untouched, -1 candidate (adjacent to a cluster detector,
-//              Def. 4.3's Lambda(C) over all clusters), >= 0 label of its cluster.
-//   R[m][W], T[m][W], pcol[m]: the elimination state of every cluster at once.  A
-//              pivot column is stored at its pivot row d: R[d] is the reduced column
-//              (bit d set, zero at every other pivot row), T[d] the set of pivot rows
-//              whose original columns XOR to R[d], pcol[d] the fault it came from.
-//              Rows of different clusters never mix, so the factorization of a merged
-//              cluster is the union of its parts: the block-swap of Sec. 4.2 is free.
-//   sred[W]    s reduced by the pivots; xsol[W] the pivot rows whose columns XOR to
-//              s - sred.  A cluster is valid (Def. 4.2) iff sred has no bit on its rows.
+//              smaller one with a CAS (Alg. 2's parallel_union), so a cluster's root is its
+//              smallest seed.  Labels are flattened to roots after every step.
+//   flab[n]    label of the cluster a fault belongs to (-1: none).
+//   cand[m][Wn] candidate set Lambda(C) of every cluster (Def. 4.3) as a bitmask over
+//              ranks, so a cluster's pick is its lowest set bit.  A detector joining a
+//              cluster adds its free faults; a merge ORs the masks; a fault joining a
+//              cluster is cleared.  (When the masks do not fit, a scan over the free faults
+//              with a 32-bit atomicMin per neighbouring cluster replaces them.)
+//   R[m][W], T[m][W], pcol[m]: the elimination state of every cluster at once.  A pivot
+//              column is stored at its pivot row d: R[d] is the reduced column (bit d set,
+//              zero at every other pivot row), T[d] the set of pivot rows whose original
+//              columns XOR to R[d], pcol[d] the fault it came from.  Rows of different
+//              clusters never mix, so the factorization of a merged cluster is the union of
+//              its parts: the block-swap of Sec. 4.2 is free.
+//   sred[W]    s reduced by the pivots; xsol[W] the pivot rows whose columns XOR to s - sred.
+//              A cluster is valid (Def. 4.2) iff sred has no bit on its rows.
 //
-// A growth step: every growing cluster takes its lowest-(LLR, index) candidate
-// (atomicMin on a 64-bit order key), all picks are applied together, clusters that now
-// share a detector (or a fault) are merged, then the new columns are eliminated one by
-// one in key order: b' = b + sum of R[d] over pivot rows d in supp(b) (one XOR per
-// nonzero of the sparse column), a new pivot at the lowest set bit of b', and
-// back-elimination of that row from the other pivots.  Validity is re-read from sred.
+// A growth step: every growing cluster takes its lowest-rank candidate, all picks are applied
+// together, clusters that now share a detector (or a fault) are merged, then the new columns
+// are eliminated one by one in rank order: b' = b + sum of R[d] over pivot rows d in supp(b)
+// (one W-word XOR per nonzero of the sparse column), a new pivot at the lowest set bit of
+// b', and back-elimination of that row from the other pivots.  Validity is re-read from sred.
 #include <climits>
 
 #include "lsd_internal.cuh"
@@ -36,51 +41,104 @@ namespace lsdgb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned long long kNoKey = ~0ull;
+constexpr unsigned kNone = 0xffffffffu;
+// candidate masks are used when they take at most this many bytes per warp
+constexpr size_t kMaskBudget = 32 << 10;
+// the Tanner graph is staged in shared memory when it takes at most this many bytes
+constexpr size_t kGraphBudget = 48 << 10;
 
-__host__ __device__ inline size_t al8(size_t x) { return (x + 7) & ~(size_t)7; }
-__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-struct Lay {
-  size_t R, T, best, newk, srt, dlab, parent, pcol, inv, flab, llr, words, scal, rflag, npk, npN,
-      ext, total;
-};
-
-__host__ __device__ inline Lay lsd_layout(int m, int n, int W, int order) {
-  Lay L;
-  size_t o = 0;
-  L.R = o; o += (size_t)m * W * 4;
-  L.T = o; o += (size_t)m * W * 4;
-  o = al8(o);
-  L.best = o; o += (size_t)m * 8;
-  L.newk = o; o += (size_t)m * 8;
-  L.srt = o; o += (size_t)m * 8;
-  L.npk = o; o += order > 0 ? (size_t)n * 8 : 0;
-  L.dlab = o; o += (size_t)m * 4;
-  L.parent = o; o += (size_t)m * 4;
-  L.pcol = o; o += (size_t)m * 4;
-  L.inv = o; o += (size_t)m * 4;
-  L.flab = o; o += (size_t)n * 4;
-  L.llr = o; o += (size_t)n * 4;
-  L.words = o; o += (size_t)4 * W * 4;
-  L.scal = o; o += 16 * 4;
-  L.npN = o; o += order > 0 ? (size_t)n * W * 4 : 0;
-  L.ext = o; o += order > 0 ? (size_t)n * 4 : 0;
-  L.rflag = o; o += (size_t)m;
-  L.total = al16(o);
-  return L;
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ constexpr int pow2_at_least(int x) {
+  int p = 32;
+  while (p < x) p <<= 1;
+  return p;
+}
+__host__ __device__ constexpr size_t max_sz(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ inline size_t graph_bytes(int m, int n, int E) {
+  return al16((size_t)(m + 1 + n + 1) * 4 + (size_t)E * 4);
 }
 
-struct Shot {
-  uint32_t *R, *T, *syn, *sred, *xsol, *cm, *npN;
-  unsigned long long *best, *newk, *srt, *npk;
-  int *dlab, *parent, *pcol, *inv, *flab, *scal, *ext;
-  float* llr;
-  unsigned char* rflag;
+// Per-warp shared-memory layout of a size class (at most MM detectors and NN faults),
+// with every offset a compile-time constant.  U holds the sort keys at init, the
+// candidate masks during growth and the staged correction bytes at the end.
+template <int MM, int NN, bool MU>
+struct Lay {
+  static constexpr int W = (MM + 31) / 32;
+  static constexpr int Wn = (NN + 31) / 32;
+  static constexpr int N2 = pow2_at_least(NN);
+  static constexpr bool kMasks = (size_t)MM * Wn * 4 <= kMaskBudget;
+  // small classes rank the keys with shuffles and need no sort buffer
+  static constexpr bool kShuffleRank = NN <= 192;
+  static constexpr size_t U = 0;
+  static constexpr size_t R = al16(max_sz(kShuffleRank ? 0 : (size_t)N2 * 8,
+                                          max_sz(kMasks ? (size_t)MM * Wn * 4 : 0, (size_t)NN)));
+  static constexpr size_t T = R + (size_t)MM * W * 4;
+  static constexpr size_t flab = T + (size_t)MM * W * 4;
+  static constexpr size_t dlab = flab + (size_t)NN * 4;
+  static constexpr size_t parent = dlab + (size_t)MM * 4;
+  static constexpr size_t best = parent + (size_t)MM * 4;
+  static constexpr size_t words = best + (size_t)MM * 4;
+  static constexpr size_t scal = words + (size_t)4 * W * 4;
+  static constexpr size_t npr = scal + 16 * 4;
+  static constexpr size_t npN = npr + (MU ? (size_t)NN * 4 : 0);
+  static constexpr size_t ext = npN + (MU ? (size_t)NN * W * 4 : 0);
+  static constexpr size_t pcol = ext + (MU ? (size_t)NN * 4 : 0);
+  static constexpr size_t inv = pcol + (size_t)MM * 2;
+  static constexpr size_t mlist = inv + (size_t)MM * 2;
+  static constexpr size_t dnew = mlist + (size_t)MM * 2;
+  static constexpr size_t newr = dnew + (size_t)MM * 2;
+  static constexpr size_t srt = newr + (size_t)MM * 2;
+  static constexpr size_t rank = srt + (size_t)MM * 2;
+  static constexpr size_t fat = rank + (size_t)NN * 2;
+  static constexpr size_t rflag = fat + (size_t)NN * 2;
+  static constexpr size_t total = al16(rflag + (size_t)MM);
 };
 
-// Order key of fault j: (LLR ascending, index ascending).  -0.0 is folded into +0.0 so
-// that the key order is the float order, with ties broken by the index.
+struct Graph {
+  const int32_t* chk_ptr;
+  const uint16_t* chk_var;
+  const int32_t* var_ptr;
+  const uint16_t* var_chk;
+};
+
+// Accessors of one warp's shot state: one base pointer plus compile-time offsets.
+template <class L>
+struct Shot {
+  unsigned char* base;
+  template <class T>
+  __device__ __forceinline__ T* at(size_t off) const {
+    return reinterpret_cast<T*>(base + off);
+  }
+  __device__ __forceinline__ unsigned long long* keys() const { return at<unsigned long long>(L::U); }
+  __device__ __forceinline__ uint32_t* cand() const { return at<uint32_t>(L::U); }
+  __device__ __forceinline__ uint8_t* cs() const { return at<uint8_t>(L::U); }
+  __device__ __forceinline__ uint32_t* R() const { return at<uint32_t>(L::R); }
+  __device__ __forceinline__ uint32_t* T() const { return at<uint32_t>(L::T); }
+  __device__ __forceinline__ int* flab() const { return at<int>(L::flab); }
+  __device__ __forceinline__ int* dlab() const { return at<int>(L::dlab); }
+  __device__ __forceinline__ int* parent() const { return at<int>(L::parent); }
+  __device__ __forceinline__ int16_t* pcol() const { return at<int16_t>(L::pcol); }
+  __device__ __forceinline__ uint32_t* best() const { return at<uint32_t>(L::best); }
+  __device__ __forceinline__ uint16_t* inv() const { return at<uint16_t>(L::inv); }
+  __device__ __forceinline__ uint16_t* mlist() const { return at<uint16_t>(L::mlist); }
+  __device__ __forceinline__ uint16_t* dnew() const { return at<uint16_t>(L::dnew); }
+  __device__ __forceinline__ uint16_t* newr() const { return at<uint16_t>(L::newr); }
+  __device__ __forceinline__ uint16_t* srt() const { return at<uint16_t>(L::srt); }
+  __device__ __forceinline__ uint32_t* syn() const { return at<uint32_t>(L::words); }
+  __device__ __forceinline__ uint32_t* sred() const { return at<uint32_t>(L::words + L::W * 4); }
+  __device__ __forceinline__ uint32_t* xsol() const { return at<uint32_t>(L::words + 2 * L::W * 4); }
+  __device__ __forceinline__ uint32_t* cm() const { return at<uint32_t>(L::words + 3 * L::W * 4); }
+  __device__ __forceinline__ int* scal() const { return at<int>(L::scal); }
+  __device__ __forceinline__ uint32_t* npr() const { return at<uint32_t>(L::npr); }
+  __device__ __forceinline__ uint32_t* npN() const { return at<uint32_t>(L::npN); }
+  __device__ __forceinline__ int* ext() const { return at<int>(L::ext); }
+  __device__ __forceinline__ uint16_t* rank() const { return at<uint16_t>(L::rank); }
+  __device__ __forceinline__ uint16_t* fat() const { return at<uint16_t>(L::fat); }
+  __device__ __forceinline__ unsigned char* rflag() const { return at<unsigned char>(L::rflag); }
+};
+
+// Order key of fault j: (LLR ascending, index ascending).  -0.0 is folded into +0.0 so that
+// the key order is the float order, with ties broken by the index.
 __device__ __forceinline__ unsigned long long llr_key(float x, int j) {
   x = __fadd_rn(x, 0.0f);
   unsigned u = __float_as_uint(x);
@@ -97,7 +155,11 @@ __device__ __forceinline__ int uf_find(const volatile int* parent, int x) {
   return x;
 }
 
-__device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
+// Union of the sets of a and b; a root that gets linked under another is recorded in the
+// merged list so that its candidate mask can be folded into the new root.
+template <class L>
+__device__ __forceinline__ void uf_unite(const Shot<L>& S, int a, int b) {
+  int* parent = S.parent();
   const volatile int* vp = parent;
   for (;;) {
     a = uf_find(vp, a);
@@ -108,7 +170,11 @@ __device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
       a = b;
       b = t;
     }
-    if (atomicCAS(parent + a, a, b) == a) return;
+    if (atomicCAS(parent + a, a, b) == a) {
+      const int slot = atomicAdd(&S.scal()[3], 1);
+      S.mlist()[slot] = (uint16_t)a;
+      return;
+    }
   }
 }
 
@@ -116,15 +182,44 @@ __device__ __forceinline__ bool bit_of(const uint32_t* v, int i) {
   return (v[i >> 5] >> (i & 31)) & 1u;
 }
 
-// Roots of all clusters (pred = every alive seed) or of the invalid ones (sred bits).
-__device__ int collect_roots(const LSDArgs& a, Shot& S, int m, bool only_invalid, int lane) {
+// Bitonic sort of keys[0..N2) ascending (one warp).
+template <int N2>
+__device__ void warp_sort(unsigned long long* keys, int lane) {
+#pragma unroll 1
+  for (int k = 2; k <= N2; k <<= 1) {
+#pragma unroll 1
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i0 = 0; i0 < N2; i0 += 32) {
+        const int i = i0 + lane;
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = keys[i], y = keys[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            keys[i] = y;
+            keys[ixj] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Roots of all clusters, or of the invalid ones (sred bits), into inv[].
+template <class L>
+__device__ int collect_roots(const LSDArgs& a, const Shot<L>& S, int m, bool only_invalid,
+                             int lane) {
   if (only_invalid) {
-    for (int d = lane; d < m; d += 32) S.rflag[d] = 0;
-    __syncwarp();
-    for (int d = lane; d < m; d += 32) {
-      if (bit_of(S.sred, d)) {
-        const int lab = S.dlab[d];
-        if (lab >= 0) S.rflag[uf_find(S.parent, lab)] = 1;
+    // labels are flattened: dlab of a clustered detector is its root
+    if (lane < L::W) {
+      uint32_t bits = S.sred()[lane];
+      while (bits) {
+        const int d = lane * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int lab = S.dlab()[d];
+        if (lab >= 0) S.rflag()[lab] = 1;
       }
     }
     __syncwarp();
@@ -132,45 +227,46 @@ __device__ int collect_roots(const LSDArgs& a, Shot& S, int m, bool only_invalid
   int count = 0;
   for (int base = 0; base < m; base += 32) {
     const int d = base + lane;
-    const bool seed = d < m && (a.single_cluster ? d == 0 : bit_of(S.syn, d));
-    const bool pred = seed && S.parent[d] == d && (!only_invalid || S.rflag[d]);
+    const bool seed = d < m && (a.single_cluster ? d == 0 : bit_of(S.syn(), d));
+    const bool pred = seed && S.parent()[d] == d && (!only_invalid || S.rflag()[d]);
     const unsigned bal = __ballot_sync(kFull, pred);
-    if (pred) S.inv[count + __popc(bal & ((1u << lane) - 1u))] = d;
+    if (pred) {
+      S.inv()[count + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
+      if (only_invalid) S.rflag()[d] = 0;
+    }
     count += __popc(bal);
   }
   __syncwarp();
-  if (only_invalid) {
-    for (int d = lane; d < m; d += 32) S.rflag[d] = 0;
-    __syncwarp();
-  }
   return count;
 }
 
-// Adds fault column gcol (key = its order key) to its cluster's factorization.
-__device__ void add_column(const LSDArgs& a, Shot& S, int m, int W, int gcol,
-                           unsigned long long key, int lane) {
-  const DevGraph& g = a.g;
+// Adds the fault of rank `rk` to its cluster's factorization.
+template <class L, bool MU>
+__device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int lane) {
+  constexpr int W = L::W;
+  const int gcol = S.fat()[rk];
   uint32_t bw = 0, tw = 0;
   if (lane < W) {
-    const int v1 = g.var_ptr[gcol + 1];
-    for (int q = g.var_ptr[gcol]; q < v1; ++q) {
-      const int d = g.var_chk[q];
+    const int v1 = G.var_ptr[gcol + 1];
+    for (int q = G.var_ptr[gcol]; q < v1; ++q) {
+      const int d = G.var_chk[q];
       if ((d >> 5) == lane) bw ^= 1u << (d & 31);
-      if (S.pcol[d] >= 0) {
-        bw ^= S.R[d * W + lane];
-        tw ^= S.T[d * W + lane];
+      if (S.pcol()[d] >= 0) {
+        bw ^= S.R()[d * W + lane];
+        tw ^= S.T()[d * W + lane];
       }
     }
   }
   const unsigned nz = __ballot_sync(kFull, lane < W && bw != 0);
   if (nz == 0) {
     // dependent column: remember its representation for LSD-mu's OSD-E
-    if (a.order > 0) {
-      const int slot = __shfl_sync(kFull, S.scal[1], 0);
-      if (lane < W) S.npN[slot * W + lane] = tw;
+    if constexpr (MU) {
+      const int slot = __shfl_sync(kFull, S.scal()[1], 0);
+      if (lane < W) S.npN()[slot * W + lane] = tw;
+      __syncwarp();
       if (lane == 0) {
-        S.npk[slot] = key;
-        S.scal[1] = slot + 1;
+        S.npr()[slot] = (uint32_t)rk;
+        S.scal()[1] = slot + 1;
       }
       __syncwarp();
     }
@@ -182,153 +278,211 @@ __device__ void add_column(const LSDArgs& a, Shot& S, int m, int W, int gcol,
   const int pw = p >> 5;
   const uint32_t pb = 1u << (p & 31);
   if (lane == pw) tw ^= pb;
-  const bool sflag = (S.sred[pw] & pb) != 0;
+  const bool sflag = (S.sred()[pw] & pb) != 0;
   if (lane < W) {
-    S.R[p * W + lane] = bw;
-    S.T[p * W + lane] = tw;
+    S.R()[p * W + lane] = bw;
+    S.T()[p * W + lane] = tw;
   }
-  if (lane == 0) S.pcol[p] = gcol;
+  if (lane == 0) S.pcol()[p] = (int16_t)gcol;
   __syncwarp();
   for (int d = lane; d < m; d += 32) {
-    if (d == p || S.pcol[d] < 0) continue;
-    if (S.R[d * W + pw] & pb) {
+    if (d == p || S.pcol()[d] < 0) continue;
+    if (S.R()[d * W + pw] & pb) {
+#pragma unroll
       for (int w = 0; w < W; ++w) {
-        S.R[d * W + w] ^= S.R[p * W + w];
-        S.T[d * W + w] ^= S.T[p * W + w];
+        S.R()[d * W + w] ^= S.R()[p * W + w];
+        S.T()[d * W + w] ^= S.T()[p * W + w];
       }
     }
   }
   if (sflag && lane < W) {
-    S.sred[lane] ^= bw;
-    S.xsol[lane] ^= tw;
+    S.sred()[lane] ^= bw;
+    S.xsol()[lane] ^= tw;
   }
   __syncwarp();
 }
 
-// One synchronous growth step of the k clusters listed in S.inv.
+// One synchronous growth step of the k clusters listed in inv[].
 // Returns 0 if clusters grew, 1 if strict and a cluster had no candidate, 2 if none grew.
-__device__ int lsd_step(const LSDArgs& a, Shot& S, int m, int n, int W, int k, bool strict,
+template <class L, bool MU>
+__device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, bool strict,
                         int lane) {
-  const DevGraph& g = a.g;
-  for (int t = lane; t < k; t += 32) {
-    const int r = S.inv[t];
-    S.best[r] = kNoKey;
-    S.rflag[r] = 1;
-  }
-  __syncwarp();
-  // find_candidate: every candidate fault offers itself to the growing clusters it touches
-  for (int j = lane; j < n; j += 32) {
-    if (S.flab[j] != -1) continue;
-    const unsigned long long key = llr_key(S.llr[j], j);
-    const int v1 = g.var_ptr[j + 1];
-    for (int q = g.var_ptr[j]; q < v1; ++q) {
-      const int lab = S.dlab[g.var_chk[q]];
-      if (lab < 0) continue;
-      const int root = uf_find(S.parent, lab);
-      if (S.rflag[root]) atomicMin(&S.best[root], key);
+  constexpr int Wn = L::Wn;
+  // ---- find_candidate: the lowest-rank candidate of every growing cluster ----
+  if constexpr (L::kMasks) {
+    for (int t = lane; t < k; t += 32) {
+      const int r = S.inv()[t];
+      const uint32_t* c = S.cand() + (size_t)r * Wn;
+      unsigned pick = kNone;
+      for (int w = 0; w < Wn; ++w) {
+        const uint32_t v = c[w];
+        if (v) {
+          pick = (unsigned)(w * 32 + __ffs(v) - 1);
+          break;
+        }
+      }
+      S.best()[r] = pick;
     }
+    __syncwarp();
+  } else {
+    for (int t = lane; t < k; t += 32) {
+      const int r = S.inv()[t];
+      S.best()[r] = kNone;
+      S.rflag()[r] = 1;
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+      if (S.flab()[j] >= 0) continue;
+      const unsigned rk = S.rank()[j];
+      const int v1 = G.var_ptr[j + 1];
+      for (int q = G.var_ptr[j]; q < v1; ++q) {
+        const int lab = S.dlab()[G.var_chk[q]];
+        if (lab >= 0 && S.rflag()[lab]) atomicMin(&S.best()[lab], rk);
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < k; t += 32) S.rflag()[S.inv()[t]] = 0;
   }
-  __syncwarp();
   bool none = false, some = false;
   for (int t = lane; t < k; t += 32) {
-    if (S.best[S.inv[t]] == kNoKey) none = true;
+    if (S.best()[S.inv()[t]] == kNone) none = true;
     else some = true;
   }
   none = __any_sync(kFull, none);
   some = __any_sync(kFull, some);
   if ((strict && none) || !some) {
-    for (int t = lane; t < k; t += 32) S.rflag[S.inv[t]] = 0;
     __syncwarp();
     return (strict && none) ? 1 : 2;
   }
-  if (lane == 0) S.scal[0] = 0;
+  if (lane == 0) {
+    S.scal()[0] = 0;  // new faults
+    S.scal()[3] = 0;  // merged labels
+    S.scal()[4] = 0;  // newly claimed detectors
+  }
   __syncwarp();
-  // parallel_union: apply every pick, merge clusters that now share a detector or a fault
+  // ---- parallel_union: apply every pick, merge clusters sharing a detector or a fault ----
   for (int t = lane; t < k; t += 32) {
-    const int r = S.inv[t];
-    S.rflag[r] = 0;
-    const unsigned long long key = S.best[r];
-    if (key == kNoKey) continue;
-    const int gcol = (int)(key & 0xffffffffu);
-    const int old = atomicCAS(&S.flab[gcol], -1, r);
+    const int r = S.inv()[t];
+    const unsigned rk = S.best()[r];
+    if (rk == kNone) continue;
+    const int gcol = S.fat()[rk];
+    const int old = atomicCAS(&S.flab()[gcol], -1, r);
     if (old == -1) {
-      const int slot = atomicAdd(&S.scal[0], 1);
-      S.newk[slot] = key;
+      const int slot = atomicAdd(&S.scal()[0], 1);
+      S.newr()[slot] = (uint16_t)rk;
     } else {
-      uf_unite(S.parent, r, old);
+      uf_unite(S, r, old);
     }
-    const int v1 = g.var_ptr[gcol + 1];
-    for (int q = g.var_ptr[gcol]; q < v1; ++q) {
-      const int d = g.var_chk[q];
-      const int o = atomicCAS(&S.dlab[d], -1, r);
+    const int v1 = G.var_ptr[gcol + 1];
+    for (int q = G.var_ptr[gcol]; q < v1; ++q) {
+      const int d = G.var_chk[q];
+      const int o = atomicCAS(&S.dlab()[d], -1, r);
       if (o == -1) {
-        const int c1 = g.chk_ptr[d + 1];
-        for (int e = g.chk_ptr[d]; e < c1; ++e) atomicCAS(&S.flab[g.chk_var[e]], -2, -1);
+        const int slot = atomicAdd(&S.scal()[4], 1);
+        S.dnew()[slot] = (uint16_t)d;
       } else if (o != r) {
-        uf_unite(S.parent, r, o);
+        uf_unite(S, r, o);
       }
     }
   }
   __syncwarp();
-  // the step's new columns in reliability order (rank by counting; keys are distinct)
-  const int n_new = S.scal[0];
-  for (int t = lane; t < n_new; t += 32) {
-    const unsigned long long kt = S.newk[t];
-    int rank = 0;
-    for (int u = 0; u < n_new; ++u) rank += (S.newk[u] < kt) ? 1 : 0;
-    S.srt[rank] = kt;
+  // ---- flatten labels to roots (later finds take one step) ----
+  for (int x = lane; x < m; x += 32) {
+    const int root = uf_find(S.parent(), x);
+    S.parent()[x] = root;
+    const int l = S.dlab()[x];
+    if (l >= 0) S.dlab()[x] = uf_find(S.parent(), l);
   }
   __syncwarp();
-  for (int t = 0; t < n_new; ++t) {
-    const unsigned long long key = S.srt[t];
-    add_column(a, S, m, W, (int)(key & 0xffffffffu), key, lane);
+  if constexpr (L::kMasks) {
+    // fold the masks of merged labels into their roots; add the free faults next to the
+    // newly claimed detectors
+    const int nm = S.scal()[3], nd = S.scal()[4];
+    for (int idx = lane; idx < nm * Wn; idx += 32) {
+      const int x = S.mlist()[idx / Wn], w = idx % Wn;
+      const uint32_t v = S.cand()[(size_t)x * Wn + w];
+      if (v) atomicOr(&S.cand()[(size_t)S.parent()[x] * Wn + w], v);
+    }
+    for (int t = lane; t < nd; t += 32) {
+      const int d = S.dnew()[t];
+      uint32_t* c = S.cand() + (size_t)S.dlab()[d] * Wn;
+      const int c1 = G.chk_ptr[d + 1];
+      for (int e = G.chk_ptr[d]; e < c1; ++e) {
+        const int f = G.chk_var[e];
+        if (S.flab()[f] < 0) {
+          const unsigned rk = S.rank()[f];
+          atomicOr(&c[rk >> 5], 1u << (rk & 31));
+        }
+      }
+    }
+    __syncwarp();
+    // the step's new faults are no longer candidates
+    const int nn = S.scal()[0];
+    for (int t = lane; t < nn; t += 32) {
+      const unsigned rk = S.newr()[t];
+      const int root = S.parent()[S.flab()[S.fat()[rk]]];
+      atomicAnd(&S.cand()[(size_t)root * Wn + (rk >> 5)], ~(1u << (rk & 31)));
+    }
+    __syncwarp();
   }
+  // ---- the step's new columns in reliability (rank) order ----
+  const int n_new = S.scal()[0];
+  for (int t = lane; t < n_new; t += 32) {
+    const unsigned kt = S.newr()[t];
+    int pos = 0;
+    for (int u = 0; u < n_new; ++u) pos += (S.newr()[u] < kt) ? 1 : 0;
+    S.srt()[pos] = (uint16_t)kt;
+  }
+  __syncwarp();
+  for (int t = 0; t < n_new; ++t) add_column<L, MU>(G, S, m, (int)S.srt()[t], lane);
   return 0;
 }
 
 // LSD-mu reprocessing (App. D): exhaustive OSD over the first min(mu, #dependent) dependent
 // columns of each cluster, in reliability order; cost = sum of 2^-32 fixed-point channel
 // weights; ties go to the smaller pattern.  Updates xsol and appends the chosen dependent
-// columns to S.ext.
-__device__ void osd_e(const LSDArgs& a, Shot& S, int m, int W, int lane) {
-  const DevGraph& g = a.g;
+// columns to ext[].
+template <class L>
+__device__ void osd_e(const LSDArgs& a, const Shot<L>& S, int m, int lane) {
+  constexpr int W = L::W;
+  const long long* wfix = a.g.wfix;
   const int order = a.order;
   const int nroots = collect_roots(a, S, m, false, lane);
-  const int n_np = S.scal[1];
+  const int n_np = S.scal()[1];
   for (int ci = 0; ci < nroots; ++ci) {
-    const int r = S.inv[ci];
+    const int r = S.inv()[ci];
+#pragma unroll
     for (int c = 0; c < W; ++c) {
       const int d = c * 32 + lane;
-      const bool in = d < m && S.dlab[d] >= 0 && uf_find(S.parent, S.dlab[d]) == r;
+      const bool in = d < m && S.dlab()[d] == r;
       const unsigned bal = __ballot_sync(kFull, in);
-      if (lane == 0) S.cm[c] = bal;
+      if (lane == 0) S.cm()[c] = bal;
     }
     __syncwarp();
     int sel[kMaxOrder];
     int nt = 0;
-    unsigned long long last = 0;
+    unsigned last = 0;
     for (int it = 0; it < order; ++it) {
-      unsigned long long bk = kNoKey;
+      unsigned bk = kNone;
       int bi = -1;
       for (int u = lane; u < n_np; u += 32) {
-        const unsigned long long ku = S.npk[u];
+        const unsigned ku = S.npr()[u];
         if (it > 0 && ku <= last) continue;
-        const int gu = (int)(ku & 0xffffffffu);
-        if (uf_find(S.parent, S.flab[gu]) != r) continue;
+        if (S.parent()[S.flab()[S.fat()[ku]]] != r) continue;
         if (ku < bk) {
           bk = ku;
           bi = u;
         }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(kFull, bk, off);
+        const unsigned ok = __shfl_xor_sync(kFull, bk, off);
         const int oi = __shfl_xor_sync(kFull, bi, off);
         if (ok < bk) {
           bk = ok;
           bi = oi;
         }
       }
-      if (bk == kNoKey) break;
+      if (bk == kNone) break;
       sel[nt++] = bi;
       last = bk;
     }
@@ -337,18 +491,19 @@ __device__ void osd_e(const LSDArgs& a, Shot& S, int m, int W, int lane) {
     int bt = 0;
     for (int t = lane; t < (1 << nt); t += 32) {
       long long cost = 0;
+#pragma unroll
       for (int w = 0; w < W; ++w) {
-        uint32_t mw = S.xsol[w] & S.cm[w];
+        uint32_t mw = S.xsol()[w] & S.cm()[w];
         for (int k2 = 0; k2 < nt; ++k2)
-          if ((t >> k2) & 1) mw ^= S.npN[sel[k2] * W + w];
+          if ((t >> k2) & 1) mw ^= S.npN()[sel[k2] * W + w];
         while (mw) {
           const int b = __ffs(mw) - 1;
           mw &= mw - 1;
-          cost += g.wfix[S.pcol[w * 32 + b]];
+          cost += wfix[S.pcol()[w * 32 + b]];
         }
       }
       for (int k2 = 0; k2 < nt; ++k2)
-        if ((t >> k2) & 1) cost += g.wfix[(int)(S.npk[sel[k2]] & 0xffffffffu)];
+        if ((t >> k2) & 1) cost += wfix[S.fat()[S.npr()[sel[k2]]]];
       if (cost < bcost) {
         bcost = cost;
         bt = t;
@@ -365,46 +520,51 @@ __device__ void osd_e(const LSDArgs& a, Shot& S, int m, int W, int lane) {
     if (lane < W) {
       uint32_t delta = 0;
       for (int k2 = 0; k2 < nt; ++k2)
-        if ((bt >> k2) & 1) delta ^= S.npN[sel[k2] * W + lane];
-      S.xsol[lane] ^= delta;
+        if ((bt >> k2) & 1) delta ^= S.npN()[sel[k2] * W + lane];
+      S.xsol()[lane] ^= delta;
     }
     if (lane == 0) {
-      int ne = S.scal[2];
+      int ne = S.scal()[2];
       for (int k2 = 0; k2 < nt; ++k2)
-        if ((bt >> k2) & 1) S.ext[ne++] = (int)(S.npk[sel[k2]] & 0xffffffffu);
-      S.scal[2] = ne;
+        if ((bt >> k2) & 1) S.ext()[ne++] = S.fat()[S.npr()[sel[k2]]];
+      S.scal()[2] = ne;
     }
     __syncwarp();
   }
 }
 
-__global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
+template <int MM, int NN, bool MU>
+__global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int graph_smem) {
+  using L = Lay<MM, NN, MU>;
+  constexpr int W = L::W, Wn = L::Wn, N2 = L::N2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int m = a.g.m, n = a.g.n;
-  const Lay L = lsd_layout(m, n, W, a.order);
-  unsigned char* base = smem + (size_t)warp * L.total;
-  Shot S;
-  S.R = reinterpret_cast<uint32_t*>(base + L.R);
-  S.T = reinterpret_cast<uint32_t*>(base + L.T);
-  S.best = reinterpret_cast<unsigned long long*>(base + L.best);
-  S.newk = reinterpret_cast<unsigned long long*>(base + L.newk);
-  S.srt = reinterpret_cast<unsigned long long*>(base + L.srt);
-  S.npk = reinterpret_cast<unsigned long long*>(base + L.npk);
-  S.dlab = reinterpret_cast<int*>(base + L.dlab);
-  S.parent = reinterpret_cast<int*>(base + L.parent);
-  S.pcol = reinterpret_cast<int*>(base + L.pcol);
-  S.inv = reinterpret_cast<int*>(base + L.inv);
-  S.flab = reinterpret_cast<int*>(base + L.flab);
-  S.llr = reinterpret_cast<float*>(base + L.llr);
-  S.syn = reinterpret_cast<uint32_t*>(base + L.words);
-  S.sred = S.syn + W;
-  S.xsol = S.sred + W;
-  S.cm = S.xsol + W;
-  S.scal = reinterpret_cast<int*>(base + L.scal);
-  S.npN = reinterpret_cast<uint32_t*>(base + L.npN);
-  S.ext = reinterpret_cast<int*>(base + L.ext);
-  S.rflag = base + L.rflag;
+  const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const int nwarps = blockDim.x >> 5;
+  Graph G;
+  if (graph_smem) {
+    int32_t* cp = reinterpret_cast<int32_t*>(smem + (size_t)nwarps * L::total);
+    int32_t* vp = cp + (m + 1);
+    uint16_t* cv = reinterpret_cast<uint16_t*>(vp + (n + 1));
+    uint16_t* vc = cv + E;
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) cp[i] = a.g.chk_ptr[i];
+    for (int j = threadIdx.x; j <= n; j += blockDim.x) vp[j] = a.g.var_ptr[j];
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      cv[e] = a.g.chk_var[e];
+      vc[e] = a.g.var_chk[e];
+    }
+    __syncthreads();
+    G.chk_ptr = cp;
+    G.var_ptr = vp;
+    G.chk_var = cv;
+    G.var_chk = vc;
+  } else {
+    G.chk_ptr = a.g.chk_ptr;
+    G.var_ptr = a.g.var_ptr;
+    G.chk_var = a.g.chk_var;
+    G.var_chk = a.g.var_chk;
+  }
+  Shot<L> S{smem + (size_t)warp * L::total};
 
   const long long count = a.count_from_ctr ? (long long)a.ctr->lsd_count : a.count;
   unsigned long long steps_acc = 0, unsolv = 0;
@@ -418,47 +578,103 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
     const float* lsrc = a.llr + (a.llr_by_item ? (long long)item : shot) * n;
     const uint8_t* ssrc = a.syndromes + shot * m;
 
+    // ---- the shot's reliability order ----
+    if constexpr (L::kShuffleRank) {
+      // rank of each key = number of smaller keys, counted with shuffles (keys are distinct)
+      constexpr int KPL = (NN + 31) / 32;
+      unsigned long long myk[KPL];
+      int rk[KPL];
+#pragma unroll
+      for (int t = 0; t < KPL; ++t) {
+        const int j = lane + 32 * t;
+        myk[t] = j < n ? llr_key(lsrc[j], j) : ~0ull;
+        rk[t] = 0;
+      }
+#pragma unroll 4
+      for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int t2 = 0; t2 < KPL; ++t2) {
+          const unsigned long long other = __shfl_sync(kFull, myk[t2], src);
+#pragma unroll
+          for (int t = 0; t < KPL; ++t) rk[t] += (other < myk[t]) ? 1 : 0;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < KPL; ++t) {
+        const int j = lane + 32 * t;
+        if (j < n) {
+          S.rank()[j] = (uint16_t)rk[t];
+          S.fat()[rk[t]] = (uint16_t)j;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j0 = 0; j0 < N2; j0 += 32) {
+        const int j = j0 + lane;
+        S.keys()[j] = j < n ? llr_key(lsrc[j], j) : ~0ull;
+      }
+      __syncwarp();
+      warp_sort<N2>(S.keys(), lane);
+      for (int r = lane; r < n; r += 32) {
+        const int j = (int)(S.keys()[r] & 0xffffffffu);
+        S.fat()[r] = (uint16_t)j;
+        S.rank()[j] = (uint16_t)r;
+      }
+    }
+    __syncwarp();
+
     // ---- init: one cluster per flipped detector ----
-    for (int j = lane; j < n; j += 32) {
-      S.llr[j] = lsrc[j];
-      S.flab[j] = -2;
-    }
+    if constexpr (L::kMasks)
+      for (int w = lane; w < m * Wn; w += 32) S.cand()[w] = 0;
+    for (int j = lane; j < n; j += 32) S.flab()[j] = -1;
     for (int d = lane; d < m; d += 32) {
-      S.dlab[d] = -1;
-      S.parent[d] = d;
-      S.pcol[d] = -1;
-      S.rflag[d] = 0;
+      S.dlab()[d] = -1;
+      S.parent()[d] = d;
+      S.pcol()[d] = -1;
+      S.rflag()[d] = 0;
     }
+#pragma unroll
     for (int c = 0; c < W; ++c) {
       const int d = c * 32 + lane;
       const unsigned bv = __ballot_sync(kFull, d < m && ssrc[d] != 0);
       if (lane == 0) {
-        S.syn[c] = bv;
-        S.sred[c] = bv;
-        S.xsol[c] = 0;
+        S.syn()[c] = bv;
+        S.sred()[c] = bv;
+        S.xsol()[c] = 0;
       }
     }
-    if (lane < 4) S.scal[lane] = 0;
+    if (lane < 8) S.scal()[lane] = 0;
     __syncwarp();
     int k = 0;
     if (a.single_cluster) {
-      for (int d = lane; d < m; d += 32) S.dlab[d] = 0;
-      for (int j = lane; j < n; j += 32)
-        if (a.g.var_ptr[j + 1] > a.g.var_ptr[j]) S.flab[j] = -1;
+      for (int d = lane; d < m; d += 32) S.dlab()[d] = 0;
+      if constexpr (L::kMasks) {
+        for (int r = lane; r < n; r += 32) {
+          const int j = S.fat()[r];
+          if (G.var_ptr[j + 1] > G.var_ptr[j]) atomicOr(&S.cand()[r >> 5], 1u << (r & 31));
+        }
+      }
       bool anys = false;
-      for (int c = 0; c < W; ++c) anys = anys || S.syn[c] != 0;
+#pragma unroll
+      for (int c = 0; c < W; ++c) anys = anys || S.syn()[c] != 0;
       k = anys ? 1 : 0;
-      if (lane == 0) S.inv[0] = 0;
+      if (lane == 0) S.inv()[0] = 0;
     } else {
       for (int b0 = 0; b0 < m; b0 += 32) {
         const int d = b0 + lane;
-        const bool f = d < m && bit_of(S.syn, d);
+        const bool f = d < m && bit_of(S.syn(), d);
         const unsigned bal = __ballot_sync(kFull, f);
         if (f) {
-          S.dlab[d] = d;
-          S.inv[k + __popc(bal & ((1u << lane) - 1u))] = d;
-          const int c1 = a.g.chk_ptr[d + 1];
-          for (int e = a.g.chk_ptr[d]; e < c1; ++e) S.flab[a.g.chk_var[e]] = -1;
+          S.dlab()[d] = d;
+          S.inv()[k + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
+          if constexpr (L::kMasks) {
+            uint32_t* c = S.cand() + (size_t)d * Wn;
+            const int c1 = G.chk_ptr[d + 1];
+            for (int e = G.chk_ptr[d]; e < c1; ++e) {
+              const unsigned rk = S.rank()[G.chk_var[e]];
+              c[rk >> 5] |= 1u << (rk & 31);
+            }
+          }
         }
         k += __popc(bal);
       }
@@ -472,7 +688,7 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
         status = LSD_SHOT_UNSOLVABLE;
         break;
       }
-      if (lsd_step(a, S, m, n, W, k, true, lane) == 1) {
+      if (lsd_step<L, MU>(G, S, m, n, k, true, lane) == 1) {
         status = LSD_SHOT_UNSOLVABLE;
         break;
       }
@@ -480,28 +696,30 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
       k = collect_roots(a, S, m, true, lane);
     }
     // ---- LSD-mu: mu more steps for every cluster, then local OSD-E ----
-    if (status == LSD_SHOT_OK_LSD && a.order > 0) {
-      for (int e = 0; e < a.order; ++e) {
-        k = collect_roots(a, S, m, false, lane);
-        if (lsd_step(a, S, m, n, W, k, false, lane) == 2) break;
+    if constexpr (MU) {
+      if (status == LSD_SHOT_OK_LSD) {
+        for (int e = 0; e < a.order; ++e) {
+          k = collect_roots(a, S, m, false, lane);
+          if (lsd_step<L, MU>(G, S, m, n, k, false, lane) == 2) break;
+        }
+        osd_e(a, S, m, lane);
       }
-      osd_e(a, S, m, W, lane);
     }
 
     // ---- statistics: nu clusters, kappa = largest cluster in columns ----
-    for (int d = lane; d < m; d += 32) S.best[d] = 0;
+    for (int d = lane; d < m; d += 32) S.best()[d] = 0;
     __syncwarp();
     for (int j = lane; j < n; j += 32) {
-      const int lab = S.flab[j];
-      if (lab >= 0) atomicAdd(&S.best[uf_find(S.parent, lab)], 1ULL);
+      const int lab = S.flab()[j];
+      if (lab >= 0) atomicAdd(&S.best()[S.parent()[lab]], 1u);
     }
     __syncwarp();
     int nu = 0, kappa = 0;
     for (int d = lane; d < m; d += 32) {
-      const bool seed = a.single_cluster ? d == 0 : bit_of(S.syn, d);
-      if (seed && S.parent[d] == d) {
+      const bool seed = a.single_cluster ? d == 0 : bit_of(S.syn(), d);
+      if (seed && S.parent()[d] == d) {
         ++nu;
-        kappa = max(kappa, (int)S.best[d]);
+        kappa = max(kappa, (int)S.best()[d]);
       }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -510,14 +728,16 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
     }
 
     // ---- global decoding: union of the local solutions (Eq. 2) ----
-    uint8_t* cs = reinterpret_cast<uint8_t*>(S.llr);  // LLRs are no longer needed
+    uint8_t* cs = S.cs();  // the masks are no longer needed
     for (int j = lane; j < n; j += 32) cs[j] = 0;
     __syncwarp();
     if (status == LSD_SHOT_OK_LSD) {
       for (int d = lane; d < m; d += 32)
-        if (bit_of(S.xsol, d)) cs[S.pcol[d]] = 1;
-      const int ne = S.scal[2];
-      for (int t = lane; t < ne; t += 32) cs[S.ext[t]] = 1;
+        if (bit_of(S.xsol(), d)) cs[S.pcol()[d]] = 1;
+      if constexpr (MU) {
+        const int ne = S.scal()[2];
+        for (int t = lane; t < ne; t += 32) cs[S.ext()[t]] = 1;
+      }
     }
     __syncwarp();
     uint8_t* co = a.corrections + shot * n;
@@ -544,6 +764,45 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int W) {
   }
 }
 
+inline bool graph_in_smem(const DevGraph& g) { return graph_bytes(g.m, g.n, g.E) <= kGraphBudget; }
+
+// Size classes (max detectors, max faults) the kernel is instantiated for.
+struct SizeClass {
+  int mm, nn;
+};
+constexpr SizeClass kClasses[] = {{40, 80}, {72, 144}, {96, 192}, {144, 288}, {256, 768}, {512, 2048}};
+constexpr int kNumClasses = sizeof(kClasses) / sizeof(kClasses[0]);
+
+int size_class(int m, int n) {
+  for (int c = 0; c < kNumClasses; ++c)
+    if (m <= kClasses[c].mm && n <= kClasses[c].nn) return c;
+  return -1;
+}
+
+#define LSD_CLASS_CASES(X)                                                       \
+  X(0, 40, 80) X(1, 72, 144) X(2, 96, 192) X(3, 144, 288) X(4, 256, 768) X(5, 512, 2048)
+
+size_t class_bytes(int c, bool mu) {
+  switch (c) {
+#define X(i, M, N) \
+  case i: return mu ? Lay<M, N, true>::total : Lay<M, N, false>::total;
+    LSD_CLASS_CASES(X)
+#undef X
+    default: return 0;
+  }
+}
+
+const void* class_kernel(int c, bool mu) {
+  switch (c) {
+#define X(i, M, N) \
+  case i: return mu ? (const void*)lsd_kernel<M, N, true> : (const void*)lsd_kernel<M, N, false>;
+    LSD_CLASS_CASES(X)
+#undef X
+    default: return nullptr;
+  }
+}
+#undef LSD_CLASS_CASES
+
 }  // namespace
 
 cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
@@ -553,20 +812,23 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
   if (err != cudaSuccess) return err;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int W = (g.m + 31) / 32;
-  if (W > kMaxLsdWords) return cudaErrorInvalidValue;
-  const size_t per = lsd_layout(g.m, g.n, W, order).total;
-  int w = warps > 0 ? warps : 8;
-  while (w > 1 && per * w > (size_t)max_smem) --w;
-  if (per * w > (size_t)max_smem) return cudaErrorInvalidValue;
-  *smem = per * w;
-  *words = W;
+  const int c = size_class(g.m, g.n);
+  if (c < 0) return cudaErrorInvalidValue;
+  const bool mu = order > 0;
+  const size_t per = class_bytes(c, mu);
+  const size_t gb = graph_in_smem(g) ? graph_bytes(g.m, g.n, g.E) : 0;
+  int w = warps > 0 ? warps : 4;
+  while (w > 1 && gb + per * w > (size_t)max_smem) --w;
+  if (gb + per * w > (size_t)max_smem) return cudaErrorInvalidValue;
+  *smem = gb + per * w;
+  *words = (g.m + 31) / 32;
   *warps_out = w;
+  const void* fn = class_kernel(c, mu);
   // the limit is a property of the function, shared by every decoder: allow the maximum
-  err = cudaFuncSetAttribute(lsd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsd_kernel, w * 32, *smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, w * 32, *smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidValue;
   *grid = per_sm * sms;
@@ -574,9 +836,12 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
 }
 
 cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  const int W = (a.g.m + 31) / 32;
-  lsd_kernel<<<grid, warps * 32, smem, st>>>(a, W);
-  return cudaGetLastError();
+  const int c = size_class(a.g.m, a.g.n);
+  if (c < 0) return cudaErrorInvalidValue;
+  const bool mu = a.order > 0;
+  const int gs = graph_in_smem(a.g) ? 1 : 0;
+  void* args[] = {const_cast<LSDArgs*>(&a), const_cast<int*>(&gs)};
+  return cudaLaunchKernel(class_kernel(c, mu), dim3(grid), dim3(warps * 32), args, smem, st);
 }
 
 }  // namespace lsdgb

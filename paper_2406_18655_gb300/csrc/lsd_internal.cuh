@@ -15,6 +15,7 @@ namespace lsdgb {
 struct DevGraph {
   int32_t m, n, E;
   int32_t max_row_deg, max_col_deg;
+  int32_t min_row_deg, min_col_deg;
   const int32_t* chk_ptr;   // [m+1]
   const uint16_t* chk_var;  // [E]  column of edge e
   const int32_t* var_ptr;   // [n+1]
@@ -77,10 +78,12 @@ struct LSDArgs {
 // Launch helpers (return a cudaError_t).
 cudaError_t launch_priors(const float* probs, float* prior, long long* wfix, int n,
                           cudaStream_t st);
-cudaError_t launch_bp(const BPArgs& a, int lanes, int grid, int block, size_t smem,
+// BP launch variants: `variant` in/out (-1 = choose); kind 0 auto, 1 generic, 2 register.
+cudaError_t launch_bp(const BPArgs& a, int variant, int grid, int block, size_t smem,
                       cudaStream_t st);
-cudaError_t bp_config(const DevGraph& g, int lanes, int method, int* grid, int* block,
-                      size_t* smem);
+cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
+                      int* grid, int* block, size_t* smem);
+int bp_num_variants();
 cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaStream_t st);
 cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
                        size_t* smem, int* words);

@@ -41,7 +41,8 @@ class Options(C.Structure):
     _fields_ = [("ms_scaling", C.c_float), ("bp_method", C.c_int32),
                 ("no_early_exit", C.c_int32), ("single_cluster", C.c_int32),
                 ("bp_lanes", C.c_int32), ("lsd_warps", C.c_int32),
-                ("reserved", C.c_int32 * 2), ("mem_budget", C.c_size_t),
+                ("bp_kernel", C.c_int32), ("reserved", C.c_int32 * 1),
+                ("mem_budget", C.c_size_t),
                 ("stream", C.c_void_p)]
 
 
@@ -123,7 +124,7 @@ class Decoder:
     def __init__(self, h, channel_probs, bp_iters: int, lsd_order: int = 0, *,
                  ms_scaling: float = 0.0, bp_method: int = 0, no_early_exit: bool = False,
                  single_cluster: bool = False, bp_lanes: int = 0, lsd_warps: int = 0,
-                 mem_budget: int = 0, stream=None):
+                 bp_kernel: int = 0, mem_budget: int = 0, stream=None):
         import torch
         h = np.asarray(h.cpu() if isinstance(h, torch.Tensor) else h, dtype=np.uint8)
         self.m, self.n = h.shape
@@ -142,6 +143,7 @@ class Decoder:
         opt.single_cluster = int(single_cluster)
         opt.bp_lanes = bp_lanes
         opt.lsd_warps = lsd_warps
+        opt.bp_kernel = bp_kernel
         opt.mem_budget = mem_budget
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt

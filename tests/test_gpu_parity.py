@@ -47,13 +47,16 @@ def test_priors_bit_exact(L):
     assert np.array_equal(got, exp)
 
 
+@pytest.mark.parametrize("kernel", [1, 0])
 @pytest.mark.parametrize("lanes", [8, 16, 32])
 @pytest.mark.parametrize("name,p,iters,shots", [
     ("bb72", 0.05, 30, 4000), ("bb144", 0.02, 50, 3000), ("bb144", 0.08, 50, 3000),
     ("bb288", 0.04, 50, 1500), ("st_bb72_d6", 0.01, 50, 1500), ("rep_boundary", 0.1, 20, 2000)])
-def test_bp_matches_oracle(L, lanes, name, p, iters, shots):
+def test_bp_matches_oracle(L, kernel, lanes, name, p, iters, shots):
+    """kernel 1: generic (graph in shared memory); 0: automatic choice, which is the
+    register-resident kernel for the regular BB codes whenever a shape with these lanes fits."""
     h, probs, e, s = sample(name, p, shots, seed=1000 + int(p * 1000) + lanes)
-    d = L.Decoder(h, probs, iters, bp_lanes=lanes)
+    d = L.Decoder(h, probs, iters, bp_lanes=lanes, bp_kernel=kernel)
     post, conv, it = d.bp(dev(s))
     torch.cuda.synchronize()
     llr, hard, used, convo = oracle.bp(h, f64(probs), s, iters, precision=1)
@@ -63,6 +66,17 @@ def test_bp_matches_oracle(L, lanes, name, p, iters, shots):
     rel = np.abs(g - llr) / np.maximum(1.0, np.abs(llr))
     assert rel.max() <= BP_TOL
     assert np.array_equal(g, llr)
+
+
+def test_register_kernel_available_for_bb_codes(L):
+    for name in ("bb72", "bb144", "bb288"):
+        h, probs, e, s = sample(name, 0.05, 300, seed=2)
+        d = L.Decoder(h, probs, 30, bp_kernel=2)
+        post, conv, it = d.bp(dev(s))
+        llr, hard, used, convo = oracle.bp(h, f64(probs), s, 30, precision=1)
+        assert np.array_equal(post.cpu().numpy().astype(np.float64), llr)
+    with pytest.raises(L.LsdError):  # irregular column degrees: no register shape
+        L.Decoder(code("st_bb72_d6"), np.full(648, 0.01, np.float32), 30, bp_kernel=2)
 
 
 def test_bp_no_early_exit_and_zero_iterations(L):
