@@ -77,7 +77,8 @@ struct Lay {
   static constexpr size_t dlab = flab + (size_t)NN * 4;
   static constexpr size_t parent = dlab + (size_t)MM * 4;
   static constexpr size_t best = parent + (size_t)MM * 4;
-  static constexpr size_t words = best + (size_t)MM * 4;
+  static constexpr size_t mark = best + (size_t)MM * 4;
+  static constexpr size_t words = mark + (size_t)MM * 4;
   static constexpr size_t scal = words + (size_t)4 * W * 4;
   static constexpr size_t npr = scal + 16 * 4;
   static constexpr size_t npN = npr + (MU ? (size_t)NN * 4 : 0);
@@ -119,6 +120,7 @@ struct Shot {
   __device__ __forceinline__ int* parent() const { return at<int>(L::parent); }
   __device__ __forceinline__ int16_t* pcol() const { return at<int16_t>(L::pcol); }
   __device__ __forceinline__ uint32_t* best() const { return at<uint32_t>(L::best); }
+  __device__ __forceinline__ unsigned* mark() const { return at<unsigned>(L::mark); }
   __device__ __forceinline__ uint16_t* inv() const { return at<uint16_t>(L::inv); }
   __device__ __forceinline__ uint16_t* mlist() const { return at<uint16_t>(L::mlist); }
   __device__ __forceinline__ uint16_t* dnew() const { return at<uint16_t>(L::dnew); }
@@ -207,33 +209,41 @@ __device__ void warp_sort(unsigned long long* keys, int lane) {
   }
 }
 
-// Roots of all clusters, or of the invalid ones (sred bits), into inv[].
+// Roots of all clusters, or of the invalid ones, into inv[].  A cluster is invalid iff the
+// reduced syndrome has a bit on one of its rows (labels are flattened, so dlab of a row is
+// its cluster's root); each such root is listed once, in no particular order (growth is
+// synchronous, so the order of the list does not matter).
 template <class L>
 __device__ int collect_roots(const LSDArgs& a, const Shot<L>& S, int m, bool only_invalid,
                              int lane) {
   if (only_invalid) {
-    // labels are flattened: dlab of a clustered detector is its root
+    if (lane == 0) S.scal()[5] = 0;
+    __syncwarp();
     if (lane < L::W) {
       uint32_t bits = S.sred()[lane];
       while (bits) {
         const int d = lane * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const int lab = S.dlab()[d];
-        if (lab >= 0) S.rflag()[lab] = 1;
+        const int root = S.dlab()[d];
+        if (root >= 0 && atomicCAS(&S.mark()[root], 0u, 1u) == 0u) {
+          const int slot = atomicAdd(&S.scal()[5], 1);
+          S.inv()[slot] = (uint16_t)root;
+        }
       }
     }
     __syncwarp();
+    const int count = S.scal()[5];
+    for (int t = lane; t < count; t += 32) S.mark()[S.inv()[t]] = 0u;
+    __syncwarp();
+    return count;
   }
   int count = 0;
   for (int base = 0; base < m; base += 32) {
     const int d = base + lane;
     const bool seed = d < m && (a.single_cluster ? d == 0 : bit_of(S.syn(), d));
-    const bool pred = seed && S.parent()[d] == d && (!only_invalid || S.rflag()[d]);
+    const bool pred = seed && S.parent()[d] == d;
     const unsigned bal = __ballot_sync(kFull, pred);
-    if (pred) {
-      S.inv()[count + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
-      if (only_invalid) S.rflag()[d] = 0;
-    }
+    if (pred) S.inv()[count + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
     count += __popc(bal);
   }
   __syncwarp();
@@ -386,18 +396,21 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     }
   }
   __syncwarp();
-  // ---- flatten labels to roots (later finds take one step) ----
-  for (int x = lane; x < m; x += 32) {
-    const int root = uf_find(S.parent(), x);
-    S.parent()[x] = root;
-    const int l = S.dlab()[x];
-    if (l >= 0) S.dlab()[x] = uf_find(S.parent(), l);
+  // ---- flatten labels to roots (later finds take one step); only after a merge ----
+  const int merged = S.scal()[3];
+  if (merged) {
+    for (int x = lane; x < m; x += 32) {
+      const int root = uf_find(S.parent(), x);
+      S.parent()[x] = root;
+      const int l = S.dlab()[x];
+      if (l >= 0) S.dlab()[x] = uf_find(S.parent(), l);
+    }
+    __syncwarp();
   }
-  __syncwarp();
   if constexpr (L::kMasks) {
     // fold the masks of merged labels into their roots; add the free faults next to the
     // newly claimed detectors
-    const int nm = S.scal()[3], nd = S.scal()[4];
+    const int nm = merged, nd = S.scal()[4];
     for (int idx = lane; idx < nm * Wn; idx += 32) {
       const int x = S.mlist()[idx / Wn], w = idx % Wn;
       const uint32_t v = S.cand()[(size_t)x * Wn + w];
@@ -632,6 +645,7 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int graph_smem) {
       S.parent()[d] = d;
       S.pcol()[d] = -1;
       S.rflag()[d] = 0;
+      S.mark()[d] = 0u;
     }
 #pragma unroll
     for (int c = 0; c < W; ++c) {
