@@ -199,6 +199,83 @@ int lsd_get_stats(lsd_decoder* dec, lsd_stats* stats);
 int lsd_decode_batch_static(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
                             uint8_t* corrections, uint8_t* status);
 
+/* ------------------------------------------------------------------------------------
+ * Learned prior (no counterpart in the paper: an extension that replaces most BP iterations
+ * by a small trained network whose per-fault LLRs feed LSD).
+ *
+ * Model, hidden width LSD_PRIOR_HIDDEN = 32, R rounds, for the decoder's H:
+ *   sigma_c = 1 - 2 s_c,  h_v = relu(lambda_v a0 + a1),  h_c = sigma_c u0 + u1
+ *   each round:  h_v += sum_{c in N(v)} MLP_cv([h_c, h_v, sigma_c])
+ *                h_c += sum_{v in N(c)} MLP_vc([h_v, h_c, sigma_c])
+ *   LLR_v = lambda_v + w_o . h_v + b_o,   MLP(x) = W2 relu(W1 x + b1) + b2,
+ *   W1: 32 x 65, W2: 32 x 32 (row-major), the two MLPs shared by all rounds.
+ * Loss: mean over shots and faults of softplus(LLR_v) - (1 - e_v) LLR_v (binary
+ * cross-entropy of P(e_v = 1) = sigmoid(-LLR_v)).
+ * Parameters: FP32 master copy, flat in the order a0, a1, u0, u1, W1_cv, b1_cv, W2_cv,
+ * b2_cv, W1_vc, b1_vc, W2_vc, b2_vc, w_o, b_o (lsd_prior_num_params() floats).  The
+ * matrix products run on the tensor cores with BF16 weights and activations and FP32
+ * accumulation; node states and the loss are FP32.  Limits: m <= 96, n <= 192 checks and
+ * faults (the states of one shot live in one CTA's shared memory).
+ * ------------------------------------------------------------------------------------ */
+#define LSD_PRIOR_HIDDEN 32
+typedef struct lsd_prior lsd_prior;
+
+/* Number of FP32 parameters of the model (6497). */
+int lsd_prior_num_params(void);
+
+/*
+ * lsd_prior_create -- a prior for decoder `dec` (which must outlive it) with `rounds`
+ * message-passing rounds (1..8).  params: host, lsd_prior_num_params() floats, or NULL for
+ * all zeros.  Uses the decoder's stream; synchronizes.
+ */
+int lsd_prior_create(lsd_prior** out, lsd_decoder* dec, int32_t rounds, const float* params);
+
+/* Copy the FP32 parameters from / to host memory (synchronizes).  Setting resets Adam. */
+int lsd_prior_set_params(lsd_prior* prior, const float* params);
+int lsd_prior_get_params(lsd_prior* prior, float* params);
+
+/* lsd_prior_forward -- LLRs of every shot: syndromes device [shots][m] bytes, llrs device
+ * [shots][n] float32.  Asynchronous. */
+int lsd_prior_forward(lsd_prior* prior, int64_t shots, const uint8_t* syndromes, float* llrs);
+
+/*
+ * lsd_prior_gradient -- loss and gradient over a batch without updating the parameters.
+ *   syndromes, errors: device [shots][m] / [shots][n] bytes (errors are the targets).
+ *   loss: host, the batch's mean loss.  grads: host, lsd_prior_num_params() floats, nullable.
+ * Synchronizes.
+ */
+int lsd_prior_gradient(lsd_prior* prior, int64_t shots, const uint8_t* syndromes,
+                       const uint8_t* errors, double* loss, float* grads);
+
+/* lsd_prior_train_step -- gradient of the batch, then one Adam step (beta 0.9, 0.999,
+ * eps 1e-8) with learning rate lr.  loss: host, nullable (if given, synchronizes). */
+int lsd_prior_train_step(lsd_prior* prior, int64_t shots, const uint8_t* syndromes,
+                         const uint8_t* errors, float lr, double* loss);
+
+/*
+ * lsd_decode_learned -- decode with the prior in place of BP: LLRs from the prior; if their
+ * hard decision satisfies s the shot is done (status 1), otherwise LSD runs on them
+ * (status 2).  Shots LSD cannot solve (status 3) are decoded again by the decoder's own
+ * BP + LSD, the fallback.  Arguments as lsd_decode_batch, except that `status` is required
+ * (the fallback reads it).  Synchronizes (the fallback needs the count of unsolved shots);
+ * stats->bp_converged counts the shots the prior's hard decision solved.
+ */
+int lsd_decode_learned(lsd_decoder* dec, lsd_prior* prior, int64_t shots,
+                       const uint8_t* syndromes, uint8_t* corrections, uint8_t* status,
+                       lsd_stats* stats);
+
+int lsd_prior_destroy(lsd_prior* prior);
+
+/*
+ * lsd_sample -- seeded i.i.d. training pairs on the device: fault j of shot k is 1 with the
+ * decoder's channel probability p_j, drawn from the xoshiro256** stream of shot first+k
+ * (state from splitmix64 applied to seed ^ (first+k+1) * 0xD1B54A32D192ED03, Blackman and
+ * Vigna), u = (x >> 11) 2^-53 < p_j in double, columns in ascending order; syndromes = H e.
+ *   errors device [shots][n] bytes, syndromes device [shots][m] bytes.  Asynchronous.
+ */
+int lsd_sample(lsd_decoder* dec, uint64_t seed, int64_t first_shot, int64_t shots,
+               uint8_t* errors, uint8_t* syndromes);
+
 /* lsd_get_priors -- copy the n float32 priors lambda_j to host memory; synchronizes. */
 int lsd_get_priors(lsd_decoder* dec, float* priors);
 

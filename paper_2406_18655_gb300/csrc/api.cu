@@ -40,6 +40,21 @@ struct lsd_decoder {
   long long launches = 0;
   int64_t last_shots = 0;
   int last_kind = 0;  // 0 none, 1 decode, 2 bp only, 3 lsd only
+  float* d_probs = nullptr;  // channel probabilities (sampler)
+};
+
+struct lsd_prior {
+  lsd_decoder* dec = nullptr;
+  int rounds = 4;
+  int np = 0;
+  float *d_params = nullptr, *d_grads = nullptr, *d_m = nullptr, *d_v = nullptr;
+  double* d_loss = nullptr;
+  double* h_loss = nullptr;  // pinned
+  float* d_scratch = nullptr;
+  float* d_llr = nullptr;
+  size_t llr_cap = 0;
+  int grid_train = 0, grid_fwd = 0;
+  int step = 0;
 };
 
 namespace {
@@ -282,6 +297,7 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   g.var_chk = d_var_chk;
   g.prior = d_prior;
   g.wfix = d_wfix;
+  d->d_probs = d_probs;
   cudaError_t ce = launch_priors(d_probs, d_prior, d_wfix, n, d->st);
   d->launches++;
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(d->st);
@@ -555,3 +571,253 @@ extern "C" int lsd_decode_batch_static(lsd_decoder* d, int64_t shots, const uint
   d->launches++;
   return e == cudaSuccess ? LSD_OK : cuda_fail(e);
 }
+
+// ---------------------------------------------------------------------------------------
+// Learned prior
+// ---------------------------------------------------------------------------------------
+namespace {
+
+void prior_free(lsd_prior* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->dec ? p->dec->st : nullptr);
+  for (void* q : {(void*)p->d_params, (void*)p->d_grads, (void*)p->d_m, (void*)p->d_v,
+                  (void*)p->d_loss, (void*)p->d_scratch, (void*)p->d_llr})
+    if (q) cudaFree(q);
+  if (p->h_loss) cudaFreeHost(p->h_loss);
+  cudaGetLastError();
+  delete p;
+}
+
+int prior_alloc(void** q, size_t bytes) {
+  cudaError_t e = cudaMalloc(q, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  return LSD_OK;
+}
+
+int prior_grads(lsd_prior* p, int64_t shots, const uint8_t* syn, const uint8_t* err) {
+  lsd_decoder* d = p->dec;
+  cudaError_t e = cudaMemsetAsync(p->d_grads, 0, sizeof(float) * p->np, d->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_loss, 0, sizeof(double), d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_prior(true, p->grid_train, d->g, p->rounds, p->d_params, shots, syn, err, nullptr,
+                   p->d_scratch, p->d_grads, p->d_loss, d->st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsd_prior_num_params(void) { return prior_num_params(); }
+
+int lsd_prior_destroy(lsd_prior* p) {
+  prior_free(p);
+  return LSD_OK;
+}
+
+int lsd_prior_create(lsd_prior** out, lsd_decoder* d, int32_t rounds, const float* params) {
+  if (!out || !d || rounds < 1 || rounds > kPriorMaxRounds) return LSD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->m > 96 || d->n > 192) return LSD_ERR_UNSUPPORTED;
+  lsd_prior* p = new (std::nothrow) lsd_prior();
+  if (!p) return LSD_ERR_OOM;
+  p->dec = d;
+  p->rounds = rounds;
+  p->np = prior_num_params();
+  cudaError_t ce = prior_config(d->m, d->n, d->E, true, &p->grid_train);
+  if (ce == cudaSuccess) ce = prior_config(d->m, d->n, d->E, false, &p->grid_fwd);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    prior_free(p);
+    return LSD_ERR_UNSUPPORTED;
+  }
+  int rc;
+  const size_t nb = sizeof(float) * p->np;
+  if ((rc = prior_alloc((void**)&p->d_params, nb)) || (rc = prior_alloc((void**)&p->d_grads, nb)) ||
+      (rc = prior_alloc((void**)&p->d_m, nb)) || (rc = prior_alloc((void**)&p->d_v, nb)) ||
+      (rc = prior_alloc((void**)&p->d_loss, sizeof(double))) ||
+      (rc = prior_alloc((void**)&p->d_scratch,
+                        sizeof(float) * prior_scratch_floats(d->m, d->n, rounds, p->grid_train)))) {
+    prior_free(p);
+    return rc;
+  }
+  if (cudaMallocHost((void**)&p->h_loss, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    prior_free(p);
+    return LSD_ERR_OOM;
+  }
+  *out = p;
+  if (params) return lsd_prior_set_params(p, params);
+  cudaMemsetAsync(p->d_params, 0, nb, d->st);
+  cudaMemsetAsync(p->d_m, 0, nb, d->st);
+  cudaMemsetAsync(p->d_v, 0, nb, d->st);
+  ce = cudaStreamSynchronize(d->st);
+  return ce == cudaSuccess ? LSD_OK : cuda_fail(ce);
+}
+
+int lsd_prior_set_params(lsd_prior* p, const float* params) {
+  if (!p || !params) return LSD_ERR_INVALID_ARG;
+  lsd_decoder* d = p->dec;
+  const size_t nb = sizeof(float) * p->np;
+  cudaError_t e = cudaMemcpyAsync(p->d_params, params, nb, cudaMemcpyHostToDevice, d->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_m, 0, nb, d->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_v, 0, nb, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  p->step = 0;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_prior_get_params(lsd_prior* p, float* params) {
+  if (!p || !params) return LSD_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(params, p->d_params, sizeof(float) * p->np,
+                                  cudaMemcpyDeviceToHost, p->dec->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->dec->st);
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_prior_forward(lsd_prior* p, int64_t shots, const uint8_t* syndromes, float* llrs) {
+  if (!p || shots < 0) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return LSD_OK;
+  if (!syndromes || !llrs) return LSD_ERR_INVALID_ARG;
+  lsd_decoder* d = p->dec;
+  cudaError_t e = launch_prior(false, p->grid_fwd, d->g, p->rounds, p->d_params, shots,
+                               syndromes, nullptr, llrs, nullptr, nullptr, nullptr, d->st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_prior_gradient(lsd_prior* p, int64_t shots, const uint8_t* syndromes,
+                       const uint8_t* errors, double* loss, float* grads) {
+  if (!p || shots <= 0 || !syndromes || !errors || !loss) return LSD_ERR_INVALID_ARG;
+  int rc = prior_grads(p, shots, syndromes, errors);
+  if (rc) return rc;
+  lsd_decoder* d = p->dec;
+  cudaError_t e = cudaMemcpyAsync(p->h_loss, p->d_loss, sizeof(double), cudaMemcpyDeviceToHost,
+                                  d->st);
+  if (e == cudaSuccess && grads)
+    e = cudaMemcpyAsync(grads, p->d_grads, sizeof(float) * p->np, cudaMemcpyDeviceToHost, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *loss = *p->h_loss / ((double)shots * d->n);
+  return LSD_OK;
+}
+
+int lsd_prior_train_step(lsd_prior* p, int64_t shots, const uint8_t* syndromes,
+                         const uint8_t* errors, float lr, double* loss) {
+  if (!p || shots <= 0 || !syndromes || !errors || !(lr > 0.f)) return LSD_ERR_INVALID_ARG;
+  int rc = prior_grads(p, shots, syndromes, errors);
+  if (rc) return rc;
+  lsd_decoder* d = p->dec;
+  p->step++;
+  cudaError_t e = launch_adam(p->d_params, p->d_grads, p->d_m, p->d_v, p->np, lr, p->step, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (loss) {
+    e = cudaMemcpyAsync(p->h_loss, p->d_loss, sizeof(double), cudaMemcpyDeviceToHost, d->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *loss = *p->h_loss / ((double)shots * d->n);
+  }
+  return LSD_OK;
+}
+
+int lsd_sample(lsd_decoder* d, uint64_t seed, int64_t first_shot, int64_t shots,
+               uint8_t* errors, uint8_t* syndromes) {
+  if (!d || shots < 0 || first_shot < 0) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) return LSD_OK;
+  if (!errors || !syndromes) return LSD_ERR_INVALID_ARG;
+  cudaError_t e = launch_sample(d->g, d->d_probs, seed, first_shot, shots, errors, syndromes, d->st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_t* syndromes,
+                       uint8_t* corrections, uint8_t* status, lsd_stats* stats) {
+  if (!d || !p || p->dec != d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  if (shots == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return LSD_OK;
+  }
+  if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  int rc = ensure_workspace(d, shots);
+  if (rc) return rc;
+  if ((size_t)shots > p->llr_cap) {
+    cudaError_t e = cudaStreamSynchronize(d->st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (p->d_llr) cudaFree(p->d_llr);
+    p->d_llr = nullptr;
+    p->llr_cap = 0;
+    if ((rc = prior_alloc((void**)&p->d_llr, sizeof(float) * (size_t)shots * d->n))) return rc;
+    p->llr_cap = (size_t)shots;
+  }
+  // the fallback needs the status of every shot
+  uint8_t* st = status;
+  if (!st) return LSD_ERR_INVALID_ARG;
+  if ((rc = reset_counters(d))) return rc;
+  cudaEventRecord(d->ev[0], d->st);
+  cudaError_t e = launch_prior(false, p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
+                               nullptr, p->d_llr, nullptr, nullptr, nullptr, d->st);
+  d->launches++;
+  if (e == cudaSuccess)
+    e = launch_hard_check(d->g, shots, p->d_llr, syndromes, corrections, st, d->d_queue,
+                          d->d_queue_llr, d->d_ctr, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[1], d->st);
+  LSDArgs l{};
+  l.g = d->g;
+  l.count_from_ctr = 1;
+  l.queue = d->d_queue;
+  l.llr = d->d_queue_llr;
+  l.llr_by_item = 1;
+  l.syndromes = syndromes;
+  l.corrections = corrections;
+  l.status = st;
+  l.order = d->order;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = d->d_ctr;
+  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEventRecord(d->ev[2], d->st);
+  d->last_shots = shots;
+  d->last_kind = 1;
+  // fallback: BP + LSD for the shots LSD could not solve
+  e = cudaMemcpyAsync(d->h_ctr, d->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const DevCounters learned = *d->h_ctr;
+  if (learned.unsolvable > 0) {
+    std::vector<uint8_t> hs((size_t)shots);
+    e = cudaMemcpy(hs.data(), st, (size_t)shots, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int64_t k = 0; k < shots; ++k) {
+      if (hs[(size_t)k] != LSD_SHOT_UNSOLVABLE) continue;
+      rc = lsd_decode_batch(d, 1, syndromes + k * d->m, corrections + k * d->n, st + k, nullptr,
+                            nullptr);
+      if (rc) return rc;
+    }
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->shots = shots;
+    stats->bp_converged = (int64_t)learned.bp_converged;
+    stats->lsd_shots = (int64_t)learned.lsd_count;
+    stats->unsolvable = (int64_t)learned.unsolvable;
+    stats->lsd_steps = (int64_t)learned.lsd_steps;
+    stats->kappa_max = learned.kappa_max;
+    stats->nu_max = learned.nu_max;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]) == cudaSuccess) stats->ms_bp = ms;
+    if (cudaEventElapsedTime(&ms, d->ev[1], d->ev[2]) == cudaSuccess) stats->ms_lsd = ms;
+    cudaGetLastError();
+  }
+  return LSD_OK;
+}
+
+}  // extern "C"

@@ -88,6 +88,25 @@ cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaS
 cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
                        size_t* smem, int* words);
 
+// Learned prior (prior.cu).
+int prior_num_params();
+size_t prior_smem(int m, int n, int E, bool train);
+size_t prior_scratch_floats(int m, int n, int rounds, int grid);
+cudaError_t prior_config(int m, int n, int E, bool train, int* grid);
+cudaError_t launch_prior(bool train, int grid, const DevGraph& g, int rounds, const float* params,
+                         long long shots, const uint8_t* syndromes, const uint8_t* errors,
+                         float* llr_out, float* scratch, float* grads, double* loss,
+                         cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int count, float lr,
+                        int step, cudaStream_t st);
+cudaError_t launch_sample(const DevGraph& g, const float* probs, unsigned long long seed,
+                          long long first, long long shots, uint8_t* errors, uint8_t* syndromes,
+                          cudaStream_t st);
+cudaError_t launch_hard_check(const DevGraph& g, long long shots, const float* llr,
+                              const uint8_t* syn, uint8_t* corr, uint8_t* status, int32_t* queue,
+                              float* queue_llr, DevCounters* ctr, cudaStream_t st);
+constexpr int kPriorMaxRounds = 8;
+
 // Limits of this build's kernels.
 constexpr int kMaxLsdWords = 16;    // LSD: m <= 32 * kMaxLsdWords detectors per shot
 constexpr int kMaxRowDeg = 32;      // BP: check degree (sign bits in one word)

@@ -28,7 +28,10 @@ SHOT_UNSOLVABLE = 3
 EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_batch",
            "lsd_postprocess_batch", "lsd_get_stats", "lsd_get_priors", "lsd_workspace_bytes",
            "lsd_kernel_launches", "lsd_destroy", "lsd_status_string",
-           "lsd_decode_batch_static")
+           "lsd_decode_batch_static", "lsd_prior_num_params", "lsd_prior_create",
+           "lsd_prior_set_params", "lsd_prior_get_params", "lsd_prior_forward",
+           "lsd_prior_gradient", "lsd_prior_train_step", "lsd_decode_learned",
+           "lsd_prior_destroy", "lsd_sample")
 
 
 class LsdError(RuntimeError):
@@ -80,6 +83,16 @@ def lib():
     L.lsd_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_destroy.argtypes = [P]
     L.lsd_decode_batch_static.argtypes = [P, C.c_int64, P, P, P]
+    L.lsd_prior_num_params.argtypes = []
+    L.lsd_prior_create.argtypes = [C.POINTER(P), P, C.c_int32, P]
+    L.lsd_prior_set_params.argtypes = [P, P]
+    L.lsd_prior_get_params.argtypes = [P, P]
+    L.lsd_prior_forward.argtypes = [P, C.c_int64, P, P]
+    L.lsd_prior_gradient.argtypes = [P, C.c_int64, P, P, C.POINTER(C.c_double), P]
+    L.lsd_prior_train_step.argtypes = [P, C.c_int64, P, P, C.c_float, C.POINTER(C.c_double)]
+    L.lsd_decode_learned.argtypes = [P, P, C.c_int64, P, P, P, C.POINTER(Stats)]
+    L.lsd_prior_destroy.argtypes = [P]
+    L.lsd_sample.argtypes = [P, C.c_uint64, C.c_int64, C.c_int64, P, P]
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -255,6 +268,29 @@ class Decoder:
         _check(lib().lsd_get_stats(self._h, C.byref(st)), "lsd_get_stats")
         return st.as_dict()
 
+    def sample(self, seed: int, shots: int, first_shot: int = 0):
+        """Seeded i.i.d. pairs on the device: (errors [shots][n], syndromes [shots][m]) uint8."""
+        import torch
+        e = torch.empty((shots, self.n), dtype=torch.uint8, device="cuda")
+        s = torch.empty((shots, self.m), dtype=torch.uint8, device="cuda")
+        _check(lib().lsd_sample(self._h, seed & 0xFFFFFFFFFFFFFFFF, first_shot, shots, _ptr(e),
+                                _ptr(s)), "lsd_sample")
+        return e, s
+
+    def decode_learned(self, prior, syndromes, want_stats: bool = False):
+        """Learned prior + LSD (BP + LSD as the fallback).  Returns (corrections, status[, stats])."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.m), "syndromes")
+        corr = torch.empty((shots, self.n), dtype=torch.uint8, device=syndromes.device)
+        status = torch.empty(shots, dtype=torch.uint8, device=syndromes.device)
+        st = Stats()
+        _check(lib().lsd_decode_learned(self._h, prior._h, shots, _ptr(syndromes), _ptr(corr),
+                                        _ptr(status), C.byref(st)), "lsd_decode_learned")
+        if want_stats:
+            return corr, status, st.as_dict()
+        return corr, status
+
     def priors(self):
         out = np.empty(self.n, np.float32)
         _check(lib().lsd_get_priors(self._h, out.ctypes.data_as(C.c_void_p)), "lsd_get_priors")
@@ -269,3 +305,72 @@ class Decoder:
         v = C.c_int64()
         _check(lib().lsd_kernel_launches(self._h, C.byref(v)), "lsd_kernel_launches")
         return v.value
+
+
+class Prior:
+    """Learned edge-MLP prior of a decoder (lsd_prior_create)."""
+
+    def __init__(self, decoder: Decoder, rounds: int = 4, params=None):
+        self.decoder = decoder
+        self.np = int(lib().lsd_prior_num_params())
+        handle = C.c_void_p()
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(params, dtype=np.float32)
+            assert buf.size == self.np
+        _check(lib().lsd_prior_create(C.byref(handle), decoder._h, rounds,
+                                      None if buf is None else buf.ctypes.data_as(C.c_void_p)),
+               "lsd_prior_create")
+        self._h = handle
+        self.rounds = rounds
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lsd_prior_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.np, np.float32)
+        _check(lib().lsd_prior_get_params(self._h, out.ctypes.data_as(C.c_void_p)),
+               "lsd_prior_get_params")
+        return out
+
+    def set_params(self, params):
+        buf = np.ascontiguousarray(params, dtype=np.float32)
+        assert buf.size == self.np
+        _check(lib().lsd_prior_set_params(self._h, buf.ctypes.data_as(C.c_void_p)),
+               "lsd_prior_set_params")
+
+    def forward(self, syndromes):
+        import torch
+        d = self.decoder
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, d.m), "syndromes")
+        llr = torch.empty((shots, d.n), dtype=torch.float32, device=syndromes.device)
+        _check(lib().lsd_prior_forward(self._h, shots, _ptr(syndromes), _ptr(llr)),
+               "lsd_prior_forward")
+        return llr
+
+    def gradient(self, syndromes, errors):
+        """(mean loss, gradient as a numpy float32 vector) of a batch; no update."""
+        shots = syndromes.shape[0]
+        loss = C.c_double()
+        g = np.empty(self.np, np.float32)
+        _check(lib().lsd_prior_gradient(self._h, shots, _ptr(syndromes), _ptr(errors),
+                                        C.byref(loss), g.ctypes.data_as(C.c_void_p)),
+               "lsd_prior_gradient")
+        return loss.value, g
+
+    def train_step(self, syndromes, errors, lr: float, want_loss: bool = False):
+        shots = syndromes.shape[0]
+        loss = C.c_double()
+        _check(lib().lsd_prior_train_step(self._h, shots, _ptr(syndromes), _ptr(errors), lr,
+                                          C.byref(loss) if want_loss else None),
+               "lsd_prior_train_step")
+        return loss.value if want_loss else None
