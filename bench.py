@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--train-pairs", type=int, default=10_000_000)
+    ap.add_argument("--learned-rounds", type=int, default=4)
+    ap.add_argument("--sweep-iters", default="5,10,20,30,50",
+                    help="BP iteration counts of the equal-LER sweep")
     return ap.parse_args()
 
 
@@ -192,6 +198,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(fn, steps, stream, flush, barrier):
+    """Device time (ms) of each call of fn, with an L2 flush before each."""
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    out = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        barrier()
+        start.record(stream)
+        fn()
+        end.record(stream)
+        end.synchronize()
+        out.append(start.elapsed_time(end))
+    return out
+
+
+def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, checker):
+    """Train the learned prior on device-sampled pairs, time learned+LSD on the step's shots,
+    and sweep BP iterations for the BP+LSD operating points at equal logical error rate."""
+    import torch
+    from paper_2406_18655_gb300.learned import init_params, train
+    from paper_2406_18655_gb300.lsd import Decoder, Prior
+
+    dec = Decoder(hx, probs, args.iters, args.order, stream=stream)
+    prior = Prior(dec, rounds=args.learned_rounds, params=init_params(args.seed))
+    tr = train(dec, prior, args.train_pairs, batch=4096, seed=args.seed + 17, lr=3e-3,
+               log_every=500)
+    for _ in range(max(args.warmup, 1)):
+        c, st = dec.decode_learned(prior, s_dev)
+    holder = {}
+
+    def run():
+        holder["c"], holder["st"], holder["stats"] = dec.decode_learned(prior, s_dev,
+                                                                        want_stats=True)
+
+    ms = timed_steps(run, args.steps, stream, flush, barrier)
+    n_shots = s_dev.shape[0]
+    ler = float(checker.failures(e_dev, holder["c"]).float().mean().item())
+    sigma = float(np.sqrt(max(ler * (1 - ler), 1.0 / n_shots) / n_shots))
+    learned = {"rounds": args.learned_rounds, "hidden": 32, "weights": "bf16 (fp32 master)",
+               "train_pairs": tr["pairs"], "train_s": tr["seconds"],
+               "train_pairs_per_s": tr["pairs_per_s"],
+               "final_loss": tr["losses"][-1][1] if tr["losses"] else None,
+               "value": n_shots / (float(np.mean(ms)) / 1000.0), "unit": UNIT,
+               "ms_per_step": float(np.mean(ms)),
+               "latency_ms": {"p50": float(np.percentile(ms, 50)),
+                              "p99": float(np.percentile(ms, 99))},
+               "ler": ler, "ler_sigma": sigma,
+               "prior_hard_decision_frac": holder["stats"]["bp_converged"] / n_shots,
+               "lsd_frac": holder["stats"]["lsd_shots"] / n_shots,
+               "kernel_ms": {"prior_and_check": holder["stats"]["ms_bp"],
+                             "lsd_kernel": holder["stats"]["ms_lsd"]}}
+    # equal-LER protocol: BP+LSD at several iteration counts
+    sweep = []
+    for it in [int(x) for x in args.sweep_iters.split(",") if x]:
+        d_it = Decoder(hx, probs, it, args.order, stream=stream)
+        corr = torch.empty_like(holder["c"])
+        stt = torch.empty_like(holder["st"])
+        for _ in range(2):
+            d_it.decode(s_dev, corr, stt)
+        ms_it = timed_steps(lambda: d_it.decode(s_dev, corr, stt), max(2, args.steps // 2),
+                            stream, flush, barrier)
+        ler_it = float(checker.failures(e_dev, corr).float().mean().item())
+        sig_it = float(np.sqrt(max(ler_it * (1 - ler_it), 1.0 / n_shots) / n_shots))
+        sweep.append({"bp_iters": it, "ler": ler_it, "ler_sigma": sig_it,
+                      "value": n_shots / (float(np.mean(ms_it)) / 1000.0),
+                      "p99_ms": float(np.percentile(ms_it, 99)),
+                      "equal_ler": bool(abs(ler_it - ler) <= 2 * np.hypot(sigma, sig_it))})
+        d_it.close()
+    learned["bp_sweep"] = sweep
+    matched = [x for x in sweep if x["equal_ler"]]
+    learned["equal_ler_pairs"] = [
+        {"bp_iters": x["bp_iters"], "bp_lsd_shots_per_s": x["value"],
+         "learned_lsd_shots_per_s": learned["value"], "bp_lsd_p99_ms": x["p99_ms"],
+         "learned_lsd_p99_ms": learned["latency_ms"]["p99"], "ler_bp": x["ler"],
+         "ler_learned": ler} for x in matched]
+    prior.close()
+    dec.close()
+    return learned
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -226,6 +314,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    tune = None
+    if not args.no_autotune:  # the project's autotuner picks the launch variants (not timed)
+        tune = dec.autotune(s_dev[: min(args.shots, 200_000)])
     for _ in range(max(args.warmup, 0)):
         dec.decode(s_dev, corr, status)
     barrier()
@@ -261,8 +352,13 @@ def run_ours(args):
 
     # logical error rate of the last step's corrections (evaluation, outside the timing)
     checker = LogicalChecker(hz)
-    fails = checker.failures(torch.from_numpy(e).cuda(), corr)
+    e_dev = torch.from_numpy(e).cuda()
+    fails = checker.failures(e_dev, corr)
     ler = float(fails.float().mean().item())
+    learned = None
+    if not args.no_learned:
+        learned = learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier,
+                              checker)
 
     # end to end through the host-buffer C-ABI call (H2D + decode + D2H each step)
     e2e = None
@@ -328,8 +424,9 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
+        "autotune": tune,
         "clocks": clk.summary(),
-        "learned": None,
+        "learned": learned,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, hx, probs.astype(np.float64), s,

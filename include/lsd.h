@@ -70,7 +70,10 @@ typedef struct lsd_options {
   int32_t lsd_warps;      /* warps per CTA of the LSD kernel: 0 = auto, else 1..16 */
   int32_t bp_kernel;      /* BP kernel: 0 = auto, 1 = generic (graph in shared memory),
                              2 = register-resident graph tables (min-sum, small codes) */
-  int32_t reserved[1];    /* must be zero */
+  int32_t lsd_kernel;     /* LSD kernel: 0 = auto, 1 = dense (state indexed by detector and
+                             fault, m <= 512, n <= 2048), 2 = sparse (state sized by what a shot
+                             touches; any m, n < 65536; no single_cluster) */
+  int32_t reserved[3];    /* must be zero */
   size_t mem_budget;      /* device bytes the decoder may hold (H, priors, workspace); 0 = no limit */
   void* stream;           /* cudaStream_t used for all work; NULL = the legacy default stream */
 } lsd_options;
@@ -86,7 +89,8 @@ typedef struct lsd_stats {
   int32_t kappa_max;     /* largest final cluster (columns) of any shot (App. A's kappa) */
   int32_t nu_max;        /* most final clusters in one shot (App. A's nu) */
   float ms_bp;           /* device time of the BP kernel, CUDA events on the decoder stream */
-  float ms_lsd;          /* device time of the LSD kernel */
+  float ms_lsd;          /* device time of the LSD kernel(s) */
+  int64_t lsd_spilled;   /* sparse LSD: shots handed to its large-capacity instance */
 } lsd_stats;
 
 /*
@@ -275,6 +279,90 @@ int lsd_prior_destroy(lsd_prior* prior);
  */
 int lsd_sample(lsd_decoder* dec, uint64_t seed, int64_t first_shot, int64_t shots,
                uint8_t* errors, uint8_t* syndromes);
+
+/* ------------------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): continuous batching of single-shot requests over
+ * several codes.  A scheduler thread keeps `slots_per_code` batches of each code in flight
+ * (each slot a decoder with its own stream); a batch launches as soon as a slot is idle and
+ * either max_batch requests wait or the oldest has waited max_wait_us, and only as many
+ * shots as the memory budget still admits.  Request buffers are read and written by the
+ * GPU directly: they must be page-locked host memory (cudaHostAlloc / cudaHostRegister) or
+ * device memory, owned by the caller and valid until the request completes.
+ * ------------------------------------------------------------------------------------ */
+typedef struct lsd_server lsd_server;
+
+typedef struct lsd_server_code {    /* one code served: the arguments of lsd_create */
+  int32_t m, n;
+  int64_t nnz;
+  const int32_t* rows;
+  const int32_t* cols;
+  const float* channel_probs;
+  int32_t bp_iters, lsd_order;
+} lsd_server_code;
+
+typedef struct lsd_server_options { /* zero = defaults */
+  int32_t slots_per_code;   /* batches of one code in flight (default 3, at most 16) */
+  int32_t max_batch;        /* shots per batch (default 8192) */
+  int32_t max_wait_us;      /* a partial batch launches once its oldest request waited this long (50) */
+  int32_t use_graphs;       /* 0: each slot's batch pipeline (gather, BP, LSD, scatter) is captured
+                               once as a CUDA graph and replayed per batch; -1: plain launches */
+  size_t mem_budget;        /* device bytes of in-flight shots (m + 2n + 2 + 4(n+1) each); 0 = no limit */
+} lsd_server_options;
+
+typedef struct lsd_server_report {
+  int64_t submitted, completed, batches, admission_waits, peak_inflight_bytes, generated;
+  double mean_batch;        /* shots per launched batch */
+  double seconds;           /* first arrival to last completion */
+  double shots_per_s;       /* completed / seconds */
+  double p50_us, p99_us, mean_us, max_us;  /* arrival-to-completion latency */
+  double offered_rate;      /* lsd_server_run_poisson: the requested arrival rate (shots/s) */
+} lsd_server_report;
+
+/* Creates the server and its decoders (each slot's workspace sized for max_batch). */
+int lsd_server_create(lsd_server** out, int32_t n_codes, const lsd_server_code* codes,
+                      const lsd_server_options* opt);
+
+/* Submits one shot: syndrome [m] bytes, correction [n] bytes and status [1] byte (both
+ * nullable) in GPU-accessible memory (see above).  Thread-safe; returns at once. */
+int lsd_server_submit(lsd_server* s, int32_t code, const uint8_t* syndrome, uint8_t* correction,
+                      uint8_t* status, int64_t* id);
+
+/* Blocks until every submitted request has completed. */
+int lsd_server_wait_all(lsd_server* s);
+
+/* Throughput, batching and latency since the last reset (reset != 0 clears them). */
+int lsd_server_get_report(lsd_server* s, lsd_server_report* report, int32_t reset);
+
+/*
+ * lsd_server_run_poisson -- load test: requests arrive as a Poisson process of `rate`
+ * shots/s for `seconds`; each picks code c with probability mix[c] / sum(mix) and the next
+ * syndrome of pools[c] ([pool_sizes[c]][m_c] bytes, GPU-accessible, cycled); outputs are
+ * discarded.  Waits for completion and fills `report` (latency from the scheduled arrival).
+ */
+int lsd_server_run_poisson(lsd_server* s, double rate, double seconds, const double* mix,
+                           const uint8_t* const* pools, const int64_t* pool_sizes, uint64_t seed,
+                           lsd_server_report* report);
+
+/* Stops the scheduler after the outstanding requests and frees everything. */
+int lsd_server_destroy(lsd_server* s);
+
+/*
+ * lsd_autotune -- time the decoder's launch variants on a sample batch and keep the fastest:
+ * every BP kernel variant compatible with H and the BP method (register-resident shapes,
+ * generic 8/16/32-lane groups, one CTA per shot), then the LSD kernel's warps per CTA
+ * (2, 4, 8, 16 for the dense kernel).  Results of the decoder do not depend on the choice.
+ *   syndromes   device [shots][m] bytes, a representative sample (e.g. 10^5 shots).
+ *   report      host, nullable: the chosen variants and their times.
+ * Allocates temporary device buffers and synchronizes.
+ */
+typedef struct lsd_tune_report {
+  int32_t bp_variant, bp_candidates;   /* chosen BP variant id and how many were timed */
+  int32_t lsd_warps, lsd_candidates;
+  float ms_bp_best, ms_bp_first;       /* best BP time and the time of the default choice */
+  float ms_lsd_best, ms_lsd_first;
+} lsd_tune_report;
+int lsd_autotune(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
+                 lsd_tune_report* report);
 
 /* lsd_get_priors -- copy the n float32 priors lambda_j to host memory; synchronizes. */
 int lsd_get_priors(lsd_decoder* dec, float* priors);

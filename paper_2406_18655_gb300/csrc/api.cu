@@ -41,6 +41,13 @@ struct lsd_decoder {
   int64_t last_shots = 0;
   int last_kind = 0;  // 0 none, 1 decode, 2 bp only, 3 lsd only
   float* d_probs = nullptr;  // channel probabilities (sampler)
+  // sparse LSD (large matrices)
+  bool sparse = false;
+  int sp_grid_small = 0, sp_grid_big = 0;
+  int* d_sp_small = nullptr;
+  int* d_sp_big = nullptr;
+  int* d_spill = nullptr;
+  size_t sp_stride_small = 0, sp_stride_big = 0, spill_cap = 0;
 };
 
 struct lsd_prior {
@@ -151,6 +158,7 @@ int fill_stats(lsd_decoder* d, int64_t shots, lsd_stats* stats, bool timed_lsd) 
   stats->lsd_steps = (int64_t)d->h_ctr->lsd_steps;
   stats->kappa_max = d->h_ctr->kappa_max;
   stats->nu_max = d->h_ctr->nu_max;
+  stats->lsd_spilled = (int64_t)d->h_ctr->spill_count;
   float ms = 0.f;
   if (d->last_kind != 3 && cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]) == cudaSuccess)
     stats->ms_bp = ms;
@@ -161,6 +169,46 @@ int fill_stats(lsd_decoder* d, int64_t shots, lsd_stats* stats, bool timed_lsd) 
 }
 
 bool valid_lanes(int l) { return l == 0 || l == 8 || l == 16 || l == 32; }
+
+// LSD launch on the decoder's queue or batch: the dense kernel, or for large matrices the
+// sparse kernel followed by its global-memory instance for the shots that spilled.
+int run_lsd(lsd_decoder* d, const LSDArgs& l, int64_t max_items) {
+  if (!d->sparse) {
+    cudaError_t e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
+    d->launches++;
+    return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+  }
+  int rc;
+  if (!d->d_sp_small) {
+    const size_t warps = (size_t)d->sp_grid_small * sparse_warps_small();
+    if ((rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_sp_small),
+                        warps * d->sp_stride_small * sizeof(int))))
+      return rc;
+    if ((rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_sp_big),
+                        (size_t)d->sp_grid_big * d->sp_stride_big * sizeof(int))))
+      return rc;
+  }
+  if ((size_t)max_items > d->spill_cap) {
+    cudaError_t e = cudaStreamSynchronize(d->st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dev_free(d, d->d_spill, d->spill_cap * sizeof(int));
+    d->d_spill = nullptr;
+    d->spill_cap = 0;
+    if ((rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_spill), (size_t)max_items * sizeof(int))))
+      return rc;
+    d->spill_cap = (size_t)max_items;
+  }
+  cudaError_t e = launch_sparse(l, false, d->sp_grid_small, d->d_sp_small, d->sp_stride_small,
+                                d->d_spill, &d->d_ctr->spill_count, nullptr, nullptr, d->st);
+  d->launches++;
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(&d->d_ctr->lsd_next, 0, sizeof(unsigned long long), d->st);
+  if (e == cudaSuccess)
+    e = launch_sparse(l, true, d->sp_grid_big, d->d_sp_big, d->sp_stride_big, nullptr, nullptr,
+                      d->d_spill, &d->d_ctr->spill_count, d->st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
 
 }  // namespace
 
@@ -205,8 +253,8 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   lsd_options o{};
   if (opt) o = *opt;
   if (o.bp_method < 0 || o.bp_method > 1 || !valid_lanes(o.bp_lanes) || o.lsd_warps < 0 ||
-      o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 2 || o.reserved[0] ||
-      o.ms_scaling < 0.f)
+      o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 2 || o.lsd_kernel < 0 ||
+      o.lsd_kernel > 2 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.ms_scaling < 0.f)
     return LSD_ERR_INVALID_ARG;
   for (int j = 0; j < n; ++j)
     if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
@@ -313,11 +361,24 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
     lsd_destroy(d);
     return LSD_ERR_UNSUPPORTED;
   }
-  ce = lsd_config(g, lsd_order, o.lsd_warps, &d->lsd_warps, &d->lsd_grid, &d->lsd_smem, &d->lsd_W);
+  ce = o.lsd_kernel == 2 ? cudaErrorInvalidValue
+                         : lsd_config(g, lsd_order, o.lsd_warps, &d->lsd_warps, &d->lsd_grid,
+                                      &d->lsd_smem, &d->lsd_W);
   if (ce == cudaSuccess) {
     d->lsd_ok = true;
   } else {
-    cudaGetLastError();  // BP still works; LSD entry points report LSD_ERR_UNSUPPORTED
+    cudaGetLastError();
+    // large matrices: the sparse LSD (not for the single-cluster mode, whose one cluster holds
+    // every detector from the start)
+    if (o.lsd_kernel != 1 && !o.single_cluster &&
+        sparse_config(g, lsd_order, &d->sp_grid_small, &d->sp_grid_big) == cudaSuccess) {
+      d->sparse = true;
+      d->lsd_ok = true;
+      d->sp_stride_small = sparse_scratch_ints(m, n, false, lsd_order > 0);
+      d->sp_stride_big = sparse_scratch_ints(m, n, true, lsd_order > 0);
+    } else {
+      cudaGetLastError();  // BP still works; LSD entry points report LSD_ERR_UNSUPPORTED
+    }
   }
   *out = d;
   return LSD_OK;
@@ -360,9 +421,8 @@ int lsd_decode_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
   l.order = d->order;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
-  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
-  d->launches++;
-  if (e != cudaSuccess) return cuda_fail(e);
+  rc = run_lsd(d, l, shots);
+  if (rc) return rc;
   cudaEventRecord(d->ev[2], d->st);
   d->last_shots = shots;
   d->last_kind = 1;
@@ -448,9 +508,8 @@ int lsd_postprocess_batch(lsd_decoder* d, int64_t shots, const float* llrs,
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   cudaEventRecord(d->ev[1], d->st);
-  cudaError_t e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
-  d->launches++;
-  if (e != cudaSuccess) return cuda_fail(e);
+  rc = run_lsd(d, l, shots);
+  if (rc) return rc;
   cudaEventRecord(d->ev[2], d->st);
   d->last_shots = shots;
   d->last_kind = 3;
@@ -531,7 +590,7 @@ extern "C" int lsd_decode_batch_static(lsd_decoder* d, int64_t shots, const uint
   if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
   if (shots == 0) return LSD_OK;
   if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
-  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  if (!d->lsd_ok || d->sparse) return LSD_ERR_UNSUPPORTED;
   const size_t ctr_bytes = round256(sizeof(DevCounters));
   const size_t queue_bytes = round256((size_t)shots * sizeof(int32_t));
   const size_t llr_bytes = (size_t)shots * (size_t)d->n * sizeof(float);
@@ -781,9 +840,8 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
   l.order = d->order;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
-  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
-  d->launches++;
-  if (e != cudaSuccess) return cuda_fail(e);
+  rc = run_lsd(d, l, shots);
+  if (rc) return rc;
   cudaEventRecord(d->ev[2], d->st);
   d->last_shots = shots;
   d->last_kind = 1;
@@ -821,3 +879,155 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------------------
+extern "C" int lsd_autotune(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
+                            lsd_tune_report* report) {
+  if (!d || shots <= 0 || shots > INT32_MAX || !syndromes) return LSD_ERR_INVALID_ARG;
+  lsd_tune_report rep{};
+  float* post = nullptr;
+  uint8_t *corr = nullptr, *st = nullptr;
+  cudaError_t e = cudaMalloc(&post, (size_t)shots * d->n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&corr, (size_t)shots * d->n);
+  if (e == cudaSuccess) e = cudaMalloc(&st, (size_t)shots);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  int rc = e == cudaSuccess ? LSD_OK : cuda_fail(e);
+  auto timed = [&](auto&& fn, float* ms) -> int {
+    float best = 0.f;
+    for (int rep_i = 0; rep_i < 3; ++rep_i) {  // first run warms up; keep the best of the rest
+      cudaEventRecord(t0, d->st);
+      int r = fn();
+      if (r) return r;
+      cudaEventRecord(t1, d->st);
+      cudaError_t ee = cudaEventSynchronize(t1);
+      if (ee != cudaSuccess) return cuda_fail(ee);
+      float v = 0.f;
+      cudaEventElapsedTime(&v, t0, t1);
+      if (rep_i == 1 || (rep_i > 1 && v < best)) best = v;
+    }
+    *ms = best;
+    return LSD_OK;
+  };
+  // ---- BP variants ----
+  if (!rc) {
+    const int v0 = d->bp_variant, g0 = d->bp_grid, b0 = d->bp_block;
+    const size_t s0 = d->bp_smem;
+    int best_v = v0, best_g = g0, best_b = b0;
+    size_t best_s = s0;
+    float best_ms = 0.f;
+    for (int v = 0; v < bp_num_variants() && !rc; ++v) {
+      int vv = v, grid = 0, block = 0;
+      size_t smem = 0;
+      if (bp_config(d->g, 0, d->opt.bp_method, 0, &vv, &grid, &block, &smem) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      d->bp_variant = vv;
+      d->bp_grid = grid;
+      d->bp_block = block;
+      d->bp_smem = smem;
+      float ms = 0.f;
+      rc = timed([&]() { return lsd_bp_batch(d, shots, syndromes, post, nullptr, nullptr); }, &ms);
+      if (rc) break;
+      rep.bp_candidates++;
+      if (v == v0) rep.ms_bp_first = ms;
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best_v = vv;
+        best_g = grid;
+        best_b = block;
+        best_s = smem;
+      }
+    }
+    d->bp_variant = best_v;
+    d->bp_grid = best_g;
+    d->bp_block = best_b;
+    d->bp_smem = best_s;
+    rep.bp_variant = best_v;
+    rep.ms_bp_best = best_ms;
+  }
+  // ---- LSD warps per CTA (dense kernel) ----
+  if (!rc && d->lsd_ok && !d->sparse) {
+    const int w0 = d->lsd_warps;
+    int best_w = w0, best_g = d->lsd_grid;
+    size_t best_s = d->lsd_smem;
+    float best_ms = 0.f;
+    const int cand[] = {2, 4, 8, 16};
+    for (int w : cand) {
+      int ww = 0, grid = 0, words = 0;
+      size_t smem = 0;
+      if (lsd_config(d->g, d->order, w, &ww, &grid, &smem, &words) != cudaSuccess || ww != w) {
+        cudaGetLastError();
+        continue;
+      }
+      d->lsd_warps = ww;
+      d->lsd_grid = grid;
+      d->lsd_smem = smem;
+      float ms = 0.f;
+      rc = timed([&]() { return lsd_decode_batch(d, shots, syndromes, corr, st, nullptr, nullptr); },
+                 &ms);
+      if (rc) break;
+      rep.lsd_candidates++;
+      if (w == w0) rep.ms_lsd_first = ms;
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best_w = ww;
+        best_g = grid;
+        best_s = smem;
+      }
+    }
+    d->lsd_warps = best_w;
+    d->lsd_grid = best_g;
+    d->lsd_smem = best_s;
+    rep.lsd_warps = best_w;
+    rep.ms_lsd_best = best_ms;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (post) cudaFree(post);
+  if (corr) cudaFree(corr);
+  if (st) cudaFree(st);
+  cudaGetLastError();
+  if (report) *report = rep;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Decode with a device-side shot count (graph capture by the serving runtime).  The
+// workspace must already hold max_shots (no allocation may happen during a capture).
+// ---------------------------------------------------------------------------------------
+int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long long* shots_dev,
+                                const uint8_t* syndromes, uint8_t* corrections, uint8_t* status) {
+  if (!d || max_shots <= 0 || !shots_dev || !syndromes || !corrections) return LSD_ERR_INVALID_ARG;
+  if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
+  if ((size_t)max_shots > d->cap_shots) return LSD_ERR_ADMISSION;
+  if (d->sparse && (!d->d_sp_small || (size_t)max_shots > d->spill_cap)) return LSD_ERR_ADMISSION;
+  int rc = reset_counters(d);
+  if (rc) return rc;
+  BPArgs a = bp_args(d, max_shots, syndromes);
+  a.shots_dev = shots_dev;
+  a.corrections = corrections;
+  a.status = status;
+  a.queue = d->d_queue;
+  a.queue_llr = d->d_queue_llr;
+  cudaError_t e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, d->st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  LSDArgs l{};
+  l.g = d->g;
+  l.count_from_ctr = 1;
+  l.queue = d->d_queue;
+  l.llr = d->d_queue_llr;
+  l.llr_by_item = 1;
+  l.syndromes = syndromes;
+  l.corrections = corrections;
+  l.status = status;
+  l.order = d->order;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = d->d_ctr;
+  return run_lsd(d, l, max_shots);
+}

@@ -62,6 +62,7 @@ template <int G, int METHOD>
 __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const long long shots = a.shots_dev ? *a.shots_dev : a.shots;
   int32_t* s_chk_ptr = reinterpret_cast<int32_t*>(smem);
   int32_t* s_var_ptr = s_chk_ptr + (m + 1);
   float* s_prior = reinterpret_cast<float*>(s_var_ptr + (n + 1));
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
     unsigned long long shot_u = 0;
     if (lane == 0) shot_u = atomicAdd(&a.ctr->next_shot, 1ULL);
     shot_u = __shfl_sync(gmask, shot_u, leader);
-    if (shot_u >= (unsigned long long)a.shots) break;
+    if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
 
     const uint8_t* sp = a.syndromes + shot * m;
@@ -229,6 +230,7 @@ template <int G, int CPL, int DC, int VPL, int DV>
 __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const long long shots = a.shots_dev ? *a.shots_dev : a.shots;
   const int lane = threadIdx.x & (G - 1);
   const int group = threadIdx.x / G;
   const unsigned gmask = group_mask<G>();
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
     unsigned long long shot_u = 0;
     if (lane == 0) shot_u = atomicAdd(&a.ctr->next_shot, 1ULL);
     shot_u = __shfl_sync(gmask, shot_u, leader);
-    if (shot_u >= (unsigned long long)a.shots) break;
+    if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
 
     const uint8_t* sp = a.syndromes + shot * m;
@@ -400,6 +402,146 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
   }
 }
 
+// BP for graphs whose state does not fit a warp group: one CTA owns one shot, the Tanner
+// graph is read through the read-only cache, and r[E], Lam[n], s[m] live in the CTA's
+// shared memory.  Same operations in the same order as bp_kernel.
+template <int METHOD>
+__global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_shot;
+  __shared__ unsigned long long s_slot;
+  const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const long long shots = a.shots_dev ? *a.shots_dev : a.shots;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* r = reinterpret_cast<float*>(smem);
+  float* Lam = r + E;
+  uint8_t* syn = reinterpret_cast<uint8_t*>(Lam + n);
+  const int32_t* __restrict__ chk_ptr = a.g.chk_ptr;
+  const uint16_t* __restrict__ chk_var = a.g.chk_var;
+  const int32_t* __restrict__ var_ptr = a.g.var_ptr;
+  const uint16_t* __restrict__ var_edge = a.g.var_edge;
+  const float* __restrict__ prior = a.g.prior;
+  const float alpha = a.alpha;
+  unsigned long long my_iters = 0, my_conv = 0;
+  for (;;) {
+    if (tid == 0) s_shot = atomicAdd(&a.ctr->next_shot, 1ULL);
+    __syncthreads();
+    const unsigned long long shot_u = s_shot;
+    if (shot_u >= (unsigned long long)shots) break;
+    const long long shot = (long long)shot_u;
+    const uint8_t* sp = a.syndromes + shot * m;
+    for (int i = tid; i < m; i += nt) syn[i] = sp[i] ? 1 : 0;
+    for (int e = tid; e < E; e += nt) r[e] = 0.f;
+    for (int j = tid; j < n; j += nt) Lam[j] = __ldg(prior + j);
+    __syncthreads();
+    int t = 0;
+    bool conv = false;
+    for (;;) {
+      const bool msgs = t < a.iters;
+      int unsat = 0;
+      for (int i = tid; i < m; i += nt) {
+        const int b = __ldg(chk_ptr + i), e1 = __ldg(chk_ptr + i + 1);
+        const unsigned si = syn[i];
+        unsigned hp = si;
+        if constexpr (METHOD == 0) {
+          float min1 = kBig, min2 = kBig;
+          int idx = 0;
+          unsigned negs = 0, sgn = si;
+          for (int e = b; e < e1; ++e) {
+            const float L = Lam[__ldg(chk_var + e)];
+            hp ^= (L < 0.f) ? 1u : 0u;
+            if (msgs) {
+              const float q = __fsub_rn(L, r[e]);
+              const float aq = fabsf(q);
+              const unsigned ng = (q < 0.f) ? 1u : 0u;
+              sgn ^= ng;
+              negs |= ng << (e - b);
+              if (aq < min1) {
+                min2 = min1;
+                min1 = aq;
+                idx = e - b;
+              } else if (aq < min2) {
+                min2 = aq;
+              }
+            }
+          }
+          if (msgs) {
+            const float m1 = __fmul_rn(alpha, min1), m2 = __fmul_rn(alpha, min2);
+            for (int e = b; e < e1; ++e) {
+              const int k = e - b;
+              const float mag = (k == idx) ? m2 : m1;
+              r[e] = ((sgn ^ (negs >> k)) & 1u) ? -mag : mag;
+            }
+          }
+        } else {
+          float qv[kMaxRowDeg];
+          for (int e = b; e < e1; ++e) {
+            const float L = Lam[__ldg(chk_var + e)];
+            hp ^= (L < 0.f) ? 1u : 0u;
+            qv[e - b] = __fsub_rn(L, r[e]);
+          }
+          if (msgs) {
+            for (int e = b; e < e1; ++e) {
+              float prod = 1.f;
+              for (int e2 = b; e2 < e1; ++e2)
+                if (e2 != e) prod = prod * tanhf(0.5f * qv[e2 - b]);
+              const float lim = 0.99999994f;
+              prod = fminf(fmaxf(prod, -lim), lim);
+              const float v = 2.f * atanhf(prod);
+              r[e] = si ? -v : v;
+            }
+          }
+        }
+        unsat |= (int)hp;
+      }
+      const int any_unsat = __syncthreads_or(unsat);
+      if (t > 0) {
+        conv = !any_unsat;
+        if (conv && a.early_exit) break;
+      }
+      if (!msgs) break;
+      for (int j = tid; j < n; j += nt) {
+        float L = __ldg(prior + j);
+        const int v1 = __ldg(var_ptr + j + 1);
+        for (int k = __ldg(var_ptr + j); k < v1; ++k) L = __fadd_rn(L, r[__ldg(var_edge + k)]);
+        Lam[j] = L;
+      }
+      __syncthreads();
+      ++t;
+    }
+    if (a.posteriors) {
+      float* po = a.posteriors + shot * n;
+      for (int j = tid; j < n; j += nt) po[j] = Lam[j];
+    }
+    if (tid == 0) {
+      if (a.converged_out) a.converged_out[shot] = conv ? 1 : 0;
+      if (a.iters_out) a.iters_out[shot] = t;
+      my_iters += (unsigned long long)t;
+      my_conv += conv ? 1ull : 0ull;
+    }
+    if (a.queue) {
+      if (conv) {
+        uint8_t* co = a.corrections + shot * n;
+        for (int j = tid; j < n; j += nt) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+        if (tid == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
+      } else {
+        if (tid == 0) {
+          s_slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
+          a.queue[s_slot] = (int32_t)shot;
+        }
+        __syncthreads();
+        float* lo = a.queue_llr + (long long)s_slot * n;
+        for (int j = tid; j < n; j += nt) lo[j] = Lam[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (my_iters) atomicAdd(&a.ctr->bp_iterations, my_iters);
+    if (my_conv) atomicAdd(&a.ctr->bp_converged, my_conv);
+  }
+}
+
 // Shapes of bp_reg_kernel: (G, CPL, DC, VPL, DV).
 struct RegShape {
   int G, cpl, dc, vpl, dv;
@@ -444,13 +586,20 @@ const void* generic_fn(int v) {
     default: return (const void*)bp_kernel<32, 1>;
   }
 }
+constexpr int kCtaBase = 6 + kNumRegShapes;  // + method: one CTA per shot
+bool is_cta(int v) { return v >= kCtaBase; }
 int lanes_of(int variant) {
+  if (is_cta(variant)) return 0;
   if (variant >= 6) return kRegShapes[variant - 6].G;
   return variant % 3 == 0 ? 8 : variant % 3 == 1 ? 16 : 32;
 }
+const void* variant_fn(int v) {
+  if (is_cta(v)) return v == kCtaBase ? (const void*)bp_cta_kernel<0> : (const void*)bp_cta_kernel<1>;
+  return v >= 6 ? kRegShapes[v - 6].fn : generic_fn(v);
+}
 }  // namespace
 
-int bp_num_variants() { return 6 + kNumRegShapes; }
+int bp_num_variants() { return kCtaBase + 2; }
 
 cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
                       int* grid, int* block, size_t* smem) {
@@ -465,8 +614,13 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
   if (*variant >= 0) {
     v = *variant;
     if (v >= bp_num_variants()) return cudaErrorInvalidValue;
-    if (v >= 6 && (method != 0 || !reg_shape_fits(kRegShapes[v - 6], g))) return cudaErrorInvalidValue;
-    if (v < 6 && (v >= 3) != (method != 0)) return cudaErrorInvalidValue;
+    if (is_cta(v)) {
+      if ((v - kCtaBase) != (method != 0 ? 1 : 0)) return cudaErrorInvalidValue;
+    } else if (v >= 6 && (method != 0 || !reg_shape_fits(kRegShapes[v - 6], g))) {
+      return cudaErrorInvalidValue;
+    } else if (v < 6 && (v >= 3) != (method != 0)) {
+      return cudaErrorInvalidValue;
+    }
   } else {
     if (method == 0 && kind != 1) {
       // least work per lane first (fewer registers, shorter per-shot latency), then the
@@ -488,25 +642,36 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
       if (kind == 2) return cudaErrorInvalidValue;
       const int l = lanes ? lanes : 32;
       v = (l == 8 ? 0 : l == 16 ? 1 : 2) + (method ? 3 : 0);
+      // a graph whose warp-group state does not fit next to the staged graph: one CTA per shot
+      if (bp_graph_bytes(g.m, g.n, g.E) + bp_group_bytes(g.m, g.n, g.E) > (size_t)max_smem)
+        v = kCtaBase + (method ? 1 : 0);
     }
   }
-  const int G = lanes_of(v);
   size_t gb, grp;
-  if (v >= 6) {
-    gb = align16((size_t)g.n * 4);
-    grp = bp_reg_group_bytes(g.n, g.E);
-  } else {
-    gb = bp_graph_bytes(g.m, g.n, g.E);
+  int b;
+  if (is_cta(v)) {
+    gb = 0;
     grp = bp_group_bytes(g.m, g.n, g.E);
+    if (grp > (size_t)max_smem) return cudaErrorInvalidValue;
+    b = g.m >= 2048 ? 512 : 256;
+  } else {
+    const int G = lanes_of(v);
+    if (v >= 6) {
+      gb = align16((size_t)g.n * 4);
+      grp = bp_reg_group_bytes(g.n, g.E);
+    } else {
+      gb = bp_graph_bytes(g.m, g.n, g.E);
+      grp = bp_group_bytes(g.m, g.n, g.E);
+    }
+    b = 256;
+    while (b > G && gb + (size_t)(b / G) * grp > (size_t)max_smem) b /= 2;
+    if (gb + (size_t)(b / G) * grp > (size_t)max_smem) return cudaErrorInvalidValue;
+    grp *= (size_t)(b / G);
   }
-  int b = 256;
-  while (b > G && gb + (size_t)(b / G) * grp > (size_t)max_smem) b /= 2;
-  if (gb + (size_t)(b / G) * grp > (size_t)max_smem) return cudaErrorInvalidValue;
   *block = b;
-  *smem = gb + (size_t)(b / G) * grp;
-  const void* fn = v >= 6 ? kRegShapes[v - 6].fn : generic_fn(v);
-  // the limit is a property of the function, shared by every decoder: allow the maximum
-  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  *smem = gb + grp;
+  const void* fn = variant_fn(v);
+  err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b, *smem);
@@ -519,7 +684,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
 
 cudaError_t launch_bp(const BPArgs& a, int variant, int grid, int block, size_t smem,
                       cudaStream_t st) {
-  const void* fn = variant >= 6 ? kRegShapes[variant - 6].fn : generic_fn(variant);
+  const void* fn = variant_fn(variant);
   void* args[] = {const_cast<BPArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }

@@ -838,8 +838,7 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
   *words = (g.m + 31) / 32;
   *warps_out = w;
   const void* fn = class_kernel(c, mu);
-  // the limit is a property of the function, shared by every decoder: allow the maximum
-  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, w * 32, *smem);

@@ -38,11 +38,13 @@ struct DevCounters {
   int nu_max;
   int timeout_flag;
   int pad;
+  unsigned long long spill_count;   // shots the small sparse LSD instance handed on
 };
 
 struct BPArgs {
   DevGraph g;
   long long shots;
+  const long long* shots_dev; // if set, the shot count is read from here at kernel start
   const uint8_t* syndromes;  // [shots][m]
   int iters;
   float alpha;
@@ -88,6 +90,16 @@ cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaS
 cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
                        size_t* smem, int* words);
 
+// Lets `fn` use all the shared memory a block may opt into (the dynamic limit is a property
+// of the function, shared by every decoder; it excludes the function's static allocation).
+inline cudaError_t allow_max_dynamic_smem(const void* fn, int max_smem) {
+  cudaFuncAttributes at{};
+  cudaError_t e = cudaFuncGetAttributes(&at, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_smem - (int)at.sharedSizeBytes);
+}
+
 // Learned prior (prior.cu).
 int prior_num_params();
 size_t prior_smem(int m, int n, int E, bool train);
@@ -106,6 +118,19 @@ cudaError_t launch_hard_check(const DevGraph& g, long long shots, const float* l
                               const uint8_t* syn, uint8_t* corr, uint8_t* status, int32_t* queue,
                               float* queue_llr, DevCounters* ctr, cudaStream_t st);
 constexpr int kPriorMaxRounds = 8;
+
+// Decode whose shot count is read from device-visible memory at run time, so that one
+// captured CUDA graph serves every batch size up to max_shots (api.cu; used by the server).
+int decode_batch_counted(lsd_decoder* dec, int64_t max_shots, const long long* shots_dev,
+                         const uint8_t* syndromes, uint8_t* corrections, uint8_t* status);
+
+// LSD for large matrices (lsd_sparse.cu).
+size_t sparse_scratch_ints(int m, int n, bool big, bool mu);
+cudaError_t sparse_config(const DevGraph& g, int order, int* grid_small, int* grid_big);
+int sparse_warps_small();
+cudaError_t launch_sparse(const LSDArgs& a, bool big, int grid, int* scratch, size_t stride,
+                          int* spill, unsigned long long* spill_count, const int* items,
+                          const unsigned long long* item_count, cudaStream_t st);
 
 // Limits of this build's kernels.
 constexpr int kMaxLsdWords = 16;    // LSD: m <= 32 * kMaxLsdWords detectors per shot

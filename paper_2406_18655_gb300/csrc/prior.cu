@@ -762,7 +762,7 @@ cudaError_t prior_config(int m, int n, int E, bool train, int* grid) {
   const size_t smem = prior_smem(m, n, E, train);
   if (smem > (size_t)max_smem) return cudaErrorInvalidValue;
   const void* fn = train ? (const void*)prior_kernel<true> : (const void*)prior_kernel<false>;
-  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPriorThreads, smem);

@@ -31,7 +31,9 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_decode_batch_static", "lsd_prior_num_params", "lsd_prior_create",
            "lsd_prior_set_params", "lsd_prior_get_params", "lsd_prior_forward",
            "lsd_prior_gradient", "lsd_prior_train_step", "lsd_decode_learned",
-           "lsd_prior_destroy", "lsd_sample")
+           "lsd_prior_destroy", "lsd_sample", "lsd_server_create", "lsd_server_submit",
+           "lsd_server_wait_all", "lsd_server_get_report", "lsd_server_run_poisson",
+           "lsd_server_destroy", "lsd_autotune")
 
 
 class LsdError(RuntimeError):
@@ -44,16 +46,27 @@ class Options(C.Structure):
     _fields_ = [("ms_scaling", C.c_float), ("bp_method", C.c_int32),
                 ("no_early_exit", C.c_int32), ("single_cluster", C.c_int32),
                 ("bp_lanes", C.c_int32), ("lsd_warps", C.c_int32),
-                ("bp_kernel", C.c_int32), ("reserved", C.c_int32 * 1),
+                ("bp_kernel", C.c_int32), ("lsd_kernel", C.c_int32),
+                ("reserved", C.c_int32 * 3),
                 ("mem_budget", C.c_size_t),
                 ("stream", C.c_void_p)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("bp_variant", C.c_int32), ("bp_candidates", C.c_int32),
+                ("lsd_warps", C.c_int32), ("lsd_candidates", C.c_int32),
+                ("ms_bp_best", C.c_float), ("ms_bp_first", C.c_float),
+                ("ms_lsd_best", C.c_float), ("ms_lsd_first", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
     _fields_ = [("shots", C.c_int64), ("bp_converged", C.c_int64), ("lsd_shots", C.c_int64),
                 ("unsolvable", C.c_int64), ("bp_iterations", C.c_int64),
                 ("lsd_steps", C.c_int64), ("kappa_max", C.c_int32), ("nu_max", C.c_int32),
-                ("ms_bp", C.c_float), ("ms_lsd", C.c_float)]
+                ("ms_bp", C.c_float), ("ms_lsd", C.c_float), ("lsd_spilled", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +106,7 @@ def lib():
     L.lsd_decode_learned.argtypes = [P, P, C.c_int64, P, P, P, C.POINTER(Stats)]
     L.lsd_prior_destroy.argtypes = [P]
     L.lsd_sample.argtypes = [P, C.c_uint64, C.c_int64, C.c_int64, P, P]
+    L.lsd_autotune.argtypes = [P, C.c_int64, P, C.POINTER(TuneReport)]
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -137,7 +151,7 @@ class Decoder:
     def __init__(self, h, channel_probs, bp_iters: int, lsd_order: int = 0, *,
                  ms_scaling: float = 0.0, bp_method: int = 0, no_early_exit: bool = False,
                  single_cluster: bool = False, bp_lanes: int = 0, lsd_warps: int = 0,
-                 bp_kernel: int = 0, mem_budget: int = 0, stream=None):
+                 bp_kernel: int = 0, lsd_kernel: int = 0, mem_budget: int = 0, stream=None):
         import torch
         h = np.asarray(h.cpu() if isinstance(h, torch.Tensor) else h, dtype=np.uint8)
         self.m, self.n = h.shape
@@ -157,6 +171,7 @@ class Decoder:
         opt.bp_lanes = bp_lanes
         opt.lsd_warps = lsd_warps
         opt.bp_kernel = bp_kernel
+        opt.lsd_kernel = lsd_kernel
         opt.mem_budget = mem_budget
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -277,6 +292,15 @@ class Decoder:
                                 _ptr(s)), "lsd_sample")
         return e, s
 
+    def autotune(self, syndromes) -> dict:
+        """Times the launch variants on a sample batch (device syndromes) and keeps the fastest."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.m), "syndromes")
+        r = TuneReport()
+        _check(lib().lsd_autotune(self._h, shots, _ptr(syndromes), C.byref(r)), "lsd_autotune")
+        return r.as_dict()
+
     def decode_learned(self, prior, syndromes, want_stats: bool = False):
         """Learned prior + LSD (BP + LSD as the fallback).  Returns (corrections, status[, stats])."""
         import torch
@@ -374,3 +398,117 @@ class Prior:
                                           C.byref(loss) if want_loss else None),
                "lsd_prior_train_step")
         return loss.value if want_loss else None
+
+
+class ServerCode(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64), ("rows", C.c_void_p),
+                ("cols", C.c_void_p), ("channel_probs", C.c_void_p), ("bp_iters", C.c_int32),
+                ("lsd_order", C.c_int32)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("slots_per_code", C.c_int32), ("max_batch", C.c_int32),
+                ("max_wait_us", C.c_int32), ("use_graphs", C.c_int32), ("mem_budget", C.c_size_t)]
+
+
+class ServerReport(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
+                ("admission_waits", C.c_int64), ("peak_inflight_bytes", C.c_int64),
+                ("generated", C.c_int64), ("mean_batch", C.c_double), ("seconds", C.c_double),
+                ("shots_per_s", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double),
+                ("mean_us", C.c_double), ("max_us", C.c_double), ("offered_rate", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        P = C.c_void_p
+        L.lsd_server_create.argtypes = [C.POINTER(P), C.c_int32, P, C.POINTER(ServerOptions)]
+        L.lsd_server_submit.argtypes = [P, C.c_int32, P, P, P, C.POINTER(C.c_int64)]
+        L.lsd_server_wait_all.argtypes = [P]
+        L.lsd_server_get_report.argtypes = [P, C.POINTER(ServerReport), C.c_int32]
+        L.lsd_server_run_poisson.argtypes = [P, C.c_double, C.c_double, P, P, P, C.c_uint64,
+                                             C.POINTER(ServerReport)]
+        L.lsd_server_destroy.argtypes = [P]
+        for name in ("lsd_server_create", "lsd_server_submit", "lsd_server_wait_all",
+                     "lsd_server_get_report", "lsd_server_run_poisson", "lsd_server_destroy"):
+            getattr(L, name).restype = C.c_int
+        L._server_ready = True
+    return L
+
+
+class Server:
+    """Continuous-batching decode server over several codes (lsd_server_*).
+
+    ``codes`` is a list of (h, channel_probs, bp_iters, lsd_order).  Request buffers must be
+    pinned host tensors (``pin_memory()``) or CUDA tensors.
+    """
+
+    def __init__(self, codes, slots_per_code: int = 0, max_batch: int = 0, max_wait_us: int = 0,
+                 mem_budget: int = 0, graphs: bool = True):
+        L = _server_lib()
+        keep = []
+        arr = (ServerCode * len(codes))()
+        self.shapes = []
+        for k, (h, probs, iters, order) in enumerate(codes):
+            h = np.asarray(h, dtype=np.uint8)
+            r, c = np.nonzero(h)
+            r = np.ascontiguousarray(r, np.int32)
+            c = np.ascontiguousarray(c, np.int32)
+            p = np.asarray(probs, np.float32)
+            if p.ndim == 0:
+                p = np.full(h.shape[1], float(p), np.float32)
+            p = np.ascontiguousarray(p)
+            keep += [r, c, p]
+            arr[k] = ServerCode(h.shape[0], h.shape[1], r.size, r.ctypes.data, c.ctypes.data,
+                                p.ctypes.data, iters, order)
+            self.shapes.append(h.shape)
+        opt = ServerOptions(slots_per_code, max_batch, max_wait_us, 0 if graphs else -1, mem_budget)
+        handle = C.c_void_p()
+        _check(L.lsd_server_create(C.byref(handle), len(codes), C.cast(arr, C.c_void_p),
+                                   C.byref(opt)), "lsd_server_create")
+        self._h = handle
+
+    def submit(self, code: int, syndrome, correction=None, status=None) -> int:
+        """syndrome / correction / status: 1-D uint8 tensors (pinned host or CUDA)."""
+        rid = C.c_int64()
+        _check(_server_lib().lsd_server_submit(
+            self._h, code, C.c_void_p(syndrome.data_ptr()),
+            None if correction is None else C.c_void_p(correction.data_ptr()),
+            None if status is None else C.c_void_p(status.data_ptr()), C.byref(rid)),
+            "lsd_server_submit")
+        return rid.value
+
+    def wait_all(self):
+        _check(_server_lib().lsd_server_wait_all(self._h), "lsd_server_wait_all")
+
+    def report(self, reset: bool = False) -> dict:
+        r = ServerReport()
+        _check(_server_lib().lsd_server_get_report(self._h, C.byref(r), int(reset)),
+               "lsd_server_get_report")
+        return r.as_dict()
+
+    def run_poisson(self, rate: float, seconds: float, mix, pools, seed: int = 1) -> dict:
+        """Poisson load test; pools[c] is a pinned uint8 tensor [k][m_c] of syndromes."""
+        nc = len(self.shapes)
+        mixa = (C.c_double * nc)(*[float(x) for x in mix])
+        ptrs = (C.c_void_p * nc)(*[C.c_void_p(t.data_ptr()) for t in pools])
+        sizes = (C.c_int64 * nc)(*[int(t.shape[0]) for t in pools])
+        r = ServerReport()
+        _check(_server_lib().lsd_server_run_poisson(self._h, rate, seconds, mixa, ptrs, sizes,
+                                                    seed, C.byref(r)), "lsd_server_run_poisson")
+        return r.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _server_lib().lsd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

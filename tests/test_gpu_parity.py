@@ -267,3 +267,14 @@ def test_full_size_bb144_million_shots(L):
     o = oracle.decode(h, f64(probs), s[idx], 50, precision=1)
     assert np.array_equal(corr.cpu().numpy()[idx], o["corrections"])
     assert np.array_equal(st.cpu().numpy()[idx], o["status"])
+
+
+def test_autotune_keeps_results(L):
+    h, probs, e, s = sample("bb144", 0.06, 20000, seed=77)
+    d = L.Decoder(h, probs, 50)
+    c0, s0 = d.decode(dev(s))
+    rep = d.autotune(dev(s[:8000]))
+    assert rep["bp_candidates"] >= 3 and rep["lsd_candidates"] >= 2
+    assert rep["ms_bp_best"] <= rep["ms_bp_first"] + 1e-6
+    c1, s1 = d.decode(dev(s))
+    assert torch.equal(c0, c1) and torch.equal(s0, s1)

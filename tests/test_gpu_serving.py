@@ -1,0 +1,148 @@
+"""Serving runtime: continuous batching over several codes, on the GPU.
+
+The phenomenological space-time matrices of the three BB codes (d = 6, 12, 18 rounds, with
+one noiseless final round; p = q = 0.003) are served together.  Every shot's correction is
+the same whether it is decoded alone, in a mix with the other codes, or by the decoder
+directly (decoding is deterministic per shot, so the tolerance is bit-exact)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2406_18655_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ROUNDS = {"bb72": 6, "bb144": 12, "bb288": 18}
+
+
+@pytest.fixture(scope="module")
+def L():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_18655_gb300 import build
+    build.build()
+    from paper_2406_18655_gb300 import lsd
+    lsd.lib()
+    return lsd
+
+
+def st_code(name, p=0.003):
+    hx = getattr(I, name)()[0]
+    d = ROUNDS[name]
+    h = I.space_time(hx, d)
+    probs = I.space_time_probs(hx.shape[1], hx.shape[0], d, p, p).astype(np.float32)
+    return h, probs
+
+
+def pool(L, h, probs, shots, seed):
+    dec = L.Decoder(h, probs, 1)
+    e, s = dec.sample(seed, shots)
+    return s.cpu().pin_memory()
+
+
+@pytest.fixture(scope="module")
+def setup(L):
+    codes = [st_code(nm) for nm in ("bb72", "bb144", "bb288")]
+    pools = [pool(L, h, p, 600, 40 + k) for k, (h, p) in enumerate(codes)]
+    return codes, pools
+
+
+def test_alone_equals_mixed_equals_direct(L, setup):
+    codes, pools = setup
+    srv = L.Server([(h, p, 50, 0) for h, p in codes], slots_per_code=3, max_batch=256,
+                   max_wait_us=100)
+    alone = []
+    for c, (h, p) in enumerate(codes):
+        out = torch.zeros((pools[c].shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+        st = torch.zeros(pools[c].shape[0], dtype=torch.uint8).pin_memory()
+        for k in range(pools[c].shape[0]):
+            srv.submit(c, pools[c][k], out[k], st[k])
+        srv.wait_all()
+        alone.append((out.clone(), st.clone()))
+    # mixed: all codes interleaved, submitted back to back
+    outs = [torch.zeros((pools[c].shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+            for c, (h, p) in enumerate(codes)]
+    sts = [torch.zeros(pools[c].shape[0], dtype=torch.uint8).pin_memory() for c in range(3)]
+    order = np.random.default_rng(0).permutation(
+        [(c, k) for c in range(3) for k in range(pools[c].shape[0])])
+    for c, k in order:
+        srv.submit(int(c), pools[c][k], outs[c][k], sts[c][k])
+    srv.wait_all()
+    rep = srv.report()
+    assert rep["completed"] == rep["submitted"]
+    for c, (h, p) in enumerate(codes):
+        assert torch.equal(outs[c], alone[c][0]), f"code {c}: mixed differs from alone"
+        assert torch.equal(sts[c], alone[c][1])
+        d = L.Decoder(h, p, 50)
+        corr, st = d.decode(pools[c].cuda())
+        assert torch.equal(corr.cpu(), outs[c]) and torch.equal(st.cpu(), sts[c])
+        syn = (outs[c].numpy().astype(np.float32) @ h.T.astype(np.float32)).astype(np.int64) % 2
+        assert np.array_equal(syn, pools[c].numpy())
+    srv.close()
+
+
+def test_graphs_equal_plain_launches(L, setup):
+    """A slot's captured graph (device-side batch size) decodes exactly like plain launches,
+    for every batch size from 1 to max_batch."""
+    codes, pools = setup
+    h, p = codes[1]
+    res = []
+    for graphs in (True, False):
+        srv = L.Server([(h, p, 50, 0)], slots_per_code=2, max_batch=64, max_wait_us=30,
+                       graphs=graphs)
+        out = torch.zeros((pools[1].shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+        st = torch.zeros(pools[1].shape[0], dtype=torch.uint8).pin_memory()
+        k = 0
+        for b in [1, 2, 3, 7, 31, 64, 65, 100]:
+            for j in range(k, min(k + b, pools[1].shape[0])):
+                srv.submit(0, pools[1][j], out[j], st[j])
+            k += b
+            srv.wait_all()
+        for j in range(k, pools[1].shape[0]):
+            srv.submit(0, pools[1][j], out[j], st[j])
+        srv.wait_all()
+        assert srv.report()["completed"] == pools[1].shape[0]
+        res.append((out, st))
+        srv.close()
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    assert (res[0][1] > 0).all()
+
+
+def test_admission_by_memory(L, setup):
+    codes, pools = setup
+    h, p = codes[1]
+    per_shot = h.shape[0] + 2 * h.shape[1] + 2 + 4 * (h.shape[1] + 1)
+    budget = 40 * per_shot
+    srv = L.Server([(h, p, 50, 0)], slots_per_code=4, max_batch=512, max_wait_us=20,
+                   mem_budget=budget)
+    out = torch.zeros((pools[1].shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+    for k in range(pools[1].shape[0]):
+        srv.submit(0, pools[1][k], out[k])
+    srv.wait_all()
+    rep = srv.report()
+    assert rep["completed"] == pools[1].shape[0]
+    assert 0 < rep["peak_inflight_bytes"] <= budget
+    assert rep["mean_batch"] <= 40
+    d = L.Decoder(h, p, 50)
+    corr, _ = d.decode(pools[1].cuda())
+    assert torch.equal(corr.cpu(), out)
+    srv.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_poisson_load(L, setup, graphs):
+    codes, pools = setup
+    srv = L.Server([(h, p, 50, 0) for h, p in codes], graphs=graphs)
+    rep = srv.run_poisson(2e5, 0.2, [1, 1, 1], pools, seed=3)
+    assert rep["completed"] == rep["generated"] > 0
+    assert rep["p99_us"] >= rep["p50_us"] > 0
+    print(f"poisson 2e5/s graphs={graphs}:", {k: round(v, 2) for k, v in rep.items()})
+    srv.close()
+
+
+def test_rejects_pageable_buffers(L, setup):
+    codes, pools = setup
+    srv = L.Server([(codes[0][0], codes[0][1], 50, 0)])
+    pageable = torch.zeros(codes[0][0].shape[0], dtype=torch.uint8)
+    with pytest.raises(L.LsdError):
+        srv.submit(0, pageable)
+    srv.close()
