@@ -218,8 +218,10 @@ int lsd_decode_batch_static(lsd_decoder* dec, int64_t shots, const uint8_t* synd
  * Parameters: FP32 master copy, flat in the order a0, a1, u0, u1, W1_cv, b1_cv, W2_cv,
  * b2_cv, W1_vc, b1_vc, W2_vc, b2_vc, w_o, b_o (lsd_prior_num_params() floats).  The
  * matrix products run on the tensor cores with BF16 weights and activations and FP32
- * accumulation; node states and the loss are FP32.  Limits: m <= 96, n <= 192 checks and
- * faults (the states of one shot live in one CTA's shared memory).
+ * accumulation; node states and the loss are FP32.  The states of one shot live in one
+ * CTA's shared memory: inference takes about 384 (n + m) + 64 max(n, m) + 16 KB bytes
+ * (BB [[288,12,18]], 201 KB, fits); training takes more (up to m = 96, n = 192), and
+ * lsd_prior_gradient / lsd_prior_train_step return LSD_ERR_UNSUPPORTED beyond that.
  * ------------------------------------------------------------------------------------ */
 #define LSD_PRIOR_HIDDEN 32
 typedef struct lsd_prior lsd_prior;
@@ -378,6 +380,11 @@ int lsd_destroy(lsd_decoder* dec);
 
 /* lsd_status_string -- static description of a return code or per-shot status. */
 const char* lsd_status_string(int code);
+
+/* lsd_last_error -- the CUDA error name and message behind the last LSD_ERR_CUDA or
+ * LSD_ERR_OOM returned on the calling host thread ("" if none).  The string belongs to the
+ * library and stays valid until the thread's next failing call. */
+const char* lsd_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -58,15 +59,16 @@ struct lsd_prior {
   double* d_loss = nullptr;
   double* h_loss = nullptr;  // pinned
   float* d_scratch = nullptr;
-  float* d_llr = nullptr;
-  size_t llr_cap = 0;
   int grid_train = 0, grid_fwd = 0;
   int step = 0;
 };
 
 namespace {
 
+thread_local char g_last_error[160] = "";
+
 int cuda_fail(cudaError_t e) {
+  lsdgb::record_cuda_error(e);
   if (e == cudaErrorMemoryAllocation) return LSD_ERR_OOM;
   return LSD_ERR_CUDA;
 }
@@ -212,7 +214,14 @@ int run_lsd(lsd_decoder* d, const LSDArgs& l, int64_t max_items) {
 
 }  // namespace
 
+void lsdgb::record_cuda_error(cudaError_t e) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e));
+}
+
 extern "C" {
+
+const char* lsd_last_error(void) { return g_last_error; }
 
 const char* lsd_status_string(int code) {
   switch (code) {
@@ -640,7 +649,7 @@ void prior_free(lsd_prior* p) {
   if (!p) return;
   cudaStreamSynchronize(p->dec ? p->dec->st : nullptr);
   for (void* q : {(void*)p->d_params, (void*)p->d_grads, (void*)p->d_m, (void*)p->d_v,
-                  (void*)p->d_loss, (void*)p->d_scratch, (void*)p->d_llr})
+                  (void*)p->d_loss, (void*)p->d_scratch})
     if (q) cudaFree(q);
   if (p->h_loss) cudaFreeHost(p->h_loss);
   cudaGetLastError();
@@ -658,6 +667,7 @@ int prior_alloc(void** q, size_t bytes) {
 
 int prior_grads(lsd_prior* p, int64_t shots, const uint8_t* syn, const uint8_t* err) {
   lsd_decoder* d = p->dec;
+  if (p->grid_train <= 0) return LSD_ERR_UNSUPPORTED;
   cudaError_t e = cudaMemsetAsync(p->d_grads, 0, sizeof(float) * p->np, d->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_loss, 0, sizeof(double), d->st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -681,26 +691,31 @@ int lsd_prior_destroy(lsd_prior* p) {
 int lsd_prior_create(lsd_prior** out, lsd_decoder* d, int32_t rounds, const float* params) {
   if (!out || !d || rounds < 1 || rounds > kPriorMaxRounds) return LSD_ERR_INVALID_ARG;
   *out = nullptr;
-  if (d->m > 96 || d->n > 192) return LSD_ERR_UNSUPPORTED;
   lsd_prior* p = new (std::nothrow) lsd_prior();
   if (!p) return LSD_ERR_OOM;
   p->dec = d;
   p->rounds = rounds;
   p->np = prior_num_params();
-  cudaError_t ce = prior_config(d->m, d->n, d->E, true, &p->grid_train);
-  if (ce == cudaSuccess) ce = prior_config(d->m, d->n, d->E, false, &p->grid_fwd);
+  cudaError_t ce = prior_config(d->m, d->n, d->E, false, &p->grid_fwd);
   if (ce != cudaSuccess) {
     cudaGetLastError();
     prior_free(p);
     return LSD_ERR_UNSUPPORTED;
+  }
+  // training is optional: its kernel keeps more per-shot state
+  if (d->m > 96 || d->n > 192 ||
+      prior_config(d->m, d->n, d->E, true, &p->grid_train) != cudaSuccess) {
+    cudaGetLastError();
+    p->grid_train = 0;
   }
   int rc;
   const size_t nb = sizeof(float) * p->np;
   if ((rc = prior_alloc((void**)&p->d_params, nb)) || (rc = prior_alloc((void**)&p->d_grads, nb)) ||
       (rc = prior_alloc((void**)&p->d_m, nb)) || (rc = prior_alloc((void**)&p->d_v, nb)) ||
       (rc = prior_alloc((void**)&p->d_loss, sizeof(double))) ||
-      (rc = prior_alloc((void**)&p->d_scratch,
-                        sizeof(float) * prior_scratch_floats(d->m, d->n, rounds, p->grid_train)))) {
+      (p->grid_train > 0 &&
+       (rc = prior_alloc((void**)&p->d_scratch,
+                         sizeof(float) * prior_scratch_floats(d->m, d->n, rounds, p->grid_train))))) {
     prior_free(p);
     return rc;
   }
@@ -805,26 +820,14 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
   if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
   int rc = ensure_workspace(d, shots);
   if (rc) return rc;
-  if ((size_t)shots > p->llr_cap) {
-    cudaError_t e = cudaStreamSynchronize(d->st);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (p->d_llr) cudaFree(p->d_llr);
-    p->d_llr = nullptr;
-    p->llr_cap = 0;
-    if ((rc = prior_alloc((void**)&p->d_llr, sizeof(float) * (size_t)shots * d->n))) return rc;
-    p->llr_cap = (size_t)shots;
-  }
   // the fallback needs the status of every shot
   uint8_t* st = status;
   if (!st) return LSD_ERR_INVALID_ARG;
   if ((rc = reset_counters(d))) return rc;
   cudaEventRecord(d->ev[0], d->st);
-  cudaError_t e = launch_prior(false, p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
-                               nullptr, p->d_llr, nullptr, nullptr, nullptr, d->st);
-  d->launches++;
-  if (e == cudaSuccess)
-    e = launch_hard_check(d->g, shots, p->d_llr, syndromes, corrections, st, d->d_queue,
-                          d->d_queue_llr, d->d_ctr, d->st);
+  cudaError_t e = launch_prior_decode(p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
+                                      nullptr, corrections, st, d->d_queue, d->d_queue_llr,
+                                      d->d_ctr, d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   cudaEventRecord(d->ev[1], d->st);
@@ -896,6 +899,13 @@ extern "C" int lsd_autotune(lsd_decoder* d, int64_t shots, const uint8_t* syndro
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   int rc = e == cudaSuccess ? LSD_OK : cuda_fail(e);
+  // A candidate that fails at launch leaves the stream and the context usable; anything
+  // else (an error the stream reports) ends the search.
+  auto skippable = [&](int r) -> bool {
+    if (r != LSD_ERR_CUDA) return false;
+    cudaGetLastError();
+    return cudaStreamSynchronize(d->st) == cudaSuccess;
+  };
   auto timed = [&](auto&& fn, float* ms) -> int {
     float best = 0.f;
     for (int rep_i = 0; rep_i < 3; ++rep_i) {  // first run warms up; keep the best of the rest
@@ -932,6 +942,10 @@ extern "C" int lsd_autotune(lsd_decoder* d, int64_t shots, const uint8_t* syndro
       d->bp_smem = smem;
       float ms = 0.f;
       rc = timed([&]() { return lsd_bp_batch(d, shots, syndromes, post, nullptr, nullptr); }, &ms);
+      if (rc && skippable(rc)) {  // the candidate did not launch: drop it
+        rc = LSD_OK;
+        continue;
+      }
       if (rc) break;
       rep.bp_candidates++;
       if (v == v0) rep.ms_bp_first = ms;
@@ -970,6 +984,10 @@ extern "C" int lsd_autotune(lsd_decoder* d, int64_t shots, const uint8_t* syndro
       float ms = 0.f;
       rc = timed([&]() { return lsd_decode_batch(d, shots, syndromes, corr, st, nullptr, nullptr); },
                  &ms);
+      if (rc && skippable(rc)) {
+        rc = LSD_OK;
+        continue;
+      }
       if (rc) break;
       rep.lsd_candidates++;
       if (w == w0) rep.ms_lsd_first = ms;

@@ -300,36 +300,38 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
       unsigned unsat = 0;
       // ---- check phase: parity of [Lam^(t) < 0] and messages r^(t+1) ----
 #pragma unroll
+      // Sign bits stand for the comparisons "< 0": the priors are finite and never -0
+      // (0 < p < 1), so no Lam and no q = Lam - r is -0 or NaN.  The two smallest
+      // magnitudes come from min/max alone; the edge holding the minimum takes the second
+      // one (on a tie both are equal, as with a first-index rule).
       for (int c = 0; c < CPL; ++c) {
         const int i = lane + G * c;
         if (i >= m) continue;
-        const unsigned si = (sbits >> c) & 1u;
-        unsigned hp = si, sgn = si, negs = 0;
+        uint32_t hp = (sbits >> c) << 31;  // bit 31: syndrome ^ signs of Lam
+        uint32_t sx = hp;                   // bit 31: syndrome ^ signs of q
         float min1 = kBig, min2 = kBig;
-        int idx = 0;
+        float aq[DC];
+        uint32_t qb[DC];
         float* rc = r + i * DC;
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
           const int j = (cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff;
           const float L = Lam[j];
-          hp ^= (L < 0.f) ? 1u : 0u;
+          hp ^= __float_as_uint(L);
           const float q = __fsub_rn(L, rc[k]);
-          const float aq = fabsf(q);
-          const unsigned ng = (q < 0.f) ? 1u : 0u;
-          sgn ^= ng;
-          negs |= ng << k;
-          const bool lt1 = aq < min1;
-          min2 = lt1 ? min1 : fminf(min2, aq);
-          min1 = lt1 ? aq : min1;
-          idx = lt1 ? k : idx;
+          qb[k] = __float_as_uint(q);
+          sx ^= qb[k];
+          aq[k] = fabsf(q);
+          min2 = fminf(min2, fmaxf(min1, aq[k]));
+          min1 = fminf(min1, aq[k]);
         }
-        unsat |= hp;
+        unsat |= hp >> 31;
         if (msgs) {
           const float m1 = __fmul_rn(alpha, min1), m2 = __fmul_rn(alpha, min2);
 #pragma unroll
           for (int k = 0; k < DC; ++k) {
-            const float mag = (k == idx) ? m2 : m1;
-            rc[k] = ((sgn ^ (negs >> k)) & 1u) ? -mag : mag;
+            const float mag = (aq[k] == min1) ? m2 : m1;
+            rc[k] = __uint_as_float(__float_as_uint(mag) | ((sx ^ qb[k]) & 0x80000000u));
           }
         }
       }

@@ -838,6 +838,10 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
   *words = (g.m + 31) / 32;
   *warps_out = w;
   const void* fn = class_kernel(c, mu);
+  cudaFuncAttributes fa{};
+  err = cudaFuncGetAttributes(&fa, fn);
+  if (err != cudaSuccess) return err;
+  if (w * 32 > fa.maxThreadsPerBlock) return cudaErrorInvalidValue;
   err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;

@@ -92,6 +92,10 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
 
 // Lets `fn` use all the shared memory a block may opt into (the dynamic limit is a property
 // of the function, shared by every decoder; it excludes the function's static allocation).
+// Records the CUDA error behind an LSD_ERR_CUDA / LSD_ERR_OOM return for lsd_last_error()
+// (per host thread).
+void record_cuda_error(cudaError_t e);
+
 inline cudaError_t allow_max_dynamic_smem(const void* fn, int max_smem) {
   cudaFuncAttributes at{};
   cudaError_t e = cudaFuncGetAttributes(&at, fn);
@@ -114,9 +118,12 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int count,
 cudaError_t launch_sample(const DevGraph& g, const float* probs, unsigned long long seed,
                           long long first, long long shots, uint8_t* errors, uint8_t* syndromes,
                           cudaStream_t st);
-cudaError_t launch_hard_check(const DevGraph& g, long long shots, const float* llr,
-                              const uint8_t* syn, uint8_t* corr, uint8_t* status, int32_t* queue,
-                              float* queue_llr, DevCounters* ctr, cudaStream_t st);
+// Inference of the learned prior: LLRs into llr_out, or (llr_out null) decode mode, where the
+// kernel takes the hard decision itself and queues the shots it does not solve for LSD.
+cudaError_t launch_prior_decode(int grid, const DevGraph& g, int rounds, const float* params,
+                                long long shots, const uint8_t* syndromes, float* llr_out,
+                                uint8_t* corrections, uint8_t* status, int32_t* queue,
+                                float* queue_llr, DevCounters* ctr, cudaStream_t st);
 constexpr int kPriorMaxRounds = 8;
 
 // Decode whose shot count is read from device-visible memory at run time, so that one

@@ -690,64 +690,387 @@ __global__ void sample_kernel(unsigned long long seed, long long first, long lon
   }
 }
 
-// Hard decision of given LLRs: if [LLR < 0] satisfies the syndrome the shot is done
-// (status 1), otherwise it is appended to the LSD work queue with its LLR row.
-__global__ void hard_check_kernel(long long shots, int m, int n, const int32_t* __restrict__ chk_ptr,
-                                  const uint16_t* __restrict__ chk_var,
-                                  const float* __restrict__ llr, const uint8_t* __restrict__ syn,
-                                  uint8_t* __restrict__ corr, uint8_t* __restrict__ status,
-                                  int32_t* __restrict__ queue, float* __restrict__ queue_llr,
-                                  DevCounters* ctr) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  unsigned long long conv = 0;
-  for (long long shot = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-       shot < shots; shot += warps) {
-    const float* l = llr + shot * n;
-    const uint8_t* s = syn + shot * m;
-    bool bad = false;
-    for (int i = lane; i < m; i += 32) {
-      int par = s[i] ? 1 : 0;
-      for (int q = chk_ptr[i]; q < chk_ptr[i + 1]; ++q) par ^= l[chk_var[q]] < 0.f ? 1 : 0;
-      bad = bad || par;
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    if (!bad) {
-      for (int j = lane; j < n; j += 32) corr[shot * n + j] = l[j] < 0.f ? 1 : 0;
-      if (lane == 0) {
-        if (status) status[shot] = LSD_SHOT_OK_BP;
-        ++conv;
+
+
+// ======================================================================================
+// Forward-only kernel on per-node projections (inference).
+//
+// Split the layer-1 matrix of a direction by input block, W1 = [W_first | W_second | w_s]:
+//   W1 x_e + b1 = W_first h_first + W_second h_second + sigma_c w_s + b1,
+// so layer 1 needs one product per node, not per edge; and since layer 2 is affine, the
+// messages into a node sum to
+//   sum_e (W2 relu(z_e) + b2) = W2 (sum_e relu(z_e)) + deg * b2,
+// one product per destination node on the summed activations.  The model is unchanged
+// (same function, different rounding order).  With
+//   A_c = W1cv[:, 0:32] h_c + sigma_c W1cv[:, 64] + b1cv,   B_v = W1cv[:, 32:64] h_v,
+//   C_v = W1vc[:, 0:32] h_v,   D_c = W1vc[:, 32:64] h_c + sigma_c W1vc[:, 64] + b1vc,
+// one round is
+//   X2: S_v = sum_{c in N(v)} relu(A_c + B_v)          (gather, FP32)
+//   G1: h_v += W2cv S_v + deg_v b2cv;  C_v, B_v from the new h_v
+//   X1: T_c = sum_{v in N(c)} relu(C_v + D_c)
+//   G2: h_c += W2vc T_c + deg_c b2vc;  A_c, D_c from the new h_c
+// and the last round stops after G1 with LLR_v = lambda_v + w_o . h_v + b_o.  The G steps
+// run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation): a warp
+// owns 16 node rows, starts the accumulators from the FP32 state, and re-packs the updated
+// state from the accumulator fragments as the A operand of the projection product.
+// One CTA owns one shot at a time; all node arrays live in shared memory.
+// ======================================================================================
+
+constexpr int kFwdWarps = 8;
+
+struct FwdArgs {
+  int m, n, rounds;
+  const int32_t* chk_ptr;
+  const uint16_t* chk_var;
+  const int32_t* var_ptr;
+  const uint16_t* var_chk;
+  const float* prior;
+  const float* params;
+  long long shots;
+  const uint8_t* syndromes;
+  float* llr_out;          // [shots][n] output LLRs, or null in decode mode:
+  // decode mode: the hard decision [LLR < 0] of a shot that satisfies its syndrome is its
+  // correction (status LSD_SHOT_OK_BP); any other shot is queued for LSD with its LLR row
+  uint8_t* corrections;
+  uint8_t* status;
+  int32_t* queue;
+  float* queue_llr;
+  DevCounters* ctr;
+};
+
+struct FLay {
+  int npad, mpad;
+  size_t hv, hc, cv, bv, ac, dc, w, vec, sig, lam, degv, degc, llr, total;
+};
+
+// FP32 states h_v, h_c; BF16 projections C_v, B_v, A_c, D_c.  The summed activations S_v
+// (T_c) overwrite B_v (D_c) in place: each is read once, by the thread that then writes
+// the same columns of the same row.
+__host__ __device__ inline FLay fwd_layout(int m, int n) {
+  FLay L;
+  L.npad = (n + 15) & ~15;
+  L.mpad = (m + 15) & ~15;
+  const size_t fv = (size_t)L.npad * HD * 4, fc = (size_t)L.mpad * HD * 4;
+  size_t o = 0;
+  L.hv = o; o += fv;
+  L.hc = o; o += fc;
+  L.cv = o; o += fv / 2;
+  L.bv = o; o += fv / 2;
+  L.ac = o; o += fc / 2;
+  L.dc = o; o += fc / 2;
+  L.w = o; o += (size_t)6 * HD * HD * 2;   // W2cv | Wv (C rows, B rows) | W2vc | Wc (A, D rows)
+  L.vec = o; o += (size_t)12 * HD * 4;
+  L.sig = o; o += a16((size_t)L.mpad * 4);
+  L.lam = o; o += a16((size_t)L.npad * 4);
+  L.degv = o; o += a16((size_t)L.npad * 4);
+  L.degc = o; o += a16((size_t)L.mpad * 4);
+  L.llr = o; o += a16((size_t)L.npad * 4);
+  L.total = o;
+  return L;
+}
+
+// vec slots of the forward kernel (x32 floats each)
+enum { F_a0 = 0, F_a1, F_u0, F_u1, F_b2cv, F_b2vc, F_wscv, F_b1cv, F_wsvc, F_b1vc, F_wo, F_bo };
+
+// FP32 [rows][32] arrays: the 4-float block b of row r is stored at block b ^ 2(r & 3), so
+// the accumulator-fragment accesses (float2, rows r0+g, columns 8j+2t) and the gather
+// accesses (float4 per lane, 8 lanes per row) are free of bank conflicts.
+__device__ __forceinline__ int fsw(int r, int col) {
+  return (r << 5) + ((((col >> 2) ^ ((r & 3) << 1)) << 2) | (col & 3));
+}
+// BF16 [rows][32] arrays: the 8-value block b of row r is stored at block b ^ ((r >> 1) & 3)
+// (conflict-free 32-bit fragment loads).
+__device__ __forceinline__ int bsw(int r, int col) {
+  return (r << 5) + ((((col >> 3) ^ ((r >> 1) & 3)) << 3) | (col & 7));
+}
+
+__device__ __forceinline__ void fa_sw(uint32_t a[4], const __nv_bfloat16* base, int r0, int k0,
+                                      int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  a[0] = ld32(base + bsw(r0 + g, k0 + 2 * t));
+  a[1] = ld32(base + bsw(r0 + g + 8, k0 + 2 * t));
+  a[2] = ld32(base + bsw(r0 + g, k0 + 2 * t + 8));
+  a[3] = ld32(base + bsw(r0 + g + 8, k0 + 2 * t + 8));
+}
+__device__ __forceinline__ void fb_sw(uint32_t b[2], const __nv_bfloat16* base, int n0, int k0,
+                                      int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  b[0] = ld32(base + bsw(n0 + g, k0 + 2 * t));
+  b[1] = ld32(base + bsw(n0 + g, k0 + 2 * t + 8));
+}
+
+struct FwdSmem {
+  float *hv, *hc, *vec, *sig, *lam, *degv, *degc, *llr;
+  __nv_bfloat16 *cv, *bv, *ac, *dc, *W2cv, *Wv, *W2vc, *Wc;
+};
+
+// G step on node rows r0..r0+15 (CHECK: check nodes, else variable nodes).
+//   has_agg: h += W2 agg + deg b2 (written back; agg = T_c in dc, S_v in bv);  proj: the
+//   two projections of the new h into (ac, dc) or (cv, bv);  otherwise (variables, last
+//   round) the output LLRs.
+template <bool CHECK>
+__device__ __forceinline__ void g_step(const FwdSmem& S, int rows, int r0, bool has_agg, bool proj,
+                                       float* llr, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int ra = r0 + g, rb = r0 + g + 8;
+  float* h = CHECK ? S.hc : S.hv;
+  float c[4][4];
+  const float* b2 = S.vec + (CHECK ? F_b2vc : F_b2cv) * HD;
+  const float* deg = CHECK ? S.degc : S.degv;
+  const float da = has_agg ? deg[ra] : 0.f, db = has_agg ? deg[rb] : 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    const float2 x = *reinterpret_cast<const float2*>(h + fsw(ra, col));
+    const float2 y = *reinterpret_cast<const float2*>(h + fsw(rb, col));
+    c[nt][0] = fmaf(da, b2[col], x.x);
+    c[nt][1] = fmaf(da, b2[col + 1], x.y);
+    c[nt][2] = fmaf(db, b2[col], y.x);
+    c[nt][3] = fmaf(db, b2[col + 1], y.y);
+  }
+  if (has_agg) {
+    const __nv_bfloat16* W2 = CHECK ? S.W2vc : S.W2cv;
+    const __nv_bfloat16* agg = CHECK ? S.dc : S.bv;
+    uint32_t af[2][4];
+    fa_sw(af[0], agg, r0, 0, lane);
+    fa_sw(af[1], agg, r0, 16, lane);
+    __syncwarp();  // the aggregate rows are overwritten by this warp's projections below
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        uint32_t bf[2];
+        fb_sw(bf, W2, nt * 8, j * 16, lane);
+        mma16816(c[nt], af[j], bf);
       }
-    } else {
-      unsigned long long slot = 0;
-      if (lane == 0) slot = atomicAdd(&ctr->lsd_count, 1ULL);
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (lane == 0) queue[slot] = (int32_t)shot;
-      for (int j = lane; j < n; j += 32) queue_llr[slot * n + j] = l[j];
+      const int col = nt * 8 + 2 * t;
+      if (ra < rows) *reinterpret_cast<float2*>(h + fsw(ra, col)) = make_float2(c[nt][0], c[nt][1]);
+      if (rb < rows) *reinterpret_cast<float2*>(h + fsw(rb, col)) = make_float2(c[nt][2], c[nt][3]);
     }
   }
-  if (lane == 0 && conv) atomicAdd(&ctr->bp_converged, conv);
+  if (!proj) {  // variables, last round: LLR_v = lambda_v + w_o . h_v + b_o
+    const float* wo = S.vec + F_wo * HD;
+    float pa = 0.f, pb = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = nt * 8 + 2 * t;
+      pa = fmaf(c[nt][0], wo[col], fmaf(c[nt][1], wo[col + 1], pa));
+      pb = fmaf(c[nt][2], wo[col], fmaf(c[nt][3], wo[col + 1], pb));
+    }
+    pa += __shfl_xor_sync(0xffffffffu, pa, 1);
+    pa += __shfl_xor_sync(0xffffffffu, pa, 2);
+    pb += __shfl_xor_sync(0xffffffffu, pb, 1);
+    pb += __shfl_xor_sync(0xffffffffu, pb, 2);
+    const float bo = S.vec[F_bo * HD];
+    if (t == 0 && ra < rows) llr[ra] = S.lam[ra] + pa + bo;
+    if (t == 0 && rb < rows) llr[rb] = S.lam[rb] + pb + bo;
+    return;
+  }
+  uint32_t ah[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    ah[j][0] = pack2(c[2 * j][0], c[2 * j][1]);
+    ah[j][1] = pack2(c[2 * j][2], c[2 * j][3]);
+    ah[j][2] = pack2(c[2 * j + 1][0], c[2 * j + 1][1]);
+    ah[j][3] = pack2(c[2 * j + 1][2], c[2 * j + 1][3]);
+  }
+  const __nv_bfloat16* Wp = CHECK ? S.Wc : S.Wv;
+  const float sa = CHECK ? S.sig[ra] : 0.f, sb = CHECK ? S.sig[rb] : 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = (nt & 3) * 8 + 2 * t;
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    if (CHECK) {
+      const float* ws = S.vec + (nt < 4 ? F_wscv : F_wsvc) * HD;
+      const float* b1 = S.vec + (nt < 4 ? F_b1cv : F_b1vc) * HD;
+      u[0] = fmaf(sa, ws[col], b1[col]);
+      u[1] = fmaf(sa, ws[col + 1], b1[col + 1]);
+      u[2] = fmaf(sb, ws[col], b1[col]);
+      u[3] = fmaf(sb, ws[col + 1], b1[col + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint32_t bf[2];
+      fb_sw(bf, Wp, nt * 8, j * 16, lane);
+      mma16816(u, ah[j], bf);
+    }
+    __nv_bfloat16* P = nt < 4 ? (CHECK ? S.ac : S.cv) : (CHECK ? S.dc : S.bv);
+    if (ra < rows) *reinterpret_cast<uint32_t*>(P + bsw(ra, col)) = pack2(u[0], u[1]);
+    if (rb < rows) *reinterpret_cast<uint32_t*>(P + bsw(rb, col)) = pack2(u[2], u[3]);
+  }
+}
+
+__device__ __forceinline__ void unpack8(const uint4 v, float f[8]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+// Gather step: for each destination node d (4 lanes of 8 columns),
+//   dst_d <- sum_{s in N(d)} relu(src_s + dst_d)   (BF16 in, FP32 sum, BF16 out in place).
+__device__ __forceinline__ void x_step(int count, const int32_t* __restrict__ ptr,
+                                       const uint16_t* __restrict__ adj,
+                                       const __nv_bfloat16* src, __nv_bfloat16* dst) {
+  for (int i = threadIdx.x; i < count * 4; i += blockDim.x) {
+    const int d = i >> 2, b = i & 3;
+    uint4* dp = reinterpret_cast<uint4*>(dst + bsw(d, 8 * b));
+    float q[8], acc[8];
+    unpack8(*dp, q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    const int e1 = __ldg(ptr + d + 1);
+    for (int e = __ldg(ptr + d); e < e1; ++e) {
+      float p[8];
+      unpack8(*reinterpret_cast<const uint4*>(src + bsw(__ldg(adj + e), 8 * b)), p);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += fmaxf(p[k] + q[k], 0.f);
+    }
+    *dp = make_uint4(pack2(acc[0], acc[1]), pack2(acc[2], acc[3]), pack2(acc[4], acc[5]),
+                     pack2(acc[6], acc[7]));
+  }
+}
+
+__global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = a.m, n = a.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const FLay L = fwd_layout(m, n);
+  FwdSmem S;
+  S.hv = reinterpret_cast<float*>(smem + L.hv);
+  S.hc = reinterpret_cast<float*>(smem + L.hc);
+  S.cv = reinterpret_cast<__nv_bfloat16*>(smem + L.cv);
+  S.bv = reinterpret_cast<__nv_bfloat16*>(smem + L.bv);
+  S.ac = reinterpret_cast<__nv_bfloat16*>(smem + L.ac);
+  S.dc = reinterpret_cast<__nv_bfloat16*>(smem + L.dc);
+  S.W2cv = reinterpret_cast<__nv_bfloat16*>(smem + L.w);
+  S.Wv = S.W2cv + HD * HD;
+  S.W2vc = S.Wv + 2 * HD * HD;
+  S.Wc = S.W2vc + HD * HD;
+  S.vec = reinterpret_cast<float*>(smem + L.vec);
+  S.sig = reinterpret_cast<float*>(smem + L.sig);
+  S.lam = reinterpret_cast<float*>(smem + L.lam);
+  S.degv = reinterpret_cast<float*>(smem + L.degv);
+  S.degc = reinterpret_cast<float*>(smem + L.degc);
+  S.llr = reinterpret_cast<float*>(smem + L.llr);
+
+  // ---- parameters (BF16 weight tiles, FP32 vectors), graph degrees, zeroed padding ----
+  const float* P = a.params;
+  for (int i = threadIdx.x; i < HD * HD; i += blockDim.x) {
+    const int r = i >> 5, k = i & 31;
+    S.W2cv[bsw(r, k)] = __float2bfloat16_rn(P[POff::W2cv + r * HD + k]);
+    S.W2vc[bsw(r, k)] = __float2bfloat16_rn(P[POff::W2vc + r * HD + k]);
+    S.Wv[bsw(r, k)] = __float2bfloat16_rn(P[POff::W1vc + r * DIN + k]);            // C
+    S.Wv[bsw(r + HD, k)] = __float2bfloat16_rn(P[POff::W1cv + r * DIN + HD + k]);  // B
+    S.Wc[bsw(r, k)] = __float2bfloat16_rn(P[POff::W1cv + r * DIN + k]);            // A
+    S.Wc[bsw(r + HD, k)] = __float2bfloat16_rn(P[POff::W1vc + r * DIN + HD + k]);  // D
+  }
+  for (int i = threadIdx.x; i < HD; i += blockDim.x) {
+    S.vec[F_a0 * HD + i] = P[POff::a0 + i];
+    S.vec[F_a1 * HD + i] = P[POff::a1 + i];
+    S.vec[F_u0 * HD + i] = P[POff::u0 + i];
+    S.vec[F_u1 * HD + i] = P[POff::u1 + i];
+    S.vec[F_b2cv * HD + i] = P[POff::b2cv + i];
+    S.vec[F_b2vc * HD + i] = P[POff::b2vc + i];
+    S.vec[F_wscv * HD + i] = P[POff::W1cv + i * DIN + 2 * HD];
+    S.vec[F_b1cv * HD + i] = P[POff::b1cv + i];
+    S.vec[F_wsvc * HD + i] = P[POff::W1vc + i * DIN + 2 * HD];
+    S.vec[F_b1vc * HD + i] = P[POff::b1vc + i];
+    S.vec[F_wo * HD + i] = P[POff::wo + i];
+    S.vec[F_bo * HD + i] = i == 0 ? P[POff::bo] : 0.f;
+  }
+  for (int j = threadIdx.x; j < L.npad; j += blockDim.x) {
+    S.lam[j] = j < n ? a.prior[j] : 0.f;
+    S.degv[j] = j < n ? (float)(a.var_ptr[j + 1] - a.var_ptr[j]) : 0.f;
+  }
+  for (int i = threadIdx.x; i < L.mpad; i += blockDim.x) {
+    S.degc[i] = i < m ? (float)(a.chk_ptr[i + 1] - a.chk_ptr[i]) : 0.f;
+    S.sig[i] = 0.f;
+  }
+  // padding rows (read by the last 16-row tile, never written) stay zero
+  for (int i = n * HD + threadIdx.x; i < L.npad * HD; i += blockDim.x) S.hv[i] = 0.f;
+  for (int i = m * HD + threadIdx.x; i < L.mpad * HD; i += blockDim.x) S.hc[i] = 0.f;
+  for (int i = n * HD / 2 + threadIdx.x; i < L.npad * HD / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(S.bv)[i] = 0u;
+  for (int i = m * HD / 2 + threadIdx.x; i < L.mpad * HD / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(S.dc)[i] = 0u;
+  __syncthreads();
+  const int vt = L.npad >> 4, ct = L.mpad >> 4, R = a.rounds;
+
+  for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
+    const uint8_t* sp = a.syndromes + shot * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) S.sig[i] = sp[i] ? -1.f : 1.f;
+    for (int i = threadIdx.x; i < n * HD; i += blockDim.x) {
+      const int v = i >> 5, k = i & 31;
+      S.hv[fsw(v, k)] = fmaxf(fmaf(S.lam[v], S.vec[F_a0 * HD + k], S.vec[F_a1 * HD + k]), 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m * HD; i += blockDim.x) {
+      const int c = i >> 5, k = i & 31;
+      S.hc[fsw(c, k)] = fmaf(S.sig[c], S.vec[F_u0 * HD + k], S.vec[F_u1 * HD + k]);
+    }
+    __syncthreads();
+    // projections of the initial states
+    for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+      if (tile < vt) g_step<false>(S, n, tile * 16, false, true, nullptr, lane);
+      else g_step<true>(S, m, (tile - vt) * 16, false, true, nullptr, lane);
+    }
+    __syncthreads();
+    float* llr = a.llr_out ? a.llr_out + shot * n : S.llr;
+    for (int r = 0; r < R; ++r) {
+      x_step(n, a.var_ptr, a.var_chk, S.ac, S.bv);
+      __syncthreads();
+      const bool last = r == R - 1;
+      for (int tile = warp; tile < vt; tile += kFwdWarps)
+        g_step<false>(S, n, tile * 16, true, !last, llr, lane);
+      __syncthreads();
+      if (last) break;
+      x_step(m, a.chk_ptr, a.chk_var, S.cv, S.dc);
+      __syncthreads();
+      for (int tile = warp; tile < ct; tile += kFwdWarps)
+        g_step<true>(S, m, tile * 16, true, true, nullptr, lane);
+      __syncthreads();
+    }
+    if (a.llr_out) continue;
+    // ---- decode mode: hard decision of the LLRs ----
+    bool bad = false;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      unsigned par = sp[i] ? 1u : 0u;
+      const int e1 = __ldg(a.chk_ptr + i + 1);
+      for (int e = __ldg(a.chk_ptr + i); e < e1; ++e) par ^= S.llr[__ldg(a.chk_var + e)] < 0.f;
+      bad = bad || par;
+    }
+    if (__syncthreads_or(bad)) {
+      __shared__ unsigned long long s_slot;
+      if (threadIdx.x == 0) {
+        s_slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
+        a.queue[s_slot] = (int32_t)shot;
+      }
+      __syncthreads();
+      float* lo = a.queue_llr + (long long)s_slot * n;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) lo[j] = S.llr[j];
+    } else {
+      uint8_t* co = a.corrections + shot * n;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) co[j] = S.llr[j] < 0.f ? 1 : 0;
+      if (threadIdx.x == 0) {
+        if (a.status) a.status[shot] = LSD_SHOT_OK_BP;
+        atomicAdd(&a.ctr->bp_converged, 1ULL);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_hard_check(const DevGraph& g, long long shots, const float* llr,
-                              const uint8_t* syn, uint8_t* corr, uint8_t* status, int32_t* queue,
-                              float* queue_llr, DevCounters* ctr, cudaStream_t st) {
-  if (shots <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long blocks = (shots + 7) / 8;
-  if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-  hard_check_kernel<<<(int)blocks, 256, 0, st>>>(shots, g.m, g.n, g.chk_ptr, g.chk_var, llr, syn,
-                                                 corr, status, queue, queue_llr, ctr);
-  return cudaGetLastError();
-}
 
 int prior_num_params() { return POff::total; }
 
-size_t prior_smem(int m, int n, int E, bool train) { return prior_layout(m, n, E, train).total; }
+size_t prior_smem(int m, int n, int E, bool train) {
+  return train ? prior_layout(m, n, E, true).total : fwd_layout(m, n).total;
+}
 
 size_t prior_scratch_floats(int m, int n, int rounds, int grid) {
   return (size_t)grid * (rounds + 1) * (n + m) * HD;
@@ -761,21 +1084,56 @@ cudaError_t prior_config(int m, int n, int E, bool train, int* grid) {
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t smem = prior_smem(m, n, E, train);
   if (smem > (size_t)max_smem) return cudaErrorInvalidValue;
-  const void* fn = train ? (const void*)prior_kernel<true> : (const void*)prior_kernel<false>;
+  const void* fn = train ? (const void*)prior_kernel<true> : (const void*)prior_fwd_kernel;
+  const int threads = train ? kPriorThreads : kFwdWarps * 32;
   err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPriorThreads, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidValue;
   *grid = per_sm * sms;
   return cudaSuccess;
 }
 
+cudaError_t launch_prior_decode(int grid, const DevGraph& g, int rounds, const float* params,
+                                long long shots, const uint8_t* syndromes, float* llr_out,
+                                uint8_t* corrections, uint8_t* status, int32_t* queue,
+                                float* queue_llr, DevCounters* ctr, cudaStream_t st) {
+  if (!llr_out && (!corrections || !queue || !queue_llr || !ctr)) return cudaErrorInvalidValue;
+  FwdArgs f{};
+  f.m = g.m;
+  f.n = g.n;
+  f.rounds = rounds;
+  f.chk_ptr = g.chk_ptr;
+  f.chk_var = g.chk_var;
+  f.var_ptr = g.var_ptr;
+  f.var_chk = g.var_chk;
+  f.prior = g.prior;
+  f.params = params;
+  f.shots = shots;
+  f.syndromes = syndromes;
+  f.llr_out = llr_out;
+  f.corrections = corrections;
+  f.status = status;
+  f.queue = queue;
+  f.queue_llr = queue_llr;
+  f.ctr = ctr;
+  const long long blocks = shots < grid ? shots : grid;
+  if (blocks <= 0) return cudaSuccess;
+  prior_fwd_kernel<<<(int)blocks, kFwdWarps * 32, fwd_layout(g.m, g.n).total, st>>>(f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prior(bool train, int grid, const DevGraph& g, int rounds, const float* params,
                          long long shots, const uint8_t* syndromes, const uint8_t* errors,
                          float* llr_out, float* scratch, float* grads, double* loss,
                          cudaStream_t st) {
+  if (!train) {
+    if (!llr_out) return cudaErrorInvalidValue;
+    return launch_prior_decode(grid, g, rounds, params, shots, syndromes, llr_out, nullptr,
+                               nullptr, nullptr, nullptr, nullptr, st);
+  }
   PriorArgs a{};
   a.m = g.m;
   a.n = g.n;
@@ -796,10 +1154,7 @@ cudaError_t launch_prior(bool train, int grid, const DevGraph& g, int rounds, co
   const size_t smem = prior_smem(g.m, g.n, g.E, train);
   const long long blocks = shots < grid ? shots : grid;
   if (blocks <= 0) return cudaSuccess;
-  if (train)
-    prior_kernel<true><<<(int)blocks, kPriorThreads, smem, st>>>(a);
-  else
-    prior_kernel<false><<<(int)blocks, kPriorThreads, smem, st>>>(a);
+  prior_kernel<true><<<(int)blocks, kPriorThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -120,7 +120,11 @@ struct lsd_server {
 
 namespace {
 
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? LSD_OK : (e == cudaErrorMemoryAllocation ? LSD_ERR_OOM : LSD_ERR_CUDA); }
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return LSD_OK;
+  lsdgb::record_cuda_error(e);
+  return e == cudaErrorMemoryAllocation ? LSD_ERR_OOM : LSD_ERR_CUDA;
+}
 
 // The GPU reads request buffers directly: they must be page-locked host memory or device
 // (or managed) memory.

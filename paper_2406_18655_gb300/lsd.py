@@ -33,12 +33,16 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_prior_gradient", "lsd_prior_train_step", "lsd_decode_learned",
            "lsd_prior_destroy", "lsd_sample", "lsd_server_create", "lsd_server_submit",
            "lsd_server_wait_all", "lsd_server_get_report", "lsd_server_run_poisson",
-           "lsd_server_destroy", "lsd_autotune")
+           "lsd_server_destroy", "lsd_autotune", "lsd_last_error")
 
 
 class LsdError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {status_string(code)} ({code})")
+        detail = ""
+        if code in (LSD_ERR_CUDA, LSD_ERR_OOM):
+            detail = lib().lsd_last_error().decode()
+            detail = f" [{detail}]" if detail else ""
+        super().__init__(f"{what}: {status_string(code)} ({code}){detail}")
         self.code = code
 
 
@@ -110,7 +114,8 @@ def lib():
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
-        getattr(L, name).restype = C.c_int if name != "lsd_status_string" else C.c_char_p
+        getattr(L, name).restype = (C.c_char_p if name in ("lsd_status_string", "lsd_last_error")
+                                    else C.c_int)
     _lib = L
     return L
 

@@ -29,6 +29,12 @@ def code(name):
             h[i, i - 1] = h[i, i] = 1
     elif name == "hgp":
         h = I.hgp_48x64()[0]
+    elif name == "irreg_37x61":
+        # irregular degrees, sizes off the 16-row tiles: column j has weight 1 + j % 4
+        rng = np.random.default_rng(5)
+        h = np.zeros((37, 61), np.uint8)
+        for j in range(61):
+            h[rng.choice(37, 1 + j % 4, replace=False), j] = 1
     else:
         raise KeyError(name)
     _CACHE[name] = h

@@ -58,17 +58,21 @@ def test_sampler_matches_host_generator(L):
     assert np.array_equal(s.cpu().numpy(), I.syndromes(h, e_host))
 
 
-@pytest.mark.parametrize("name", ["bb72", "bb144"])
-def test_forward_matches_oracle(L, name):
+@pytest.mark.parametrize("name,rounds", [("bb72", 4), ("bb144", 4), ("bb288", 4),
+                                         ("irreg_37x61", 1), ("irreg_37x61", 3)])
+def test_forward_matches_oracle(L, name, rounds):
+    """The inference kernel (per-node projections) against the oracle's per-edge MLPs:
+    several 16-row tiles with a ragged last tile, irregular degrees, 1 to 4 rounds."""
     h, probs, e, s = sample(name, 0.06, 64, seed=11)
     theta = params_case(3)
     d = L.Decoder(h, probs, 10)
-    pr = L.Prior(d, rounds=4, params=theta.astype(np.float32))
+    pr = L.Prior(d, rounds=rounds, params=theta.astype(np.float32))
     llr = pr.forward(torch.from_numpy(s).cuda()).cpu().numpy().astype(np.float64)
     lam = np.log((1 - probs.astype(np.float64)) / probs.astype(np.float64))
-    ref, _ = P.forward(P.Graph(h), theta.astype(np.float32).astype(np.float64), s, lam)
+    ref, _ = P.forward(P.Graph(h), theta.astype(np.float32).astype(np.float64), s, lam,
+                       rounds=rounds)
     err = np.abs(llr - ref) / np.maximum(1.0, np.abs(ref))
-    print(f"forward {name}: max rel err {err.max():.3e}, mean {err.mean():.3e}")
+    print(f"forward {name} R={rounds}: max rel err {err.max():.3e}, mean {err.mean():.3e}")
     assert err.max() <= 5e-3
 
 
