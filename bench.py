@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--sweep-iters", default="3,5,8,10,12,14,16,20,30,50",
                     help="BP iteration counts of the equal-LER sweep")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true",
+                    help="skip the p sweep (BB144, LSD-0/6) and the HGP legs")
+    ap.add_argument("--hgp-shots", type=int, default=100_000)
     ap.add_argument("--serving-loads", default="1e4,1e5,1e6,1e7",
                     help="offered loads (shots/s) of the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=0.5)
@@ -295,6 +298,77 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
     return learned
 
 
+def _timed_decode(dec, s_dev, corr, status, steps, stream, flush, barrier):
+    for _ in range(2):
+        dec.decode(s_dev, corr, status)
+    ms = timed_steps(lambda: dec.decode(s_dev, corr, status), steps, stream, flush, barrier)
+    _, _, st = dec.decode(s_dev, corr, status, want_stats=True)
+    return ms, st
+
+
+def p_sweep_leg(args, hx, hz, stream, flush, barrier, checker):
+    """BB[[144,12,12]], p in {0.01, ..., 0.10}, 10^6 shots per p, BP 50 + LSD-0 and LSD-6."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.lsd import Decoder
+    n = hx.shape[1]
+    out = []
+    for p in (0.01, 0.02, 0.04, 0.06, 0.08, 0.10):
+        probs = np.full(n, p, np.float32)
+        e = I.sample_errors(args.seed + int(p * 1000), args.shots, probs.astype(np.float64))
+        s_dev = torch.from_numpy(I.syndromes(hx, e)).cuda()
+        e_dev = torch.from_numpy(e).cuda()
+        corr = torch.empty((args.shots, n), dtype=torch.uint8, device="cuda")
+        status = torch.empty(args.shots, dtype=torch.uint8, device="cuda")
+        for order in (0, 6):
+            dec = Decoder(hx, probs, args.iters, order, stream=stream)
+            dec.autotune(s_dev[: min(args.shots, 200_000)])
+            ms, st = _timed_decode(dec, s_dev, corr, status, 3, stream, flush, barrier)
+            ler = float(checker.failures(e_dev, corr).float().mean().item())
+            out.append({"p": p, "lsd_order": order, "shots_per_s": args.shots / (np.mean(ms) / 1e3),
+                        "ms_per_step": float(np.mean(ms)), "p99_ms": float(np.percentile(ms, 99)),
+                        "ler": ler, "lsd_frac": st["lsd_shots"] / args.shots,
+                        "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
+                        "kappa_max": st["kappa_max"], "nu_max": st["nu_max"]})
+            dec.close()
+    return {"code": "BB[[144,12,12]]", "shots_per_p": args.shots, "bp_iters": args.iters,
+            "points": out}
+
+
+def hgp_leg(args, stream, flush, barrier):
+    """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
+    {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.evaluate import LogicalChecker
+    from paper_2406_18655_gb300.lsd import Decoder
+    hx, hz = I.hgp_48x64()
+    n = hx.shape[1]
+    checker = LogicalChecker(hz)
+    out = []
+    for p, shots in ((0.02, args.hgp_shots), (0.05, max(1, args.hgp_shots // 20))):
+        probs = np.full(n, p, np.float32)
+        for order in (0, 10):
+            dec = Decoder(hx, probs, 100, order, stream=stream)
+            e, s_dev = dec.sample(args.seed + int(p * 1000), shots)
+            corr = torch.empty((shots, n), dtype=torch.uint8, device="cuda")
+            status = torch.empty(shots, dtype=torch.uint8, device="cuda")
+            ms, st = _timed_decode(dec, s_dev, corr, status, 2, stream, flush, barrier)
+            ler = float(checker.failures(e, corr).float().mean().item())
+            out.append({"p": p, "lsd_order": order, "shots": shots,
+                        "shots_per_s": shots / (np.mean(ms) / 1e3),
+                        "ms_per_step": float(np.mean(ms)), "ler": ler,
+                        "bp_converged_frac": st["bp_converged"] / shots,
+                        "lsd_frac": st["lsd_shots"] / shots, "lsd_spilled": st["lsd_spilled"],
+                        "mean_bp_iters": st["bp_iterations"] / shots,
+                        "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
+                        "kappa_max": st["kappa_max"], "nu_max": st["nu_max"]})
+            dec.close()
+    return {"code": "HGP of a seeded (3,4)-regular 48x64 matrix, H_X 3072x6400, E=21504",
+            "bp_iters": 100, "note": "p = 0.05 percolates: fewer shots (shots / 20)",
+            "points": out}
+
+
 def serving_leg(args):
     """Poisson arrivals mixing the space-time matrices of the BB [[72,12,6]], [[144,12,12]]
     and [[288,12,18]] codes (phenomenological noise p = q = 0.003 over d = 6, 12, 18 noisy
@@ -428,7 +502,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(args.shots * m),
                "d2h_bytes_per_step": int(args.shots * (n + 1))}
 
-    serving = None
+    serving = p_sweep = hgp = None
+    if rank == 0 and not args.no_sweeps:
+        p_sweep = p_sweep_leg(args, hx, hz, stream, flush, barrier, checker)
+        hgp = hgp_leg(args, stream, flush, barrier)
     if not args.no_serving and rank == 0:
         serving = serving_leg(args)
 
@@ -477,6 +554,8 @@ def run_ours(args):
         "autotune": tune,
         "clocks": clk.summary(),
         "learned": learned,
+        "p_sweep": p_sweep,
+        "hgp": hgp,
         "serving": serving,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -100,6 +100,7 @@ struct Graph {
   const uint16_t* chk_var;
   const int32_t* var_ptr;
   const uint16_t* var_chk;
+  int max_col_deg;
 };
 
 // Accessors of one warp's shot state: one base pointer plus compile-time offsets.
@@ -141,11 +142,13 @@ struct Shot {
 
 // Order key of fault j: (LLR ascending, index ascending).  -0.0 is folded into +0.0 so that
 // the key order is the float order, with ties broken by the index.
-__device__ __forceinline__ unsigned long long llr_key(float x, int j) {
+__device__ __forceinline__ unsigned llr_bits(float x) {
   x = __fadd_rn(x, 0.0f);
-  unsigned u = __float_as_uint(x);
-  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-  return ((unsigned long long)u << 32) | (unsigned)j;
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long llr_key(float x, int j) {
+  return ((unsigned long long)llr_bits(x) << 32) | (unsigned)j;
 }
 
 __device__ __forceinline__ int uf_find(const volatile int* parent, int x) {
@@ -364,35 +367,43 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     __syncwarp();
     return (strict && none) ? 1 : 2;
   }
-  if (lane == 0) {
-    S.scal()[0] = 0;  // new faults
-    S.scal()[3] = 0;  // merged labels
-    S.scal()[4] = 0;  // newly claimed detectors
-  }
+  if (lane == 0) S.scal()[3] = 0;  // merged labels
   __syncwarp();
   // ---- parallel_union: apply every pick, merge clusters sharing a detector or a fault ----
-  for (int t = lane; t < k; t += 32) {
-    const int r = S.inv()[t];
-    const unsigned rk = S.best()[r];
-    if (rk == kNone) continue;
-    const int gcol = S.fat()[rk];
-    const int old = atomicCAS(&S.flab()[gcol], -1, r);
-    if (old == -1) {
-      const int slot = atomicAdd(&S.scal()[0], 1);
-      S.newr()[slot] = (uint16_t)rk;
-    } else {
-      uf_unite(S, r, old);
+  // (the lists of new faults and newly claimed detectors are filled by ballots)
+  const unsigned below = (1u << lane) - 1u;
+  int n_new = 0, n_det = 0;
+  for (int base = 0; base < k; base += 32) {
+    const int t = base + lane;
+    const int r = t < k ? S.inv()[t] : 0;
+    const unsigned rk = t < k ? S.best()[r] : kNone;
+    const bool pick = rk != kNone;
+    int gcol = 0, q0 = 0, q1 = 0;
+    bool fresh = false;
+    if (pick) {
+      gcol = S.fat()[rk];
+      const int old = atomicCAS(&S.flab()[gcol], -1, r);
+      fresh = old == -1;
+      if (!fresh) uf_unite(S, r, old);
+      q0 = G.var_ptr[gcol];
+      q1 = G.var_ptr[gcol + 1];
     }
-    const int v1 = G.var_ptr[gcol + 1];
-    for (int q = G.var_ptr[gcol]; q < v1; ++q) {
-      const int d = G.var_chk[q];
-      const int o = atomicCAS(&S.dlab()[d], -1, r);
-      if (o == -1) {
-        const int slot = atomicAdd(&S.scal()[4], 1);
-        S.dnew()[slot] = (uint16_t)d;
-      } else if (o != r) {
-        uf_unite(S, r, o);
+    const unsigned bf = __ballot_sync(kFull, fresh);
+    if (fresh) S.newr()[n_new + __popc(bf & below)] = (uint16_t)rk;
+    n_new += __popc(bf);
+    for (int qq = 0; qq < G.max_col_deg; ++qq) {
+      const int q = q0 + qq;
+      int d = 0;
+      bool claim = false;
+      if (q < q1) {
+        d = G.var_chk[q];
+        const int o = atomicCAS(&S.dlab()[d], -1, r);
+        claim = o == -1;
+        if (!claim && o != r) uf_unite(S, r, o);
       }
+      const unsigned bd = __ballot_sync(kFull, claim);
+      if (claim) S.dnew()[n_det + __popc(bd & below)] = (uint16_t)d;
+      n_det += __popc(bd);
     }
   }
   __syncwarp();
@@ -410,7 +421,7 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
   if constexpr (L::kMasks) {
     // fold the masks of merged labels into their roots; add the free faults next to the
     // newly claimed detectors
-    const int nm = merged, nd = S.scal()[4];
+    const int nm = merged, nd = n_det;
     for (int idx = lane; idx < nm * Wn; idx += 32) {
       const int x = S.mlist()[idx / Wn], w = idx % Wn;
       const uint32_t v = S.cand()[(size_t)x * Wn + w];
@@ -430,7 +441,7 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     }
     __syncwarp();
     // the step's new faults are no longer candidates
-    const int nn = S.scal()[0];
+    const int nn = n_new;
     for (int t = lane; t < nn; t += 32) {
       const unsigned rk = S.newr()[t];
       const int root = S.parent()[S.flab()[S.fat()[rk]]];
@@ -439,7 +450,6 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     __syncwarp();
   }
   // ---- the step's new columns in reliability (rank) order ----
-  const int n_new = S.scal()[0];
   for (int t = lane; t < n_new; t += 32) {
     const unsigned kt = S.newr()[t];
     int pos = 0;
@@ -571,11 +581,13 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int graph_smem) {
     G.var_ptr = vp;
     G.chk_var = cv;
     G.var_chk = vc;
+    G.max_col_deg = a.g.max_col_deg;
   } else {
     G.chk_ptr = a.g.chk_ptr;
     G.var_ptr = a.g.var_ptr;
     G.chk_var = a.g.chk_var;
     G.var_chk = a.g.var_chk;
+    G.max_col_deg = a.g.max_col_deg;
   }
   Shot<L> S{smem + (size_t)warp * L::total};
 
@@ -593,23 +605,31 @@ __global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int graph_smem) {
 
     // ---- the shot's reliability order ----
     if constexpr (L::kShuffleRank) {
-      // rank of each key = number of smaller keys, counted with shuffles (keys are distinct)
+      // rank of fault j = number of keys (bits', j') before (bits, j), counted with shuffles
+      // of the 32-bit LLR bits; the index tie-break is known from the positions: fault
+      // j' = src + 32 t2 precedes j = lane + 32 t on equal bits iff t2 < t, or t2 == t and
+      // src < lane.  Padding entries (j >= n) carry the largest bits and the largest index.
       constexpr int KPL = (NN + 31) / 32;
-      unsigned long long myk[KPL];
+      unsigned myk[KPL];
       int rk[KPL];
 #pragma unroll
       for (int t = 0; t < KPL; ++t) {
         const int j = lane + 32 * t;
-        myk[t] = j < n ? llr_key(lsrc[j], j) : ~0ull;
+        myk[t] = j < n ? llr_bits(lsrc[j]) : 0xffffffffu;
         rk[t] = 0;
       }
-#pragma unroll 4
+#pragma unroll 2
       for (int src = 0; src < 32; ++src) {
+        const bool before = src < lane;
 #pragma unroll
         for (int t2 = 0; t2 < KPL; ++t2) {
-          const unsigned long long other = __shfl_sync(kFull, myk[t2], src);
+          const unsigned other = __shfl_sync(kFull, myk[t2], src);
 #pragma unroll
-          for (int t = 0; t < KPL; ++t) rk[t] += (other < myk[t]) ? 1 : 0;
+          for (int t = 0; t < KPL; ++t) {
+            if (t2 < t) rk[t] += (other <= myk[t]) ? 1 : 0;
+            else if (t2 > t) rk[t] += (other < myk[t]) ? 1 : 0;
+            else rk[t] += (other < myk[t] || (before && other == myk[t])) ? 1 : 0;
+          }
         }
       }
 #pragma unroll

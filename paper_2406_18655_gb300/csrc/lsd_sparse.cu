@@ -205,11 +205,16 @@ __device__ int collect_all(const SShot<L>& S, int lane) {
 
 // Adds fault g (order key `key`) to its cluster's factorization, rows in slot space.  Lane l
 // holds words l, l+32, ... of the column being reduced.
+// Only the first wc = ceil(slots / 32) words of a row can be nonzero: rows are written in
+// full (zeros past the slots in use) when they become pivots, and every later update XORs
+// rows that are zero there too.
 template <class L, bool MU, int CAP>
 __device__ void add_column(const SGraph& G, const SShot<L>& S, int g, unsigned long long key,
                            int lane) {
   constexpr int W = L::W;
   constexpr int WC = (W + 31) / 32;
+  const int nsl = min(S.scal()[S_SLOTS], CAP);
+  const int wc = (nsl + 31) >> 5;
   uint32_t bw[WC], tw[WC];
 #pragma unroll
   for (int c = 0; c < WC; ++c) bw[c] = tw[c] = 0;
@@ -220,7 +225,7 @@ __device__ void add_column(const SGraph& G, const SShot<L>& S, int g, unsigned l
 #pragma unroll
     for (int c = 0; c < WC; ++c) {
       const int w = c * 32 + lane;
-      if (w < W) {
+      if (w < wc) {
         if ((sl >> 5) == w) bw[c] ^= 1u << (sl & 31);
         if (piv) {
           bw[c] ^= S.R()[sl * W + w];
@@ -276,13 +281,22 @@ __device__ void add_column(const SGraph& G, const SShot<L>& S, int g, unsigned l
   }
   if (lane == 0) S.pcol()[p] = g;
   __syncwarp();
-  const int nsl = min(S.scal()[S_SLOTS], CAP);
-  for (int d = lane; d < nsl; d += 32) {
-    if (d == p || S.pcol()[d] < 0) continue;
-    if (S.R()[d * W + pw] & pb) {
-      for (int w = 0; w < W; ++w) {
-        S.R()[d * W + w] ^= S.R()[p * W + w];
-        S.T()[d * W + w] ^= S.T()[p * W + w];
+  // back-elimination: rows holding bit p found by ballot, each XORed by the whole warp
+  // (lane = word) with the new pivot row, which the lanes still hold in registers
+  for (int d0 = 0; d0 < nsl; d0 += 32) {
+    const int d = d0 + lane;
+    const bool hit = d < nsl && d != p && S.pcol()[d] >= 0 && (S.R()[d * W + pw] & pb) != 0;
+    unsigned bal = __ballot_sync(kFull, hit);
+    while (bal) {
+      const int dd = d0 + __ffs(bal) - 1;
+      bal &= bal - 1;
+#pragma unroll
+      for (int c = 0; c < WC; ++c) {
+        const int w = c * 32 + lane;
+        if (w < wc) {
+          S.R()[dd * W + w] ^= bw[c];
+          S.T()[dd * W + w] ^= tw[c];
+        }
       }
     }
   }
