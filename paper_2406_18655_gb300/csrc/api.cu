@@ -31,6 +31,9 @@ struct lsd_decoder {
   size_t cap_shots = 0;
   uint8_t* d_stage = nullptr;  // host-buffer entry point: syndromes | corrections | status
   size_t stage_cap = 0;
+  // host-buffer entry point: copy streams and per-chunk events of the pipelined path
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  cudaEvent_t cev[2 * 8] = {};
   // launch shapes
   int bp_variant = -1, bp_grid = 0, bp_block = 0;
   size_t bp_smem = 0;
@@ -246,6 +249,13 @@ int lsd_destroy(lsd_decoder* d) {
   if (d->h_ctr) cudaFreeHost(d->h_ctr);
   for (auto& e : d->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaStream_t c : {d->cp_in, d->cp_out})
+    if (c) {
+      cudaStreamSynchronize(c);
+      cudaStreamDestroy(c);
+    }
+  for (auto& e : d->cev)
+    if (e) cudaEventDestroy(e);
   cudaGetLastError();
   delete d;
   return LSD_OK;
@@ -458,6 +468,44 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
   uint8_t* dsyn = d->d_stage;
   uint8_t* dcor = dsyn + (size_t)shots * d->m;
   uint8_t* dst = dcor + (size_t)shots * d->n;
+  // Large batches without statistics run as a pipeline of chunks: chunk i+1's syndromes
+  // copy in and chunk i-1's corrections copy out (two copy streams) while chunk i decodes.
+  constexpr int64_t kMinChunk = 65536;
+  constexpr int kMaxChunks = 8;
+  const int chunks = (int)std::min<int64_t>(kMaxChunks, shots / kMinChunk);
+  if (!stats && chunks >= 2) {
+    cudaError_t e = cudaSuccess;
+    if (!d->cp_in) e = cudaStreamCreateWithFlags(&d->cp_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !d->cp_out) e = cudaStreamCreateWithFlags(&d->cp_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 * kMaxChunks && e == cudaSuccess; ++i)
+      if (!d->cev[i]) e = cudaEventCreateWithFlags(&d->cev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int64_t base = 0;
+    for (int i = 0; i < chunks; ++i) {
+      const int64_t cnt = shots * (i + 1) / chunks - base;
+      const size_t sm = (size_t)base * d->m, sn = (size_t)base * d->n;
+      e = cudaMemcpyAsync(dsyn + sm, syndromes + sm, (size_t)cnt * d->m, cudaMemcpyHostToDevice,
+                          d->cp_in);
+      if (e == cudaSuccess) e = cudaEventRecord(d->cev[2 * i], d->cp_in);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->st, d->cev[2 * i], 0);
+      if (e != cudaSuccess) return cuda_fail(e);
+      const int rc = lsd_decode_batch(d, cnt, dsyn + sm, dcor + sn, dst + base, nullptr, nullptr);
+      if (rc) return rc;
+      e = cudaEventRecord(d->cev[2 * i + 1], d->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->cp_out, d->cev[2 * i + 1], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(corrections + sn, dcor + sn, (size_t)cnt * d->n,
+                            cudaMemcpyDeviceToHost, d->cp_out);
+      if (e == cudaSuccess && status)
+        e = cudaMemcpyAsync(status + base, dst + base, (size_t)cnt, cudaMemcpyDeviceToHost,
+                            d->cp_out);
+      if (e != cudaSuccess) return cuda_fail(e);
+      base += cnt;
+    }
+    e = cudaStreamSynchronize(d->cp_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+    return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+  }
   cudaError_t e = cudaMemcpyAsync(dsyn, syndromes, (size_t)shots * d->m, cudaMemcpyHostToDevice,
                                   d->st);
   if (e != cudaSuccess) return cuda_fail(e);

@@ -808,25 +808,61 @@ struct FwdSmem {
 //   has_agg: h += W2 agg + deg b2 (written back; agg = T_c in dc, S_v in bv);  proj: the
 //   two projections of the new h into (ac, dc) or (cv, bv);  otherwise (variables, last
 //   round) the output LLRs.
+//   init (syn != null): the initial states h_v = relu(lambda_v a0 + a1), h_c = sigma_c u0 + u1
+//   are formed in registers (and sigma_c recorded) instead of read.
 template <bool CHECK>
 __device__ __forceinline__ void g_step(const FwdSmem& S, int rows, int r0, bool has_agg, bool proj,
-                                       float* llr, int lane) {
+                                       float* llr, int lane, const uint8_t* syn = nullptr) {
   const int g = lane >> 2, t = lane & 3;
   const int ra = r0 + g, rb = r0 + g + 8;
   float* h = CHECK ? S.hc : S.hv;
   float c[4][4];
-  const float* b2 = S.vec + (CHECK ? F_b2vc : F_b2cv) * HD;
-  const float* deg = CHECK ? S.degc : S.degv;
-  const float da = has_agg ? deg[ra] : 0.f, db = has_agg ? deg[rb] : 0.f;
+  if (syn) {
+    float xa = 0.f, xb = 0.f;  // lambda_v or sigma_c of the two rows (0 on padding rows)
+    if (CHECK) {
+      xa = ra < rows ? (syn[ra] ? -1.f : 1.f) : 0.f;
+      xb = rb < rows ? (syn[rb] ? -1.f : 1.f) : 0.f;
+      if (t == 0) {
+        S.sig[ra] = xa;
+        S.sig[rb] = xb;
+      }
+    } else {
+      xa = S.lam[ra];
+      xb = S.lam[rb];
+    }
+    const float* w0 = S.vec + (CHECK ? F_u0 : F_a0) * HD;
+    const float* w1 = S.vec + (CHECK ? F_u1 : F_a1) * HD;
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int col = nt * 8 + 2 * t;
-    const float2 x = *reinterpret_cast<const float2*>(h + fsw(ra, col));
-    const float2 y = *reinterpret_cast<const float2*>(h + fsw(rb, col));
-    c[nt][0] = fmaf(da, b2[col], x.x);
-    c[nt][1] = fmaf(da, b2[col + 1], x.y);
-    c[nt][2] = fmaf(db, b2[col], y.x);
-    c[nt][3] = fmaf(db, b2[col + 1], y.y);
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int col = nt * 8 + 2 * t + q;
+        float za = fmaf(xa, w0[col], w1[col]), zb = fmaf(xb, w0[col], w1[col]);
+        if (!CHECK) {
+          za = fmaxf(za, 0.f);
+          zb = fmaxf(zb, 0.f);
+        }
+        c[nt][q] = ra < rows ? za : 0.f;
+        c[nt][2 + q] = rb < rows ? zb : 0.f;
+      }
+      const int col = nt * 8 + 2 * t;
+      if (ra < rows) *reinterpret_cast<float2*>(h + fsw(ra, col)) = make_float2(c[nt][0], c[nt][1]);
+      if (rb < rows) *reinterpret_cast<float2*>(h + fsw(rb, col)) = make_float2(c[nt][2], c[nt][3]);
+    }
+  } else {
+    const float* b2 = S.vec + (CHECK ? F_b2vc : F_b2cv) * HD;
+    const float* deg = CHECK ? S.degc : S.degv;
+    const float da = has_agg ? deg[ra] : 0.f, db = has_agg ? deg[rb] : 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = nt * 8 + 2 * t;
+      const float2 x = *reinterpret_cast<const float2*>(h + fsw(ra, col));
+      const float2 y = *reinterpret_cast<const float2*>(h + fsw(rb, col));
+      c[nt][0] = fmaf(da, b2[col], x.x);
+      c[nt][1] = fmaf(da, b2[col + 1], x.y);
+      c[nt][2] = fmaf(db, b2[col], y.x);
+      c[nt][3] = fmaf(db, b2[col + 1], y.y);
+    }
   }
   if (has_agg) {
     const __nv_bfloat16* W2 = CHECK ? S.W2vc : S.W2cv;
@@ -909,13 +945,14 @@ __device__ __forceinline__ void unpack8(const uint4 v, float f[8]) {
   }
 }
 
-// Gather step: for each destination node d (4 lanes of 8 columns),
-//   dst_d <- sum_{s in N(d)} relu(src_s + dst_d)   (BF16 in, FP32 sum, BF16 out in place).
-__device__ __forceinline__ void x_step(int count, const int32_t* __restrict__ ptr,
+// The gather step for the 16 destination rows r0..r0+15 of one warp (4 lanes per row).
+__device__ __forceinline__ void x_tile(int count, int r0, const int32_t* __restrict__ ptr,
                                        const uint16_t* __restrict__ adj,
-                                       const __nv_bfloat16* src, __nv_bfloat16* dst) {
-  for (int i = threadIdx.x; i < count * 4; i += blockDim.x) {
-    const int d = i >> 2, b = i & 3;
+                                       const __nv_bfloat16* src, __nv_bfloat16* dst, int lane) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int task = lane + 32 * i, d = r0 + (task >> 2), b = task & 3;
+    if (d >= count) continue;
     uint4* dp = reinterpret_cast<uint4*>(dst + bsw(d, 8 * b));
     float q[8], acc[8];
     unpack8(*dp, q);
@@ -931,6 +968,7 @@ __device__ __forceinline__ void x_step(int count, const int32_t* __restrict__ pt
     *dp = make_uint4(pack2(acc[0], acc[1]), pack2(acc[2], acc[3]), pack2(acc[4], acc[5]),
                      pack2(acc[6], acc[7]));
   }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a) {
@@ -1001,36 +1039,27 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a)
 
   for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
     const uint8_t* sp = a.syndromes + shot * m;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) S.sig[i] = sp[i] ? -1.f : 1.f;
-    for (int i = threadIdx.x; i < n * HD; i += blockDim.x) {
-      const int v = i >> 5, k = i & 31;
-      S.hv[fsw(v, k)] = fmaxf(fmaf(S.lam[v], S.vec[F_a0 * HD + k], S.vec[F_a1 * HD + k]), 0.f);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m * HD; i += blockDim.x) {
-      const int c = i >> 5, k = i & 31;
-      S.hc[fsw(c, k)] = fmaf(S.sig[c], S.vec[F_u0 * HD + k], S.vec[F_u1 * HD + k]);
-    }
-    __syncthreads();
-    // projections of the initial states
+    // initial states and their projections, one 16-row tile per warp
     for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
-      if (tile < vt) g_step<false>(S, n, tile * 16, false, true, nullptr, lane);
-      else g_step<true>(S, m, (tile - vt) * 16, false, true, nullptr, lane);
+      if (tile < vt) g_step<false>(S, n, tile * 16, false, true, nullptr, lane, sp);
+      else g_step<true>(S, m, (tile - vt) * 16, false, true, nullptr, lane, sp);
     }
     __syncthreads();
     float* llr = a.llr_out ? a.llr_out + shot * n : S.llr;
+    // a round: each warp gathers the aggregates of its own rows and updates them at once
+    // (the gathers read the other node type's projections, complete after the barrier)
     for (int r = 0; r < R; ++r) {
-      x_step(n, a.var_ptr, a.var_chk, S.ac, S.bv);
-      __syncthreads();
       const bool last = r == R - 1;
-      for (int tile = warp; tile < vt; tile += kFwdWarps)
+      for (int tile = warp; tile < vt; tile += kFwdWarps) {
+        x_tile(n, tile * 16, a.var_ptr, a.var_chk, S.ac, S.bv, lane);
         g_step<false>(S, n, tile * 16, true, !last, llr, lane);
+      }
       __syncthreads();
       if (last) break;
-      x_step(m, a.chk_ptr, a.chk_var, S.cv, S.dc);
-      __syncthreads();
-      for (int tile = warp; tile < ct; tile += kFwdWarps)
+      for (int tile = warp; tile < ct; tile += kFwdWarps) {
+        x_tile(m, tile * 16, a.chk_ptr, a.chk_var, S.cv, S.dc, lane);
         g_step<true>(S, m, tile * 16, true, true, nullptr, lane);
+      }
       __syncthreads();
     }
     if (a.llr_out) continue;

@@ -239,6 +239,22 @@ def test_host_buffer_entry_point(L):
     assert np.array_equal(out.numpy(), c_host)
 
 
+def test_host_buffer_pipeline_matches_device_decode(L):
+    """A batch large enough for the chunked copy/decode pipeline (ragged chunk sizes) gives
+    the same corrections and statuses as one device-resident call."""
+    h, probs, e, s = sample("bb144", 0.05, 300_001, seed=21)
+    d = L.Decoder(h, probs, 50)
+    c_dev, st_dev = d.decode(dev(s))
+    pinned = torch.from_numpy(s).pin_memory()
+    out = torch.empty((s.shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+    stt = torch.empty(s.shape[0], dtype=torch.uint8).pin_memory()
+    for _ in range(2):  # the second call reuses the streams, events and staging buffers
+        out.zero_()
+        stt.zero_()
+        d.decode_host(pinned, out, stt)
+        assert torch.equal(out, c_dev.cpu()) and torch.equal(stt, st_dev.cpu())
+
+
 def test_memory_budget_admission(L):
     h, probs, e, s = sample("bb144", 0.05, 10, seed=3)
     with pytest.raises(L.LsdError) as ei:
