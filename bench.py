@@ -230,6 +230,8 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
     from paper_2406_18655_gb300.lsd import Decoder, Prior
 
     dec = Decoder(hx, probs, args.iters, args.order, stream=stream)
+    if not args.no_autotune:
+        dec.autotune(s_dev[: min(s_dev.shape[0], 200_000)])  # LSD warps of the learned path
     prior = Prior(dec, rounds=args.learned_rounds, params=init_params(args.seed))
     tr = train(dec, prior, args.train_pairs, batch=4096, seed=args.seed + 17, lr=3e-3,
                log_every=500)
@@ -262,6 +264,8 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
     sweep = []
     for it in [int(x) for x in args.sweep_iters.split(",") if x]:
         d_it = Decoder(hx, probs, it, args.order, stream=stream)
+        if not args.no_autotune:
+            d_it.autotune(s_dev[: min(s_dev.shape[0], 200_000)])
         corr = torch.empty_like(holder["c"])
         stt = torch.empty_like(holder["st"])
         for _ in range(2):
