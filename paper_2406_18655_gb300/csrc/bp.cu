@@ -544,6 +544,179 @@ __global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
   }
 }
 
+// BP for large row-regular graphs (hypergraph-product codes): one CTA of NT threads owns one
+// shot; like bp_reg_kernel, thread t keeps the column indices of checks t, t + NT, ... and the
+// edge slots of variables t, t + NT, ... in registers (two 16-bit indices per register), so
+// no graph table is read while iterating.  Columns of degree < DV are padded with the slot
+// of a message that stays zero (r[E]), added last, which leaves Lambda unchanged.  r[E + 1]
+// and Lam[n] live in shared memory.  Same operations in the same order as bp_kernel<G, 0>.
+template <int NT, int CPL, int DC, int VPL, int DV>
+__global__ void __launch_bounds__(NT, 1) bp_regcta_kernel(BPArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_shot;
+  __shared__ unsigned long long s_slot;
+  const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const long long shots = a.shots_dev ? *a.shots_dev : a.shots;
+  const int tid = threadIdx.x;
+  float* r = reinterpret_cast<float*>(smem);           // [E + 1], r[E] == 0
+  float* Lam = r + align16((size_t)(E + 1) * 4) / 4;   // [n]
+  float* s_prior = Lam + align16((size_t)n * 4) / 4;   // [n]
+  const float alpha = a.alpha;
+  uint32_t cv[CPL][(DC + 1) / 2];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int i = tid + NT * c;
+#pragma unroll
+    for (int k = 0; k < (DC + 1) / 2; ++k) cv[c][k] = 0;
+    if (i < m) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) cv[c][k >> 1] |= (uint32_t)a.g.chk_var[i * DC + k] << (16 * (k & 1));
+    }
+  }
+  uint32_t ve[VPL][(DV + 1) / 2];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int j = tid + NT * v;
+#pragma unroll
+    for (int k = 0; k < (DV + 1) / 2; ++k) ve[v][k] = 0;
+    if (j < n) {
+      const int q0 = a.g.var_ptr[j], deg = a.g.var_ptr[j + 1] - q0;
+#pragma unroll
+      for (int k = 0; k < DV; ++k) {
+        const uint32_t e = k < deg ? (uint32_t)a.g.var_edge[q0 + k] : (uint32_t)E;
+        ve[v][k >> 1] |= e << (16 * (k & 1));
+      }
+      s_prior[j] = a.g.prior[j];
+    }
+  }
+  if (tid == 0) r[E] = 0.f;
+  unsigned long long my_iters = 0, my_conv = 0;
+  for (;;) {
+    if (tid == 0) s_shot = atomicAdd(&a.ctr->next_shot, 1ULL);
+    __syncthreads();
+    const unsigned long long shot_u = s_shot;
+    if (shot_u >= (unsigned long long)shots) break;
+    const long long shot = (long long)shot_u;
+    const uint8_t* sp = a.syndromes + shot * m;
+    unsigned sbits = 0;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int i = tid + NT * c;
+      if (i < m) {
+        if (sp[i]) sbits |= 1u << c;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      const int j = tid + NT * v;
+      if (j < n) Lam[j] = s_prior[j];
+    }
+    __syncthreads();
+    int t = 0;
+    bool conv = false;
+    for (;;) {
+      const bool msgs = t < a.iters;
+      unsigned unsat = 0;
+      // ---- check phase (the update of bp_reg_kernel) ----
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int i = tid + NT * c;
+        if (i >= m) continue;
+        uint32_t hp = (sbits >> c) << 31;
+        uint32_t sx = hp;
+        float min1 = kBig, min2 = kBig;
+        float aq[DC];
+        uint32_t qb[DC];
+        float* rc = r + i * DC;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+          const int j = (cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff;
+          const float L = Lam[j];
+          hp ^= __float_as_uint(L);
+          const float q = __fsub_rn(L, rc[k]);
+          qb[k] = __float_as_uint(q);
+          sx ^= qb[k];
+          aq[k] = fabsf(q);
+          min2 = fminf(min2, fmaxf(min1, aq[k]));
+          min1 = fminf(min1, aq[k]);
+        }
+        unsat |= hp >> 31;
+        if (msgs) {
+          const float m1 = __fmul_rn(alpha, min1), m2 = __fmul_rn(alpha, min2);
+#pragma unroll
+          for (int k = 0; k < DC; ++k) {
+            const float mag = (aq[k] == min1) ? m2 : m1;
+            rc[k] = __uint_as_float(__float_as_uint(mag) | ((sx ^ qb[k]) & 0x80000000u));
+          }
+        }
+      }
+      const int any_unsat = __syncthreads_or((int)unsat);
+      if (t > 0) {
+        conv = !any_unsat;
+        if (conv && a.early_exit) break;
+      }
+      if (!msgs) break;
+      // ---- variable phase ----
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int j = tid + NT * v;
+        if (j >= n) continue;
+        float L = s_prior[j];
+#pragma unroll
+        for (int k = 0; k < DV; ++k) L = __fadd_rn(L, r[(ve[v][k >> 1] >> (16 * (k & 1))) & 0xffff]);
+        Lam[j] = L;
+      }
+      __syncthreads();
+      ++t;
+    }
+    // ---- outputs ----
+    if (a.posteriors) {
+      float* po = a.posteriors + shot * n;
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int j = tid + NT * v;
+        if (j < n) po[j] = Lam[j];
+      }
+    }
+    if (tid == 0) {
+      if (a.converged_out) a.converged_out[shot] = conv ? 1 : 0;
+      if (a.iters_out) a.iters_out[shot] = t;
+      my_iters += (unsigned long long)t;
+      my_conv += conv ? 1ull : 0ull;
+    }
+    if (a.queue) {
+      if (conv) {
+        uint8_t* co = a.corrections + shot * n;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const int j = tid + NT * v;
+          if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+        }
+        if (tid == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
+      } else {
+        if (tid == 0) {
+          s_slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
+          a.queue[s_slot] = (int32_t)shot;
+        }
+        __syncthreads();
+        float* lo = a.queue_llr + (long long)s_slot * n;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const int j = tid + NT * v;
+          if (j < n) lo[j] = Lam[j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (my_iters) atomicAdd(&a.ctr->bp_iterations, my_iters);
+    if (my_conv) atomicAdd(&a.ctr->bp_converged, my_conv);
+  }
+}
+
 // Shapes of bp_reg_kernel: (G, CPL, DC, VPL, DV).
 struct RegShape {
   int G, cpl, dc, vpl, dv;
@@ -588,20 +761,46 @@ const void* generic_fn(int v) {
     default: return (const void*)bp_kernel<32, 1>;
   }
 }
-constexpr int kCtaBase = 6 + kNumRegShapes;  // + method: one CTA per shot
-bool is_cta(int v) { return v >= kCtaBase; }
+// Shapes of bp_regcta_kernel: (NT, CPL, DC, VPL, DV); rows of degree exactly DC, columns of
+// degree at most DV.
+struct RegCtaShape {
+  int nt, cpl, dc, vpl, dv;
+  const void* fn;
+};
+#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx) \
+  {NT, C, DCx, V, DVx, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx>}
+const RegCtaShape kRegCtaShapes[] = {
+    LSD_REGCTA_SHAPE(768, 4, 7, 9, 4),   // m <= 3072, n <= 6912 (HGP of a 48 x 64 (3,4) code)
+    LSD_REGCTA_SHAPE(512, 6, 7, 13, 4),  // same graphs, fewer threads
+};
+#undef LSD_REGCTA_SHAPE
+constexpr int kNumRegCtaShapes = sizeof(kRegCtaShapes) / sizeof(kRegCtaShapes[0]);
+
+size_t regcta_smem(const DevGraph& g) {
+  return align16((size_t)(g.E + 1) * 4) + 2 * align16((size_t)g.n * 4);
+}
+bool regcta_fits(const RegCtaShape& s, const DevGraph& g) {
+  return g.m <= s.nt * s.cpl && g.n <= s.nt * s.vpl && g.min_row_deg == s.dc &&
+         g.max_row_deg == s.dc && g.max_col_deg <= s.dv && g.E < 65535 && g.n <= 65535;
+}
+
+constexpr int kCtaBase = 6 + kNumRegShapes;     // + method: one CTA per shot
+constexpr int kRegCtaBase = kCtaBase + 2;       // + i: kRegCtaShapes[i]
+bool is_cta(int v) { return v >= kCtaBase && v < kRegCtaBase; }
+bool is_regcta(int v) { return v >= kRegCtaBase; }
 int lanes_of(int variant) {
-  if (is_cta(variant)) return 0;
+  if (is_cta(variant) || is_regcta(variant)) return 0;
   if (variant >= 6) return kRegShapes[variant - 6].G;
   return variant % 3 == 0 ? 8 : variant % 3 == 1 ? 16 : 32;
 }
 const void* variant_fn(int v) {
+  if (is_regcta(v)) return kRegCtaShapes[v - kRegCtaBase].fn;
   if (is_cta(v)) return v == kCtaBase ? (const void*)bp_cta_kernel<0> : (const void*)bp_cta_kernel<1>;
   return v >= 6 ? kRegShapes[v - 6].fn : generic_fn(v);
 }
 }  // namespace
 
-int bp_num_variants() { return kCtaBase + 2; }
+int bp_num_variants() { return kRegCtaBase + kNumRegCtaShapes; }
 
 cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
                       int* grid, int* block, size_t* smem) {
@@ -616,7 +815,9 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
   if (*variant >= 0) {
     v = *variant;
     if (v >= bp_num_variants()) return cudaErrorInvalidValue;
-    if (is_cta(v)) {
+    if (is_regcta(v)) {
+      if (method != 0 || !regcta_fits(kRegCtaShapes[v - kRegCtaBase], g)) return cudaErrorInvalidValue;
+    } else if (is_cta(v)) {
       if ((v - kCtaBase) != (method != 0 ? 1 : 0)) return cudaErrorInvalidValue;
     } else if (v >= 6 && (method != 0 || !reg_shape_fits(kRegShapes[v - 6], g))) {
       return cudaErrorInvalidValue;
@@ -640,18 +841,39 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
         }
       }
     }
+    if (v < 0 && kind == 2) {  // register tables requested: a CTA shape, or nothing
+      if (method == 0)
+        for (int i = 0; i < kNumRegCtaShapes; ++i)
+          if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(g) <= (size_t)max_smem) {
+            v = kRegCtaBase + i;
+            break;
+          }
+      if (v < 0) return cudaErrorInvalidValue;
+    }
     if (v < 0) {
-      if (kind == 2) return cudaErrorInvalidValue;
       const int l = lanes ? lanes : 32;
       v = (l == 8 ? 0 : l == 16 ? 1 : 2) + (method ? 3 : 0);
-      // a graph whose warp-group state does not fit next to the staged graph: one CTA per shot
-      if (bp_graph_bytes(g.m, g.n, g.E) + bp_group_bytes(g.m, g.n, g.E) > (size_t)max_smem)
+      // a graph whose warp-group state does not fit next to the staged graph: one CTA per
+      // shot, with register tables when the graph is row-regular and a shape fits
+      if (bp_graph_bytes(g.m, g.n, g.E) + bp_group_bytes(g.m, g.n, g.E) > (size_t)max_smem) {
         v = kCtaBase + (method ? 1 : 0);
+        if (method == 0 && kind != 1)
+          for (int i = 0; i < kNumRegCtaShapes; ++i)
+            if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(g) <= (size_t)max_smem) {
+              v = kRegCtaBase + i;
+              break;
+            }
+      }
     }
   }
   size_t gb, grp;
   int b;
-  if (is_cta(v)) {
+  if (is_regcta(v)) {
+    gb = 0;
+    grp = regcta_smem(g);
+    if (grp > (size_t)max_smem) return cudaErrorInvalidValue;
+    b = kRegCtaShapes[v - kRegCtaBase].nt;
+  } else if (is_cta(v)) {
     gb = 0;
     grp = bp_group_bytes(g.m, g.n, g.E);
     if (grp > (size_t)max_smem) return cudaErrorInvalidValue;

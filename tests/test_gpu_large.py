@@ -29,7 +29,10 @@ def f64(a):
 
 
 @pytest.mark.parametrize("name,p,iters,order,shots", [
-    ("st_bb144_d12", 0.01, 50, 0, 300), ("hgp", 0.02, 100, 0, 120), ("hgp", 0.02, 100, 10, 60)])
+    ("st_bb144_d12", 0.01, 50, 0, 300), ("hgp", 0.02, 100, 0, 120), ("hgp", 0.02, 100, 10, 60),
+    # percolating regime: a third of the shots reach LSD with clusters of hundreds to
+    # thousands of columns (the global-memory spill instance)
+    ("hgp", 0.05, 100, 0, 200), ("hgp", 0.05, 100, 10, 100)])
 def test_large_decode_matches_oracle(L, name, p, iters, order, shots):
     h, probs, e, s = sample(name, p, shots, seed=31 + order)
     d = L.Decoder(h, probs, iters, order)
@@ -42,13 +45,30 @@ def test_large_decode_matches_oracle(L, name, p, iters, order, shots):
           f"spilled {stats['lsd_spilled']}")
 
 
-def test_large_bp_matches_oracle(L):
+@pytest.mark.parametrize("bp_kernel", [0, 1])
+def test_large_bp_matches_oracle(L, bp_kernel):
+    """HGP (3072 x 6400, rows of weight 7, columns of weight 3 and 4): the register-table CTA
+    kernel (auto) and the CTA kernel that reads the graph through the cache (generic)."""
     h, probs, e, s = sample("hgp", 0.03, 40, seed=5)
-    d = L.Decoder(h, probs, 40)
+    d = L.Decoder(h, probs, 40, bp_kernel=bp_kernel)
     post, conv, it = d.bp(dev(s))
     llr, hard, used, convo = oracle.bp(h, f64(probs), s, 40, precision=1)
     assert np.array_equal(it.cpu().numpy(), used)
     assert np.array_equal(post.cpu().numpy().astype(np.float64), llr)
+
+
+def test_large_autotune_keeps_results(L):
+    """Every BP variant the autotuner times on HGP gives the same decode."""
+    h, probs, e, s = sample("hgp", 0.04, 300, seed=6)
+    d = L.Decoder(h, probs, 100)
+    c0, s0 = d.decode(dev(s))
+    rep = d.autotune(dev(s))
+    assert rep["bp_candidates"] >= 3
+    c1, s1 = d.decode(dev(s))
+    assert torch.equal(c0, c1) and torch.equal(s0, s1)
+    o = oracle.decode(h, f64(probs), s, 100, precision=1)
+    assert np.array_equal(c1.cpu().numpy(), o["corrections"])
+    print("hgp autotune:", rep)
 
 
 @pytest.mark.parametrize("order", [0, 6])
