@@ -38,9 +38,10 @@ UNIT = "shots/s"
 # and subtract, and the hard-decision parity (about ten integer / FP32 operations).
 OPS_PER_EDGE_ITER = 10
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes per launch of bp_kernel on this workload from the committed ncu capture
-# (profiles/bp_kernel_bb144_p005.md); None when the kernel has changed since.
-BP_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one 10^6-shot launch of bp_reg_kernel<32,3,6,5,3> on this
+# workload, from a one-pass ncu capture of the full workload
+# (profiles/bp_reg_kernel_bb144_p005.md); None once the kernel changes.
+BP_TRAFFIC_BYTES = 75704832 + 152049408
 
 
 def parse():
