@@ -64,6 +64,7 @@ struct SGraph {
   const uint16_t* chk_var;
   const int32_t* var_ptr;
   const uint16_t* var_chk;
+  int max_col_deg;
 };
 
 template <class L>
@@ -323,28 +324,50 @@ __device__ int sparse_step(const SGraph& G, const SShot<L>& S, const float* llr,
     S.gflag()[r] = 1;
   }
   __syncwarp();
-  // find_candidate over the compacted candidate list
+  // find_candidate over the compacted candidate list, 4 entries per lane at a time: the
+  // dependent loads (entry, state, column, labels) of the four are issued together
   {
     const int nf = S.scal()[S_NFRONT];
+    const unsigned below = (1u << lane) - 1u;
     int kept = 0;
-    for (int b = 0; b < nf; b += 32) {
-      const int i = b + lane;
-      int f = -1;
-      if (i < nf) {
-        f = S.front[i];
-        if (S.fst[f] != -1) f = -1;
+    for (int b = 0; b < nf; b += 128) {
+      int f[4], q0[4], q1[4];
+      unsigned long long key[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = b + 32 * u + lane;
+        f[u] = i < nf ? S.front[i] : -1;
       }
-      const unsigned bal = __ballot_sync(kFull, f >= 0);
-      if (f >= 0) {
-        S.front[kept + __popc(bal & ((1u << lane) - 1u))] = f;
-        const unsigned long long key = llr_key(llr[f], f);
-        const int v1 = G.var_ptr[f + 1];
-        for (int q = G.var_ptr[f]; q < v1; ++q) {
-          const int r = S.dlab[G.var_chk[q]];
-          if (r >= 0 && S.gflag()[r]) atomicMin(&S.best()[r], key);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (f[u] >= 0 && S.fst[f[u]] != -1) f[u] = -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        key[u] = kNoKey;
+        q0[u] = q1[u] = 0;
+        if (f[u] >= 0) {
+          key[u] = llr_key(llr[f[u]], f[u]);
+          q0[u] = G.var_ptr[f[u]];
+          q1[u] = G.var_ptr[f[u] + 1];
         }
       }
-      kept += __popc(bal);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned bal = __ballot_sync(kFull, f[u] >= 0);
+        if (f[u] >= 0) S.front[kept + __popc(bal & below)] = f[u];
+        kept += __popc(bal);
+      }
+      for (int qq = 0; qq < G.max_col_deg; ++qq) {
+        int r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0[u] + qq;
+          r[u] = q < q1[u] ? S.dlab[G.var_chk[q]] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (r[u] >= 0 && S.gflag()[r[u]]) atomicMin(&S.best()[r[u]], key[u]);
+      }
       __syncwarp();
     }
     if (lane == 0) S.scal()[S_NFRONT] = kept;
@@ -524,7 +547,7 @@ __device__ void sparse_osd_e(const LSDArgs& a, const SShot<L>& S, int lane) {
 // Work items come from a.queue / a.count as in lsd.cu.  Shots that overflow the capacity are
 // appended to spill[] (spill_count) when spill != nullptr, else reported unsolvable.
 template <int CAP, int SC, bool MU, bool GLOBAL_RT>
-__global__ void __launch_bounds__(128) lsd_sparse_kernel(LSDArgs a, int* scratch, size_t stride,
+__global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scratch, size_t stride,
                                                          int* spill, unsigned long long* spill_count,
                                                          const int* items, const unsigned long long* item_count) {
   using L = SLay<CAP, SC, MU>;
@@ -542,7 +565,7 @@ __global__ void __launch_bounds__(128) lsd_sparse_kernel(LSDArgs a, int* scratch
   S.fst = ws + 2 * m;
   S.front = ws + 2 * m + n;
   S.rt = GLOBAL_RT ? reinterpret_cast<unsigned char*>(ws + 2 * m + 2 * n) : S.sm + L::sm_total;
-  SGraph G{a.g.chk_ptr, a.g.chk_var, a.g.var_ptr, a.g.var_chk};
+  SGraph G{a.g.chk_ptr, a.g.chk_var, a.g.var_ptr, a.g.var_chk, a.g.max_col_deg};
 
   long long count;
   if (items) count = (long long)*item_count;
