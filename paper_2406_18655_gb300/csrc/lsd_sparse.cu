@@ -556,7 +556,9 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
   const int m = a.g.m, n = a.g.n;
-  const size_t per_sm = L::sm_total + (GLOBAL_RT ? 0 : L::rt_total);
+  // the spill instance keeps all of its state in its global scratch (no shared memory), so
+  // that many of its warps can be resident per SM
+  const size_t per_sm = GLOBAL_RT ? 0 : L::sm_total + L::rt_total;
   SShot<L> S;
   S.sm = smem + (size_t)warp * per_sm;
   int* ws = scratch + (size_t)gw * stride;
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
   S.fst = ws + 2 * m;
   S.front = ws + 2 * m + n;
   S.rt = GLOBAL_RT ? reinterpret_cast<unsigned char*>(ws + 2 * m + 2 * n) : S.sm + L::sm_total;
+  if (GLOBAL_RT) S.sm = S.rt + L::rt_total;
   SGraph G{a.g.chk_ptr, a.g.chk_var, a.g.var_ptr, a.g.var_chk, a.g.max_col_deg};
 
   long long count;
@@ -773,10 +776,7 @@ size_t small_smem() {
   return (size_t)kSparseWarps * (SLay<kSmallCap, kSmallSeeds, MU>::sm_total +
                                  SLay<kSmallCap, kSmallSeeds, MU>::rt_total);
 }
-template <bool MU>
-size_t big_smem() {
-  return (size_t)SLay<kBigCap, kBigSeeds, MU>::sm_total;  // one warp per CTA
-}
+constexpr int kBigWarpsPerSm = 4;  // spill-instance warps (one per CTA) per SM
 
 }  // namespace
 
@@ -785,7 +785,8 @@ size_t big_smem() {
 size_t sparse_scratch_ints(int m, int n, bool big, bool mu) {
   size_t s = (size_t)2 * m + (size_t)2 * n;
   if (big)
-    s += (mu ? SLay<kBigCap, kBigSeeds, true>::rt_total : SLay<kBigCap, kBigSeeds, false>::rt_total) / 4;
+    s += (mu ? SLay<kBigCap, kBigSeeds, true>::rt_total + SLay<kBigCap, kBigSeeds, true>::sm_total
+             : SLay<kBigCap, kBigSeeds, false>::rt_total + SLay<kBigCap, kBigSeeds, false>::sm_total) / 4;
   return (s + 3) & ~(size_t)3;
 }
 
@@ -798,21 +799,16 @@ cudaError_t sparse_config(const DevGraph& g, int order, int* grid_small, int* gr
   const bool mu = order > 0;
   const void* fs = mu ? (const void*)lsd_sparse_kernel<kSmallCap, kSmallSeeds, true, false>
                       : (const void*)lsd_sparse_kernel<kSmallCap, kSmallSeeds, false, false>;
-  const void* fb = mu ? (const void*)lsd_sparse_kernel<kBigCap, kBigSeeds, true, true>
-                      : (const void*)lsd_sparse_kernel<kBigCap, kBigSeeds, false, true>;
   const size_t ss = mu ? small_smem<true>() : small_smem<false>();
-  const size_t sb = mu ? big_smem<true>() : big_smem<false>();
-  if (ss > (size_t)max_smem || sb > (size_t)max_smem) return cudaErrorInvalidValue;
+  if (ss > (size_t)max_smem) return cudaErrorInvalidValue;
   err = allow_max_dynamic_smem(fs, max_smem);
-  if (err == cudaSuccess)
-    err = allow_max_dynamic_smem(fb, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs, kSparseWarps * 32, ss);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidValue;
   *grid_small = per_sm * sms;
-  *grid_big = sms;  // one warp per SM: the spill instance holds megabytes of scratch per warp
+  *grid_big = sms * kBigWarpsPerSm;  // each spill warp holds megabytes of global scratch
   return cudaSuccess;
 }
 
@@ -831,12 +827,11 @@ cudaError_t launch_sparse(const LSDArgs& a, bool big, int grid, int* scratch, si
       lsd_sparse_kernel<kSmallCap, kSmallSeeds, false, false><<<grid, kSparseWarps * 32, smem, st>>>(
           a, scratch, stride, spill, spill_count, items, item_count);
   } else {
-    const size_t smem = mu ? big_smem<true>() : big_smem<false>();
     if (mu)
-      lsd_sparse_kernel<kBigCap, kBigSeeds, true, true><<<grid, 32, smem, st>>>(
+      lsd_sparse_kernel<kBigCap, kBigSeeds, true, true><<<grid, 32, 0, st>>>(
           a, scratch, stride, nullptr, nullptr, items, item_count);
     else
-      lsd_sparse_kernel<kBigCap, kBigSeeds, false, true><<<grid, 32, smem, st>>>(
+      lsd_sparse_kernel<kBigCap, kBigSeeds, false, true><<<grid, 32, 0, st>>>(
           a, scratch, stride, nullptr, nullptr, items, item_count);
   }
   return cudaGetLastError();
