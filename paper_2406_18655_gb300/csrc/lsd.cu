@@ -557,7 +557,7 @@ __device__ void osd_e(const LSDArgs& a, const Shot<L>& S, int m, int lane) {
 }
 
 template <int MM, int NN, bool MU>
-__global__ void __launch_bounds__(256) lsd_kernel(LSDArgs a, int graph_smem) {
+__global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int graph_smem) {
   using L = Lay<MM, NN, MU>;
   constexpr int W = L::W, Wn = L::Wn, N2 = L::N2;
   extern __shared__ __align__(16) unsigned char smem[];
