@@ -9,15 +9,10 @@
 //   LLR_v = lambda_v + w_o . h_v + b_o
 //   MLP(x) = W2 relu(W1 x + b1) + b2   (W1: 32 x 65, W2: 32 x 32)
 //
-// One CTA owns one shot at a time; node states (FP32) live in shared memory.  A warp
-// handles 16 edges at a time: it gathers X = [h_first | h_second | sigma | 1 | 0...]
-// (16 x 80, BF16) into its staging tile, runs the two layers with mma.sync m16n8k16
-// (the layer-1 accumulator fragments are re-packed in registers as the A operand of layer
-// 2), and scatter-adds the 16 x 32 messages into the destination accumulators.  The
-// backward pass recomputes layer 1 from the saved node states, forms da1 = dm W2 and
-// dx = dz1 W1 on the tensor cores, and the weight gradients dW2 = dm^T a1 and
-// dW1 = dz1^T X (its column 65 is the bias gradient) with transposed operand loads from
-// the staging tiles.
+// Inference (prior_fwd_kernel) and training (prior_train_kernel) both evaluate the model
+// on per-node products (see the comment above prior_fwd_kernel); Adam updates the FP32
+// master parameters (adam_kernel) and sample_kernel draws training pairs.
+
 #include <cuda_bf16.h>
 
 #include "lsd_internal.cuh"
@@ -27,10 +22,7 @@ namespace lsdgb {
 namespace {
 
 constexpr int HD = 32;        // hidden width
-constexpr int XK = 80;        // padded layer-1 input: 32 + 32 + sigma + one + 14 zeros
 constexpr int DIN = 2 * HD + 1;
-constexpr int NWARP = 8;
-constexpr int kPriorThreads = NWARP * 32;
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -41,56 +33,6 @@ struct POff {
   static constexpr int W1vc = b2cv + HD, b1vc = W1vc + HD * DIN, W2vc = b1vc + HD,
                        b2vc = W2vc + HD * HD;
   static constexpr int wo = b2vc + HD, bo = wo + HD, total = bo + 1;
-};
-
-// Shared-memory layout of the prior kernel (runtime n, m, E).
-struct PLay {
-  size_t hv, hc, accv, accc, gv, gc, W1, W2, W1T, W2T, vec, dW1, dW2, db2, stage, ec, ev, sig,
-      lam, llr, err, total;
-};
-
-__host__ __device__ inline PLay prior_layout(int m, int n, int E, bool train) {
-  PLay L;
-  size_t o = 0;
-  L.hv = o; o += a16((size_t)n * HD * 4);
-  L.hc = o; o += a16((size_t)m * HD * 4);
-  L.accv = o; o += a16((size_t)n * HD * 4);
-  L.accc = o; o += a16((size_t)m * HD * 4);
-  L.gv = o; o += train ? a16((size_t)n * HD * 4) : 0;
-  L.gc = o; o += train ? a16((size_t)m * HD * 4) : 0;
-  L.W1 = o; o += 2 * (size_t)HD * XK * 2;     // [dir][32][80] bf16
-  L.W2 = o; o += 2 * (size_t)HD * HD * 2;     // [dir][32][32]
-  L.W1T = o; o += 2 * (size_t)XK * HD * 2;    // [dir][80][32]
-  L.W2T = o; o += 2 * (size_t)HD * HD * 2;    // [dir][32][32]
-  L.vec = o; o += 16 * HD * 4;                 // a0 a1 u0 u1 b1cv b2cv b1vc b2vc wo (+bo)
-  L.dW1 = o; o += train ? 2 * (size_t)HD * XK * 4 : 0;
-  L.dW2 = o; o += train ? 2 * (size_t)HD * HD * 4 : 0;
-  L.db2 = o; o += train ? 16 * HD * 4 : 0;     // db2cv db2vc da0 da1 du0 du1 dwo dbo
-  L.stage = o; o += (size_t)NWARP * (16 * XK * 2 + 3 * 16 * HD * 2);
-  L.ec = o; o += a16((size_t)E * 2);
-  L.ev = o; o += a16((size_t)E * 2);
-  L.sig = o; o += a16((size_t)m * 4);
-  L.lam = o; o += a16((size_t)n * 4);
-  L.llr = o; o += a16((size_t)n * 4);
-  L.err = o; o += a16((size_t)n);
-  L.total = a16(o);
-  return L;
-}
-
-struct PriorArgs {
-  int m, n, E, rounds;
-  const int32_t* chk_ptr;
-  const uint16_t* chk_var;
-  const float* prior;      // lambda_j
-  const float* params;     // flat FP32 parameters
-  long long shots;
-  const uint8_t* syndromes;
-  const uint8_t* errors;   // training targets (train only)
-  float* llr_out;          // [shots][n] (forward only, nullable)
-  float* scratch;          // per-CTA saved node states (train only)
-  float* grads;            // flat FP32 gradient accumulator (train only)
-  double* loss;            // loss sum accumulator (train only)
-  float inv_norm;          // 1 / (shots * n)
 };
 
 // ---- mma.sync helpers (PTX ISA fragment layouts for m16n8k16 .bf16) ----
@@ -111,526 +53,6 @@ __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
 }
 __device__ __forceinline__ uint32_t pack_bf(const __nv_bfloat16 lo, const __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// A[r][k] = base[r*ld + k] (row-major tile), rows r0.., cols k0..k0+15
-__device__ __forceinline__ void frag_a_row(uint32_t a[4], const __nv_bfloat16* base, int ld,
-                                           int r0, int k0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  a[0] = ld32(base + (r0 + g) * ld + k0 + 2 * t);
-  a[1] = ld32(base + (r0 + g + 8) * ld + k0 + 2 * t);
-  a[2] = ld32(base + (r0 + g) * ld + k0 + 2 * t + 8);
-  a[3] = ld32(base + (r0 + g + 8) * ld + k0 + 2 * t + 8);
-}
-// A[r][k] = base[k*ld + r] (transposed source)
-__device__ __forceinline__ void frag_a_col(uint32_t a[4], const __nv_bfloat16* base, int ld,
-                                           int r0, int k0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  const int r = r0 + g, k = k0 + 2 * t;
-  a[0] = pack_bf(base[k * ld + r], base[(k + 1) * ld + r]);
-  a[1] = pack_bf(base[k * ld + r + 8], base[(k + 1) * ld + r + 8]);
-  a[2] = pack_bf(base[(k + 8) * ld + r], base[(k + 9) * ld + r]);
-  a[3] = pack_bf(base[(k + 8) * ld + r + 8], base[(k + 9) * ld + r + 8]);
-}
-// B[k][n] = base[n*ld + k] ([N][K] storage)
-__device__ __forceinline__ void frag_b_nk(uint32_t b[2], const __nv_bfloat16* base, int ld,
-                                          int n0, int k0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  b[0] = ld32(base + (n0 + g) * ld + k0 + 2 * t);
-  b[1] = ld32(base + (n0 + g) * ld + k0 + 2 * t + 8);
-}
-// B[k][n] = base[k*ld + n] ([K][N] storage)
-__device__ __forceinline__ void frag_b_kn(uint32_t b[2], const __nv_bfloat16* base, int ld,
-                                          int k0, int n0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  const int k = k0 + 2 * t, n = n0 + g;
-  b[0] = pack_bf(base[k * ld + n], base[(k + 1) * ld + n]);
-  b[1] = pack_bf(base[(k + 8) * ld + n], base[(k + 9) * ld + n]);
-}
-
-struct Smem {
-  float *hv, *hc, *accv, *accc, *gv, *gc, *vec, *dW1, *dW2, *db2, *sig, *lam, *llr;
-  __nv_bfloat16 *W1, *W2, *W1T, *W2T;
-  unsigned char* stage;
-  uint16_t *ec, *ev;
-  uint8_t* err;
-};
-
-// vec slots (x32 floats each)
-enum { V_a0 = 0, V_a1, V_u0, V_u1, V_b1cv, V_b2cv, V_b1vc, V_b2vc, V_wo, V_bo };
-// db2 slots
-enum { G_b2cv = 0, G_b2vc, G_a0, G_a1, G_u0, G_u1, G_wo, G_bo };
-
-// Gathers X for edges tile*16.. into the warp's staging tile (BF16 [16][80]).
-// dir 0 (check -> variable): X = [h_c, h_v, sigma_c, 1]; dir 1: X = [h_v, h_c, sigma_c, 1].
-__device__ __forceinline__ void stage_x(const Smem& S, const PriorArgs& a, int dir, int tile,
-                                        __nv_bfloat16* Xs, int lane) {
-  for (int idx = lane; idx < 16 * (XK / 2); idx += 32) {
-    const int row = idx / (XK / 2), col = 2 * (idx % (XK / 2));
-    const int e = tile * 16 + row;
-    float x0 = 0.f, x1 = 0.f;
-    if (e < a.E) {
-      const int c = S.ec[e], v = S.ev[e];
-      const float* first = dir == 0 ? S.hc + c * HD : S.hv + v * HD;
-      const float* second = dir == 0 ? S.hv + v * HD : S.hc + c * HD;
-      if (col < HD) {
-        x0 = first[col];
-        x1 = first[col + 1];
-      } else if (col < 2 * HD) {
-        x0 = second[col - HD];
-        x1 = second[col - HD + 1];
-      } else if (col == 2 * HD) {
-        x0 = S.sig[c];
-        x1 = 1.f;
-      }
-    }
-    *reinterpret_cast<uint32_t*>(Xs + row * XK + col) = pack2(x0, x1);
-  }
-  __syncwarp();
-}
-
-// Layer 1 of direction dir on the staged X: z1 (16 x 32) as four accumulator fragments.
-__device__ __forceinline__ void layer1(const Smem& S, int dir, const __nv_bfloat16* Xs,
-                                       float z[4][4], int lane) {
-  const int t = lane & 3;
-  const float* b1 = S.vec + (dir == 0 ? V_b1cv : V_b1vc) * HD;
-  const __nv_bfloat16* W1 = S.W1 + dir * HD * XK;
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    z[nt][0] = z[nt][2] = b1[nt * 8 + 2 * t];
-    z[nt][1] = z[nt][3] = b1[nt * 8 + 2 * t + 1];
-  }
-#pragma unroll
-  for (int ks = 0; ks < XK / 16; ++ks) {
-    uint32_t af[4];
-    frag_a_row(af, Xs, XK, 0, ks * 16, lane);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      uint32_t bf[2];
-      frag_b_nk(bf, W1, XK, nt * 8, ks * 16, lane);
-      mma16816(z[nt], af, bf);
-    }
-  }
-}
-
-// One message half-round (forward): messages of direction dir into the destination
-// accumulators.
-__device__ void pass_forward(const Smem& S, const PriorArgs& a, int dir, int warp, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(S.stage + warp * (16 * XK * 2 + 3 * 16 * HD * 2));
-  const float* b2 = S.vec + (dir == 0 ? V_b2cv : V_b2vc) * HD;
-  const __nv_bfloat16* W2 = S.W2 + dir * HD * HD;
-  float* acc = dir == 0 ? S.accv : S.accc;
-  const int ntiles = (a.E + 15) / 16;
-  for (int tile = warp; tile < ntiles; tile += NWARP) {
-    stage_x(S, a, dir, tile, Xs, lane);
-    float z[4][4];
-    layer1(S, dir, Xs, z, lane);
-    uint32_t a2[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      a2[j][0] = pack2(fmaxf(z[2 * j][0], 0.f), fmaxf(z[2 * j][1], 0.f));
-      a2[j][1] = pack2(fmaxf(z[2 * j][2], 0.f), fmaxf(z[2 * j][3], 0.f));
-      a2[j][2] = pack2(fmaxf(z[2 * j + 1][0], 0.f), fmaxf(z[2 * j + 1][1], 0.f));
-      a2[j][3] = pack2(fmaxf(z[2 * j + 1][2], 0.f), fmaxf(z[2 * j + 1][3], 0.f));
-    }
-    const int e0 = tile * 16 + g, e1 = e0 + 8;
-    const int d0 = e0 < a.E ? (dir == 0 ? S.ev[e0] : S.ec[e0]) : -1;
-    const int d1 = e1 < a.E ? (dir == 0 ? S.ev[e1] : S.ec[e1]) : -1;
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      float c[4];
-      c[0] = c[2] = b2[nt * 8 + 2 * t];
-      c[1] = c[3] = b2[nt * 8 + 2 * t + 1];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        uint32_t bf[2];
-        frag_b_nk(bf, W2, HD, nt * 8, j * 16, lane);
-        mma16816(c, a2[j], bf);
-      }
-      if (d0 >= 0) {
-        atomicAdd(&acc[d0 * HD + nt * 8 + 2 * t], c[0]);
-        atomicAdd(&acc[d0 * HD + nt * 8 + 2 * t + 1], c[1]);
-      }
-      if (d1 >= 0) {
-        atomicAdd(&acc[d1 * HD + nt * 8 + 2 * t], c[2]);
-        atomicAdd(&acc[d1 * HD + nt * 8 + 2 * t + 1], c[3]);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// One message half-round (backward) of direction dir: gradient dm of every message is the
-// gradient state of its destination; adds dx to the source accumulators and the weight
-// gradients to the CTA accumulators.
-__device__ void pass_backward(const Smem& S, const PriorArgs& a, int dir, int warp, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  unsigned char* wb = S.stage + warp * (16 * XK * 2 + 3 * 16 * HD * 2);
-  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(wb);
-  __nv_bfloat16* A1s = Xs + 16 * XK;
-  __nv_bfloat16* DMs = A1s + 16 * HD;
-  __nv_bfloat16* DZs = DMs + 16 * HD;
-  const __nv_bfloat16* W1T = S.W1T + dir * XK * HD;
-  const __nv_bfloat16* W2T = S.W2T + dir * HD * HD;
-  const float* gdst = dir == 0 ? S.gv : S.gc;          // gradient of the destination states
-  float* acc_first = dir == 0 ? S.accc : S.accv;      // x[0:32]
-  float* acc_second = dir == 0 ? S.accv : S.accc;     // x[32:64]
-  float* dW1 = S.dW1 + dir * HD * XK;
-  float* dW2 = S.dW2 + dir * HD * HD;
-  float db2 = 0.f;  // lane's column of db2
-  const int ntiles = (a.E + 15) / 16;
-  for (int tile = warp; tile < ntiles; tile += NWARP) {
-    stage_x(S, a, dir, tile, Xs, lane);
-    float z[4][4];
-    layer1(S, dir, Xs, z, lane);
-    const int e0 = tile * 16 + g, e1 = e0 + 8;
-    // a1 tile (for dW2) and dm tile (gathered gradient of the destinations)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      *reinterpret_cast<uint32_t*>(A1s + g * HD + nt * 8 + 2 * t) =
-          pack2(fmaxf(z[nt][0], 0.f), fmaxf(z[nt][1], 0.f));
-      *reinterpret_cast<uint32_t*>(A1s + (g + 8) * HD + nt * 8 + 2 * t) =
-          pack2(fmaxf(z[nt][2], 0.f), fmaxf(z[nt][3], 0.f));
-    }
-    for (int idx = lane; idx < 16 * (HD / 2); idx += 32) {
-      const int row = idx / (HD / 2), col = 2 * (idx % (HD / 2));
-      const int e = tile * 16 + row;
-      float v0 = 0.f, v1 = 0.f;
-      if (e < a.E) {
-        const int d = dir == 0 ? S.ev[e] : S.ec[e];
-        v0 = gdst[d * HD + col];
-        v1 = gdst[d * HD + col + 1];
-      }
-      *reinterpret_cast<uint32_t*>(DMs + row * HD + col) = pack2(v0, v1);
-    }
-    __syncwarp();
-    // db2: column sums of dm (lane = column)
-    for (int row = 0; row < 16; ++row) db2 += __bfloat162float(DMs[row * HD + lane]);
-    // da1 = dm W2 ; dz1 = da1 * [z1 > 0]
-    float dz[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) dz[nt][0] = dz[nt][1] = dz[nt][2] = dz[nt][3] = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      uint32_t af[4];
-      frag_a_row(af, DMs, HD, 0, j * 16, lane);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        uint32_t bf[2];
-        frag_b_nk(bf, W2T, HD, nt * 8, j * 16, lane);
-        mma16816(dz[nt], af, bf);
-      }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dz[nt][q] = z[nt][q] > 0.f ? dz[nt][q] : 0.f;
-      *reinterpret_cast<uint32_t*>(DZs + g * HD + nt * 8 + 2 * t) = pack2(dz[nt][0], dz[nt][1]);
-      *reinterpret_cast<uint32_t*>(DZs + (g + 8) * HD + nt * 8 + 2 * t) =
-          pack2(dz[nt][2], dz[nt][3]);
-    }
-    __syncwarp();
-    // dx = dz1 W1 (columns 0..63), scattered to the two endpoint accumulators
-    {
-      uint32_t af[2][4];
-      frag_a_row(af[0], DZs, HD, 0, 0, lane);
-      frag_a_row(af[1], DZs, HD, 0, 16, lane);
-      const int c0 = e0 < a.E ? S.ec[e0] : -1, v0 = e0 < a.E ? S.ev[e0] : -1;
-      const int c1 = e1 < a.E ? S.ec[e1] : -1, v1 = e1 < a.E ? S.ev[e1] : -1;
-      const int f0 = dir == 0 ? c0 : v0, s0 = dir == 0 ? v0 : c0;
-      const int f1 = dir == 0 ? c1 : v1, s1 = dir == 0 ? v1 : c1;
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          uint32_t bf[2];
-          frag_b_nk(bf, W1T, HD, nt * 8, j * 16, lane);
-          mma16816(c, af[j], bf);
-        }
-        const int col = (nt & 3) * 8 + 2 * t;
-        float* dst0 = nt < 4 ? (f0 >= 0 ? acc_first + f0 * HD : nullptr)
-                             : (s0 >= 0 ? acc_second + s0 * HD : nullptr);
-        float* dst1 = nt < 4 ? (f1 >= 0 ? acc_first + f1 * HD : nullptr)
-                             : (s1 >= 0 ? acc_second + s1 * HD : nullptr);
-        if (dst0) {
-          atomicAdd(dst0 + col, c[0]);
-          atomicAdd(dst0 + col + 1, c[1]);
-        }
-        if (dst1) {
-          atomicAdd(dst1 + col, c[2]);
-          atomicAdd(dst1 + col + 1, c[3]);
-        }
-      }
-    }
-    // dW2 += dm^T a1  (32 x 32, k = the 16 edges)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      uint32_t af[4];
-      frag_a_col(af, DMs, HD, mt * 16, 0, lane);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        uint32_t bf[2];
-        frag_b_kn(bf, A1s, HD, 0, nt * 8, lane);
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-        mma16816(c, af, bf);
-        float* w = dW2 + (mt * 16 + g) * HD + nt * 8 + 2 * t;
-        atomicAdd(w, c[0]);
-        atomicAdd(w + 1, c[1]);
-        atomicAdd(w + 8 * HD, c[2]);
-        atomicAdd(w + 8 * HD + 1, c[3]);
-      }
-    }
-    // dW1 += dz1^T X  (32 x 72 used: inputs 0..64 and the bias column 65)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      uint32_t af[4];
-      frag_a_col(af, DZs, HD, mt * 16, 0, lane);
-#pragma unroll
-      for (int nt = 0; nt < 9; ++nt) {
-        uint32_t bf[2];
-        frag_b_kn(bf, Xs, XK, 0, nt * 8, lane);
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-        mma16816(c, af, bf);
-        float* w = dW1 + (mt * 16 + g) * XK + nt * 8 + 2 * t;
-        atomicAdd(w, c[0]);
-        atomicAdd(w + 1, c[1]);
-        atomicAdd(w + 8 * XK, c[2]);
-        atomicAdd(w + 8 * XK + 1, c[3]);
-      }
-    }
-    __syncwarp();
-  }
-  atomicAdd(&S.db2[(dir == 0 ? G_b2cv : G_b2vc) * HD + lane], db2);
-}
-
-__device__ __forceinline__ void cta_zero(float* p, int count) {
-  for (int i = threadIdx.x; i < count; i += blockDim.x) p[i] = 0.f;
-}
-
-// h_dst += acc (and optionally copies h_dst to `save`)
-__device__ __forceinline__ void cta_add(float* h, const float* acc, int count, float* save) {
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    const float v = h[i] + acc[i];
-    h[i] = v;
-    if (save) save[i] = v;
-  }
-}
-
-template <bool TRAIN>
-__global__ void __launch_bounds__(kPriorThreads) prior_kernel(PriorArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int m = a.m, n = a.n, E = a.E;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const PLay L = prior_layout(m, n, E, TRAIN);
-  Smem S;
-  S.hv = reinterpret_cast<float*>(smem + L.hv);
-  S.hc = reinterpret_cast<float*>(smem + L.hc);
-  S.accv = reinterpret_cast<float*>(smem + L.accv);
-  S.accc = reinterpret_cast<float*>(smem + L.accc);
-  S.gv = reinterpret_cast<float*>(smem + L.gv);
-  S.gc = reinterpret_cast<float*>(smem + L.gc);
-  S.W1 = reinterpret_cast<__nv_bfloat16*>(smem + L.W1);
-  S.W2 = reinterpret_cast<__nv_bfloat16*>(smem + L.W2);
-  S.W1T = reinterpret_cast<__nv_bfloat16*>(smem + L.W1T);
-  S.W2T = reinterpret_cast<__nv_bfloat16*>(smem + L.W2T);
-  S.vec = reinterpret_cast<float*>(smem + L.vec);
-  S.dW1 = reinterpret_cast<float*>(smem + L.dW1);
-  S.dW2 = reinterpret_cast<float*>(smem + L.dW2);
-  S.db2 = reinterpret_cast<float*>(smem + L.db2);
-  S.stage = smem + L.stage;
-  S.ec = reinterpret_cast<uint16_t*>(smem + L.ec);
-  S.ev = reinterpret_cast<uint16_t*>(smem + L.ev);
-  S.sig = reinterpret_cast<float*>(smem + L.sig);
-  S.lam = reinterpret_cast<float*>(smem + L.lam);
-  S.llr = reinterpret_cast<float*>(smem + L.llr);
-  S.err = reinterpret_cast<uint8_t*>(smem + L.err);
-
-  // ---- parameters: BF16 weight tiles (and their transposes), FP32 vectors ----
-  const float* P = a.params;
-  for (int i = threadIdx.x; i < 2 * HD * XK; i += blockDim.x) {
-    const int dir = i / (HD * XK), r = (i / XK) % HD, k = i % XK;
-    const float v = k < DIN ? P[(dir ? POff::W1vc : POff::W1cv) + r * DIN + k] : 0.f;
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    S.W1[i] = b;
-    S.W1T[dir * XK * HD + k * HD + r] = b;
-  }
-  for (int i = threadIdx.x; i < 2 * HD * HD; i += blockDim.x) {
-    const int dir = i / (HD * HD), r = (i / HD) % HD, k = i % HD;
-    const __nv_bfloat16 b = __float2bfloat16_rn(P[(dir ? POff::W2vc : POff::W2cv) + r * HD + k]);
-    S.W2[i] = b;
-    S.W2T[dir * HD * HD + k * HD + r] = b;
-  }
-  for (int i = threadIdx.x; i < HD; i += blockDim.x) {
-    S.vec[V_a0 * HD + i] = P[POff::a0 + i];
-    S.vec[V_a1 * HD + i] = P[POff::a1 + i];
-    S.vec[V_u0 * HD + i] = P[POff::u0 + i];
-    S.vec[V_u1 * HD + i] = P[POff::u1 + i];
-    S.vec[V_b1cv * HD + i] = P[POff::b1cv + i];
-    S.vec[V_b2cv * HD + i] = P[POff::b2cv + i];
-    S.vec[V_b1vc * HD + i] = P[POff::b1vc + i];
-    S.vec[V_b2vc * HD + i] = P[POff::b2vc + i];
-    S.vec[V_wo * HD + i] = P[POff::wo + i];
-  }
-  if (threadIdx.x == 0) S.vec[V_bo * HD] = P[POff::bo];
-  for (int i = threadIdx.x; i < m; i += blockDim.x)
-    for (int e = a.chk_ptr[i]; e < a.chk_ptr[i + 1]; ++e) {
-      S.ec[e] = (uint16_t)i;
-      S.ev[e] = a.chk_var[e];
-    }
-  for (int j = threadIdx.x; j < n; j += blockDim.x) S.lam[j] = a.prior[j];
-  if (TRAIN) {
-    cta_zero(S.dW1, 2 * HD * XK);
-    cta_zero(S.dW2, 2 * HD * HD);
-    cta_zero(S.db2, 16 * HD);
-  }
-  __syncthreads();
-  const int R = a.rounds;
-  float* save = TRAIN ? a.scratch + (size_t)blockIdx.x * (R + 1) * (n + m) * HD : nullptr;
-  double loss_acc = 0.0;
-
-  for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
-    // ---- init ----
-    const uint8_t* sp = a.syndromes + shot * m;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) S.sig[i] = sp[i] ? -1.f : 1.f;
-    if (TRAIN)
-      for (int j = threadIdx.x; j < n; j += blockDim.x) S.err[j] = a.errors[shot * n + j];
-    __syncthreads();
-    for (int i = threadIdx.x; i < n * HD; i += blockDim.x) {
-      const int v = i / HD, k = i % HD;
-      const float z = fmaf(S.lam[v], S.vec[V_a0 * HD + k], S.vec[V_a1 * HD + k]);
-      S.hv[i] = fmaxf(z, 0.f);
-      if (TRAIN) save[i] = S.hv[i];
-    }
-    for (int i = threadIdx.x; i < m * HD; i += blockDim.x) {
-      const int c = i / HD, k = i % HD;
-      S.hc[i] = fmaf(S.sig[c], S.vec[V_u0 * HD + k], S.vec[V_u1 * HD + k]);
-      if (TRAIN) save[n * HD + i] = S.hc[i];
-    }
-    __syncthreads();
-    // ---- rounds ----
-    for (int r = 0; r < R; ++r) {
-      float* sv = TRAIN ? save + (size_t)(r + 1) * (n + m) * HD : nullptr;
-      cta_zero(S.accv, n * HD);
-      __syncthreads();
-      pass_forward(S, a, 0, warp, lane);
-      __syncthreads();
-      cta_add(S.hv, S.accv, n * HD, sv);
-      cta_zero(S.accc, m * HD);
-      __syncthreads();
-      pass_forward(S, a, 1, warp, lane);
-      __syncthreads();
-      cta_add(S.hc, S.accc, m * HD, sv ? sv + n * HD : nullptr);
-      __syncthreads();
-    }
-    // ---- output LLRs ----
-    for (int v = warp; v < n; v += NWARP) {
-      float d = S.hv[v * HD + lane] * S.vec[V_wo * HD + lane];
-      for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-      if (lane == 0) {
-        const float l = S.lam[v] + d + S.vec[V_bo * HD];
-        S.llr[v] = l;
-        if (!TRAIN && a.llr_out) a.llr_out[shot * n + v] = l;
-      }
-    }
-    __syncthreads();
-    if (!TRAIN) continue;
-
-    // ---- loss and dL/dLLR ----
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const float l = S.llr[v];
-      const float y = S.err[v] ? 1.f : 0.f;
-      const float sp_l = l > 0.f ? l + log1pf(__expf(-l)) : log1pf(__expf(l));
-      loss_acc += (double)(sp_l - (1.f - y) * l);
-      const float sg = 1.f / (1.f + __expf(-l));
-      S.llr[v] = (sg - (1.f - y)) * a.inv_norm;  // now dLLR
-    }
-    __syncthreads();
-    // dw_o, db_o (lane = hidden unit), g_v = dLLR w_o, g_c = 0
-    {
-      float dwo = 0.f, dbo = 0.f;
-      for (int v = warp; v < n; v += NWARP) {
-        dwo += S.llr[v] * S.hv[v * HD + lane];
-        dbo += lane == 0 ? S.llr[v] : 0.f;
-      }
-      atomicAdd(&S.db2[G_wo * HD + lane], dwo);
-      if (lane == 0) atomicAdd(&S.db2[G_bo * HD], dbo);
-    }
-    for (int i = threadIdx.x; i < n * HD; i += blockDim.x)
-      S.gv[i] = S.llr[i / HD] * S.vec[V_wo * HD + (i % HD)];
-    cta_zero(S.gc, m * HD);
-    __syncthreads();
-    for (int r = R - 1; r >= 0; --r) {
-      const float* st0 = save + (size_t)r * (n + m) * HD;        // h_v^r, h_c^r
-      const float* st1 = save + (size_t)(r + 1) * (n + m) * HD;  // h_v^{r+1}, h_c^{r+1}
-      // direction v -> c of round r: inputs h_v^{r+1}, h_c^r
-      for (int i = threadIdx.x; i < n * HD; i += blockDim.x) S.hv[i] = st1[i];
-      for (int i = threadIdx.x; i < m * HD; i += blockDim.x) S.hc[i] = st0[n * HD + i];
-      cta_zero(S.accv, n * HD);
-      cta_zero(S.accc, m * HD);
-      __syncthreads();
-      pass_backward(S, a, 1, warp, lane);
-      __syncthreads();
-      cta_add(S.gv, S.accv, n * HD, nullptr);
-      cta_add(S.gc, S.accc, m * HD, nullptr);
-      // direction c -> v of round r: inputs h_c^r, h_v^r
-      for (int i = threadIdx.x; i < n * HD; i += blockDim.x) S.hv[i] = st0[i];
-      cta_zero(S.accv, n * HD);
-      cta_zero(S.accc, m * HD);
-      __syncthreads();
-      pass_backward(S, a, 0, warp, lane);
-      __syncthreads();
-      cta_add(S.gv, S.accv, n * HD, nullptr);
-      cta_add(S.gc, S.accc, m * HD, nullptr);
-      __syncthreads();
-    }
-    // init-layer gradients (hv holds h_v^0 = relu(z_v^0): z > 0 iff h > 0)
-    {
-      float da0 = 0.f, da1 = 0.f, du0 = 0.f, du1 = 0.f;
-      for (int v = warp; v < n; v += NWARP) {
-        const float z = fmaf(S.lam[v], S.vec[V_a0 * HD + lane], S.vec[V_a1 * HD + lane]);
-        const float gz = z > 0.f ? S.gv[v * HD + lane] : 0.f;
-        da0 += gz * S.lam[v];
-        da1 += gz;
-      }
-      for (int c = warp; c < m; c += NWARP) {
-        du0 += S.gc[c * HD + lane] * S.sig[c];
-        du1 += S.gc[c * HD + lane];
-      }
-      atomicAdd(&S.db2[G_a0 * HD + lane], da0);
-      atomicAdd(&S.db2[G_a1 * HD + lane], da1);
-      atomicAdd(&S.db2[G_u0 * HD + lane], du0);
-      atomicAdd(&S.db2[G_u1 * HD + lane], du1);
-    }
-    __syncthreads();
-  }
-  if (!TRAIN) return;
-  // ---- flush the CTA's gradients ----
-  __syncthreads();
-  float* G = a.grads;
-  for (int i = threadIdx.x; i < 2 * HD * XK; i += blockDim.x) {
-    const int dir = i / (HD * XK), r = (i / XK) % HD, k = i % XK;
-    const float v = S.dW1[i];
-    if (k < DIN) atomicAdd(&G[(dir ? POff::W1vc : POff::W1cv) + r * DIN + k], v);
-    else if (k == DIN) atomicAdd(&G[(dir ? POff::b1vc : POff::b1cv) + r], v);
-  }
-  for (int i = threadIdx.x; i < 2 * HD * HD; i += blockDim.x) {
-    const int dir = i / (HD * HD), rk = i % (HD * HD);
-    atomicAdd(&G[(dir ? POff::W2vc : POff::W2cv) + rk], S.dW2[i]);
-  }
-  for (int i = threadIdx.x; i < HD; i += blockDim.x) {
-    atomicAdd(&G[POff::b2cv + i], S.db2[G_b2cv * HD + i]);
-    atomicAdd(&G[POff::b2vc + i], S.db2[G_b2vc * HD + i]);
-    atomicAdd(&G[POff::a0 + i], S.db2[G_a0 * HD + i]);
-    atomicAdd(&G[POff::a1 + i], S.db2[G_a1 * HD + i]);
-    atomicAdd(&G[POff::u0 + i], S.db2[G_u0 * HD + i]);
-    atomicAdd(&G[POff::u1 + i], S.db2[G_u1 * HD + i]);
-    atomicAdd(&G[POff::wo + i], S.db2[G_wo * HD + i]);
-  }
-  if (threadIdx.x == 0) atomicAdd(&G[POff::bo], S.db2[G_bo * HD]);
-  for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-  if (lane == 0 && loss_acc != 0.0) atomicAdd(a.loss, loss_acc);
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
@@ -812,7 +234,8 @@ struct FwdSmem {
 //   are formed in registers (and sigma_c recorded) instead of read.
 template <bool CHECK>
 __device__ __forceinline__ void g_step(const FwdSmem& S, int rows, int r0, bool has_agg, bool proj,
-                                       float* llr, int lane, const uint8_t* syn = nullptr) {
+                                       float* llr, int lane, const uint8_t* syn = nullptr,
+                                       __nv_bfloat16* save = nullptr) {
   const int g = lane >> 2, t = lane & 3;
   const int ra = r0 + g, rb = r0 + g + 8;
   float* h = CHECK ? S.hc : S.hv;
@@ -882,6 +305,14 @@ __device__ __forceinline__ void g_step(const FwdSmem& S, int rows, int r0, bool 
       const int col = nt * 8 + 2 * t;
       if (ra < rows) *reinterpret_cast<float2*>(h + fsw(ra, col)) = make_float2(c[nt][0], c[nt][1]);
       if (rb < rows) *reinterpret_cast<float2*>(h + fsw(rb, col)) = make_float2(c[nt][2], c[nt][3]);
+    }
+  }
+  if (save) {  // training: the new state rounded to BF16, row-major, for the backward pass
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = nt * 8 + 2 * t;
+      if (ra < rows) *reinterpret_cast<uint32_t*>(save + ra * HD + col) = pack2(c[nt][0], c[nt][1]);
+      if (rb < rows) *reinterpret_cast<uint32_t*>(save + rb * HD + col) = pack2(c[nt][2], c[nt][3]);
     }
   }
   if (!proj) {  // variables, last round: LLR_v = lambda_v + w_o . h_v + b_o
@@ -1092,17 +523,608 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a)
   }
 }
 
+
+// ======================================================================================
+// Training on per-node products: the forward pass of prior_fwd_kernel (the states of every
+// round saved in BF16 to a per-CTA scratch), the loss, and the backward pass of the same
+// decomposition, round by round in reverse.  With W1cv = [Ucv | Vcv | w_s] (h_c, h_v, sigma
+// blocks) and W1vc = [Uvc | Vvc | w_s'] (h_v', h_c, sigma blocks), for round t with output
+// gradients g_hv' = dL/dh_v^{t+1} and g_hc' = dL/dh_c^{t+1}:
+//   vc half:  gT_c = W2vc^T g_hc'       y_e = C_v + D_c
+//             gC_v = sum_c gT_c [y_e > 0]    gD_c = gT_c * #{v in N(c) : y_e > 0}
+//             g_hv' += Uvc^T gC_v             g_hc = g_hc' + Vvc^T gD_c
+//   cv half:  gS_v = W2cv^T g_hv'       z_e = A_c + B_v
+//             gA_c = sum_v gS_v [z_e > 0]    gB_v = gS_v * #{c in N(v) : z_e > 0}
+//             g_hc += Ucv^T gA_c              g_hv = g_hv' + Vcv^T gB_v
+//   weights:  dW2vc += sum_c g_hc' T_c^T, dVvc += sum_c gD_c h_c^T, dUvc += sum_v gC_v h_v'^T,
+//             dW2cv += sum_v g_hv' S_v^T, dUcv += sum_c gA_c h_c^T, dVcv += sum_v gB_v h_v^T;
+//             db2 = sum deg g_h', db1 = sum gD (gA), dw_s = sum sigma gD (gA).
+// All products run on mma.sync with BF16 operands and FP32 accumulation.  Warps 0-5 each own
+// one weight gradient and keep it in registers across every shot of the launch; warps 6-7
+// accumulate the vector gradients.  One CTA (8 warps) per SM and shot.
+// ======================================================================================
+
+struct TrainArgs {
+  int m, n, rounds;
+  const int32_t* chk_ptr;
+  const uint16_t* chk_var;
+  const int32_t* var_ptr;
+  const uint16_t* var_chk;
+  const float* prior;
+  const float* params;
+  long long shots;
+  const uint8_t* syndromes;
+  const uint8_t* errors;
+  __nv_bfloat16* scratch;  // per CTA: (R + 1) n + R m rows of 32 BF16 states
+  float* grads;
+  double* loss;
+  float inv_norm;
+};
+
+struct TLay {
+  int npad, mpad;
+  size_t hv, hc, cv, bv, ac, dc, hvA, hvB, hcA, Sv, Tc, gT, gD, gA, gC, gS, gB, ghv, ghc;
+  size_t w, wt, vec, vg, sig, lam, degv, degc, llr, total;
+};
+
+__host__ __device__ inline TLay train_layout(int m, int n) {
+  TLay L;
+  L.npad = (n + 15) & ~15;
+  L.mpad = (m + 15) & ~15;
+  const size_t fv = (size_t)L.npad * HD * 4, fc = (size_t)L.mpad * HD * 4;
+  const size_t bv = fv / 2, bc = fc / 2;
+  size_t o = 0;
+  L.hv = o; o += fv;
+  L.hc = o; o += fc;
+  L.cv = o; o += bv;
+  L.bv = o; o += bv;
+  L.hvA = o; o += bv;
+  L.hvB = o; o += bv;
+  L.Sv = o; o += bv;
+  L.gC = o; o += bv;
+  L.gS = o; o += bv;
+  L.gB = o; o += bv;
+  L.ghv = o; o += bv;
+  L.ac = o; o += bc;
+  L.dc = o; o += bc;
+  L.hcA = o; o += bc;
+  L.Tc = o; o += bc;
+  L.gT = o; o += bc;
+  L.gD = o; o += bc;
+  L.gA = o; o += bc;
+  L.ghc = o; o += bc;
+  L.w = o; o += (size_t)6 * HD * HD * 2;
+  L.wt = o; o += (size_t)6 * HD * HD * 2;
+  L.vec = o; o += (size_t)12 * HD * 4;
+  L.vg = o; o += (size_t)12 * HD * 4;
+  L.sig = o; o += a16((size_t)L.mpad * 4);
+  L.lam = o; o += a16((size_t)L.npad * 4);
+  L.degv = o; o += a16((size_t)L.npad * 4);
+  L.degc = o; o += a16((size_t)L.mpad * 4);
+  L.llr = o; o += a16((size_t)L.npad * 4);
+  L.total = o;
+  return L;
+}
+
+// vector-gradient slots
+enum { VG_b2cv = 0, VG_b2vc, VG_wscv, VG_b1cv, VG_wsvc, VG_b1vc, VG_a0, VG_a1, VG_u0, VG_u1,
+       VG_wo, VG_bo };
+
+// acc[NT] += A[r0 .. r0+15][0..32) (BF16, swizzled) x W[w0 .. w0 + 8 NT)^T
+template <int NT>
+__device__ __forceinline__ void tile_mm(float acc[NT][4], const __nv_bfloat16* A, int r0,
+                                        const __nv_bfloat16* Wt, int w0, int lane) {
+  uint32_t af[2][4];
+  fa_sw(af[0], A, r0, 0, lane);
+  fa_sw(af[1], A, r0, 16, lane);
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint32_t bf[2];
+      fb_sw(bf, Wt, w0 + nt * 8, j * 16, lane);
+      mma16816(acc[nt], af[j], bf);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void tile_store_bf16(__nv_bfloat16* dst, int r0, int rows,
+                                                const float acc[NT][4], int lane) {
+  const int g = lane >> 2, t = lane & 3, ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    if (ra < rows) *reinterpret_cast<uint32_t*>(dst + bsw(ra, col)) = pack2(acc[nt][0], acc[nt][1]);
+    if (rb < rows) *reinterpret_cast<uint32_t*>(dst + bsw(rb, col)) = pack2(acc[nt][2], acc[nt][3]);
+  }
+}
+
+// FP32 state rows r0..r0+15 += A x W^T (in place), optionally copied out in BF16.
+__device__ __forceinline__ void tile_update_f32(float* h, const __nv_bfloat16* A, int r0, int rows,
+                                                const __nv_bfloat16* Wt, __nv_bfloat16* copy,
+                                                int lane) {
+  const int g = lane >> 2, t = lane & 3, ra = r0 + g, rb = r0 + g + 8;
+  float acc[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    const float2 x = *reinterpret_cast<const float2*>(h + fsw(ra, col));
+    const float2 y = *reinterpret_cast<const float2*>(h + fsw(rb, col));
+    acc[nt][0] = x.x;
+    acc[nt][1] = x.y;
+    acc[nt][2] = y.x;
+    acc[nt][3] = y.y;
+  }
+  tile_mm<4>(acc, A, r0, Wt, 0, lane);
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    if (ra < rows) *reinterpret_cast<float2*>(h + fsw(ra, col)) = make_float2(acc[nt][0], acc[nt][1]);
+    if (rb < rows) *reinterpret_cast<float2*>(h + fsw(rb, col)) = make_float2(acc[nt][2], acc[nt][3]);
+  }
+  if (copy) tile_store_bf16<4>(copy, r0, rows, acc, lane);
+}
+
+__device__ __forceinline__ float bf_at(const __nv_bfloat16* base, int r, int c) {
+  return __bfloat162float(base[bsw(r, c)]);
+}
+__device__ __forceinline__ uint32_t bf_pair(const __nv_bfloat16* base, int r0, int r1, int c) {
+  return pack_bf(base[bsw(r0, c)], base[bsw(r1, c)]);
+}
+
+// acc (32 x 32, j x k) += sum over rows of G[row][j] H[row][k]  (rows 0..K, K % 16 == 0; the
+// padding rows of G and H are zero)
+__device__ __forceinline__ void wgrad_mm(float acc[2][4][4], const __nv_bfloat16* G,
+                                         const __nv_bfloat16* H, int K, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const int ka = k0 + 2 * t, kb = ka + 8;
+    uint32_t af[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int j = mt * 16 + g;
+      af[mt][0] = bf_pair(G, ka, ka + 1, j);
+      af[mt][1] = bf_pair(G, ka, ka + 1, j + 8);
+      af[mt][2] = bf_pair(G, kb, kb + 1, j);
+      af[mt][3] = bf_pair(G, kb, kb + 1, j + 8);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      uint32_t bf[2];
+      const int kk = nt * 8 + g;
+      bf[0] = bf_pair(H, ka, ka + 1, kk);
+      bf[1] = bf_pair(H, kb, kb + 1, kk);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], af[mt], bf);
+    }
+  }
+}
+
+// Copy `rows` rows of 32 BF16 values (row-major, global) into a swizzled shared array.
+__device__ __forceinline__ void load_rows(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows) {
+  for (int i = threadIdx.x; i < rows * 4; i += blockDim.x) {
+    const int r = i >> 2, b = i & 3;
+    *reinterpret_cast<uint4*>(dst + bsw(r, 8 * b)) =
+        *reinterpret_cast<const uint4*>(src + r * HD + 8 * b);
+  }
+}
+
+__global__ void __launch_bounds__(kFwdWarps * 32, 1) prior_train_kernel(TrainArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = a.m, n = a.n, R = a.rounds;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TLay L = train_layout(m, n);
+  auto BF = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(smem + off); };
+  FwdSmem S;
+  S.hv = reinterpret_cast<float*>(smem + L.hv);
+  S.hc = reinterpret_cast<float*>(smem + L.hc);
+  S.cv = BF(L.cv);
+  S.bv = BF(L.bv);
+  S.ac = BF(L.ac);
+  S.dc = BF(L.dc);
+  S.W2cv = BF(L.w);
+  S.Wv = S.W2cv + HD * HD;
+  S.W2vc = S.Wv + 2 * HD * HD;
+  S.Wc = S.W2vc + HD * HD;
+  S.vec = reinterpret_cast<float*>(smem + L.vec);
+  S.sig = reinterpret_cast<float*>(smem + L.sig);
+  S.lam = reinterpret_cast<float*>(smem + L.lam);
+  S.degv = reinterpret_cast<float*>(smem + L.degv);
+  S.degc = reinterpret_cast<float*>(smem + L.degc);
+  S.llr = reinterpret_cast<float*>(smem + L.llr);
+  __nv_bfloat16 *hvA = BF(L.hvA), *hvB = BF(L.hvB), *hcA = BF(L.hcA), *Sv = BF(L.Sv),
+                *Tc = BF(L.Tc), *gT = BF(L.gT), *gD = BF(L.gD), *gA = BF(L.gA), *gC = BF(L.gC),
+                *gS = BF(L.gS), *gB = BF(L.gB), *ghv = BF(L.ghv), *ghc = BF(L.ghc);
+  __nv_bfloat16* WT = BF(L.wt);  // transposed weights: W2vc, Vvc, Uvc, W2cv, Ucv, Vcv
+  float* vg = reinterpret_cast<float*>(smem + L.vg);
+  float* gv = S.hv;  // after the forward pass: dL/dh_v, dL/dh_c
+  float* gc = S.hc;
+
+  // ---- parameters, graph degrees, zero padding ----
+  const float* P = a.params;
+  for (int i = threadIdx.x; i < HD * HD; i += blockDim.x) {
+    const int r = i >> 5, k = i & 31;
+    const float w2cv = P[POff::W2cv + r * HD + k], w2vc = P[POff::W2vc + r * HD + k];
+    const float ucv = P[POff::W1cv + r * DIN + k], vcv = P[POff::W1cv + r * DIN + HD + k];
+    const float uvc = P[POff::W1vc + r * DIN + k], vvc = P[POff::W1vc + r * DIN + HD + k];
+    S.W2cv[bsw(r, k)] = __float2bfloat16_rn(w2cv);
+    S.W2vc[bsw(r, k)] = __float2bfloat16_rn(w2vc);
+    S.Wv[bsw(r, k)] = __float2bfloat16_rn(uvc);        // C
+    S.Wv[bsw(r + HD, k)] = __float2bfloat16_rn(vcv);   // B
+    S.Wc[bsw(r, k)] = __float2bfloat16_rn(ucv);        // A
+    S.Wc[bsw(r + HD, k)] = __float2bfloat16_rn(vvc);   // D
+    // transposes (row k, column r)
+    WT[0 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(w2vc);
+    WT[1 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(vvc);
+    WT[2 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(uvc);
+    WT[3 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(w2cv);
+    WT[4 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(ucv);
+    WT[5 * HD * HD + bsw(k, r)] = __float2bfloat16_rn(vcv);
+  }
+  for (int i = threadIdx.x; i < HD; i += blockDim.x) {
+    S.vec[F_a0 * HD + i] = P[POff::a0 + i];
+    S.vec[F_a1 * HD + i] = P[POff::a1 + i];
+    S.vec[F_u0 * HD + i] = P[POff::u0 + i];
+    S.vec[F_u1 * HD + i] = P[POff::u1 + i];
+    S.vec[F_b2cv * HD + i] = P[POff::b2cv + i];
+    S.vec[F_b2vc * HD + i] = P[POff::b2vc + i];
+    S.vec[F_wscv * HD + i] = P[POff::W1cv + i * DIN + 2 * HD];
+    S.vec[F_b1cv * HD + i] = P[POff::b1cv + i];
+    S.vec[F_wsvc * HD + i] = P[POff::W1vc + i * DIN + 2 * HD];
+    S.vec[F_b1vc * HD + i] = P[POff::b1vc + i];
+    S.vec[F_wo * HD + i] = P[POff::wo + i];
+    S.vec[F_bo * HD + i] = i == 0 ? P[POff::bo] : 0.f;
+  }
+  for (int i = threadIdx.x; i < 12 * HD; i += blockDim.x) vg[i] = 0.f;
+  for (int j = threadIdx.x; j < L.npad; j += blockDim.x) {
+    S.lam[j] = j < n ? a.prior[j] : 0.f;
+    S.degv[j] = j < n ? (float)(a.var_ptr[j + 1] - a.var_ptr[j]) : 0.f;
+  }
+  for (int i = threadIdx.x; i < L.mpad; i += blockDim.x) {
+    S.degc[i] = i < m ? (float)(a.chk_ptr[i + 1] - a.chk_ptr[i]) : 0.f;
+    S.sig[i] = 0.f;
+  }
+  // every node array starts zero, so its padding rows stay zero
+  {
+    uint32_t* z = reinterpret_cast<uint32_t*>(smem + L.hv);
+    const size_t words = (L.w - L.hv) / 4;
+    for (size_t i = threadIdx.x; i < words; i += blockDim.x) z[i] = 0u;
+  }
+  __syncthreads();
+  const int vt = L.npad >> 4, ct = L.mpad >> 4;
+  __nv_bfloat16* save = a.scratch + (size_t)blockIdx.x * ((size_t)(R + 1) * n + (size_t)R * m) * HD;
+  auto save_hv = [&](int t) { return save + (size_t)t * n * HD; };
+  auto save_hc = [&](int t) { return save + (size_t)(R + 1) * n * HD + (size_t)t * m * HD; };
+
+  float wacc[2][4][4];  // warps 0-5: one weight gradient (32 x 32)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wacc[i][j][q] = 0.f;
+  double loss_acc = 0.0;
+
+  for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
+    const uint8_t* sp = a.syndromes + shot * m;
+    const uint8_t* ep = a.errors + shot * n;
+    // ================= forward (prior_fwd_kernel, saving every state) =================
+    for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+      if (tile < vt) g_step<false>(S, n, tile * 16, false, true, nullptr, lane, sp, save_hv(0));
+      else g_step<true>(S, m, (tile - vt) * 16, false, true, nullptr, lane, sp, save_hc(0));
+    }
+    __syncthreads();
+    for (int r = 0; r < R; ++r) {
+      const bool last = r == R - 1;
+      for (int tile = warp; tile < vt; tile += kFwdWarps) {
+        x_tile(n, tile * 16, a.var_ptr, a.var_chk, S.ac, S.bv, lane);
+        g_step<false>(S, n, tile * 16, true, !last, S.llr, lane, nullptr, save_hv(r + 1));
+      }
+      __syncthreads();
+      if (last) break;
+      for (int tile = warp; tile < ct; tile += kFwdWarps) {
+        x_tile(m, tile * 16, a.chk_ptr, a.chk_var, S.cv, S.dc, lane);
+        g_step<true>(S, m, tile * 16, true, true, nullptr, lane, nullptr, save_hc(r + 1));
+      }
+      __syncthreads();
+    }
+    // ================= loss, dL/dLLR, output layer =================
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      const float l = S.llr[v];
+      const float y = ep[v] ? 1.f : 0.f;
+      const float sp_l = l > 0.f ? l + log1pf(__expf(-l)) : log1pf(__expf(l));
+      loss_acc += (double)(sp_l - (1.f - y) * l);
+      S.llr[v] = (1.f / (1.f + __expf(-l)) - (1.f - y)) * a.inv_norm;
+    }
+    __syncthreads();
+    {
+      float dwo = 0.f, dbo = 0.f;
+      for (int v = warp; v < n; v += kFwdWarps) {
+        dwo = fmaf(S.llr[v], S.hv[fsw(v, lane)], dwo);
+        dbo += S.llr[v];
+      }
+      atomicAdd(&vg[VG_wo * HD + lane], dwo);
+      if (lane == 0) atomicAdd(&vg[VG_bo * HD], dbo);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * HD; i += blockDim.x) {
+      const int v = i >> 5, k = i & 31;
+      gv[fsw(v, k)] = S.llr[v] * S.vec[F_wo * HD + k];
+    }
+    for (int i = threadIdx.x; i < m * HD; i += blockDim.x) gc[fsw(i >> 5, i & 31)] = 0.f;
+    __syncthreads();
+    // ================= backward, rounds in reverse =================
+    for (int r = R - 1; r >= 0; --r) {
+      // states of the round and the BF16 copy of dL/dh_c^{r+1}
+      load_rows(hvB, save_hv(r + 1), n);
+      load_rows(hvA, save_hv(r), n);
+      load_rows(hcA, save_hc(r), m);
+      for (int i = threadIdx.x; i < m * HD / 2; i += blockDim.x) {
+        const int c = i >> 4, k = 2 * (i & 15);
+        const float2 x = *reinterpret_cast<const float2*>(gc + fsw(c, k));
+        *reinterpret_cast<uint32_t*>(ghc + bsw(c, k)) = pack2(x.x, x.y);
+      }
+      __syncthreads();
+      // projections A, D (checks), B, C (variables); gT = W2vc^T g_hc'
+      for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+        const int g = lane >> 2, t = lane & 3;
+        if (tile < vt) {
+          const int r0 = tile * 16;
+          float accB[4][4] = {}, accC[4][4] = {};
+          tile_mm<4>(accB, hvA, r0, S.Wv, HD, lane);
+          tile_mm<4>(accC, hvB, r0, S.Wv, 0, lane);
+          tile_store_bf16<4>(S.bv, r0, n, accB, lane);
+          tile_store_bf16<4>(S.cv, r0, n, accC, lane);
+        } else {
+          const int r0 = (tile - vt) * 16, ra = r0 + g, rb = r0 + g + 8;
+          const float sa = S.sig[ra], sb = S.sig[rb];
+          float accA[4][4], accD[4][4], accT[4][4] = {};
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int col = nt * 8 + 2 * t + q;
+              accA[nt][q] = fmaf(sa, S.vec[F_wscv * HD + col], S.vec[F_b1cv * HD + col]);
+              accA[nt][2 + q] = fmaf(sb, S.vec[F_wscv * HD + col], S.vec[F_b1cv * HD + col]);
+              accD[nt][q] = fmaf(sa, S.vec[F_wsvc * HD + col], S.vec[F_b1vc * HD + col]);
+              accD[nt][2 + q] = fmaf(sb, S.vec[F_wsvc * HD + col], S.vec[F_b1vc * HD + col]);
+            }
+          tile_mm<4>(accA, hcA, r0, S.Wc, 0, lane);
+          tile_mm<4>(accD, hcA, r0, S.Wc, HD, lane);
+          tile_mm<4>(accT, ghc, r0, WT, 0, lane);
+          tile_store_bf16<4>(S.ac, r0, m, accA, lane);
+          tile_store_bf16<4>(S.dc, r0, m, accD, lane);
+          tile_store_bf16<4>(gT, r0, m, accT, lane);
+        }
+      }
+      __syncthreads();
+      // gathers of the vc half (and S for dW2cv): 4 lanes of 8 columns per node
+      for (int i = threadIdx.x; i < (n + m) * 4; i += blockDim.x) {
+        const int b = i & 3;
+        float x0[8], acc1[8], acc2[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc1[k] = acc2[k] = 0.f;
+        if (i < n * 4) {  // variable v: S_v, gC_v
+          const int v = i >> 2;
+          float bvv[8];
+          unpack8(*reinterpret_cast<const uint4*>(S.cv + bsw(v, 8 * b)), x0);
+          unpack8(*reinterpret_cast<const uint4*>(S.bv + bsw(v, 8 * b)), bvv);
+          for (int e = a.var_ptr[v]; e < a.var_ptr[v + 1]; ++e) {
+            const int c = a.var_chk[e];
+            float av[8], dv[8], tv[8];
+            unpack8(*reinterpret_cast<const uint4*>(S.ac + bsw(c, 8 * b)), av);
+            unpack8(*reinterpret_cast<const uint4*>(S.dc + bsw(c, 8 * b)), dv);
+            unpack8(*reinterpret_cast<const uint4*>(gT + bsw(c, 8 * b)), tv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              acc1[k] += fmaxf(av[k] + bvv[k], 0.f);
+              acc2[k] += (x0[k] + dv[k] > 0.f) ? tv[k] : 0.f;
+            }
+          }
+          *reinterpret_cast<uint4*>(Sv + bsw(v, 8 * b)) =
+              make_uint4(pack2(acc1[0], acc1[1]), pack2(acc1[2], acc1[3]), pack2(acc1[4], acc1[5]),
+                         pack2(acc1[6], acc1[7]));
+          *reinterpret_cast<uint4*>(gC + bsw(v, 8 * b)) =
+              make_uint4(pack2(acc2[0], acc2[1]), pack2(acc2[2], acc2[3]), pack2(acc2[4], acc2[5]),
+                         pack2(acc2[6], acc2[7]));
+        } else {  // check c: T_c, gD_c
+          const int c = (i >> 2) - n;
+          float tv[8];
+          unpack8(*reinterpret_cast<const uint4*>(S.dc + bsw(c, 8 * b)), x0);
+          unpack8(*reinterpret_cast<const uint4*>(gT + bsw(c, 8 * b)), tv);
+          for (int e = a.chk_ptr[c]; e < a.chk_ptr[c + 1]; ++e) {
+            const int v = a.chk_var[e];
+            float cvv[8];
+            unpack8(*reinterpret_cast<const uint4*>(S.cv + bsw(v, 8 * b)), cvv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const float y = cvv[k] + x0[k];
+              acc1[k] += fmaxf(y, 0.f);
+              acc2[k] += y > 0.f ? 1.f : 0.f;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc2[k] *= tv[k];
+          *reinterpret_cast<uint4*>(Tc + bsw(c, 8 * b)) =
+              make_uint4(pack2(acc1[0], acc1[1]), pack2(acc1[2], acc1[3]), pack2(acc1[4], acc1[5]),
+                         pack2(acc1[6], acc1[7]));
+          *reinterpret_cast<uint4*>(gD + bsw(c, 8 * b)) =
+              make_uint4(pack2(acc2[0], acc2[1]), pack2(acc2[2], acc2[3]), pack2(acc2[4], acc2[5]),
+                         pack2(acc2[6], acc2[7]));
+        }
+      }
+      __syncthreads();
+      // g_hv' += Uvc^T gC (and its BF16 copy);  g_hc = g_hc' + Vvc^T gD
+      for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+        if (tile < vt) tile_update_f32(gv, gC, tile * 16, n, WT + 2 * HD * HD, ghv, lane);
+        else tile_update_f32(gc, gD, (tile - vt) * 16, m, WT + 1 * HD * HD, nullptr, lane);
+      }
+      __syncthreads();
+      // gS = W2cv^T g_hv'
+      for (int tile = warp; tile < vt; tile += kFwdWarps) {
+        float acc[4][4] = {};
+        tile_mm<4>(acc, ghv, tile * 16, WT + 3 * HD * HD, 0, lane);
+        tile_store_bf16<4>(gS, tile * 16, n, acc, lane);
+      }
+      __syncthreads();
+      // gathers of the cv half: gA_c, gB_v
+      for (int i = threadIdx.x; i < (n + m) * 4; i += blockDim.x) {
+        const int b = i & 3;
+        float x0[8], acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+        if (i < n * 4) {  // variable v: gB_v = gS_v * #{c : A_c + B_v > 0}
+          const int v = i >> 2;
+          float sv[8];
+          unpack8(*reinterpret_cast<const uint4*>(S.bv + bsw(v, 8 * b)), x0);
+          unpack8(*reinterpret_cast<const uint4*>(gS + bsw(v, 8 * b)), sv);
+          for (int e = a.var_ptr[v]; e < a.var_ptr[v + 1]; ++e) {
+            float av[8];
+            unpack8(*reinterpret_cast<const uint4*>(S.ac + bsw(a.var_chk[e], 8 * b)), av);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += (av[k] + x0[k] > 0.f) ? 1.f : 0.f;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc[k] *= sv[k];
+          *reinterpret_cast<uint4*>(gB + bsw(v, 8 * b)) =
+              make_uint4(pack2(acc[0], acc[1]), pack2(acc[2], acc[3]), pack2(acc[4], acc[5]),
+                         pack2(acc[6], acc[7]));
+        } else {  // check c: gA_c = sum_v gS_v [A_c + B_v > 0]
+          const int c = (i >> 2) - n;
+          unpack8(*reinterpret_cast<const uint4*>(S.ac + bsw(c, 8 * b)), x0);
+          for (int e = a.chk_ptr[c]; e < a.chk_ptr[c + 1]; ++e) {
+            const int v = a.chk_var[e];
+            float bvv[8], sv[8];
+            unpack8(*reinterpret_cast<const uint4*>(S.bv + bsw(v, 8 * b)), bvv);
+            unpack8(*reinterpret_cast<const uint4*>(gS + bsw(v, 8 * b)), sv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += (x0[k] + bvv[k] > 0.f) ? sv[k] : 0.f;
+          }
+          *reinterpret_cast<uint4*>(gA + bsw(c, 8 * b)) =
+              make_uint4(pack2(acc[0], acc[1]), pack2(acc[2], acc[3]), pack2(acc[4], acc[5]),
+                         pack2(acc[6], acc[7]));
+        }
+      }
+      __syncthreads();
+      // g_hc += Ucv^T gA;  g_hv = g_hv' + Vcv^T gB;  then the parameter gradients of the round
+      for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+        if (tile < vt) tile_update_f32(gv, gB, tile * 16, n, WT + 5 * HD * HD, nullptr, lane);
+        else tile_update_f32(gc, gA, (tile - vt) * 16, m, WT + 4 * HD * HD, nullptr, lane);
+      }
+      switch (warp) {
+        case 0: wgrad_mm(wacc, ghc, Tc, L.mpad, lane); break;   // dW2vc
+        case 1: wgrad_mm(wacc, gD, hcA, L.mpad, lane); break;   // dVvc
+        case 2: wgrad_mm(wacc, gC, hvB, L.npad, lane); break;   // dUvc
+        case 3: wgrad_mm(wacc, ghv, Sv, L.npad, lane); break;   // dW2cv
+        case 4: wgrad_mm(wacc, gA, hcA, L.mpad, lane); break;   // dUcv
+        case 5: wgrad_mm(wacc, gB, hvA, L.npad, lane); break;   // dVcv
+        case 6: {
+          float b2 = 0.f, ws = 0.f, b1 = 0.f;
+          for (int c = 0; c < m; ++c) {
+            const float gd = bf_at(gD, c, lane);
+            b2 = fmaf(S.degc[c], bf_at(ghc, c, lane), b2);
+            ws = fmaf(S.sig[c], gd, ws);
+            b1 += gd;
+          }
+          vg[VG_b2vc * HD + lane] += b2;
+          vg[VG_wsvc * HD + lane] += ws;
+          vg[VG_b1vc * HD + lane] += b1;
+          break;
+        }
+        default: {
+          float b2 = 0.f, ws = 0.f, b1 = 0.f;
+          for (int v = 0; v < n; ++v) b2 = fmaf(S.degv[v], bf_at(ghv, v, lane), b2);
+          for (int c = 0; c < m; ++c) {
+            const float ga = bf_at(gA, c, lane);
+            ws = fmaf(S.sig[c], ga, ws);
+            b1 += ga;
+          }
+          vg[VG_b2cv * HD + lane] += b2;
+          vg[VG_wscv * HD + lane] += ws;
+          vg[VG_b1cv * HD + lane] += b1;
+          break;
+        }
+      }
+      __syncthreads();
+    }
+    // ================= the initial states =================
+    if (warp == 0) {
+      float d0 = 0.f, d1 = 0.f;
+      for (int v = 0; v < n; ++v) {
+        const float z = fmaf(S.lam[v], S.vec[F_a0 * HD + lane], S.vec[F_a1 * HD + lane]);
+        const float gz = z > 0.f ? gv[fsw(v, lane)] : 0.f;
+        d0 = fmaf(gz, S.lam[v], d0);
+        d1 += gz;
+      }
+      vg[VG_a0 * HD + lane] += d0;
+      vg[VG_a1 * HD + lane] += d1;
+    } else if (warp == 1) {
+      float d0 = 0.f, d1 = 0.f;
+      for (int c = 0; c < m; ++c) {
+        const float gcv = gc[fsw(c, lane)];
+        d0 = fmaf(S.sig[c], gcv, d0);
+        d1 += gcv;
+      }
+      vg[VG_u0 * HD + lane] += d0;
+      vg[VG_u1 * HD + lane] += d1;
+    }
+    __syncthreads();
+  }
+  // ---- flush the CTA's gradients ----
+  float* G = a.grads;
+  if (warp < 6) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = mt * 16 + g + (q >> 1) * 8, k = nt * 8 + 2 * t + (q & 1);
+          int idx;
+          switch (warp) {
+            case 0: idx = POff::W2vc + j * HD + k; break;
+            case 1: idx = POff::W1vc + j * DIN + HD + k; break;
+            case 2: idx = POff::W1vc + j * DIN + k; break;
+            case 3: idx = POff::W2cv + j * HD + k; break;
+            case 4: idx = POff::W1cv + j * DIN + k; break;
+            default: idx = POff::W1cv + j * DIN + HD + k; break;
+          }
+          atomicAdd(&G[idx], wacc[mt][nt][q]);
+        }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < HD; k += blockDim.x) {
+    atomicAdd(&G[POff::b2cv + k], vg[VG_b2cv * HD + k]);
+    atomicAdd(&G[POff::b2vc + k], vg[VG_b2vc * HD + k]);
+    atomicAdd(&G[POff::W1cv + k * DIN + 2 * HD], vg[VG_wscv * HD + k]);
+    atomicAdd(&G[POff::b1cv + k], vg[VG_b1cv * HD + k]);
+    atomicAdd(&G[POff::W1vc + k * DIN + 2 * HD], vg[VG_wsvc * HD + k]);
+    atomicAdd(&G[POff::b1vc + k], vg[VG_b1vc * HD + k]);
+    atomicAdd(&G[POff::a0 + k], vg[VG_a0 * HD + k]);
+    atomicAdd(&G[POff::a1 + k], vg[VG_a1 * HD + k]);
+    atomicAdd(&G[POff::u0 + k], vg[VG_u0 * HD + k]);
+    atomicAdd(&G[POff::u1 + k], vg[VG_u1 * HD + k]);
+    atomicAdd(&G[POff::wo + k], vg[VG_wo * HD + k]);
+  }
+  if (threadIdx.x == 0) atomicAdd(&G[POff::bo], vg[VG_bo * HD]);
+  for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+  if (lane == 0 && loss_acc != 0.0) atomicAdd(a.loss, loss_acc);
+}
+
 }  // namespace
 
 
 int prior_num_params() { return POff::total; }
 
 size_t prior_smem(int m, int n, int E, bool train) {
-  return train ? prior_layout(m, n, E, true).total : fwd_layout(m, n).total;
+  (void)E;
+  return train ? train_layout(m, n).total : fwd_layout(m, n).total;
 }
 
 size_t prior_scratch_floats(int m, int n, int rounds, int grid) {
-  return (size_t)grid * (rounds + 1) * (n + m) * HD;
+  // BF16 states: (R + 1) variable and R check rows of 32 values per CTA
+  return ((size_t)grid * ((size_t)(rounds + 1) * n + (size_t)rounds * m) * HD + 1) / 2;
 }
 
 cudaError_t prior_config(int m, int n, int E, bool train, int* grid) {
@@ -1113,8 +1135,8 @@ cudaError_t prior_config(int m, int n, int E, bool train, int* grid) {
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t smem = prior_smem(m, n, E, train);
   if (smem > (size_t)max_smem) return cudaErrorInvalidValue;
-  const void* fn = train ? (const void*)prior_kernel<true> : (const void*)prior_fwd_kernel;
-  const int threads = train ? kPriorThreads : kFwdWarps * 32;
+  const void* fn = train ? (const void*)prior_train_kernel : (const void*)prior_fwd_kernel;
+  const int threads = kFwdWarps * 32;
   err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -1163,27 +1185,27 @@ cudaError_t launch_prior(bool train, int grid, const DevGraph& g, int rounds, co
     return launch_prior_decode(grid, g, rounds, params, shots, syndromes, llr_out, nullptr,
                                nullptr, nullptr, nullptr, nullptr, st);
   }
-  PriorArgs a{};
+  TrainArgs a{};
   a.m = g.m;
   a.n = g.n;
-  a.E = g.E;
   a.rounds = rounds;
   a.chk_ptr = g.chk_ptr;
   a.chk_var = g.chk_var;
+  a.var_ptr = g.var_ptr;
+  a.var_chk = g.var_chk;
   a.prior = g.prior;
   a.params = params;
   a.shots = shots;
   a.syndromes = syndromes;
   a.errors = errors;
-  a.llr_out = llr_out;
-  a.scratch = scratch;
+  a.scratch = reinterpret_cast<__nv_bfloat16*>(scratch);
   a.grads = grads;
   a.loss = loss;
   a.inv_norm = shots > 0 ? (float)(1.0 / ((double)shots * g.n)) : 0.f;
-  const size_t smem = prior_smem(g.m, g.n, g.E, train);
+  (void)llr_out;
   const long long blocks = shots < grid ? shots : grid;
   if (blocks <= 0) return cudaSuccess;
-  prior_kernel<true><<<(int)blocks, kPriorThreads, smem, st>>>(a);
+  prior_train_kernel<<<(int)blocks, kFwdWarps * 32, train_layout(g.m, g.n).total, st>>>(a);
   return cudaGetLastError();
 }
 
