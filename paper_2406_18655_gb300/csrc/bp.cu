@@ -17,6 +17,7 @@
 // check order.  The parity test of Lam^(t) is fused into check phase t+1.
 // Every float operation on the min-sum path is an explicit round-to-nearest intrinsic
 // (no contraction), so results do not depend on compiler fusion.
+#include "bp_shot.cuh"
 #include "lsd_internal.cuh"
 
 namespace lsdgb {
@@ -241,31 +242,9 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
   float* r = reinterpret_cast<float*>(smem + align16((size_t)n * 4) +
                                       (size_t)group * bp_reg_group_bytes(n, E));
   float* Lam = r + E;
-  const float alpha = a.alpha;
-
-  // ---- the lane's graph tables: column indices of its checks, edge slots of its variables
-  uint32_t cv[CPL][(DC + 1) / 2];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int i = lane + G * c;
-#pragma unroll
-    for (int k = 0; k < (DC + 1) / 2; ++k) cv[c][k] = 0;
-    if (i < m) {
-#pragma unroll
-      for (int k = 0; k < DC; ++k) cv[c][k >> 1] |= (uint32_t)a.g.chk_var[i * DC + k] << (16 * (k & 1));
-    }
-  }
-  uint32_t ve[VPL][(DV + 1) / 2];
-#pragma unroll
-  for (int v = 0; v < VPL; ++v) {
-    const int j = lane + G * v;
-#pragma unroll
-    for (int k = 0; k < (DV + 1) / 2; ++k) ve[v][k] = 0;
-    if (j < n) {
-#pragma unroll
-      for (int k = 0; k < DV; ++k) ve[v][k >> 1] |= (uint32_t)a.g.var_edge[j * DV + k] << (16 * (k & 1));
-    }
-  }
+  bpreg::Tables<CPL, DC, VPL, DV> T;
+  bpreg::load_tables<G>(a.g, lane, T);
+  (void)m;
 
   unsigned long long my_iters = 0, my_conv = 0;
   for (;;) {
@@ -274,86 +253,8 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
     shot_u = __shfl_sync(gmask, shot_u, leader);
     if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
-
-    const uint8_t* sp = a.syndromes + shot * m;
-    unsigned sbits = 0;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int i = lane + G * c;
-      if (i < m) {
-        if (sp[i]) sbits |= 1u << c;
-#pragma unroll
-        for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < VPL; ++v) {
-      const int j = lane + G * v;
-      if (j < n) Lam[j] = s_prior[j];
-    }
-    __syncwarp(gmask);
-
-    int t = 0;
     bool conv = false;
-    for (;;) {
-      const bool msgs = t < a.iters;
-      unsigned unsat = 0;
-      // ---- check phase: parity of [Lam^(t) < 0] and messages r^(t+1) ----
-#pragma unroll
-      // Sign bits stand for the comparisons "< 0": the priors are finite and never -0
-      // (0 < p < 1), so no Lam and no q = Lam - r is -0 or NaN.  The two smallest
-      // magnitudes come from min/max alone; the edge holding the minimum takes the second
-      // one (on a tie both are equal, as with a first-index rule).
-      for (int c = 0; c < CPL; ++c) {
-        const int i = lane + G * c;
-        if (i >= m) continue;
-        uint32_t hp = (sbits >> c) << 31;  // bit 31: syndrome ^ signs of Lam
-        uint32_t sx = hp;                   // bit 31: syndrome ^ signs of q
-        float min1 = kBig, min2 = kBig;
-        float aq[DC];
-        uint32_t qb[DC];
-        float* rc = r + i * DC;
-#pragma unroll
-        for (int k = 0; k < DC; ++k) {
-          const int j = (cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff;
-          const float L = Lam[j];
-          hp ^= __float_as_uint(L);
-          const float q = __fsub_rn(L, rc[k]);
-          qb[k] = __float_as_uint(q);
-          sx ^= qb[k];
-          aq[k] = fabsf(q);
-          min2 = fminf(min2, fmaxf(min1, aq[k]));
-          min1 = fminf(min1, aq[k]);
-        }
-        unsat |= hp >> 31;
-        if (msgs) {
-          const float m1 = __fmul_rn(alpha, min1), m2 = __fmul_rn(alpha, min2);
-#pragma unroll
-          for (int k = 0; k < DC; ++k) {
-            const float mag = (aq[k] == min1) ? m2 : m1;
-            rc[k] = __uint_as_float(__float_as_uint(mag) | ((sx ^ qb[k]) & 0x80000000u));
-          }
-        }
-      }
-      if (t > 0) {
-        conv = !__any_sync(gmask, unsat != 0);
-        if (conv && a.early_exit) break;
-      }
-      if (!msgs) break;
-      __syncwarp(gmask);
-      // ---- variable phase: Lam^(t+1) ----
-#pragma unroll
-      for (int v = 0; v < VPL; ++v) {
-        const int j = lane + G * v;
-        if (j >= n) continue;
-        float L = s_prior[j];
-#pragma unroll
-        for (int k = 0; k < DV; ++k) L = __fadd_rn(L, r[(ve[v][k >> 1] >> (16 * (k & 1))) & 0xffff]);
-        Lam[j] = L;
-      }
-      __syncwarp(gmask);
-      ++t;
-    }
+    const int t = bpreg::shot_bp<G>(a, T, shot, r, Lam, s_prior, lane, gmask, conv);
 
     // ---- outputs (each lane writes its own variables) ----
     if (a.posteriors) {

@@ -556,10 +556,223 @@ __device__ void osd_e(const LSDArgs& a, const Shot<L>& S, int m, int lane) {
   }
 }
 
+// Per-warp running statistics of the shots a warp decodes.
+struct LsdAcc {
+  unsigned long long steps = 0, unsolvable = 0;
+  int kappa_max = 0, nu_max = 0;
+};
+
+__device__ __forceinline__ void lsd_flush(const LSDArgs& a, const LsdAcc& acc, int lane) {
+  if (lane == 0) {
+    if (acc.steps) atomicAdd(&a.ctr->lsd_steps, acc.steps);
+    if (acc.unsolvable) atomicAdd(&a.ctr->unsolvable, acc.unsolvable);
+    atomicMax(&a.ctr->kappa_max, acc.kappa_max);
+    atomicMax(&a.ctr->nu_max, acc.nu_max);
+  }
+}
+
+// LSD (Alg. 1, LSD-mu of App. D) of one shot by one warp: lsrc = the shot's soft
+// information (global or shared memory), ssrc = its syndrome; writes its correction and
+// status.
+template <int MM, int NN, bool MU>
+__device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
+                                         const Shot<Lay<MM, NN, MU>>& S, const float* lsrc,
+                                         const uint8_t* ssrc, long long shot, int lane,
+                                         LsdAcc& acc) {
+  using L = Lay<MM, NN, MU>;
+  constexpr int W = L::W, Wn = L::Wn, N2 = L::N2;
+  const int m = a.g.m, n = a.g.n;
+  // ---- the shot's reliability order ----
+  if constexpr (L::kShuffleRank) {
+    // rank of fault j = number of keys (bits', j') before (bits, j), counted with shuffles
+    // of the 32-bit LLR bits; the index tie-break is known from the positions: fault
+    // j' = src + 32 t2 precedes j = lane + 32 t on equal bits iff t2 < t, or t2 == t and
+    // src < lane.  Padding entries (j >= n) carry the largest bits and the largest index.
+    constexpr int KPL = (NN + 31) / 32;
+    unsigned myk[KPL];
+    int rk[KPL];
+#pragma unroll
+    for (int t = 0; t < KPL; ++t) {
+      const int j = lane + 32 * t;
+      myk[t] = j < n ? llr_bits(lsrc[j]) : 0xffffffffu;
+      rk[t] = 0;
+    }
+#pragma unroll 2
+    for (int src = 0; src < 32; ++src) {
+      const bool before = src < lane;
+#pragma unroll
+      for (int t2 = 0; t2 < KPL; ++t2) {
+        const unsigned other = __shfl_sync(kFull, myk[t2], src);
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) {
+          if (t2 < t) rk[t] += (other <= myk[t]) ? 1 : 0;
+          else if (t2 > t) rk[t] += (other < myk[t]) ? 1 : 0;
+          else rk[t] += (other < myk[t] || (before && other == myk[t])) ? 1 : 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KPL; ++t) {
+      const int j = lane + 32 * t;
+      if (j < n) {
+        S.rank()[j] = (uint16_t)rk[t];
+        S.fat()[rk[t]] = (uint16_t)j;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j0 = 0; j0 < N2; j0 += 32) {
+      const int j = j0 + lane;
+      S.keys()[j] = j < n ? llr_key(lsrc[j], j) : ~0ull;
+    }
+    __syncwarp();
+    warp_sort<N2>(S.keys(), lane);
+    for (int r = lane; r < n; r += 32) {
+      const int j = (int)(S.keys()[r] & 0xffffffffu);
+      S.fat()[r] = (uint16_t)j;
+      S.rank()[j] = (uint16_t)r;
+    }
+  }
+  __syncwarp();
+
+  // ---- init: one cluster per flipped detector ----
+  if constexpr (L::kMasks)
+    for (int w = lane; w < m * Wn; w += 32) S.cand()[w] = 0;
+  for (int j = lane; j < n; j += 32) S.flab()[j] = -1;
+  for (int d = lane; d < m; d += 32) {
+    S.dlab()[d] = -1;
+    S.parent()[d] = d;
+    S.pcol()[d] = -1;
+    S.rflag()[d] = 0;
+    S.mark()[d] = 0u;
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const int d = c * 32 + lane;
+    const unsigned bv = __ballot_sync(kFull, d < m && ssrc[d] != 0);
+    if (lane == 0) {
+      S.syn()[c] = bv;
+      S.sred()[c] = bv;
+      S.xsol()[c] = 0;
+    }
+  }
+  if (lane < 8) S.scal()[lane] = 0;
+  __syncwarp();
+  int k = 0;
+  if (a.single_cluster) {
+    for (int d = lane; d < m; d += 32) S.dlab()[d] = 0;
+    if constexpr (L::kMasks) {
+      for (int r = lane; r < n; r += 32) {
+        const int j = S.fat()[r];
+        if (G.var_ptr[j + 1] > G.var_ptr[j]) atomicOr(&S.cand()[r >> 5], 1u << (r & 31));
+      }
+    }
+    bool anys = false;
+#pragma unroll
+    for (int c = 0; c < W; ++c) anys = anys || S.syn()[c] != 0;
+    k = anys ? 1 : 0;
+    if (lane == 0) S.inv()[0] = 0;
+  } else {
+    for (int b0 = 0; b0 < m; b0 += 32) {
+      const int d = b0 + lane;
+      const bool f = d < m && bit_of(S.syn(), d);
+      const unsigned bal = __ballot_sync(kFull, f);
+      if (f) {
+        S.dlab()[d] = d;
+        S.inv()[k + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
+        if constexpr (L::kMasks) {
+          uint32_t* c = S.cand() + (size_t)d * Wn;
+          const int c1 = G.chk_ptr[d + 1];
+          for (int e = G.chk_ptr[d]; e < c1; ++e) {
+            const unsigned rk = S.rank()[G.chk_var[e]];
+            c[rk >> 5] |= 1u << (rk & 31);
+          }
+        }
+      }
+      k += __popc(bal);
+    }
+  }
+  __syncwarp();
+
+  // ---- LSD-0: grow every invalid cluster until all are valid ----
+  int status = LSD_SHOT_OK_LSD, steps = 0;
+  while (k > 0) {
+    if (steps > n) {  // each step adds a column: cannot be reached
+      status = LSD_SHOT_UNSOLVABLE;
+      break;
+    }
+    if (lsd_step<L, MU>(G, S, m, n, k, true, lane) == 1) {
+      status = LSD_SHOT_UNSOLVABLE;
+      break;
+    }
+    ++steps;
+    k = collect_roots(a, S, m, true, lane);
+  }
+  // ---- LSD-mu: mu more steps for every cluster, then local OSD-E ----
+  if constexpr (MU) {
+    if (status == LSD_SHOT_OK_LSD) {
+      for (int e = 0; e < a.order; ++e) {
+        k = collect_roots(a, S, m, false, lane);
+        if (lsd_step<L, MU>(G, S, m, n, k, false, lane) == 2) break;
+      }
+      osd_e(a, S, m, lane);
+    }
+  }
+
+  // ---- statistics: nu clusters, kappa = largest cluster in columns ----
+  for (int d = lane; d < m; d += 32) S.best()[d] = 0;
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) {
+    const int lab = S.flab()[j];
+    if (lab >= 0) atomicAdd(&S.best()[S.parent()[lab]], 1u);
+  }
+  __syncwarp();
+  int nu = 0, kappa = 0;
+  for (int d = lane; d < m; d += 32) {
+    const bool seed = a.single_cluster ? d == 0 : bit_of(S.syn(), d);
+    if (seed && S.parent()[d] == d) {
+      ++nu;
+      kappa = max(kappa, (int)S.best()[d]);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    nu += __shfl_xor_sync(kFull, nu, off);
+    kappa = max(kappa, __shfl_xor_sync(kFull, kappa, off));
+  }
+
+  // ---- global decoding: union of the local solutions (Eq. 2) ----
+  uint8_t* cs = S.cs();  // the masks are no longer needed
+  for (int j = lane; j < n; j += 32) cs[j] = 0;
+  __syncwarp();
+  if (status == LSD_SHOT_OK_LSD) {
+    for (int d = lane; d < m; d += 32)
+      if (bit_of(S.xsol(), d)) cs[S.pcol()[d]] = 1;
+    if constexpr (MU) {
+      const int ne = S.scal()[2];
+      for (int t = lane; t < ne; t += 32) cs[S.ext()[t]] = 1;
+    }
+  }
+  __syncwarp();
+  uint8_t* co = a.corrections + shot * n;
+  for (int j = lane; j < n; j += 32) co[j] = cs[j];
+  if (lane == 0) {
+    if (a.status) a.status[shot] = (uint8_t)status;
+    if (a.shot_info) {
+      a.shot_info[3 * shot] = nu;
+      a.shot_info[3 * shot + 1] = kappa;
+      a.shot_info[3 * shot + 2] = steps;
+    }
+  }
+  acc.steps += steps;
+  acc.unsolvable += status == LSD_SHOT_UNSOLVABLE ? 1 : 0;
+  acc.kappa_max = max(acc.kappa_max, kappa);
+  acc.nu_max = max(acc.nu_max, nu);
+  __syncwarp();
+}
+
 template <int MM, int NN, bool MU>
 __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int graph_smem) {
   using L = Lay<MM, NN, MU>;
-  constexpr int W = L::W, Wn = L::Wn, N2 = L::N2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = a.g.m, n = a.g.n, E = a.g.E;
@@ -592,8 +805,7 @@ __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int gra
   Shot<L> S{smem + (size_t)warp * L::total};
 
   const long long count = a.count_from_ctr ? (long long)a.ctr->lsd_count : a.count;
-  unsigned long long steps_acc = 0, unsolv = 0;
-  int kappa_max = 0, nu_max = 0;
+  LsdAcc acc;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(&a.ctr->lsd_next, 1ULL);
@@ -601,201 +813,9 @@ __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int gra
     if (item >= (unsigned long long)count) break;
     const long long shot = a.queue ? (long long)a.queue[item] : (long long)item;
     const float* lsrc = a.llr + (a.llr_by_item ? (long long)item : shot) * n;
-    const uint8_t* ssrc = a.syndromes + shot * m;
-
-    // ---- the shot's reliability order ----
-    if constexpr (L::kShuffleRank) {
-      // rank of fault j = number of keys (bits', j') before (bits, j), counted with shuffles
-      // of the 32-bit LLR bits; the index tie-break is known from the positions: fault
-      // j' = src + 32 t2 precedes j = lane + 32 t on equal bits iff t2 < t, or t2 == t and
-      // src < lane.  Padding entries (j >= n) carry the largest bits and the largest index.
-      constexpr int KPL = (NN + 31) / 32;
-      unsigned myk[KPL];
-      int rk[KPL];
-#pragma unroll
-      for (int t = 0; t < KPL; ++t) {
-        const int j = lane + 32 * t;
-        myk[t] = j < n ? llr_bits(lsrc[j]) : 0xffffffffu;
-        rk[t] = 0;
-      }
-#pragma unroll 2
-      for (int src = 0; src < 32; ++src) {
-        const bool before = src < lane;
-#pragma unroll
-        for (int t2 = 0; t2 < KPL; ++t2) {
-          const unsigned other = __shfl_sync(kFull, myk[t2], src);
-#pragma unroll
-          for (int t = 0; t < KPL; ++t) {
-            if (t2 < t) rk[t] += (other <= myk[t]) ? 1 : 0;
-            else if (t2 > t) rk[t] += (other < myk[t]) ? 1 : 0;
-            else rk[t] += (other < myk[t] || (before && other == myk[t])) ? 1 : 0;
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < KPL; ++t) {
-        const int j = lane + 32 * t;
-        if (j < n) {
-          S.rank()[j] = (uint16_t)rk[t];
-          S.fat()[rk[t]] = (uint16_t)j;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j0 = 0; j0 < N2; j0 += 32) {
-        const int j = j0 + lane;
-        S.keys()[j] = j < n ? llr_key(lsrc[j], j) : ~0ull;
-      }
-      __syncwarp();
-      warp_sort<N2>(S.keys(), lane);
-      for (int r = lane; r < n; r += 32) {
-        const int j = (int)(S.keys()[r] & 0xffffffffu);
-        S.fat()[r] = (uint16_t)j;
-        S.rank()[j] = (uint16_t)r;
-      }
-    }
-    __syncwarp();
-
-    // ---- init: one cluster per flipped detector ----
-    if constexpr (L::kMasks)
-      for (int w = lane; w < m * Wn; w += 32) S.cand()[w] = 0;
-    for (int j = lane; j < n; j += 32) S.flab()[j] = -1;
-    for (int d = lane; d < m; d += 32) {
-      S.dlab()[d] = -1;
-      S.parent()[d] = d;
-      S.pcol()[d] = -1;
-      S.rflag()[d] = 0;
-      S.mark()[d] = 0u;
-    }
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const int d = c * 32 + lane;
-      const unsigned bv = __ballot_sync(kFull, d < m && ssrc[d] != 0);
-      if (lane == 0) {
-        S.syn()[c] = bv;
-        S.sred()[c] = bv;
-        S.xsol()[c] = 0;
-      }
-    }
-    if (lane < 8) S.scal()[lane] = 0;
-    __syncwarp();
-    int k = 0;
-    if (a.single_cluster) {
-      for (int d = lane; d < m; d += 32) S.dlab()[d] = 0;
-      if constexpr (L::kMasks) {
-        for (int r = lane; r < n; r += 32) {
-          const int j = S.fat()[r];
-          if (G.var_ptr[j + 1] > G.var_ptr[j]) atomicOr(&S.cand()[r >> 5], 1u << (r & 31));
-        }
-      }
-      bool anys = false;
-#pragma unroll
-      for (int c = 0; c < W; ++c) anys = anys || S.syn()[c] != 0;
-      k = anys ? 1 : 0;
-      if (lane == 0) S.inv()[0] = 0;
-    } else {
-      for (int b0 = 0; b0 < m; b0 += 32) {
-        const int d = b0 + lane;
-        const bool f = d < m && bit_of(S.syn(), d);
-        const unsigned bal = __ballot_sync(kFull, f);
-        if (f) {
-          S.dlab()[d] = d;
-          S.inv()[k + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
-          if constexpr (L::kMasks) {
-            uint32_t* c = S.cand() + (size_t)d * Wn;
-            const int c1 = G.chk_ptr[d + 1];
-            for (int e = G.chk_ptr[d]; e < c1; ++e) {
-              const unsigned rk = S.rank()[G.chk_var[e]];
-              c[rk >> 5] |= 1u << (rk & 31);
-            }
-          }
-        }
-        k += __popc(bal);
-      }
-    }
-    __syncwarp();
-
-    // ---- LSD-0: grow every invalid cluster until all are valid ----
-    int status = LSD_SHOT_OK_LSD, steps = 0;
-    while (k > 0) {
-      if (steps > n) {  // each step adds a column: cannot be reached
-        status = LSD_SHOT_UNSOLVABLE;
-        break;
-      }
-      if (lsd_step<L, MU>(G, S, m, n, k, true, lane) == 1) {
-        status = LSD_SHOT_UNSOLVABLE;
-        break;
-      }
-      ++steps;
-      k = collect_roots(a, S, m, true, lane);
-    }
-    // ---- LSD-mu: mu more steps for every cluster, then local OSD-E ----
-    if constexpr (MU) {
-      if (status == LSD_SHOT_OK_LSD) {
-        for (int e = 0; e < a.order; ++e) {
-          k = collect_roots(a, S, m, false, lane);
-          if (lsd_step<L, MU>(G, S, m, n, k, false, lane) == 2) break;
-        }
-        osd_e(a, S, m, lane);
-      }
-    }
-
-    // ---- statistics: nu clusters, kappa = largest cluster in columns ----
-    for (int d = lane; d < m; d += 32) S.best()[d] = 0;
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-      const int lab = S.flab()[j];
-      if (lab >= 0) atomicAdd(&S.best()[S.parent()[lab]], 1u);
-    }
-    __syncwarp();
-    int nu = 0, kappa = 0;
-    for (int d = lane; d < m; d += 32) {
-      const bool seed = a.single_cluster ? d == 0 : bit_of(S.syn(), d);
-      if (seed && S.parent()[d] == d) {
-        ++nu;
-        kappa = max(kappa, (int)S.best()[d]);
-      }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      nu += __shfl_xor_sync(kFull, nu, off);
-      kappa = max(kappa, __shfl_xor_sync(kFull, kappa, off));
-    }
-
-    // ---- global decoding: union of the local solutions (Eq. 2) ----
-    uint8_t* cs = S.cs();  // the masks are no longer needed
-    for (int j = lane; j < n; j += 32) cs[j] = 0;
-    __syncwarp();
-    if (status == LSD_SHOT_OK_LSD) {
-      for (int d = lane; d < m; d += 32)
-        if (bit_of(S.xsol(), d)) cs[S.pcol()[d]] = 1;
-      if constexpr (MU) {
-        const int ne = S.scal()[2];
-        for (int t = lane; t < ne; t += 32) cs[S.ext()[t]] = 1;
-      }
-    }
-    __syncwarp();
-    uint8_t* co = a.corrections + shot * n;
-    for (int j = lane; j < n; j += 32) co[j] = cs[j];
-    if (lane == 0) {
-      if (a.status) a.status[shot] = (uint8_t)status;
-      if (a.shot_info) {
-        a.shot_info[3 * shot] = nu;
-        a.shot_info[3 * shot + 1] = kappa;
-        a.shot_info[3 * shot + 2] = steps;
-      }
-    }
-    steps_acc += steps;
-    unsolv += status == LSD_SHOT_UNSOLVABLE ? 1 : 0;
-    kappa_max = max(kappa_max, kappa);
-    nu_max = max(nu_max, nu);
-    __syncwarp();
+    lsd_shot<MM, NN, MU>(a, G, S, lsrc, a.syndromes + shot * m, shot, lane, acc);
   }
-  if (lane == 0) {
-    if (steps_acc) atomicAdd(&a.ctr->lsd_steps, steps_acc);
-    if (unsolv) atomicAdd(&a.ctr->unsolvable, unsolv);
-    atomicMax(&a.ctr->kappa_max, kappa_max);
-    atomicMax(&a.ctr->nu_max, nu_max);
-  }
+  lsd_flush(a, acc, lane);
 }
 
 inline bool graph_in_smem(const DevGraph& g) { return graph_bytes(g.m, g.n, g.E) <= kGraphBudget; }
