@@ -29,6 +29,14 @@ def code(name):
             h[i, i - 1] = h[i, i] = 1
     elif name == "hgp":
         h = I.hgp_48x64()[0]
+    elif name == "ldpc_96x192":
+        # (3,6)-regular, girth >= 6: the 96-detector / 192-fault LSD class (shuffle ranks of
+        # six keys per lane)
+        h = I.random_regular_ldpc(96, 192, 3, 6, seed=3)
+    elif name == "ldpc_480x960":
+        # the largest dense LSD class (512 x 2048: bitonic sort, no candidate masks, 16-word
+        # elimination rows)
+        h = I.random_regular_ldpc(480, 960, 3, 6, seed=4)
     elif name == "irreg_37x61":
         # irregular degrees, sizes off the 16-row tiles: column j has weight 1 + j % 4
         rng = np.random.default_rng(5)

@@ -126,7 +126,9 @@ def _rounded_llrs(shape, seed):
     ("st_bb72_d6", 0.02, 0, False, "bp"), ("rep_boundary", 0.15, 0, False, "ties"),
     ("bb72", 0.05, 0, True, "bp"), ("bb144", 0.05, 0, True, "ties"),
     ("bb72", 0.08, 6, False, "bp"), ("bb144", 0.06, 6, False, "bp"),
-    ("bb144", 0.06, 10, False, "ties"), ("bb72", 0.05, 1, False, "bp")])
+    ("bb144", 0.06, 10, False, "ties"), ("bb72", 0.05, 1, False, "bp"),
+    ("ldpc_96x192", 0.06, 0, False, "bp"), ("ldpc_96x192", 0.06, 6, False, "ties"),
+    ("ldpc_480x960", 0.04, 0, False, "bp"), ("ldpc_480x960", 0.04, 4, False, "bp")])
 def test_lsd_bit_exact_given_identical_soft_information(L, name, p, order, single, soft):
     h, probs, e, s = sample(name, p, 1500, seed=77 + order + int(100 * p))
     if soft == "bp":
@@ -161,7 +163,8 @@ def test_single_cluster_equals_osd0(L):
 
 @pytest.mark.parametrize("name,p,iters,order", [
     ("bb72", 0.05, 30, 0), ("bb144", 0.05, 50, 0), ("bb144", 0.08, 50, 6),
-    ("bb288", 0.06, 50, 0), ("st_bb72_d6", 0.02, 50, 0)])
+    ("bb288", 0.06, 50, 0), ("st_bb72_d6", 0.02, 50, 0), ("ldpc_96x192", 0.05, 50, 0),
+    ("ldpc_480x960", 0.07, 50, 0)])
 def test_decode_matches_oracle(L, name, p, iters, order):
     h, probs, e, s = sample(name, p, 4000, seed=300 + iters + order)
     d = L.Decoder(h, probs, iters, order)
