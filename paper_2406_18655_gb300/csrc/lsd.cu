@@ -597,7 +597,7 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
       myk[t] = j < n ? llr_bits(lsrc[j]) : 0xffffffffu;
       rk[t] = 0;
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int src = 0; src < 32; ++src) {
       const bool before = src < lane;
 #pragma unroll
