@@ -138,7 +138,8 @@ __global__ void sample_kernel(unsigned long long seed, long long first, long lon
 // One CTA owns one shot at a time; all node arrays live in shared memory.
 // ======================================================================================
 
-constexpr int kFwdWarps = 8;
+constexpr int kFwdWarps = 8;    // training kernel (warps 0-5 own the weight gradients)
+constexpr int kInfWarps = 9;    // inference kernel: 9 warps give BB144's 9 variable tiles one each
 
 struct FwdArgs {
   int m, n, rounds;
@@ -402,7 +403,7 @@ __device__ __forceinline__ void x_tile(int count, int r0, const int32_t* __restr
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(kInfWarps * 32, 3) prior_fwd_kernel(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.m, n = a.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a)
   for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
     const uint8_t* sp = a.syndromes + shot * m;
     // initial states and their projections, one 16-row tile per warp
-    for (int tile = warp; tile < vt + ct; tile += kFwdWarps) {
+    for (int tile = warp; tile < vt + ct; tile += kInfWarps) {
       if (tile < vt) g_step<false>(S, n, tile * 16, false, true, nullptr, lane, sp);
       else g_step<true>(S, m, (tile - vt) * 16, false, true, nullptr, lane, sp);
     }
@@ -481,13 +482,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 3) prior_fwd_kernel(FwdArgs a)
     // (the gathers read the other node type's projections, complete after the barrier)
     for (int r = 0; r < R; ++r) {
       const bool last = r == R - 1;
-      for (int tile = warp; tile < vt; tile += kFwdWarps) {
+      for (int tile = warp; tile < vt; tile += kInfWarps) {
         x_tile(n, tile * 16, a.var_ptr, a.var_chk, S.ac, S.bv, lane);
         g_step<false>(S, n, tile * 16, true, !last, llr, lane);
       }
       __syncthreads();
       if (last) break;
-      for (int tile = warp; tile < ct; tile += kFwdWarps) {
+      for (int tile = warp; tile < ct; tile += kInfWarps) {
         x_tile(m, tile * 16, a.chk_ptr, a.chk_var, S.cv, S.dc, lane);
         g_step<true>(S, m, tile * 16, true, true, nullptr, lane);
       }
@@ -1136,7 +1137,7 @@ cudaError_t prior_config(int m, int n, int E, bool train, int* grid) {
   const size_t smem = prior_smem(m, n, E, train);
   if (smem > (size_t)max_smem) return cudaErrorInvalidValue;
   const void* fn = train ? (const void*)prior_train_kernel : (const void*)prior_fwd_kernel;
-  const int threads = kFwdWarps * 32;
+  const int threads = (train ? kFwdWarps : kInfWarps) * 32;
   err = allow_max_dynamic_smem(fn, max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -1172,7 +1173,7 @@ cudaError_t launch_prior_decode(int grid, const DevGraph& g, int rounds, const f
   f.ctr = ctr;
   const long long blocks = shots < grid ? shots : grid;
   if (blocks <= 0) return cudaSuccess;
-  prior_fwd_kernel<<<(int)blocks, kFwdWarps * 32, fwd_layout(g.m, g.n).total, st>>>(f);
+  prior_fwd_kernel<<<(int)blocks, kInfWarps * 32, fwd_layout(g.m, g.n).total, st>>>(f);
   return cudaGetLastError();
 }
 
