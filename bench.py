@@ -414,7 +414,7 @@ def run_ours(args):
     from paper_2406_18655_gb300 import inputs as I
     from paper_2406_18655_gb300.evaluate import LogicalChecker
     from paper_2406_18655_gb300.lsd import Decoder
-    from paper_2406_18655_gb300.shard import job_throughput, shard
+    from paper_2406_18655_gb300.shard import job_throughput, max_over_ranks, shard, sum_over_ranks
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -481,7 +481,16 @@ def run_ours(args):
     checker = LogicalChecker(hz)
     e_dev = torch.from_numpy(e).cuda()
     fails = checker.failures(e_dev, corr)
-    ler = float(fails.float().mean().item())
+    # end-of-run reductions over the ranks: failure and shot counts, the largest clusters,
+    # the slowest rank's time of every step
+    ler = (sum_over_ranks(float(fails.sum().item()), device="cuda")
+           / sum_over_ranks(float(args.shots), device="cuda"))
+    kappa_max = int(max_over_ranks(kappa_max, device="cuda"))
+    nu_max = int(max_over_ranks(nu_max, device="cuda"))
+    step_ms = [max_over_ranks(t, device="cuda") for t in step_ms]
+    all_shots = sum_over_ranks(float(args.steps * args.shots), device="cuda")
+    conv_frac = sum_over_ranks(float(conv_sum), device="cuda") / all_shots
+    lsd_frac = sum_over_ranks(float(lsd_sum), device="cuda") / all_shots
     learned = None
     if not args.no_learned:
         learned = learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier,
@@ -548,8 +557,8 @@ def run_ours(args):
                        "p99": float(np.percentile(step_ms, 99)),
                        "what": "batch latency of one step (10^6 shots, device-resident)"},
         "ler": ler,
-        "bp_converged_frac": conv_sum / (args.steps * args.shots),
-        "lsd_frac": lsd_sum / (args.steps * args.shots),
+        "bp_converged_frac": conv_frac,
+        "lsd_frac": lsd_frac,
         "mean_bp_iters": iters_per_step / args.shots,
         "kappa_max": kappa_max, "nu_max": nu_max,
         "kernel_ms": {"bp_kernel": bp_ms_avg, "lsd_kernel": float(np.mean(lsd_ms))},
