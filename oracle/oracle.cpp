@@ -31,6 +31,11 @@
 //     every cluster (merges allowed, clusters stay valid), then exhaustive
 //     OSD-E over the first min(mu, #non-pivots) non-pivot columns of each
 //     cluster.  Costs are sums of channel-prior weights in 2^-32 fixed point.
+//     Alternatively (the BB experiment of App. D, which fixes the local
+//     reprocessing to OSD-CS-4) the combination sweep of order w over the
+//     cluster's non-pivot columns in reliability order: no flip, every single
+//     non-pivot column, every pair among the first w; the first pattern of
+//     least cost in that order wins.
 //   * Logical failure: residual r = e + e_hat is a logical error iff
 //     r is not in the row space of H_Z (rank test).
 //
@@ -257,7 +262,8 @@ enum { ST_OK_BP = 1, ST_OK_LSD = 2, ST_UNSOLVABLE = 3 };
 struct LsdOut { int status, nu, kappa, steps; };
 
 LsdOut lsd_shot(const Graph& g, const uint8_t* s, const double* llr, const int64_t* wfix,
-                int order, int single, uint8_t* out, int32_t* det_lab, int32_t* fault_lab) {
+                int order, int osd_cs, int single, uint8_t* out, int32_t* det_lab,
+                int32_t* fault_lab) {
   const int m = g.m, n = g.n, W = nwords(std::max(m, 1)), NW = nwords(std::max(n, 1));
   auto before = [&](int a, int b) { return llr[a] < llr[b] || (llr[a] == llr[b] && a < b); };
   Bits S(W, 0);
@@ -401,21 +407,35 @@ LsdOut lsd_shot(const Graph& g, const uint8_t* s, const double* llr, const int64
       if (!e.add(g.colbits[c.cols[p]], (int)p)) nonpiv.push_back((int)p);
     std::sort(nonpiv.begin(), nonpiv.end(),
               [&](int a, int b) { return before(c.cols[a], c.cols[b]); });
-    const int nt = std::min<int>(order, (int)nonpiv.size());
+    // the flip patterns (sets of non-pivot positions), in the order that breaks cost ties
+    std::vector<std::vector<int>> patterns;
+    if (order > 0 && osd_cs >= 0) {  // combination sweep of order osd_cs
+      patterns.push_back({});
+      for (int k = 0; k < (int)nonpiv.size(); ++k) patterns.push_back({k});
+      const int wp = std::min<int>(osd_cs, (int)nonpiv.size());
+      for (int i = 0; i < wp; ++i)
+        for (int j = i + 1; j < wp; ++j) patterns.push_back({i, j});
+    } else {  // exhaustive over the first min(mu, #non-pivots)
+      const int nt = std::min<int>(order, (int)nonpiv.size());
+      for (int64_t t = 0; t < ((int64_t)1 << nt); ++t) {
+        std::vector<int> pat;
+        for (int k = 0; k < nt; ++k) if ((t >> k) & 1) pat.push_back(k);
+        patterns.push_back(pat);
+      }
+    }
     Bits target(W);
     for (int w = 0; w < W; ++w) target[w] = S[w] & c.dets[w];
     int64_t best_cost = std::numeric_limits<int64_t>::max();
     std::vector<int> best_sol;
-    for (int64_t t = 0; t < ((int64_t)1 << nt); ++t) {
+    for (const auto& pat : patterns) {
       Bits rhs = target;
-      for (int k = 0; k < nt; ++k)
-        if ((t >> k) & 1) xorin(rhs, g.colbits[c.cols[nonpiv[k]]]);
+      for (int k : pat) xorin(rhs, g.colbits[c.cols[nonpiv[k]]]);
       Bits comb;
       if (!e.reduce(rhs, comb)) { res.status = ST_UNSOLVABLE; break; }
       std::vector<int> sol;
       for (size_t p = 0; p < c.cols.size(); ++p) if (bit(comb, (int)p)) sol.push_back(c.cols[p]);
-      for (int k = 0; k < nt; ++k) if ((t >> k) & 1) sol.push_back(c.cols[nonpiv[k]]);
-      if (nt == 0) { best_sol = sol; break; }
+      for (int k : pat) sol.push_back(c.cols[nonpiv[k]]);
+      if (patterns.size() == 1) { best_sol = sol; break; }
       int64_t cost = 0;
       for (int j : sol) cost += wfix[j];
       if (cost < best_cost) { best_cost = cost; best_sol = sol; }
@@ -537,8 +557,9 @@ int32_t orc_osd0(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const i
 // and fault_lab [shots][n] (nullable) receive the final cluster label of each node.
 int orc_lsd(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
             int64_t shots, const uint8_t* syndromes, const double* llrs, const double* probs,
-            int32_t order, int32_t single_cluster, int32_t nthreads, uint8_t* corrections,
-            uint8_t* status, int32_t* info, int32_t* det_lab, int32_t* fault_lab) {
+            int32_t order, int32_t osd_cs, int32_t single_cluster, int32_t nthreads,
+            uint8_t* corrections, uint8_t* status, int32_t* info, int32_t* det_lab,
+            int32_t* fault_lab) {
   Graph g;
   if (build_graph(m, n, nnz, rows, cols, g)) return -1;
   std::vector<int64_t> w;
@@ -548,7 +569,7 @@ int orc_lsd(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const int32_
   }
   parallel_for(shots, nthreads, [&](int64_t k) {
     LsdOut r = lsd_shot(g, syndromes + (size_t)k * m, llrs + (size_t)k * n, w.data(), order,
-                        single_cluster, corrections + (size_t)k * n,
+                        osd_cs, single_cluster, corrections + (size_t)k * n,
                         det_lab ? det_lab + (size_t)k * m : nullptr,
                         fault_lab ? fault_lab + (size_t)k * n : nullptr);
     status[k] = (uint8_t)r.status;
@@ -562,9 +583,9 @@ int orc_lsd(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const int32_
 // precision as in orc_bp.  llr_out [shots][n] nullable; info [shots][3] nullable.
 int orc_decode(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
                const double* probs, int64_t shots, const uint8_t* syndromes, int32_t bp_iters,
-               double alpha, int32_t lsd_order, int32_t precision, int32_t nthreads,
-               uint8_t* corrections, uint8_t* status, int32_t* bp_iters_used, int32_t* info,
-               double* llr_out) {
+               double alpha, int32_t lsd_order, int32_t osd_cs, int32_t precision,
+               int32_t nthreads, uint8_t* corrections, uint8_t* status, int32_t* bp_iters_used,
+               int32_t* info, double* llr_out) {
   Graph g;
   if (build_graph(m, n, nnz, rows, cols, g)) return -1;
   std::vector<int> cep, ce;
@@ -595,7 +616,7 @@ int orc_decode(int32_t m, int32_t n, int64_t nnz, const int32_t* rows, const int
       if (info) { info[3 * k] = 0; info[3 * k + 1] = 0; info[3 * k + 2] = 0; }
       return;
     }
-    LsdOut r = lsd_shot(g, s, L.data(), w.data(), lsd_order, 0, out, nullptr, nullptr);
+    LsdOut r = lsd_shot(g, s, L.data(), w.data(), lsd_order, osd_cs, 0, out, nullptr, nullptr);
     status[k] = (uint8_t)r.status;
     if (info) { info[3 * k] = r.nu; info[3 * k + 1] = r.kappa; info[3 * k + 2] = r.steps; }
   });

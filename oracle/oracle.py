@@ -26,8 +26,9 @@ def lib():
         _lib.orc_gf2_solve.restype = i32
         _lib.orc_osd0.argtypes = [i32, i32, i64, P, P, P, P, P]
         _lib.orc_osd0.restype = i32
-        _lib.orc_lsd.argtypes = [i32, i32, i64, P, P, i64, P, P, P, i32, i32, i32, P, P, P, P, P]
-        _lib.orc_decode.argtypes = [i32, i32, i64, P, P, P, i64, P, i32, f64, i32, i32, i32,
+        _lib.orc_lsd.argtypes = [i32, i32, i64, P, P, i64, P, P, P, i32, i32, i32, i32, P, P, P,
+                                 P, P]
+        _lib.orc_decode.argtypes = [i32, i32, i64, P, P, P, i64, P, i32, f64, i32, i32, i32, i32,
                                     P, P, P, P, P]
         _lib.orc_logical_failures.argtypes = [i32, i32, P, i64, P, i32, P]
     return _lib
@@ -98,8 +99,11 @@ def osd0(h, syndrome, llr):
     return bool(ok), out
 
 
-def lsd(h, syndromes, llrs, order=0, probs=None, single_cluster=False, nthreads=0, labels=False):
-    """LSD on given soft information.
+def lsd(h, syndromes, llrs, order=0, probs=None, single_cluster=False, nthreads=0, labels=False,
+        osd_cs=-1):
+    """LSD on given soft information.  order = mu (LSD-mu, App. D); osd_cs = -1 reprocesses
+    each cluster with OSD-E of order mu, osd_cs = w >= 0 with the combination sweep of
+    order w (needs mu >= 1).
 
     Returns dict(corrections, status, nu, kappa, steps[, det_lab, fault_lab]).
     """
@@ -114,7 +118,7 @@ def lsd(h, syndromes, llrs, order=0, probs=None, single_cluster=False, nthreads=
     info = np.zeros((shots, 3), np.int32)
     dl = np.zeros((shots, m), np.int32) if labels else None
     fl = np.zeros((shots, n), np.int32) if labels else None
-    rc = lib().orc_lsd(m, n, r.size, _p(r), _p(c), shots, _p(s), _p(l), _p(p), order,
+    rc = lib().orc_lsd(m, n, r.size, _p(r), _p(c), shots, _p(s), _p(l), _p(p), order, osd_cs,
                        int(single_cluster), nthreads, _p(corr), _p(st), _p(info), _p(dl), _p(fl))
     if rc:
         raise ValueError("orc_lsd: invalid arguments")
@@ -126,7 +130,7 @@ def lsd(h, syndromes, llrs, order=0, probs=None, single_cluster=False, nthreads=
 
 
 def decode(h, probs, syndromes, bp_iters, alpha=0.625, lsd_order=0, precision=1, nthreads=0,
-           want_llr=False):
+           want_llr=False, osd_cs=-1):
     """BP then LSD.  Returns dict(corrections, status, bp_iters, nu, kappa, steps[, llr])."""
     m, n, r, c = _coo(h)
     s = np.ascontiguousarray(np.atleast_2d(syndromes), dtype=np.uint8)
@@ -138,8 +142,8 @@ def decode(h, probs, syndromes, bp_iters, alpha=0.625, lsd_order=0, precision=1,
     info = np.zeros((shots, 3), np.int32)
     llr = np.zeros((shots, n), np.float64) if want_llr else None
     rc = lib().orc_decode(m, n, r.size, _p(r), _p(c), _p(p), shots, _p(s), bp_iters, alpha,
-                          lsd_order, precision, nthreads, _p(corr), _p(st), _p(used), _p(info),
-                          _p(llr))
+                          lsd_order, osd_cs, precision, nthreads, _p(corr), _p(st), _p(used),
+                          _p(info), _p(llr))
     if rc:
         raise ValueError("orc_decode: invalid arguments")
     out = dict(corrections=corr, status=st, bp_iters=used, nu=info[:, 0], kappa=info[:, 1],

@@ -134,6 +134,106 @@ def test_lsd_mu_exhaustive_on_small_clusters(oracle_lib):
     assert checked > 20
 
 
+def _cs_patterns(nonpiv: int, w: int):
+    """Combination sweep of order w over nonpiv ranked non-pivot columns: no flip, every single
+    column, every pair among the first w (App. D, OSD-CS-w)."""
+    pats = [()] + [(k,) for k in range(nonpiv)]
+    return pats + list(itertools.combinations(range(min(w, nonpiv)), 2))
+
+
+@pytest.mark.parametrize("w", [0, 2, 4, 7])
+def test_osd_cs_brute_force_single_cluster(oracle_lib, w):
+    """With one cluster grown over every column (mu >= n), the combination sweep returns the
+    least-cost solution of H e = s among those whose non-pivot part is one of the sweep's
+    patterns; pivots are the first independent columns in reliability order.  Brute force over
+    all 2^n vectors, written from that definition alone."""
+    g = I.Xoshiro256ss(77 + w, np.arange(4, dtype=np.uint64))
+    checked = 0
+    for trial in range(12):
+        m, n = 6, 13
+        rng = np.random.default_rng(1000 * w + trial)
+        h = (rng.random((m, n)) < 0.35).astype(np.uint8)
+        h[:, :m] |= np.eye(m, dtype=np.uint8)  # full row rank, every syndrome solvable
+        h = h[:, rng.permutation(n)]
+        zero = np.nonzero(h.sum(0) == 0)[0]  # a column on no detector never joins a cluster
+        h[rng.integers(0, m, zero.size), zero] = 1
+        p = rng.uniform(0.01, 0.2, n)
+        wfix = np.round(np.log((1 - p) / p).astype(np.float32).astype(np.float64) * 2 ** 32)
+        shots = 6
+        s = rng.integers(0, 2, (shots, m)).astype(np.uint8)
+        llr = np.round(rng.uniform(-2, 6, (shots, n)), 3)
+        r = oracle_lib.lsd(h, s, llr, order=n, osd_cs=w, probs=p, single_cluster=True)
+        assert np.all(r["status"] == 2)
+        xs = ((np.arange(2 ** n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)
+        for k in range(shots):
+            if not s[k].any():
+                assert not r["corrections"][k].any()
+                continue
+            order = sorted(range(n), key=lambda j: (llr[k][j], j))
+            piv, nonpiv = [], []
+            for j in order:
+                cand = piv + [j]
+                if oracle_lib.gf2_rank(h[:, cand]) == len(cand):
+                    piv.append(j)
+                else:
+                    nonpiv.append(j)
+            ok = np.all((xs @ h.T.astype(np.int64)) % 2 == s[k], axis=1)
+            best, best_x = None, None
+            for pat in _cs_patterns(len(nonpiv), w):
+                want = np.zeros(n, np.int64)
+                want[[nonpiv[i] for i in pat]] = 1
+                sel = ok & np.all(xs[:, nonpiv] == want[nonpiv], axis=1)
+                assert sel.sum() == 1  # pivots form a basis of the column space
+                x = xs[sel][0]
+                cost = x @ wfix
+                if best is None or cost < best:
+                    best, best_x = cost, x
+            assert np.array_equal(r["corrections"][k].astype(np.int64), best_x)
+            checked += 1
+    assert checked > 50
+
+
+def _cost(corr, wfix):
+    return corr.astype(np.int64) @ wfix.astype(np.int64)
+
+
+def test_osd_cs_orders_nest(oracle_lib):
+    """The sweeps nest: the patterns of OSD-CS-w contain those of OSD-CS-w' for w' < w, and at
+    mu = 2 those of OSD-E-2, on the same clusters (growth does not depend on the local
+    reprocessing), so the total cost can only fall along that chain."""
+    h = I.bb72()[0]
+    g = I.Xoshiro256ss(5, np.arange(72, dtype=np.uint64))
+    g.uniform()
+    p = 0.02 + 0.14 * g.uniform()
+    e = I.sample_errors(23, 160, p)
+    s = I.syndromes(h, e)
+    llr, hard, used, conv = oracle_lib.bp(h, p, s, iters=30, precision=1)
+    wfix = np.round(np.log((1 - p) / p).astype(np.float32).astype(np.float64) * 2 ** 32)
+    runs = {}
+    for key, kw in {"E2": dict(order=2), "CS0": dict(order=2, osd_cs=0),
+                    "CS2": dict(order=2, osd_cs=2), "CS4": dict(order=2, osd_cs=4)}.items():
+        r = oracle_lib.lsd(h, s, llr, probs=p, labels=True, **kw)
+        assert np.all(r["status"] == 2)
+        assert np.array_equal((r["corrections"].astype(int) @ h.T) % 2, s)
+        runs[key] = r
+    for a in ("CS0", "CS2", "CS4"):
+        assert np.array_equal(runs[a]["fault_lab"], runs["E2"]["fault_lab"])
+    cost = {k: np.array([_cost(c, wfix) for c in r["corrections"]]) for k, r in runs.items()}
+    assert np.all(cost["CS2"] <= cost["E2"])
+    assert np.all(cost["CS2"] <= cost["CS0"])
+    assert np.all(cost["CS4"] <= cost["CS2"])
+    assert np.any(cost["CS4"] < cost["E2"])  # the sweep reaches further than OSD-E-2
+
+
+def test_osd_cs_without_mu_is_lsd0(oracle_lib):
+    """mu = 0 means no reprocessing whatever the sweep order."""
+    h = I.bb72()[0]
+    e, s, llr, conv = _bp_llrs(oracle_lib, h, 0.08, 60, seed=3)
+    r0 = oracle_lib.lsd(h, s, llr)
+    r1 = oracle_lib.lsd(h, s, llr, osd_cs=4)
+    assert np.array_equal(r0["corrections"], r1["corrections"])
+
+
 def test_unsolvable_syndrome(oracle_lib):
     """s outside image(H): the cluster exhausts its component and LSD reports status 3."""
     h = np.array([[1, 1, 0], [1, 1, 0], [0, 0, 1]], np.uint8)  # rows 0 and 1 are equal
