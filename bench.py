@@ -340,6 +340,35 @@ def p_sweep_leg(args, hx, hz, stream, flush, barrier, checker):
             "points": out}
 
 
+def lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker):
+    """BB[[144,12,12]] at p = 0.06, 10^6 shots: LSD-mu with mu as a fraction of the n fault
+    nodes and OSD-CS-4 local reprocessing (App. D's BB experiment, code-capacity noise)."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.lsd import Decoder
+    n = hx.shape[1]
+    p = 0.06
+    probs = np.full(n, p, np.float32)
+    e = I.sample_errors(args.seed + 606, args.shots, probs.astype(np.float64))
+    s_dev = torch.from_numpy(I.syndromes(hx, e)).cuda()
+    e_dev = torch.from_numpy(e).cuda()
+    corr = torch.empty((args.shots, n), dtype=torch.uint8, device="cuda")
+    status = torch.empty(args.shots, dtype=torch.uint8, device="cuda")
+    out = []
+    for frac in (0.0, 0.01, 0.02, 0.05, 0.1, 0.2):
+        order = int(round(frac * n))
+        dec = Decoder(hx, probs, args.iters, order, osd_cs=4 if order else None, stream=stream)
+        ms, st = _timed_decode(dec, s_dev, corr, status, 3, stream, flush, barrier)
+        ler = float(checker.failures(e_dev, corr).float().mean().item())
+        out.append({"mu_frac": frac, "lsd_order": order, "osd": "CS-4" if order else "-",
+                    "shots_per_s": args.shots / (np.mean(ms) / 1e3), "ler": ler,
+                    "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
+                    "kappa_max": st["kappa_max"], "nu_max": st["nu_max"]})
+        dec.close()
+    return {"code": "BB[[144,12,12]]", "p": p, "shots": args.shots, "bp_iters": args.iters,
+            "points": out}
+
+
 def hgp_leg(args, stream, flush, barrier):
     """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
     {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
@@ -516,9 +545,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(args.shots * m),
                "d2h_bytes_per_step": int(args.shots * (n + 1))}
 
-    serving = p_sweep = hgp = None
+    serving = p_sweep = hgp = lsd_mu = None
     if rank == 0 and not args.no_sweeps:
         p_sweep = p_sweep_leg(args, hx, hz, stream, flush, barrier, checker)
+        lsd_mu = lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker)
         hgp = hgp_leg(args, stream, flush, barrier)
     if not args.no_serving and rank == 0:
         serving = serving_leg(args)
@@ -569,6 +599,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "learned": learned,
         "p_sweep": p_sweep,
+        "lsd_mu_cs4": lsd_mu,
         "hgp": hgp,
         "serving": serving,
     }

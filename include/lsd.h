@@ -76,7 +76,14 @@ typedef struct lsd_options {
   int32_t lsd_kernel;     /* LSD kernel: 0 = auto, 1 = dense (state indexed by detector and
                              fault, m <= 512, n <= 2048), 2 = sparse (state sized by what a shot
                              touches; any m, n < 65536; no single_cluster) */
-  int32_t reserved[3];    /* must be zero */
+  int32_t osd_method;     /* local reprocessing of LSD-mu (lsd_order > 0, App. D): 0 = exhaustive
+                             OSD-E over the first mu dependent columns of each cluster
+                             (lsd_order <= 12; default); 1 = combination sweep OSD-CS-w: no
+                             flip, every single dependent column, every pair among the first
+                             w, in reliability order, the first least-cost pattern winning
+                             (lsd_order <= 65535 extra growth steps) */
+  int32_t osd_cs_order;   /* w of OSD-CS-w, 0..8; must be 0 unless osd_method == 1 */
+  int32_t reserved;       /* must be zero */
   size_t mem_budget;      /* device bytes the decoder may hold (H, priors, workspace); 0 = no limit */
   void* stream;           /* cudaStream_t used for all work; NULL = the legacy default stream */
 } lsd_options;
@@ -106,7 +113,9 @@ typedef struct lsd_stats {
  *                  lambda_j = ln((1-p_j)/p_j) (Sec. 4.1's LLR form) are computed on the
  *                  device in double and rounded to float32.
  *   bp_iters       maximum BP iterations, >= 0 (0 = LSD on the priors alone).
- *   lsd_order      mu of LSD-mu (App. D), 0..12; 0 = LSD-0.
+ *   lsd_order      mu of LSD-mu (App. D): extra growth steps per cluster before the local
+ *                  reprocessing; 0 = LSD-0; at most 12 with OSD-E (opt->osd_method 0), 65535
+ *                  with OSD-CS.
  *   opt            nullable; see lsd_options.
  * The decoder copies H and the priors to the device; the caller's arrays may be freed
  * after the call.  Synchronizes its stream before returning.

@@ -16,7 +16,7 @@ using namespace lsdgb;
 
 struct lsd_decoder {
   int m = 0, n = 0, E = 0;
-  int bp_iters = 0, order = 0;
+  int bp_iters = 0, order = 0, osd_cs = -1;
   lsd_options opt{};
   float alpha = 0.625f;
   cudaStream_t st = nullptr;
@@ -267,13 +267,16 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   if (!out) return LSD_ERR_INVALID_ARG;
   *out = nullptr;
   if (m < 1 || n < 1 || nnz < 0 || (nnz > 0 && (!rows || !cols)) || !channel_probs ||
-      bp_iters < 0 || lsd_order < 0 || lsd_order > kMaxOrder)
+      bp_iters < 0 || lsd_order < 0)
     return LSD_ERR_INVALID_ARG;
   lsd_options o{};
   if (opt) o = *opt;
   if (o.bp_method < 0 || o.bp_method > 1 || !valid_lanes(o.bp_lanes) || o.lsd_warps < 0 ||
       o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 2 || o.lsd_kernel < 0 ||
-      o.lsd_kernel > 2 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.ms_scaling < 0.f)
+      o.lsd_kernel > 2 || o.reserved || o.ms_scaling < 0.f || o.osd_method < 0 ||
+      o.osd_method > 1 || o.osd_cs_order < 0 || o.osd_cs_order > kMaxCsOrder ||
+      (o.osd_method == 0 && o.osd_cs_order != 0) ||
+      lsd_order > (o.osd_method == 1 ? kMaxCsGrowth : kMaxOrder))
     return LSD_ERR_INVALID_ARG;
   for (int j = 0; j < n; ++j)
     if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
@@ -321,6 +324,7 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   d->E = E;
   d->bp_iters = bp_iters;
   d->order = lsd_order;
+  d->osd_cs = o.osd_method == 1 ? o.osd_cs_order : -1;
   d->opt = o;
   d->alpha = o.ms_scaling > 0.f ? o.ms_scaling : 0.625f;
   d->st = static_cast<cudaStream_t>(o.stream);
@@ -438,6 +442,7 @@ int lsd_decode_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
   l.corrections = corrections;
   l.status = status;
   l.order = d->order;
+  l.osd_cs = d->osd_cs;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   rc = run_lsd(d, l, shots);
@@ -562,6 +567,7 @@ int lsd_postprocess_batch(lsd_decoder* d, int64_t shots, const float* llrs,
   l.status = status;
   l.shot_info = shot_info;
   l.order = d->order;
+  l.osd_cs = d->osd_cs;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   cudaEventRecord(d->ev[1], d->st);
@@ -681,6 +687,7 @@ extern "C" int lsd_decode_batch_static(lsd_decoder* d, int64_t shots, const uint
   l.corrections = corrections;
   l.status = status;
   l.order = d->order;
+  l.osd_cs = d->osd_cs;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = ctr;
   e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, d->st);
@@ -889,6 +896,7 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
   l.corrections = corrections;
   l.status = st;
   l.order = d->order;
+  l.osd_cs = d->osd_cs;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   rc = run_lsd(d, l, shots);
@@ -1093,6 +1101,7 @@ int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long lo
   l.corrections = corrections;
   l.status = status;
   l.order = d->order;
+  l.osd_cs = d->osd_cs;
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   return run_lsd(d, l, max_shots);

@@ -556,6 +556,130 @@ __device__ void osd_e(const LSDArgs& a, const Shot<L>& S, int m, int lane) {
   }
 }
 
+// Cost of cluster r's local solution (xsol masked by cm) with the dependent columns of slots
+// u1 and u2 flipped (-1 = none).
+template <class L>
+__device__ __forceinline__ long long pattern_cost(const LSDArgs& a, const Shot<L>& S, int u1,
+                                                  int u2) {
+  constexpr int W = L::W;
+  const long long* wfix = a.g.wfix;
+  long long cost = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    uint32_t mw = S.xsol()[w] & S.cm()[w];
+    if (u1 >= 0) mw ^= S.npN()[u1 * W + w];
+    if (u2 >= 0) mw ^= S.npN()[u2 * W + w];
+    while (mw) {
+      const int b = __ffs(mw) - 1;
+      mw &= mw - 1;
+      cost += wfix[S.pcol()[w * 32 + b]];
+    }
+  }
+  if (u1 >= 0) cost += wfix[S.fat()[S.npr()[u1]]];
+  if (u2 >= 0) cost += wfix[S.fat()[S.npr()[u2]]];
+  return cost;
+}
+
+// LSD-mu reprocessing with the combination sweep OSD-CS-w (App. D's BB experiment): per
+// cluster the patterns are no flip, every single dependent column, and every pair among the
+// first w dependent columns in reliability order; the least cost wins, ties going to the
+// earlier pattern in that order.  A pattern is ranked by (cost, class, key): class 0 = no
+// flip, 1 = single (key = the column's rank), 2 = pair (key = i * 16 + j).
+template <class L>
+__device__ void osd_cs(const LSDArgs& a, const Shot<L>& S, int m, int lane) {
+  constexpr int W = L::W;
+  const int nroots = collect_roots(a, S, m, false, lane);
+  const int n_np = S.scal()[1];
+  const int w_cs = a.osd_cs;
+  for (int ci = 0; ci < nroots; ++ci) {
+    const int r = S.inv()[ci];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const int d = c * 32 + lane;
+      const bool in = d < m && S.dlab()[d] == r;
+      const unsigned bal = __ballot_sync(kFull, in);
+      if (lane == 0) S.cm()[c] = bal;
+    }
+    __syncwarp();
+    // the first w dependent columns of the cluster, by repeated minimum over the ranks
+    int sel[kMaxCsOrder];
+    int nt = 0;
+    unsigned last = 0;
+    for (int it = 0; it < w_cs; ++it) {
+      unsigned bk = kNone;
+      int bi = -1;
+      for (int u = lane; u < n_np; u += 32) {
+        const unsigned ku = S.npr()[u];
+        if (it > 0 && ku <= last) continue;
+        if (S.parent()[S.flab()[S.fat()[ku]]] != r) continue;
+        if (ku < bk) {
+          bk = ku;
+          bi = u;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned ok = __shfl_xor_sync(kFull, bk, off);
+        const int oi = __shfl_xor_sync(kFull, bi, off);
+        if (ok < bk) {
+          bk = ok;
+          bi = oi;
+        }
+      }
+      if (bk == kNone) break;
+      sel[nt++] = bi;
+      last = bk;
+    }
+    long long bc = LLONG_MAX;
+    int bcls = 3, bkey = 0, b1 = -1, b2 = -1;
+    auto consider = [&](long long c, int cls, int key, int u1, int u2) {
+      if (c < bc || (c == bc && (cls < bcls || (cls == bcls && key < bkey)))) {
+        bc = c;
+        bcls = cls;
+        bkey = key;
+        b1 = u1;
+        b2 = u2;
+      }
+    };
+    if (lane == 0) consider(pattern_cost(a, S, -1, -1), 0, 0, -1, -1);
+    for (int u = lane; u < n_np; u += 32) {
+      const unsigned ku = S.npr()[u];
+      if (S.parent()[S.flab()[S.fat()[ku]]] != r) continue;
+      consider(pattern_cost(a, S, u, -1), 1, (int)ku, u, -1);
+    }
+    const int npairs = nt * (nt - 1) / 2;
+    for (int t = lane; t < npairs; t += 32) {
+      int i = 0, rem = t;
+      while (rem >= nt - 1 - i) {
+        rem -= nt - 1 - i;
+        ++i;
+      }
+      const int j = i + 1 + rem;
+      consider(pattern_cost(a, S, sel[i], sel[j]), 2, i * 16 + j, sel[i], sel[j]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const long long oc = __shfl_xor_sync(kFull, bc, off);
+      const int ocls = __shfl_xor_sync(kFull, bcls, off);
+      const int okey = __shfl_xor_sync(kFull, bkey, off);
+      const int o1 = __shfl_xor_sync(kFull, b1, off);
+      const int o2 = __shfl_xor_sync(kFull, b2, off);
+      consider(oc, ocls, okey, o1, o2);
+    }
+    if (b1 < 0) continue;  // no flip: OSD-0's local solution stands
+    if (lane < W) {
+      uint32_t delta = S.npN()[b1 * W + lane];
+      if (b2 >= 0) delta ^= S.npN()[b2 * W + lane];
+      S.xsol()[lane] ^= delta;
+    }
+    if (lane == 0) {
+      int ne = S.scal()[2];
+      S.ext()[ne++] = S.fat()[S.npr()[b1]];
+      if (b2 >= 0) S.ext()[ne++] = S.fat()[S.npr()[b2]];
+      S.scal()[2] = ne;
+    }
+    __syncwarp();
+  }
+}
+
 // Per-warp running statistics of the shots a warp decodes.
 struct LsdAcc {
   unsigned long long steps = 0, unsolvable = 0;
@@ -715,7 +839,10 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
         k = collect_roots(a, S, m, false, lane);
         if (lsd_step<L, MU>(G, S, m, n, k, false, lane) == 2) break;
       }
-      osd_e(a, S, m, lane);
+      if (a.osd_cs >= 0)
+        osd_cs(a, S, m, lane);
+      else
+        osd_e(a, S, m, lane);
     }
   }
 

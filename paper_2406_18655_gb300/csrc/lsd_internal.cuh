@@ -72,7 +72,8 @@ struct LSDArgs {
   uint8_t* corrections;       // [shots][n]
   uint8_t* status;            // [shots] nullable
   int32_t* shot_info;         // [shots][3] nullable
-  int order;                  // LSD-mu order
+  int order;                  // LSD-mu: extra growth steps per cluster
+  int osd_cs;                 // LSD-mu reprocessing: -1 = OSD-E of order `order`, w >= 0 = OSD-CS-w
   int single_cluster;
   DevCounters* ctr;
 };
@@ -142,6 +143,8 @@ cudaError_t launch_sparse(const LSDArgs& a, bool big, int grid, int* scratch, si
 // Limits of this build's kernels.
 constexpr int kMaxLsdWords = 16;    // LSD: m <= 32 * kMaxLsdWords detectors per shot
 constexpr int kMaxRowDeg = 32;      // BP: check degree (sign bits in one word)
-constexpr int kMaxOrder = 12;       // LSD-mu order
+constexpr int kMaxOrder = 12;       // LSD-mu order with OSD-E (2^mu patterns per cluster)
+constexpr int kMaxCsGrowth = 65535; // LSD-mu growth steps with OSD-CS
+constexpr int kMaxCsOrder = 8;      // w of OSD-CS-w
 
 }  // namespace lsdgb

@@ -544,6 +544,129 @@ __device__ void sparse_osd_e(const LSDArgs& a, const SShot<L>& S, int lane) {
   }
 }
 
+// Cost of cluster r's local solution (xsol masked by cm) with the dependent columns of slots
+// u1 and u2 flipped (-1 = none).
+template <class L>
+__device__ __forceinline__ long long sparse_pattern_cost(const LSDArgs& a, const SShot<L>& S,
+                                                         int u1, int u2) {
+  constexpr int W = L::W;
+  const long long* wfix = a.g.wfix;
+  long long cost = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t mw = S.xsol()[w] & S.cm()[w];
+    if (u1 >= 0) mw ^= S.npN()[u1 * W + w];
+    if (u2 >= 0) mw ^= S.npN()[u2 * W + w];
+    while (mw) {
+      const int b = __ffs(mw) - 1;
+      mw &= mw - 1;
+      cost += wfix[S.pcol()[w * 32 + b]];
+    }
+  }
+  if (u1 >= 0) cost += wfix[(int)(S.npk()[u1] & 0xffffffffu)];
+  if (u2 >= 0) cost += wfix[(int)(S.npk()[u2] & 0xffffffffu)];
+  return cost;
+}
+
+// OSD-CS-w reprocessing of every cluster (App. D), as osd_cs in lsd.cu: no flip, every
+// single dependent column, every pair among the first w in key order; ranked by
+// (cost, class, key) with class 0 = no flip, 1 = single (key = the column's 64-bit order
+// key), 2 = pair (key = i * 16 + j).
+template <class L>
+__device__ void sparse_osd_cs(const LSDArgs& a, const SShot<L>& S, int lane) {
+  constexpr int W = L::W;
+  const int nroots = collect_all(S, lane);
+  const int n_np = S.scal()[S_NP];
+  const int nsl = S.scal()[S_SLOTS];
+  const int w_cs = a.osd_cs;
+  for (int ci = 0; ci < nroots; ++ci) {
+    const int r = S.inv()[ci];
+    for (int c = 0; c < W; ++c) {
+      const int sl = c * 32 + lane;
+      const bool in = sl < nsl && S.dlab[S.dslot()[sl]] == r;
+      const unsigned bal = __ballot_sync(kFull, in);
+      if (lane == 0) S.cm()[c] = bal;
+    }
+    __syncwarp();
+    int sel[kMaxCsOrder];
+    int nt = 0;
+    unsigned long long last = 0;
+    for (int it = 0; it < w_cs; ++it) {
+      unsigned long long bk = kNoKey;
+      int bi = -1;
+      for (int u = lane; u < n_np; u += 32) {
+        const unsigned long long ku = S.npk()[u];
+        if (it > 0 && ku <= last) continue;
+        if (S.parent()[S.fst[(int)(ku & 0xffffffffu)]] != r) continue;
+        if (ku < bk) {
+          bk = ku;
+          bi = u;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(kFull, bk, off);
+        const int oi = __shfl_xor_sync(kFull, bi, off);
+        if (ok < bk) {
+          bk = ok;
+          bi = oi;
+        }
+      }
+      if (bk == kNoKey) break;
+      sel[nt++] = bi;
+      last = bk;
+    }
+    long long bc = LLONG_MAX;
+    int bcls = 3, b1 = -1, b2 = -1;
+    unsigned long long bkey = 0;
+    auto consider = [&](long long c, int cls, unsigned long long key, int u1, int u2) {
+      if (c < bc || (c == bc && (cls < bcls || (cls == bcls && key < bkey)))) {
+        bc = c;
+        bcls = cls;
+        bkey = key;
+        b1 = u1;
+        b2 = u2;
+      }
+    };
+    if (lane == 0) consider(sparse_pattern_cost(a, S, -1, -1), 0, 0, -1, -1);
+    for (int u = lane; u < n_np; u += 32) {
+      const unsigned long long ku = S.npk()[u];
+      if (S.parent()[S.fst[(int)(ku & 0xffffffffu)]] != r) continue;
+      consider(sparse_pattern_cost(a, S, u, -1), 1, ku, u, -1);
+    }
+    const int npairs = nt * (nt - 1) / 2;
+    for (int t = lane; t < npairs; t += 32) {
+      int i = 0, rem = t;
+      while (rem >= nt - 1 - i) {
+        rem -= nt - 1 - i;
+        ++i;
+      }
+      const int j = i + 1 + rem;
+      consider(sparse_pattern_cost(a, S, sel[i], sel[j]), 2, (unsigned long long)(i * 16 + j),
+               sel[i], sel[j]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const long long oc = __shfl_xor_sync(kFull, bc, off);
+      const int ocls = __shfl_xor_sync(kFull, bcls, off);
+      const unsigned long long okey = __shfl_xor_sync(kFull, bkey, off);
+      const int o1 = __shfl_xor_sync(kFull, b1, off);
+      const int o2 = __shfl_xor_sync(kFull, b2, off);
+      consider(oc, ocls, okey, o1, o2);
+    }
+    if (b1 < 0) continue;  // no flip: OSD-0's local solution stands
+    for (int w = lane; w < W; w += 32) {
+      uint32_t delta = S.npN()[b1 * W + w];
+      if (b2 >= 0) delta ^= S.npN()[b2 * W + w];
+      S.xsol()[w] ^= delta;
+    }
+    if (lane == 0) {
+      int ne = S.scal()[S_EXT];
+      S.ext()[ne++] = (int)(S.npk()[b1] & 0xffffffffu);
+      if (b2 >= 0) S.ext()[ne++] = (int)(S.npk()[b2] & 0xffffffffu);
+      S.scal()[S_EXT] = ne;
+    }
+    __syncwarp();
+  }
+}
+
 // Work items come from a.queue / a.count as in lsd.cu.  Shots that overflow the capacity are
 // appended to spill[] (spill_count) when spill != nullptr, else reported unsolvable.
 template <int CAP, int SC, bool MU, bool GLOBAL_RT>
@@ -675,7 +798,12 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
           }
           if (rc == 2) break;
         }
-        if (status == LSD_SHOT_OK_LSD) sparse_osd_e(a, S, lane);
+        if (status == LSD_SHOT_OK_LSD) {
+          if (a.osd_cs >= 0)
+            sparse_osd_cs(a, S, lane);
+          else
+            sparse_osd_e(a, S, lane);
+        }
       }
     }
     if (status == kSpill) {

@@ -51,7 +51,8 @@ class Options(C.Structure):
                 ("no_early_exit", C.c_int32), ("single_cluster", C.c_int32),
                 ("bp_lanes", C.c_int32), ("lsd_warps", C.c_int32),
                 ("bp_kernel", C.c_int32), ("lsd_kernel", C.c_int32),
-                ("reserved", C.c_int32 * 3),
+                ("osd_method", C.c_int32), ("osd_cs_order", C.c_int32),
+                ("reserved", C.c_int32),
                 ("mem_budget", C.c_size_t),
                 ("stream", C.c_void_p)]
 
@@ -150,13 +151,16 @@ class Decoder:
 
     ``h`` is a dense 0/1 matrix (numpy or torch, m x n).  ``stream`` is a
     ``torch.cuda.Stream`` (default: the current stream at construction); all work of
-    this decoder runs on it.
+    this decoder runs on it.  ``osd_cs = None`` reprocesses LSD-mu's clusters with OSD-E of
+    order mu, ``osd_cs = w`` with the combination sweep OSD-CS-w (then lsd_order may exceed
+    12: it only counts growth steps).
     """
 
     def __init__(self, h, channel_probs, bp_iters: int, lsd_order: int = 0, *,
                  ms_scaling: float = 0.0, bp_method: int = 0, no_early_exit: bool = False,
                  single_cluster: bool = False, bp_lanes: int = 0, lsd_warps: int = 0,
-                 bp_kernel: int = 0, lsd_kernel: int = 0, mem_budget: int = 0, stream=None):
+                 bp_kernel: int = 0, lsd_kernel: int = 0, mem_budget: int = 0, stream=None,
+                 osd_cs: int | None = None):
         import torch
         h = np.asarray(h.cpu() if isinstance(h, torch.Tensor) else h, dtype=np.uint8)
         self.m, self.n = h.shape
@@ -177,6 +181,8 @@ class Decoder:
         opt.lsd_warps = lsd_warps
         opt.bp_kernel = bp_kernel
         opt.lsd_kernel = lsd_kernel
+        opt.osd_method = 0 if osd_cs is None else 1
+        opt.osd_cs_order = 0 if osd_cs is None else osd_cs
         opt.mem_budget = mem_budget
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -188,6 +194,7 @@ class Decoder:
         self._h = handle
         self.bp_iters = bp_iters
         self.lsd_order = lsd_order
+        self.osd_cs = osd_cs
 
     # -- lifetime ---------------------------------------------------------------------
     def close(self):

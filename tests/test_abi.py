@@ -70,8 +70,15 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lsdlib):
     assert L.lsd_create(C.byref(h), 2, 2, 3, P(rows), P(cols), P(p), 10, 99, None) == -1
     # nonzero reserved option
     opt = lsdlib.Options()
-    opt.reserved[0] = 1
+    opt.reserved = 1
     assert L.lsd_create(C.byref(h), 2, 2, 3, P(rows), P(cols), P(p), 10, 0, C.byref(opt)) == -1
+    # OSD-CS: sweep order beyond 8, a sweep order without the sweep, an unknown method, and
+    # growth beyond 65535 steps
+    for method, w, order in ((1, 9, 4), (0, 2, 4), (2, 0, 4), (1, 4, 65536)):
+        opt = lsdlib.Options()
+        opt.osd_method, opt.osd_cs_order = method, w
+        assert L.lsd_create(C.byref(h), 2, 2, 3, P(rows), P(cols), P(p), 10, order,
+                            C.byref(opt)) == -1
     assert not h.value
     # NULL handles are rejected or ignored
     assert L.lsd_destroy(None) == 0

@@ -149,6 +149,42 @@ def test_lsd_bit_exact_given_identical_soft_information(L, name, p, order, singl
     assert np.array_equal(info[:, 2], r["steps"])
 
 
+@pytest.mark.parametrize("name,p,order,w,soft,kernel", [
+    ("bb72", 0.08, 2, 4, "bp", 1), ("bb144", 0.06, 6, 4, "bp", 1),
+    ("bb144", 0.06, 3, 7, "ties", 1), ("bb144", 0.08, 29, 4, "bp", 1),
+    ("bb144", 0.06, 6, 0, "bp", 1), ("bb144", 0.06, 58, 8, "ties", 1),
+    ("bb144", 0.06, 6, 4, "bp", 2), ("bb144", 0.08, 29, 8, "ties", 2),
+    ("ldpc_96x192", 0.06, 4, 4, "bp", 0), ("ldpc_480x960", 0.04, 14, 4, "bp", 0),
+    ("ldpc_480x960", 0.04, 14, 4, "ties", 2)])
+def test_lsd_osd_cs_bit_exact(L, name, p, order, w, soft, kernel):
+    """LSD-mu with the combination sweep OSD-CS-w (App. D), dense and sparse LSD kernels,
+    growth beyond OSD-E's order limit (29 and 58 steps = 10 % and 20 % of BB144's n)."""
+    h, probs, e, s = sample(name, p, 1500, seed=501 + order + w)
+    if soft == "bp":
+        llr, *_ = oracle.bp(h, f64(probs), s, 30, precision=1)
+        llr = llr.astype(np.float32)
+    else:
+        llr = _rounded_llrs((s.shape[0], h.shape[1]), 7 + order)
+    d = L.Decoder(h, probs, 30, order, osd_cs=w, lsd_kernel=kernel)
+    corr, st, info = d.postprocess(dev(llr), dev(s))
+    torch.cuda.synchronize()
+    r = oracle.lsd(h, s, llr.astype(np.float64), order=order, probs=f64(probs), osd_cs=w)
+    assert np.array_equal(st.cpu().numpy(), r["status"])
+    assert np.array_equal(corr.cpu().numpy(), r["corrections"])
+    info = info.cpu().numpy()
+    assert np.array_equal(info[:, 0], r["nu"])
+    assert np.array_equal(info[:, 1], r["kappa"])
+
+
+def test_decode_osd_cs_matches_oracle(L):
+    h, probs, e, s = sample("bb144", 0.08, 4000, seed=909)
+    d = L.Decoder(h, probs, 30, 14, osd_cs=4)
+    corr, st, stats = d.decode(dev(s), want_stats=True)
+    o = oracle.decode(h, f64(probs), s, 30, lsd_order=14, osd_cs=4, precision=1)
+    assert np.array_equal(st.cpu().numpy(), o["status"])
+    assert np.array_equal(corr.cpu().numpy(), o["corrections"])
+
+
 def test_single_cluster_equals_osd0(L):
     h, probs, e, s = sample("bb144", 0.05, 200, seed=9)
     llr, *_ = oracle.bp(h, f64(probs), s, 20, precision=1)
