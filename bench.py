@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-sweeps", action="store_true",
                     help="skip the p sweep (BB144, LSD-0/6) and the HGP legs")
     ap.add_argument("--hgp-shots", type=int, default=100_000)
+    ap.add_argument("--window-shots", type=int, default=200_000)
     ap.add_argument("--serving-loads", default="1e4,1e5,1e6,1e7",
                     help="offered loads (shots/s) of the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=0.5)
@@ -369,6 +370,47 @@ def lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker):
             "points": out}
 
 
+def window_leg(args, hx, hz, stream, flush, barrier, checker):
+    """BB[[144,12,12]] over d = 12 noisy syndrome rounds plus a noiseless one, phenomenological
+    noise p = q: (3,1) overlapping windows (Methods 4.3) against one decode of the whole
+    space-time matrix (936 x 2592), BP 30 + LSD-0, the same device-sampled shots."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.lsd import Decoder, WindowDecoder
+    m, n = hx.shape
+    d, shots = 12, args.window_shots
+    out = []
+    for p in (0.003, 0.006):
+        glob = Decoder(I.space_time(hx, d), I.space_time_probs(n, m, d, p, p).astype(np.float32),
+                       30, stream=stream)
+        e, s = glob.sample(args.seed + int(p * 1e4), shots)
+        win = WindowDecoder(hx, np.full(n, p, np.float32), np.full(m, p, np.float32), d, 3, 1,
+                            bp_iters=30, stream=stream)
+        corr = torch.empty((shots, d * (n + m)), dtype=torch.uint8, device="cuda")
+        status = torch.empty(shots, dtype=torch.uint8, device="cuda")
+        zeros = torch.zeros((shots, n), dtype=torch.uint8, device="cuda")
+        point = {"p": p, "q": p}
+        for kind, dec in (("window_3_1", win), ("global", glob)):
+            fn = lambda: dec.decode(s, corr, status)  # noqa: E731
+            for _ in range(2):
+                fn()
+            ms = timed_steps(fn, 3, stream, flush, barrier)
+            _, _, st = dec.decode(s, corr, status, want_stats=True)
+            resid = ((e ^ corr).view(shots, d, n + m)[:, :, :n].sum(dim=1) % 2).to(torch.uint8)
+            fails = checker.failures(resid, zeros)
+            point[kind] = {"shots_per_s": shots / (np.mean(ms) / 1e3),
+                           "ms_per_step": float(np.mean(ms)), "ler": float(fails.float().mean()),
+                           "unsolvable": int((status == 3).sum().item()),
+                           "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
+                           "window_decodes": st["shots"] // shots,
+                           "kappa_max": st["kappa_max"]}
+        out.append(point)
+        win.close()
+        glob.close()
+    return {"code": "BB[[144,12,12]] space-time, d = 12 noisy rounds + 1 noiseless",
+            "shots": shots, "bp_iters": 30, "lsd_order": 0, "points": out}
+
+
 def hgp_leg(args, stream, flush, barrier):
     """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
     {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
@@ -545,10 +587,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(args.shots * m),
                "d2h_bytes_per_step": int(args.shots * (n + 1))}
 
-    serving = p_sweep = hgp = lsd_mu = None
+    serving = p_sweep = hgp = lsd_mu = windows = None
     if rank == 0 and not args.no_sweeps:
         p_sweep = p_sweep_leg(args, hx, hz, stream, flush, barrier, checker)
         lsd_mu = lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker)
+        windows = window_leg(args, hx, hz, stream, flush, barrier, checker)
         hgp = hgp_leg(args, stream, flush, barrier)
     if not args.no_serving and rank == 0:
         serving = serving_leg(args)
@@ -600,6 +643,7 @@ def run_ours(args):
         "learned": learned,
         "p_sweep": p_sweep,
         "lsd_mu_cs4": lsd_mu,
+        "windows": windows,
         "hgp": hgp,
         "serving": serving,
     }

@@ -298,6 +298,69 @@ int lsd_sample(lsd_decoder* dec, uint64_t seed, int64_t first_shot, int64_t shot
                uint8_t* errors, uint8_t* syndromes);
 
 /* ------------------------------------------------------------------------------------
+ * Overlapping-window decoding of repeated syndrome rounds (Methods 4.3: a (w, c) = (3, 1)
+ * window, w rounds decoded, the c oldest committed).  Phenomenological noise on a code H
+ * (m x n): d noisy syndrome rounds and one noiseless round.  Detector block t (t = 0..d,
+ * m bytes each) is the difference of syndrome rounds t and t-1; the faults of round t
+ * (t = 0..d-1, n + m bytes each) are the n data faults (flipping block t through H) and
+ * then the m measurement faults (flipping blocks t and t+1).  A shot's syndrome is its
+ * (d+1) m detector bytes, block by block; its correction d (n+m) fault bytes, round by round.
+ *
+ * Windows start at t = 0, c, 2c, ...  A window with t + w - 1 < d holds blocks t..t+w-1 and
+ * fault rounds t..t+w-1 (the measurement faults of its last round flip only its last block
+ * inside it), is decoded by BP + LSD, and commits its first c rounds: they are written to
+ * the correction, and the measurement faults of its round c-1 flip the first block of the
+ * next window.  The first window with t + w - 1 >= d (it reaches block d) or t + c >= d (it
+ * would commit the last round; only possible when c = w) is the final one: blocks t..d,
+ * rounds t..d-1, all committed.  Every window is decoded exactly as lsd_decode_batch decodes
+ * its matrix with the channel probabilities of its columns.
+ * ------------------------------------------------------------------------------------ */
+typedef struct lsd_window lsd_window;
+
+/*
+ * lsd_window_create -- a window decoder.
+ *   out            receives the handle.
+ *   m, n, nnz, rows, cols   H as for lsd_create (host COO).
+ *   p_data         host, n probabilities in (0, 1) of the data faults of every round.
+ *   q_meas         host, m probabilities in (0, 1) of the measurement faults.
+ *   rounds         d >= 1 noisy rounds.
+ *   window, commit w >= 1 and 1 <= c <= w.
+ *   bp_iters, lsd_order, opt   as for lsd_create, applied to the decoder of every window
+ *                  (opt->stream is the stream of all the work).
+ * Builds two decoders: the inner window's matrix (w m x w (n+m)) and the final window's
+ * ((d - t_f + 1) m x (d - t_f) (n+m), t_f its first round); only the final one when w > d.
+ * Errors as lsd_create.
+ */
+int lsd_window_create(lsd_window** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
+                      const int32_t* cols, const float* p_data, const float* q_meas,
+                      int32_t rounds, int32_t window, int32_t commit, int32_t bp_iters,
+                      int32_t lsd_order, const lsd_options* opt);
+
+/*
+ * lsd_window_decode -- decode `shots` shots window by window.  Asynchronous unless
+ * stats != NULL.
+ *   syndromes    device [shots][(d+1) m] bytes (read only).
+ *   corrections  device [shots][d (n+m)] bytes, every byte written.
+ *   status       device [shots] bytes, nullable: the largest per-shot status of any window
+ *                (LSD_SHOT_UNSOLVABLE if some window's syndrome was outside its image).
+ *   stats        nullable: the sums over windows of every window decode's lsd_stats
+ *                (shots counts window decodes; kappa_max, nu_max are maxima); synchronizes.
+ * Workspace (window syndromes, corrections and status: about shots (w m + w (n+m) + 1)
+ * bytes, one more block per shot when c = w) is
+ * allocated on first use and kept; the work of one call runs on the decoder's stream, so
+ * calls on the same stream are ordered.
+ */
+int lsd_window_decode(lsd_window* win, int64_t shots, const uint8_t* syndromes,
+                      uint8_t* corrections, uint8_t* status, lsd_stats* stats);
+
+/* lsd_window_kernel_launches -- kernels launched so far by the window decoder and the
+ * decoders of its windows. */
+int lsd_window_kernel_launches(const lsd_window* win, int64_t* count);
+
+/* lsd_window_destroy -- free the window decoder; NULL is a no-op.  Synchronizes. */
+int lsd_window_destroy(lsd_window* win);
+
+/* ------------------------------------------------------------------------------------
  * Serving (no counterpart in the paper): continuous batching of single-shot requests over
  * several codes.  A scheduler thread keeps `slots_per_code` batches of each code in flight
  * (each slot a decoder with its own stream); a batch launches as soon as a slot is idle and

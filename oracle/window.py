@@ -13,8 +13,11 @@ a running syndrome S, initially the shot's syndrome:
 
     t = 0
     loop:
-        if t + w - 1 >= d: the final window holds blocks t..d and fault rounds t..d-1;
-                            decode it, commit all of it, stop
+        if t + w - 1 >= d or t + c >= d:
+                            the final window holds blocks t..d and fault rounds t..d-1;
+                            decode it, commit all of it, stop (the second condition only
+                            matters for c = w, where the windows would otherwise leave the
+                            noiseless block d alone in a window without faults)
         else:               the window holds blocks t..t+w-1 and fault rounds t..t+w-1
                             (the measurement faults of its last round reach one block past
                             the window; inside it they flip only that last block); decode
@@ -70,7 +73,7 @@ def window_decode(h, p_data, q_meas, d: int, syndromes, w: int = 3, c: int = 1,
     status = np.zeros(shots, np.uint8)
     t, windows = 0, 0
     while True:
-        final = t + w - 1 >= d
+        final = t + w - 1 >= d or t + c >= d
         rounds = d - t if final else w
         blocks = rounds + 1 if final else w
         hw = window_matrix(h, rounds, blocks)

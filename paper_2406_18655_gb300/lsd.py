@@ -33,7 +33,8 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_prior_gradient", "lsd_prior_train_step", "lsd_decode_learned",
            "lsd_prior_destroy", "lsd_sample", "lsd_server_create", "lsd_server_submit",
            "lsd_server_wait_all", "lsd_server_get_report", "lsd_server_run_poisson",
-           "lsd_server_destroy", "lsd_autotune", "lsd_last_error")
+           "lsd_server_destroy", "lsd_autotune", "lsd_last_error", "lsd_window_create",
+           "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy")
 
 
 class LsdError(RuntimeError):
@@ -112,6 +113,12 @@ def lib():
     L.lsd_prior_destroy.argtypes = [P]
     L.lsd_sample.argtypes = [P, C.c_uint64, C.c_int64, C.c_int64, P, P]
     L.lsd_autotune.argtypes = [P, C.c_int64, P, C.POINTER(TuneReport)]
+    L.lsd_window_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int64, P, P, P, P,
+                                     C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                     C.POINTER(Options)]
+    L.lsd_window_decode.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
+    L.lsd_window_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
+    L.lsd_window_destroy.argtypes = [P]
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -340,6 +347,90 @@ class Decoder:
     def kernel_launches(self) -> int:
         v = C.c_int64()
         _check(lib().lsd_kernel_launches(self._h, C.byref(v)), "lsd_kernel_launches")
+        return v.value
+
+
+class WindowDecoder:
+    """(w, c) overlapping-window decoder of d noisy syndrome rounds of ``h`` plus a noiseless
+    one (``lsd_window_create``; Methods 4.3 uses w = 3, c = 1).  ``p_data`` (n) and
+    ``q_meas`` (m) are the per-round fault probabilities; the remaining keywords are those
+    of :class:`Decoder`, applied to every window."""
+
+    def __init__(self, h, p_data, q_meas, rounds: int, window: int = 3, commit: int = 1,
+                 bp_iters: int = 30, lsd_order: int = 0, *, osd_cs: int | None = None,
+                 bp_kernel: int = 0, lsd_kernel: int = 0, stream=None):
+        import torch
+        h = np.asarray(h.cpu() if isinstance(h, torch.Tensor) else h, dtype=np.uint8)
+        self.m, self.n = h.shape
+        self.d = rounds
+        rows, cols = np.nonzero(h)
+        rows = np.ascontiguousarray(rows, np.int32)
+        cols = np.ascontiguousarray(cols, np.int32)
+
+        def probs(v, k):
+            v = np.asarray(v, dtype=np.float32)
+            return np.ascontiguousarray(np.full(k, float(v), np.float32) if v.ndim == 0 else v)
+        p = probs(p_data, self.n)
+        q = probs(q_meas, self.m)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt = Options()
+        opt.bp_kernel = bp_kernel
+        opt.lsd_kernel = lsd_kernel
+        opt.osd_method = 0 if osd_cs is None else 1
+        opt.osd_cs_order = 0 if osd_cs is None else osd_cs
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        handle = C.c_void_p()
+        _check(lib().lsd_window_create(C.byref(handle), self.m, self.n, rows.size,
+                                       rows.ctypes.data_as(C.c_void_p),
+                                       cols.ctypes.data_as(C.c_void_p),
+                                       p.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
+                                       rounds, window, commit, bp_iters, lsd_order, C.byref(opt)),
+               "lsd_window_create")
+        self._h = handle
+
+    @property
+    def syndrome_len(self) -> int:
+        return (self.d + 1) * self.m
+
+    @property
+    def fault_len(self) -> int:
+        return self.d * (self.n + self.m)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lsd_window_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, syndromes, corrections=None, status=None, want_stats: bool = False):
+        """Device syndromes [shots][(d+1) m] -> (corrections [shots][d (n+m)], status[, stats])."""
+        import torch
+        shots = syndromes.shape[0]
+        _dev_tensor(syndromes, torch.uint8, (shots, self.syndrome_len), "syndromes")
+        dev = syndromes.device
+        if corrections is None:
+            corrections = torch.empty((shots, self.fault_len), dtype=torch.uint8, device=dev)
+        if status is None:
+            status = torch.empty(shots, dtype=torch.uint8, device=dev)
+        _dev_tensor(corrections, torch.uint8, (shots, self.fault_len), "corrections")
+        _dev_tensor(status, torch.uint8, (shots,), "status")
+        st = Stats() if want_stats else None
+        _check(lib().lsd_window_decode(self._h, shots, _ptr(syndromes), _ptr(corrections),
+                                       _ptr(status), C.byref(st) if st is not None else None),
+               "lsd_window_decode")
+        if want_stats:
+            return corrections, status, st.as_dict()
+        return corrections, status
+
+    def kernel_launches(self) -> int:
+        v = C.c_int64()
+        _check(lib().lsd_window_kernel_launches(self._h, C.byref(v)),
+               "lsd_window_kernel_launches")
         return v.value
 
 

@@ -80,6 +80,14 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lsdlib):
         assert L.lsd_create(C.byref(h), 2, 2, 3, P(rows), P(cols), P(p), 10, order,
                             C.byref(opt)) == -1
     assert not h.value
+    # window decoder: commit beyond the window, no rounds, an index out of range
+    pq = np.full(2, 0.1, np.float32)
+    for d, w, c, r in ((3, 3, 4, rows), (0, 3, 1, rows), (3, 0, 1, rows), (3, 3, 0, rows),
+                       (3, 3, 1, bad)):
+        assert L.lsd_window_create(C.byref(h), 2, 2, 3, P(r), P(cols), P(pq), P(pq), d, w, c, 10,
+                                   0, None) == -1
+    assert L.lsd_window_destroy(None) == 0
+    assert L.lsd_window_decode(None, 1, None, None, None, None) == -1
     # NULL handles are rejected or ignored
     assert L.lsd_destroy(None) == 0
     assert L.lsd_decode_batch(None, 1, None, None, None, None, None) == -1

@@ -44,11 +44,12 @@ def test_one_window_is_global_decoding(W, oracle_lib, d, w):
 
 
 @pytest.mark.parametrize("d,w,c,p", [(6, 3, 1, 0.01), (6, 3, 1, 0.03), (12, 3, 1, 0.02),
-                                     (6, 4, 2, 0.02), (5, 2, 1, 0.02)])
+                                     (6, 4, 2, 0.02), (5, 2, 1, 0.02), (6, 3, 3, 0.02),
+                                     (7, 3, 3, 0.02), (1, 3, 1, 0.05)])
 def test_windowed_correction_explains_the_syndrome(W, d, w, c, p):
     """Committed faults explain every detector: H_st e_hat = s for the full space-time matrix,
-    and the running syndrome is left at zero; the number of windows is ceil((d - w + 1) / c)
-    inner windows plus the final one."""
+    and the running syndrome is left at zero; the windows start at 0, c, 2c, ... up to the
+    first that reaches block d or commits the last round."""
     h = I.bb72()[0]
     m, n = h.shape
     e, s = _sample(h, d, p, p, 150, seed=int(1000 * p) + d + w)
@@ -59,7 +60,7 @@ def test_windowed_correction_explains_the_syndrome(W, d, w, c, p):
     assert not r["residual_syndrome"].any()
     inner = 0
     t = 0
-    while t + w - 1 < d:
+    while t + w - 1 < d and t + c < d:
         inner += 1
         t += c
     assert r["windows"] == inner + 1
