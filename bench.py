@@ -404,11 +404,44 @@ def window_leg(args, hx, hz, stream, flush, barrier, checker):
                            "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
                            "window_decodes": st["shots"] // shots,
                            "kappa_max": st["kappa_max"]}
+        if p == 0.003:
+            point["streaming"] = _stream_latency(win, s, d, m, n, stream)
         out.append(point)
         win.close()
         glob.close()
     return {"code": "BB[[144,12,12]] space-time, d = 12 noisy rounds + 1 noiseless",
             "shots": shots, "bp_iters": 30, "lsd_order": 0, "points": out}
+
+
+def _stream_latency(win, s, d, m, n, stream):
+    """Rounds pushed one at a time to S concurrent streams (lsd_window_stream_push); the
+    latency of a push is host time from the call to its results on the host side of the
+    stream (synchronize), the real-time figure a control loop would see."""
+    import torch
+    res = []
+    for streams in (1000, 10000, 100000):
+        if streams > s.shape[0]:
+            continue
+        blocks = s[:streams].view(streams, d + 1, m)
+        blocks = [blocks[:, b].contiguous() for b in range(d + 1)]
+        corr = torch.empty((streams, d * (n + m)), dtype=torch.uint8, device="cuda")
+        st = torch.empty(streams, dtype=torch.uint8, device="cuda")
+        lat = []
+        for rep in range(4):
+            win.stream_reset(streams)
+            stream.synchronize()
+            for b in range(d + 1):
+                t0 = time.perf_counter()
+                _, count = win.stream_push(blocks[b], corr, st)
+                stream.synchronize()
+                if rep > 0 and count:
+                    lat.append((time.perf_counter() - t0) * 1e6)
+        lat = np.array(lat)
+        res.append({"streams": streams, "window_pushes": int(lat.size),
+                    "p50_us": float(np.percentile(lat, 50)),
+                    "p99_us": float(np.percentile(lat, 99)),
+                    "stream_rounds_per_s": streams / (np.mean(lat) / 1e6)})
+    return res
 
 
 def hgp_leg(args, stream, flush, barrier):

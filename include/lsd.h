@@ -353,6 +353,31 @@ int lsd_window_create(lsd_window** out, int32_t m, int32_t n, int64_t nnz, const
 int lsd_window_decode(lsd_window* win, int64_t shots, const uint8_t* syndromes,
                       uint8_t* corrections, uint8_t* status, lsd_stats* stats);
 
+/*
+ * Streaming: the same windows, decoded as the rounds arrive.  `shots` concurrent streams
+ * (for example one per logical block) deliver detector block t = 0, 1, ..., d one push at a
+ * time; a push that completes a window (its last block, or block d for the final window)
+ * decodes it for every stream and commits its first c rounds (all remaining rounds for the
+ * final window).  The committed corrections equal lsd_window_decode's on the same blocks.
+ *
+ * lsd_window_stream_reset -- start (or restart) `shots` >= 1 streams; allocates the
+ *   syndrome history (shots (d+1) m bytes) and the window workspace on first use.
+ * lsd_window_stream_push -- the next detector block of every stream.
+ *   block        device [shots][m] bytes (read before the call's work completes on the stream).
+ *   corrections  device [shots][d (n+m)] bytes, the same buffer for every push of a stream:
+ *                a push that commits rounds [first, first + count) writes exactly those.
+ *   status       device [shots] bytes, nullable, the same buffer for every push: largest
+ *                window status so far (valid once a window has been committed).
+ *   first_round, rounds_committed   host, nullable: the committed range (count 0 when the
+ *                push completed no window).
+ *   Asynchronous on the decoder's stream.  More than d + 1 pushes, or a push before a reset,
+ *   is LSD_ERR_INVALID_ARG.  The stream keeps the last window's corrections in the decoder's
+ *   workspace: a lsd_window_decode call between two pushes of a stream breaks it (reset it).
+ */
+int lsd_window_stream_reset(lsd_window* win, int64_t shots);
+int lsd_window_stream_push(lsd_window* win, const uint8_t* block, uint8_t* corrections,
+                           uint8_t* status, int32_t* first_round, int32_t* rounds_committed);
+
 /* lsd_window_kernel_launches -- kernels launched so far by the window decoder and the
  * decoders of its windows. */
 int lsd_window_kernel_launches(const lsd_window* win, int64_t* count);

@@ -28,6 +28,12 @@ struct lsd_window {
   uint8_t* wst = nullptr;
   size_t cap = 0;
   int64_t launches = 0;
+  // streaming state: syndrome history [scap][(d+1) m] of `sshots` streams, blocks received,
+  // the next window's first round, and the last decoded window (rounds, committed rounds)
+  uint8_t* hist = nullptr;
+  size_t scap = 0;
+  int64_t sshots = -1;
+  int received = 0, t_next = 0, prev_t = -1, prev_wr = 0, prev_commit = 0;
 };
 
 namespace {
@@ -41,21 +47,23 @@ int wfail(cudaError_t e) {
 // couple of coalesced passes).  Sizes in units of T (bytes, or 4-byte words when every row
 // and block size is a multiple of 4):
 //   F = n + m (one fault round), M = m (one detector block), N = n.
-// Commit: rounds 0..commit-1 of the decoded window (row wc_row) -> rounds t..t+commit-1 of
-// the correction (row c_row); status = max over windows.  Gather: blocks t_next..t_next+bn-1
-// of the syndrome (row s_row) -> the next window's syndrome; its first block also takes the
-// measurement faults of the last committed round.
+// Commit (t >= 0 and do_commit): rounds 0..commit-1 of the decoded window (row wc_row) ->
+// rounds t..t+commit-1 of the correction (row c_row); status = max over windows.  Gather
+// (t_next >= 0): blocks t_next..t_next+bn-1 of the syndrome (row s_row) -> the next window's
+// syndrome; when t >= 0 its first block also takes the measurement faults of round
+// commit-1 of the window at t (the last committed round).
 template <class T>
 __global__ void __launch_bounds__(256) window_step_kernel(
     long long shots, int F, int M, int N, int s_row, int c_row, const T* __restrict__ syn,
     const T* __restrict__ wc, int wc_row, const uint8_t* __restrict__ wst, int t, int commit,
-    T* __restrict__ out, uint8_t* __restrict__ status, int t_next, int bn, T* __restrict__ ws) {
+    int do_commit, T* __restrict__ out, uint8_t* __restrict__ status, int t_next, int bn,
+    T* __restrict__ ws) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < shots;
        k += warps) {
     const T* wrow = wc + k * wc_row;
-    if (t >= 0) {
+    if (t >= 0 && do_commit) {
       T* orow = out + k * c_row + (long long)t * F;
       for (int j = lane; j < commit * F; j += 32) orow[j] = wrow[j];
       if (lane == 0 && status) {
@@ -73,6 +81,18 @@ __global__ void __launch_bounds__(256) window_step_kernel(
         dst[j] = v;
       }
     }
+  }
+}
+
+// Streaming: detector block b of every stream ([shots][m]) into the history [shots][(d+1) m].
+__global__ void __launch_bounds__(256) block_store_kernel(long long shots, int m, int s_row, int b,
+                                                         const uint8_t* __restrict__ block,
+                                                         uint8_t* __restrict__ hist) {
+  const long long total = shots * m;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / m;
+    hist[k * s_row + (long long)b * m + (i - k * m)] = block[i];
   }
 }
 
@@ -138,7 +158,7 @@ int ensure(lsd_window* W, int64_t shots) {
 }
 
 int launch_step(lsd_window* W, int64_t shots, const uint8_t* syn, int wr, int t, int commit,
-                uint8_t* out, uint8_t* status, int t_next, int bn) {
+                bool do_commit, uint8_t* out, uint8_t* status, int t_next, int bn) {
   const int m = W->m, n = W->n, F = n + m, d = W->d;
   const bool words = m % 4 == 0 && n % 4 == 0 && ((uintptr_t)syn & 3) == 0 &&
                      ((uintptr_t)out & 3) == 0;
@@ -148,12 +168,12 @@ int launch_step(lsd_window* W, int64_t shots, const uint8_t* syn, int wr, int t,
     window_step_kernel<uint32_t><<<grid, 256, 0, W->st>>>(
         shots, F / 4, m / 4, n / 4, (d + 1) * m / 4, d * F / 4,
         reinterpret_cast<const uint32_t*>(syn), reinterpret_cast<const uint32_t*>(W->wc),
-        wr * F / 4, W->wst, t, commit, reinterpret_cast<uint32_t*>(out), status, t_next, bn,
-        reinterpret_cast<uint32_t*>(W->ws));
+        wr * F / 4, W->wst, t, commit, do_commit ? 1 : 0, reinterpret_cast<uint32_t*>(out),
+        status, t_next, bn, reinterpret_cast<uint32_t*>(W->ws));
   } else {
     window_step_kernel<uint8_t><<<grid, 256, 0, W->st>>>(
-        shots, F, m, n, (d + 1) * m, d * F, syn, W->wc, wr * F, W->wst, t, commit, out, status,
-        t_next, bn, W->ws);
+        shots, F, m, n, (d + 1) * m, d * F, syn, W->wc, wr * F, W->wst, t, commit,
+        do_commit ? 1 : 0, out, status, t_next, bn, W->ws);
   }
   W->launches++;
   cudaError_t e = cudaGetLastError();
@@ -222,7 +242,7 @@ int lsd_window_decode(lsd_window* W, int64_t shots, const uint8_t* syndromes,
   const int d = W->d, w = W->w, c = W->c;
   auto blocks_of = [&](int t) { return t == W->t_final ? d - t + 1 : w; };
   // the first window's syndromes
-  rc = launch_step(W, shots, syndromes, 0, -1, 0, corrections, status, 0, blocks_of(0));
+  rc = launch_step(W, shots, syndromes, 0, -1, 0, false, corrections, status, 0, blocks_of(0));
   if (rc) return rc;
   for (int t = 0;; t += c) {
     const bool final = t == W->t_final;
@@ -246,7 +266,7 @@ int lsd_window_decode(lsd_window* W, int64_t shots, const uint8_t* syndromes,
     const int wr = final ? d - t : w;
     const int commit = final ? d - t : c;
     const int t_next = final ? -1 : t + c;
-    rc = launch_step(W, shots, syndromes, wr, t, commit, corrections, status, t_next,
+    rc = launch_step(W, shots, syndromes, wr, t, commit, true, corrections, status, t_next,
                      final ? 0 : blocks_of(t_next));
     if (rc) return rc;
     if (final) break;
@@ -255,6 +275,74 @@ int lsd_window_decode(lsd_window* W, int64_t shots, const uint8_t* syndromes,
     cudaError_t e = cudaStreamSynchronize(W->st);
     if (e != cudaSuccess) return wfail(e);
   }
+  return LSD_OK;
+}
+
+int lsd_window_stream_reset(lsd_window* W, int64_t shots) {
+  if (!W || shots < 1 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
+  int rc = ensure(W, shots);
+  if (rc) return rc;
+  const size_t need = (size_t)shots * (W->d + 1) * W->m;
+  if (need > W->scap) {
+    cudaError_t e = cudaStreamSynchronize(W->st);
+    if (e != cudaSuccess) return wfail(e);
+    cudaFree(W->hist);
+    W->hist = nullptr;
+    W->scap = 0;
+    e = cudaMalloc(&W->hist, need);
+    if (e != cudaSuccess) return wfail(e);
+    W->scap = need;
+  }
+  W->sshots = shots;
+  W->received = 0;
+  W->t_next = 0;
+  W->prev_t = -1;
+  W->prev_wr = W->prev_commit = 0;
+  return LSD_OK;
+}
+
+int lsd_window_stream_push(lsd_window* W, const uint8_t* block, uint8_t* corrections,
+                           uint8_t* status, int32_t* first_round, int32_t* rounds_committed) {
+  if (!W || !block || !corrections || W->sshots < 1 || W->received > W->d)
+    return LSD_ERR_INVALID_ARG;
+  if (first_round) *first_round = 0;
+  if (rounds_committed) *rounds_committed = 0;
+  const int64_t shots = W->sshots;
+  const int d = W->d, m = W->m;
+  {
+    const long long total = (long long)shots * m;
+    const int grid = (int)std::max<long long>(
+        1, std::min<long long>((total + 255) / 256, (long long)W->sms * 8));
+    block_store_kernel<<<grid, 256, 0, W->st>>>(shots, m, (d + 1) * m, W->received, block,
+                                                 W->hist);
+    W->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(e);
+  }
+  const int last = W->received++;
+  const int t = W->t_next;
+  if (t > d) return LSD_OK;  // every round already committed
+  const bool final = t == W->t_final;
+  const int need = final ? d : t + W->w - 1;
+  if (last < need) return LSD_OK;
+  const int blocks = final ? d - t + 1 : W->w;
+  // gather the window (its first block takes the last committed round's measurement faults)
+  int rc = launch_step(W, shots, W->hist, W->prev_wr, W->prev_t, W->prev_commit, false,
+                       corrections, status, t, blocks);
+  if (rc) return rc;
+  rc = lsd_decode_batch(final ? W->fin : W->inner, shots, W->ws, W->wc, W->wst, nullptr,
+                        nullptr);
+  if (rc) return rc;
+  const int wr = final ? d - t : W->w;
+  const int commit = final ? d - t : W->c;
+  rc = launch_step(W, shots, W->hist, wr, t, commit, true, corrections, status, -1, 0);
+  if (rc) return rc;
+  W->prev_t = t;
+  W->prev_wr = wr;
+  W->prev_commit = commit;
+  W->t_next = final ? d + 1 : t + W->c;
+  if (first_round) *first_round = t;
+  if (rounds_committed) *rounds_committed = commit;
   return LSD_OK;
 }
 
@@ -269,10 +357,11 @@ int lsd_window_kernel_launches(const lsd_window* W, int64_t* count) {
 
 int lsd_window_destroy(lsd_window* W) {
   if (!W) return LSD_OK;
-  if (W->st || W->cap) cudaStreamSynchronize(W->st);
+  if (W->st || W->cap || W->scap) cudaStreamSynchronize(W->st);
   cudaFree(W->ws);
   cudaFree(W->wc);
   cudaFree(W->wst);
+  cudaFree(W->hist);
   lsd_destroy(W->inner);
   lsd_destroy(W->fin);
   delete W;

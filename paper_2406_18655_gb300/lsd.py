@@ -34,7 +34,8 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_prior_destroy", "lsd_sample", "lsd_server_create", "lsd_server_submit",
            "lsd_server_wait_all", "lsd_server_get_report", "lsd_server_run_poisson",
            "lsd_server_destroy", "lsd_autotune", "lsd_last_error", "lsd_window_create",
-           "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy")
+           "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy",
+           "lsd_window_stream_reset", "lsd_window_stream_push")
 
 
 class LsdError(RuntimeError):
@@ -119,6 +120,9 @@ def lib():
     L.lsd_window_decode.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
     L.lsd_window_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_window_destroy.argtypes = [P]
+    L.lsd_window_stream_reset.argtypes = [P, C.c_int64]
+    L.lsd_window_stream_push.argtypes = [P, P, P, P, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int32)]
     L.lsd_status_string.argtypes = [C.c_int]
     L.lsd_status_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -426,6 +430,26 @@ class WindowDecoder:
         if want_stats:
             return corrections, status, st.as_dict()
         return corrections, status
+
+    def stream_reset(self, shots: int):
+        """Start `shots` concurrent streams whose detector blocks arrive one push at a time."""
+        _check(lib().lsd_window_stream_reset(self._h, shots), "lsd_window_stream_reset")
+        self._stream_shots = shots
+
+    def stream_push(self, block, corrections, status=None):
+        """Next detector block [shots][m] of every stream; returns (first_round, count) of the
+        rounds committed into `corrections` [shots][d (n+m)] (count 0: no window completed)."""
+        import torch
+        shots = self._stream_shots
+        _dev_tensor(block, torch.uint8, (shots, self.m), "block")
+        _dev_tensor(corrections, torch.uint8, (shots, self.fault_len), "corrections")
+        if status is not None:
+            _dev_tensor(status, torch.uint8, (shots,), "status")
+        first, count = C.c_int32(), C.c_int32()
+        _check(lib().lsd_window_stream_push(self._h, _ptr(block), _ptr(corrections),
+                                            _ptr(status), C.byref(first), C.byref(count)),
+               "lsd_window_stream_push")
+        return first.value, count.value
 
     def kernel_launches(self) -> int:
         v = C.c_int64()

@@ -106,3 +106,30 @@ def test_repeated_calls_and_growing_batches(L):
     assert torch.equal(small, big[:700]) and torch.equal(small, again)
     o = OW.window_decode(h, _f32(p, n), _f32(p, m), d, s[:700])
     assert np.array_equal(small.cpu().numpy(), o["corrections"])
+
+
+@pytest.mark.parametrize("d,w,c", [(12, 3, 1), (6, 4, 2), (6, 3, 3), (3, 5, 1)])
+def test_streaming_pushes_match_batch_decode(L, d, w, c):
+    """Blocks pushed one at a time give the batch decoder's corrections; each push commits the
+    rounds of the window it completes, in order, and every round exactly once."""
+    h = code("bb72")
+    m, n = h.shape
+    p, shots = 0.02, 1200
+    s = _case(h, d, p, p, shots, seed=53 + d + w + c)
+    wd = L.WindowDecoder(h, np.full(n, p, np.float32), np.full(m, p, np.float32), d, w, c)
+    s_dev = torch.from_numpy(s).cuda()
+    ref, rst = wd.decode(s_dev)
+    corr = torch.full((shots, d * (n + m)), 7, dtype=torch.uint8, device="cuda")
+    st = torch.empty(shots, dtype=torch.uint8, device="cuda")
+    wd.stream_reset(shots)
+    blocks = s_dev.view(shots, d + 1, m)
+    done = 0
+    for b in range(d + 1):
+        first, count = wd.stream_push(blocks[:, b].contiguous(), corr, st)
+        if count:
+            assert first == done
+            done += count
+    assert done == d
+    assert torch.equal(corr, ref) and torch.equal(st, rst)
+    with pytest.raises(L.LsdError):
+        wd.stream_push(blocks[:, 0].contiguous(), corr, st)
