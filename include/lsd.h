@@ -386,6 +386,61 @@ int lsd_window_kernel_launches(const lsd_window* win, int64_t* count);
 int lsd_window_destroy(lsd_window* win);
 
 /* ------------------------------------------------------------------------------------
+ * One giant shot on the whole GPU (App. B's P-LSD, Alg. 2): a single syndrome of a large
+ * code (any m, n below 2^31 and fewer than 2^31 edges; the batch decoder stops at 65535)
+ * decoded by BP with one thread per check and per variable, then, if BP does not converge,
+ * by LSD with every cluster grown in parallel: clusters take their best candidate at once,
+ * merge through a lock-free union-find, and keep their own on-the-fly elimination in
+ * blocks of a device arena.  Corrections and status equal lsd_decode_batch's (LSD-0) on the
+ * same shot.  Limits: a cluster spans at most 8192 detectors (LSD_ERR_UNSUPPORTED beyond);
+ * the arena holds every block a call allocates (LSD_ERR_ADMISSION when it runs out).
+ * ------------------------------------------------------------------------------------ */
+typedef struct lsd_giant lsd_giant;
+
+typedef struct lsd_giant_info {
+  int32_t status;          /* LSD_SHOT_* */
+  int32_t bp_iterations;   /* BP iterations run (lsd_giant_decode) */
+  int32_t nu, kappa;       /* final clusters; largest cluster in columns (App. A) */
+  int32_t steps;           /* LSD-0 growth steps */
+  int32_t reserved;
+  int64_t arena_bytes_used;
+  float ms_bp, ms_lsd;     /* device time of the BP and LSD phases (CUDA events) */
+} lsd_giant_info;
+
+/*
+ * lsd_giant_create -- decoder of one large check matrix.
+ *   m, n, nnz, rows, cols, channel_probs, bp_iters   as lsd_create (host COO, no duplicates).
+ *   arena_bytes    device bytes of the cluster arena; 0 = 256 MiB.
+ *   opt            nullable; ms_scaling and stream are used, the other fields ignored.
+ * Device memory: about 20 (m + n) + 12 E bytes plus the arena.  Synchronizes.
+ */
+int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
+                     const int32_t* cols, const float* channel_probs, int32_t bp_iters,
+                     size_t arena_bytes, const lsd_options* opt);
+
+/*
+ * lsd_giant_decode -- BP (min-sum, flooding, early exit on H e_hat = s, Sec. 4.3), then
+ * P-LSD on the posteriors when BP does not converge.  Synchronous (one host round trip per
+ * growth step).
+ *   syndrome     device [m] bytes.   correction  device [n] bytes (written).
+ *   posteriors   device [n] float32, nullable: the BP posteriors.
+ *   info         host, nullable.
+ */
+int lsd_giant_decode(lsd_giant* dec, const uint8_t* syndrome, uint8_t* correction,
+                     float* posteriors, lsd_giant_info* info);
+
+/* lsd_giant_postprocess -- P-LSD alone on given soft information llr (device [n] float32),
+ * as lsd_postprocess_batch for one shot.  Synchronous. */
+int lsd_giant_postprocess(lsd_giant* dec, const float* llr, const uint8_t* syndrome,
+                          uint8_t* correction, lsd_giant_info* info);
+
+/* lsd_giant_kernel_launches -- kernels launched so far by the giant-shot decoder. */
+int lsd_giant_kernel_launches(const lsd_giant* dec, int64_t* count);
+
+/* lsd_giant_destroy -- free the decoder; NULL is a no-op.  Synchronizes. */
+int lsd_giant_destroy(lsd_giant* dec);
+
+/* ------------------------------------------------------------------------------------
  * Serving (no counterpart in the paper): continuous batching of single-shot requests over
  * several codes.  A scheduler thread keeps `slots_per_code` batches of each code in flight
  * (each slot a decoder with its own stream); a batch launches as soon as a slot is idle and

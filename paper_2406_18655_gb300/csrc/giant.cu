@@ -1,0 +1,1019 @@
+// One giant shot decoded by the whole GPU: BP (Sec. 4.3) with one thread per check and per
+// variable, then P-LSD (App. B, Alg. 2): every invalid cluster grows in parallel, clusters
+// merge through a lock-free union-find, and each cluster keeps its own on-the-fly
+// elimination (Sec. 4.2) in a block of a device arena.
+//
+// Results are those of the batch decoder (and of the oracle) on the same shot: growth is
+// synchronous, ties are broken by the (LLR, index) key, and a cluster's pivot columns do not
+// depend on how its elimination rows are numbered.
+//
+// Cluster state.  Clusters are named by seed ordinal (flipped detectors in the order the
+// seeding kernel meets them; the labels do not affect any result).  A cluster root r owns a
+// block of cap[r] slots (a multiple of 32; W = cap/32 words per row):
+//   R[cap][W]   reduced pivot rows over the cluster's slots (row p exists iff pcol[p] >= 0)
+//   T[cap][W]   the combination of pivot columns giving each row
+//   pcol[cap]   pivot column of a slot (-1 none), det[cap] detector of a slot
+//   sred[W]     the cluster's syndrome reduced by the pivots (zero iff valid, Def. 4.2)
+//   xsol[W]     the pivot columns whose sum gives the cleared part of the syndrome
+// A detector's slot in its cluster is lslot[d].  When clusters merge, the absorbed blocks
+// are copied into the root's (new) block at an offset, rows shifted by that many bits: the
+// row supports are disjoint, so the merged rows stay reduced.
+//
+// Per growth step (one host round trip):
+//   find      every candidate fault offers its key to the growing clusters next to it
+//   union     each invalid cluster takes its best candidate; collisions unite clusters
+//   flatten   union-find paths compressed to one hop
+//   plan      slot offsets of absorbed clusters and of newly claimed detectors, per root
+//   relocate  a root that merged or outgrew its block moves to a new, larger block
+//   absorb    absorbed blocks copied (shifted) into their root's block
+//   claim     new detectors get slots; faults next to them become candidates
+//   add       each changed root adds its new columns in key order (on-the-fly elimination)
+//   collect   the invalid roots of the next step
+#include <algorithm>
+#include <climits>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "lsd_internal.cuh"
+
+using namespace lsdgb;
+
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr unsigned long long kNoKey = ~0ull;
+constexpr int kWcMax = 8;                     // reduction words per lane
+constexpr int kMaxSlots = 32 * 32 * kWcMax;   // 8192 detectors per cluster
+constexpr int kUfLimit = 1 << 20;             // bound on union-find retries and path length
+// a minimum over an empty set (a check of degree 1): 2^100, as in the batch kernels
+constexpr float kEmptyMinF = 1267650600228229401496703205376.0f;
+
+struct GCtr {
+  // whole call
+  int ns, nfront, unsolvable, overflow, uf_fail, too_big;
+  int bp_stop, bp_unsat, bp_iters, bp_conv;
+  int nu, kappa;
+  int ninv[2];
+  // reset every step
+  int nmerged, nchg, nnew, nclaim, bucket_top, pad;
+  unsigned long long arena_top;  // words
+};
+
+struct GD {
+  int m, n;
+  const int *chk_ptr, *chk_var, *var_ptr, *var_edge, *var_chk;
+  const float* prior;
+  // BP
+  float *q, *r, *lam;
+  uint8_t* hard;
+  // per detector / per fault
+  int *dlab, *lslot, *fst, *front;
+  // per seed ordinal (at most m)
+  int *parent, *inv0, *inv1, *mlist, *chg, *cap, *nsl, *ncol, *valid, *grow, *mark, *extra,
+      *newslots, *aoff, *newcnt, *boff;
+  unsigned long long *best, *blk;
+  // per step lists (at most m entries each)
+  int *nc_g, *nc_r, *nc_rank, *bucket, *cl_d, *cl_r, *cl_rel;
+  unsigned long long* nc_key;
+  unsigned* arena;
+  unsigned long long arena_words;
+  GCtr* ctr;
+};
+
+__host__ __device__ inline size_t blk_words(int C) {
+  const int W = C >> 5;
+  return 2 * (size_t)C * W + 2 * (size_t)C + 2 * (size_t)W;
+}
+
+struct Blk {
+  unsigned* b;
+  int C, W;
+  __device__ unsigned* R(int p) const { return b + (size_t)p * W; }
+  __device__ unsigned* T(int p) const { return b + (size_t)C * W + (size_t)p * W; }
+  __device__ int* pcol() const { return reinterpret_cast<int*>(b + 2 * (size_t)C * W); }
+  __device__ int* det() const { return pcol() + C; }
+  __device__ unsigned* sred() const { return reinterpret_cast<unsigned*>(det() + C); }
+  __device__ unsigned* xsol() const { return sred() + W; }
+};
+
+__device__ __forceinline__ Blk blk_at(const GD& g, unsigned long long off, int C) {
+  Blk B;
+  B.b = g.arena + off;
+  B.C = C;
+  B.W = C >> 5;
+  return B;
+}
+
+__device__ __forceinline__ Blk blk_of(const GD& g, int r) {
+  return blk_at(g, g.blk[r], g.cap[r]);
+}
+
+__device__ long long arena_alloc(const GD& g, size_t words) {
+  const unsigned long long off = atomicAdd(&g.ctr->arena_top, (unsigned long long)words);
+  if (off + words > g.arena_words) {
+    atomicOr(&g.ctr->overflow, 1);
+    return -1;
+  }
+  return (long long)off;
+}
+
+__device__ __forceinline__ unsigned long long llr_key(float x, int j) {
+  x = __fadd_rn(x, 0.0f);  // -0 -> +0
+  unsigned u = __float_as_uint(x);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned)j;
+}
+
+__device__ __forceinline__ long long gtid() {
+  return (long long)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+__device__ __forceinline__ long long gwarp() { return gtid() >> 5; }
+__device__ __forceinline__ long long gwarps() { return gstride() >> 5; }
+
+// ---------------------------------------------------------------------------------------
+// BP over one shot (flooding min-sum, every operation rounded to float in the order of the
+// batch kernels and of the oracle's FP32 mirror)
+// ---------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) gbp_init(GD g) {
+  const long long E = g.chk_ptr[g.m];
+  for (long long k = gtid(); k < E; k += gstride()) g.q[k] = g.prior[g.chk_var[k]];
+  for (long long j = gtid(); j < g.n; j += gstride()) {
+    g.lam[j] = g.prior[j];
+    g.hard[j] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict__ s,
+                                                  float alpha) {
+  if (*(volatile int*)&g.ctr->bp_stop) return;
+  for (long long i = gtid(); i < g.m; i += gstride()) {
+    const int k0 = g.chk_ptr[i], k1 = g.chk_ptr[i + 1];
+    unsigned par = s[i] ? 1u : 0u;
+    float m1 = kEmptyMinF, m2 = kEmptyMinF;
+    int am = -1;
+    for (int k = k0; k < k1; ++k) {
+      const float v = g.q[k];
+      par ^= __float_as_uint(v) >> 31;
+      const float a = fabsf(v);
+      if (a < m1) {
+        m2 = m1;
+        m1 = a;
+        am = k;
+      } else if (a < m2) {
+        m2 = a;
+      }
+    }
+    for (int k = k0; k < k1; ++k) {
+      const float mag = __fmul_rn(alpha, k == am ? m2 : m1);
+      const unsigned neg = par ^ (__float_as_uint(g.q[k]) >> 31);
+      g.r[k] = neg ? -mag : mag;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) gbp_var(GD g) {
+  if (*(volatile int*)&g.ctr->bp_stop) return;
+  for (long long j = gtid(); j < g.n; j += gstride()) {
+    const int a0 = g.var_ptr[j], a1 = g.var_ptr[j + 1];
+    float L = g.prior[j];
+    for (int a = a0; a < a1; ++a) L = __fadd_rn(L, g.r[g.var_edge[a]]);
+    g.lam[j] = L;
+    for (int a = a0; a < a1; ++a) {
+      const int e = g.var_edge[a];
+      g.q[e] = __fsub_rn(L, g.r[e]);
+    }
+    g.hard[j] = L < 0.0f ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__ s) {
+  if (*(volatile int*)&g.ctr->bp_stop) return;
+  bool bad = false;
+  for (long long i = gtid(); i < g.m; i += gstride()) {
+    unsigned par = s[i] ? 1u : 0u;
+    for (int k = g.chk_ptr[i]; k < g.chk_ptr[i + 1]; ++k) par ^= g.hard[g.chk_var[k]];
+    bad |= (par & 1u) != 0;
+  }
+  if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(&g.ctr->bp_unsat, 1);
+}
+
+__global__ void gbp_decide(GD g) {
+  if (g.ctr->bp_stop) return;
+  g.ctr->bp_iters += 1;
+  const int ok = g.ctr->bp_unsat == 0;
+  g.ctr->bp_conv = ok;
+  g.ctr->bp_unsat = 0;
+  if (ok) g.ctr->bp_stop = 1;
+}
+
+__global__ void __launch_bounds__(256) gcopy_hard(GD g, uint8_t* __restrict__ corr) {
+  for (long long j = gtid(); j < g.n; j += gstride()) corr[j] = g.hard[j];
+}
+
+// ---------------------------------------------------------------------------------------
+// P-LSD
+// ---------------------------------------------------------------------------------------
+
+__device__ int gfind(const GD& g, int x) {
+  const volatile int* par = g.parent;
+  for (int it = 0; it < kUfLimit; ++it) {
+    const int p = par[x];
+    if (p == x) return x;
+    x = p;
+  }
+  atomicOr(&g.ctr->uf_fail, 1);
+  return x;
+}
+
+// Links the larger root under the smaller; the absorbed root is listed once in mlist.
+__device__ void gunite(const GD& g, int a, int b) {
+  for (int it = 0; it < kUfLimit; ++it) {
+    a = gfind(g, a);
+    b = gfind(g, b);
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(g.parent + a, a, b) == a) {
+      const int k = atomicAdd(&g.ctr->nmerged, 1);
+      g.mlist[k] = a;
+      return;
+    }
+  }
+  atomicOr(&g.ctr->uf_fail, 1);
+}
+
+__device__ __forceinline__ void add_candidates(const GD& g, int d) {
+  for (int e = g.chk_ptr[d]; e < g.chk_ptr[d + 1]; ++e) {
+    const int f = g.chk_var[e];
+    if (atomicCAS(&g.fst[f], -2, -1) == -2) g.front[atomicAdd(&g.ctr->nfront, 1)] = f;
+  }
+}
+
+__global__ void __launch_bounds__(256) glsd_reset(GD g) {
+  for (long long d = gtid(); d < g.m; d += gstride()) g.dlab[d] = -1;
+  for (long long j = gtid(); j < g.n; j += gstride()) g.fst[j] = -2;
+}
+
+// One cluster per flipped detector (Alg. 2's initialization), each in a 32-slot block.
+__global__ void __launch_bounds__(256) glsd_seed(GD g, const uint8_t* __restrict__ s) {
+  constexpr int C = 32;
+  const size_t words = blk_words(C);
+  for (long long d = gtid(); d < g.m; d += gstride()) {
+    if (!s[d]) continue;
+    const int ord = atomicAdd(&g.ctr->ns, 1);
+    g.dlab[d] = ord;
+    g.lslot[d] = 0;
+    g.parent[ord] = ord;
+    g.inv0[ord] = ord;
+    const long long off = arena_alloc(g, words);
+    if (off < 0) continue;
+    g.blk[ord] = (unsigned long long)off;
+    g.cap[ord] = C;
+    g.nsl[ord] = 1;
+    g.ncol[ord] = 0;
+    g.valid[ord] = 0;
+    g.grow[ord] = 1;
+    g.best[ord] = kNoKey;
+    g.mark[ord] = 0;
+    g.extra[ord] = 0;
+    g.newslots[ord] = 0;
+    g.newcnt[ord] = 0;
+    const Blk B = blk_at(g, (unsigned long long)off, C);
+    for (size_t w = 0; w < words; ++w) B.b[w] = 0u;
+    for (int p = 0; p < C; ++p) B.pcol()[p] = -1;
+    B.det()[0] = (int)d;
+    B.sred()[0] = 1u;
+    add_candidates(g, (int)d);
+  }
+}
+
+__global__ void glsd_seed_count(GD g) { g.ctr->ninv[0] = g.ctr->ns; }
+
+// find_candidate: every live candidate offers its key to the growing roots next to it.
+__global__ void __launch_bounds__(256) glsd_find(GD g, const float* __restrict__ llr) {
+  const int nf = g.ctr->nfront;
+  for (long long i = gtid(); i < nf; i += gstride()) {
+    const int f = g.front[i];
+    if (g.fst[f] != -1) continue;
+    const unsigned long long key = llr_key(llr[f], f);
+    for (int q = g.var_ptr[f]; q < g.var_ptr[f + 1]; ++q) {
+      const int c = g.dlab[g.var_chk[q]];
+      if (c < 0) continue;
+      const int R = g.parent[c];
+      if (g.grow[R]) atomicMin(&g.best[R], key);
+    }
+  }
+}
+
+// parallel_union: each invalid cluster takes its pick; collisions unite.
+__global__ void __launch_bounds__(256) glsd_union(GD g, int par) {
+  const int cnt = g.ctr->ninv[par];
+  const int* inv = par ? g.inv1 : g.inv0;
+  for (long long t = gtid(); t < cnt; t += gstride()) {
+    const int r = inv[t];
+    const unsigned long long key = g.best[r];
+    if (key == kNoKey) {
+      atomicOr(&g.ctr->unsolvable, 1);
+      continue;
+    }
+    const int f = (int)(key & 0xffffffffu);
+    const int old = atomicCAS(&g.fst[f], -1, r);
+    if (old == -1) {
+      const int k = atomicAdd(&g.ctr->nnew, 1);
+      g.nc_g[k] = f;
+      g.nc_r[k] = r;
+      g.nc_key[k] = key;
+    } else {
+      gunite(g, r, old);
+    }
+    for (int q = g.var_ptr[f]; q < g.var_ptr[f + 1]; ++q) {
+      const int d = g.var_chk[q];
+      const int o = atomicCAS(&g.dlab[d], -1, r);
+      if (o == -1) {
+        const int k = atomicAdd(&g.ctr->nclaim, 1);
+        g.cl_d[k] = d;
+        g.cl_r[k] = r;
+      } else if (o != r) {
+        gunite(g, r, o);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) glsd_flatten(GD g) {
+  const int ns = g.ctr->ns;
+  for (long long x = gtid(); x < ns; x += gstride()) g.parent[x] = gfind(g, (int)x);
+}
+
+__device__ __forceinline__ void mark_changed(const GD& g, int R) {
+  if (atomicCAS(&g.mark[R], 0, 1) == 0) g.chg[atomicAdd(&g.ctr->nchg, 1)] = R;
+}
+
+// Offsets inside each root's grown block: absorbed clusters, then new detectors; ranks of
+// the new columns.
+__global__ void __launch_bounds__(256) glsd_plan(GD g) {
+  const int nm = g.ctr->nmerged, nc = g.ctr->nclaim, nn = g.ctr->nnew;
+  for (long long t = gtid(); t < (long long)nm + nc + nn; t += gstride()) {
+    if (t < nm) {
+      const int A = g.mlist[t];
+      const int R = g.parent[A];
+      g.aoff[A] = atomicAdd(&g.extra[R], g.nsl[A]);
+      mark_changed(g, R);
+    } else if (t < nm + nc) {
+      const int k = (int)(t - nm);
+      const int R = g.parent[g.cl_r[k]];
+      g.cl_rel[k] = atomicAdd(&g.newslots[R], 1);
+      mark_changed(g, R);
+    } else {
+      const int k = (int)(t - nm - nc);
+      const int R = g.parent[g.nc_r[k]];
+      g.nc_rank[k] = atomicAdd(&g.newcnt[R], 1);
+      mark_changed(g, R);
+    }
+  }
+}
+
+// A root that merged or outgrew its block moves to a new zeroed block (its own slots copied
+// at the same positions); every changed root reserves room for its new columns' list.
+__global__ void __launch_bounds__(256) glsd_relocate(GD g) {
+  const int lane = threadIdx.x & 31;
+  const int nchg = g.ctr->nchg;
+  for (long long t = gwarp(); t < nchg; t += gwarps()) {
+    const int R = g.chg[t];
+    const int base = g.nsl[R];
+    const int need = base + g.extra[R] + g.newslots[R];
+    if (lane == 0) g.boff[R] = atomicAdd(&g.ctr->bucket_top, g.newcnt[R]);
+    if (need > kMaxSlots) {
+      if (lane == 0) atomicOr(&g.ctr->too_big, 1);
+      continue;
+    }
+    const Blk O = blk_of(g, R);
+    if (g.extra[R] == 0 && need <= O.C) {
+      for (int p = base + lane; p < need; p += 32) O.pcol()[p] = -1;
+      continue;
+    }
+    const int want = need + need / 2;
+    const int C = max(O.C, min(kMaxSlots, max(32, (want + 31) & ~31)));  // never shrinks
+    const size_t words = blk_words(C);
+    long long off = 0;
+    if (lane == 0) off = arena_alloc(g, words);
+    off = __shfl_sync(kFullMask, off, 0);
+    if (off < 0) continue;
+    const Blk N = blk_at(g, (unsigned long long)off, C);
+    for (size_t w = lane; w < words; w += 32) N.b[w] = 0u;
+    __syncwarp();
+    for (int p = lane; p < C; p += 32) N.pcol()[p] = p < base ? O.pcol()[p] : -1;
+    for (int p = lane; p < base; p += 32) N.det()[p] = O.det()[p];
+    for (int w = lane; w < O.W; w += 32) {
+      N.sred()[w] = O.sred()[w];
+      N.xsol()[w] = O.xsol()[w];
+    }
+    for (int p = 0; p < base; ++p) {
+      if (O.pcol()[p] < 0) continue;
+      for (int w = lane; w < O.W; w += 32) {
+        N.R(p)[w] = O.R(p)[w];
+        N.T(p)[w] = O.T(p)[w];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      g.blk[R] = (unsigned long long)off;
+      g.cap[R] = C;
+    }
+  }
+}
+
+// Word w of a bit vector `src` (sw words) shifted up by `sh` bits.
+__device__ __forceinline__ unsigned shifted_word(const unsigned* src, int sw, int sh, int w) {
+  const int q = sh >> 5, b = sh & 31;
+  const int i = w - q;
+  unsigned v = (i >= 0 && i < sw) ? src[i] << b : 0u;
+  if (b && i - 1 >= 0 && i - 1 < sw) v |= src[i - 1] >> (32 - b);
+  return v;
+}
+
+// Absorbed clusters copied into their root's block at their offset (rows shifted).
+__global__ void __launch_bounds__(256) glsd_absorb(GD g) {
+  const int lane = threadIdx.x & 31;
+  const int nm = g.ctr->nmerged;
+  for (long long t = gwarp(); t < nm; t += gwarps()) {
+    const int A = g.mlist[t];
+    const int R = g.parent[A];
+    if (g.ctr->too_big || g.ctr->overflow) continue;
+    const Blk S = blk_of(g, A), D = blk_of(g, R);
+    const int o = g.nsl[R] + g.aoff[A];
+    const int nA = g.nsl[A];
+    for (int p = lane; p < nA; p += 32) {
+      D.pcol()[o + p] = S.pcol()[p];
+      const int d = S.det()[p];
+      D.det()[o + p] = d;
+      g.lslot[d] = o + p;
+    }
+    const int w0 = o >> 5, w1 = min(D.W, ((o + nA + 31) >> 5) + 1);
+    for (int w = w0 + lane; w < w1; w += 32) {
+      const unsigned a = shifted_word(S.sred(), S.W, o, w);
+      const unsigned b = shifted_word(S.xsol(), S.W, o, w);
+      if (a) atomicOr(&D.sred()[w], a);
+      if (b) atomicOr(&D.xsol()[w], b);
+    }
+    for (int p = 0; p < nA; ++p) {
+      if (S.pcol()[p] < 0) continue;
+      for (int w = w0 + lane; w < w1; w += 32) {
+        D.R(o + p)[w] = shifted_word(S.R(p), S.W, o, w);
+        D.T(o + p)[w] = shifted_word(S.T(p), S.W, o, w);
+      }
+    }
+    if (lane == 0) atomicAdd(&g.ncol[R], g.ncol[A]);
+  }
+}
+
+// New detectors take their slots; faults next to them become candidates (Def. 4.3); the new
+// columns are placed in their root's list.
+__global__ void __launch_bounds__(256) glsd_claim(GD g) {
+  const int nc = g.ctr->nclaim, nn = g.ctr->nnew;
+  if (g.ctr->too_big || g.ctr->overflow) return;
+  for (long long t = gtid(); t < (long long)nc + nn; t += gstride()) {
+    if (t < nc) {
+      const int k = (int)t;
+      const int d = g.cl_d[k];
+      const int R = g.parent[g.cl_r[k]];
+      const int slot = g.nsl[R] + g.extra[R] + g.cl_rel[k];
+      const Blk D = blk_of(g, R);
+      D.det()[slot] = d;
+      g.lslot[d] = slot;
+      add_candidates(g, d);
+    } else {
+      const int k = (int)(t - nc);
+      const int R = g.parent[g.nc_r[k]];
+      g.bucket[g.boff[R] + g.nc_rank[k]] = k;
+    }
+  }
+}
+
+// Adds fault f to the elimination of block D (nslots slots in use), as the batch kernels do.
+__device__ void gadd_column(const GD& g, const Blk& D, int nslots, int f, int lane) {
+  const int wc = (nslots + 31) >> 5;
+  unsigned bw[kWcMax], tw[kWcMax];
+#pragma unroll
+  for (int c = 0; c < kWcMax; ++c) bw[c] = tw[c] = 0u;
+  for (int q = g.var_ptr[f]; q < g.var_ptr[f + 1]; ++q) {
+    const int sl = g.lslot[g.var_chk[q]];
+    const bool piv = D.pcol()[sl] >= 0;
+#pragma unroll
+    for (int c = 0; c < kWcMax; ++c) {
+      const int w = c * 32 + lane;
+      if (w < wc) {
+        if ((sl >> 5) == w) bw[c] ^= 1u << (sl & 31);
+        if (piv) {
+          bw[c] ^= D.R(sl)[w];
+          tw[c] ^= D.T(sl)[w];
+        }
+      }
+    }
+  }
+  int p = -1;
+#pragma unroll
+  for (int c = 0; c < kWcMax; ++c) {
+    const unsigned nz = __ballot_sync(kFullMask, bw[c] != 0u);
+    if (p < 0 && nz) {
+      const int wl = __ffs(nz) - 1;
+      const unsigned word = __shfl_sync(kFullMask, bw[c], wl);
+      p = (c * 32 + wl) * 32 + __ffs(word) - 1;
+    }
+  }
+  if (p < 0) return;  // dependent column: the cluster's span does not change
+  const int pw = p >> 5;
+  const unsigned pb = 1u << (p & 31);
+#pragma unroll
+  for (int c = 0; c < kWcMax; ++c)
+    if (c * 32 + lane == pw) tw[c] ^= pb;
+  const bool sflag = (D.sred()[pw] & pb) != 0u;
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < kWcMax; ++c) {
+    const int w = c * 32 + lane;
+    if (w < wc) {
+      D.R(p)[w] = bw[c];
+      D.T(p)[w] = tw[c];
+    }
+  }
+  if (lane == 0) D.pcol()[p] = f;
+  __syncwarp();
+  for (int d0 = 0; d0 < nslots; d0 += 32) {
+    const int d = d0 + lane;
+    const bool hit = d < nslots && d != p && D.pcol()[d] >= 0 && (D.R(d)[pw] & pb) != 0u;
+    unsigned bal = __ballot_sync(kFullMask, hit);
+    while (bal) {
+      const int dd = d0 + __ffs(bal) - 1;
+      bal &= bal - 1;
+#pragma unroll
+      for (int c = 0; c < kWcMax; ++c) {
+        const int w = c * 32 + lane;
+        if (w < wc) {
+          D.R(dd)[w] ^= bw[c];
+          D.T(dd)[w] ^= tw[c];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (sflag) {
+#pragma unroll
+    for (int c = 0; c < kWcMax; ++c) {
+      const int w = c * 32 + lane;
+      if (w < wc) {
+        D.sred()[w] ^= bw[c];
+        D.xsol()[w] ^= tw[c];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// on_the_fly_elimination of every changed root: its new columns in key order, then its
+// validity.
+__global__ void __launch_bounds__(256) glsd_add(GD g) {
+  const int lane = threadIdx.x & 31;
+  const int nchg = g.ctr->nchg;
+  if (g.ctr->too_big || g.ctr->overflow) return;
+  for (long long t = gwarp(); t < nchg; t += gwarps()) {
+    const int R = g.chg[t];
+    const int nslots = g.nsl[R] + g.extra[R] + g.newslots[R];
+    const Blk D = blk_of(g, R);
+    const int cnt = g.newcnt[R];
+    const int* bk = g.bucket + g.boff[R];
+    unsigned long long last = 0;
+    for (int it = 0; it < cnt; ++it) {
+      unsigned long long best = kNoKey;
+      int bi = -1;
+      for (int u = lane; u < cnt; u += 32) {
+        const int k = bk[u];
+        const unsigned long long key = g.nc_key[k];
+        if ((it == 0 || key > last) && key < best) {
+          best = key;
+          bi = k;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kFullMask, best, off);
+        const int oi = __shfl_xor_sync(kFullMask, bi, off);
+        if (ob < best) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      last = best;
+      gadd_column(g, D, nslots, g.nc_g[bi], lane);
+    }
+    bool any = false;
+    for (int w = lane; w < ((nslots + 31) >> 5); w += 32) any |= D.sred()[w] != 0u;
+    any = __any_sync(kFullMask, any);
+    if (lane == 0) {
+      g.valid[R] = any ? 0 : 1;
+      g.ncol[R] += cnt;
+      g.nsl[R] = nslots;
+      g.extra[R] = 0;
+      g.newslots[R] = 0;
+      g.newcnt[R] = 0;
+      g.mark[R] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) glsd_collect(GD g, int par_next) {
+  const int ns = g.ctr->ns;
+  int* inv = par_next ? g.inv1 : g.inv0;
+  for (long long x = gtid(); x < ns; x += gstride()) {
+    const bool invalid = g.parent[x] == x && !g.valid[x];
+    g.grow[x] = invalid ? 1 : 0;
+    if (invalid) {
+      g.best[x] = kNoKey;
+      inv[atomicAdd(&g.ctr->ninv[par_next], 1)] = (int)x;
+    }
+  }
+}
+
+// Local solutions (Eq. 2): the pivot columns in each root's xsol; nu and kappa.
+__global__ void __launch_bounds__(256) glsd_solve(GD g, uint8_t* __restrict__ corr, int write) {
+  const int lane = threadIdx.x & 31;
+  const int ns = g.ctr->ns;
+  for (long long x = gwarp(); x < ns; x += gwarps()) {
+    if (g.parent[x] != x) continue;
+    if (lane == 0) {
+      atomicAdd(&g.ctr->nu, 1);
+      atomicMax(&g.ctr->kappa, g.ncol[x]);
+    }
+    if (!write) continue;
+    const Blk D = blk_of(g, (int)x);
+    const int nx = g.nsl[x];
+    for (int p = lane; p < nx; p += 32) {
+      const int c = D.pcol()[p];
+      if (c >= 0 && ((D.xsol()[p >> 5] >> (p & 31)) & 1u)) corr[c] = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) gzero(uint8_t* __restrict__ p, long long nbytes) {
+  for (long long i = gtid(); i < nbytes; i += gstride()) p[i] = 0;
+}
+
+}  // namespace
+
+struct lsd_giant {
+  int m = 0, n = 0;
+  long long E = 0;
+  int bp_iters = 0;
+  float alpha = 0.625f;
+  cudaStream_t st = nullptr;
+  int sms = 0;
+  GD g{};
+  GCtr* h_ctr = nullptr;  // pinned
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  int64_t launches = 0;
+};
+
+namespace {
+
+int gfail(cudaError_t e) {
+  record_cuda_error(e);
+  return e == cudaErrorMemoryAllocation ? LSD_ERR_OOM : LSD_ERR_CUDA;
+}
+
+template <class T>
+int galloc(lsd_giant* G, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return gfail(e);
+  }
+  G->allocs.push_back(*p);
+  G->bytes += bytes;
+  return LSD_OK;
+}
+
+int grid_threads(const lsd_giant* G) { return G->sms * 8; }
+
+int read_ctr(lsd_giant* G) {
+  cudaError_t e = cudaMemcpyAsync(G->h_ctr, G->g.ctr, sizeof(GCtr), cudaMemcpyDeviceToHost,
+                                  G->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->st);
+  return e == cudaSuccess ? LSD_OK : gfail(e);
+}
+
+int check_launch(lsd_giant* G) {
+  G->launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LSD_OK : gfail(e);
+}
+
+// P-LSD of the shot; writes corr (zero unless solved) and the info fields.
+int run_plsd(lsd_giant* G, const float* llr, const uint8_t* s, uint8_t* corr,
+             lsd_giant_info* info) {
+  const GD& g = G->g;
+  const int grid = grid_threads(G);
+  int rc;
+  // counters of the whole call (BP fields are kept)
+  {
+    cudaError_t e = cudaMemsetAsync(g.ctr, 0, offsetof(GCtr, bp_stop), G->st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(&g.ctr->nu, 0, sizeof(GCtr) - offsetof(GCtr, nu), G->st);
+    if (e != cudaSuccess) return gfail(e);
+  }
+  glsd_reset<<<grid, 256, 0, G->st>>>(g);
+  if ((rc = check_launch(G))) return rc;
+  glsd_seed<<<grid, 256, 0, G->st>>>(g, s);
+  if ((rc = check_launch(G))) return rc;
+  glsd_seed_count<<<1, 1, 0, G->st>>>(g);
+  if ((rc = check_launch(G))) return rc;
+  gzero<<<grid, 256, 0, G->st>>>(corr, G->n);
+  if ((rc = check_launch(G))) return rc;
+  int status = LSD_SHOT_OK_LSD, steps = 0, par = 0;
+  for (;;) {
+    if ((rc = read_ctr(G))) return rc;
+    const GCtr& h = *G->h_ctr;
+    if (h.overflow) return LSD_ERR_ADMISSION;
+    if (h.uf_fail) return LSD_ERR_TIMEOUT;
+    if (h.too_big) return LSD_ERR_UNSUPPORTED;
+    if (h.unsolvable) {
+      status = LSD_SHOT_UNSOLVABLE;
+      break;
+    }
+    if (h.ninv[par] == 0) break;
+    if (steps > G->n) {
+      status = LSD_SHOT_UNSOLVABLE;
+      break;
+    }
+    const int nxt = par ^ 1;
+    cudaError_t e = cudaMemsetAsync(&g.ctr->nmerged, 0, 6 * sizeof(int), G->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&g.ctr->ninv[nxt], 0, sizeof(int), G->st);
+    if (e != cudaSuccess) return gfail(e);
+    glsd_find<<<grid, 256, 0, G->st>>>(g, llr);
+    if ((rc = check_launch(G))) return rc;
+    glsd_union<<<grid, 256, 0, G->st>>>(g, par);
+    if ((rc = check_launch(G))) return rc;
+    glsd_flatten<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_plan<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_relocate<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_absorb<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_claim<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_add<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_collect<<<grid, 256, 0, G->st>>>(g, nxt);
+    if ((rc = check_launch(G))) return rc;
+    // a step in which some invalid cluster found no candidate does not count (Alg. 1)
+    if ((rc = read_ctr(G))) return rc;
+    if (G->h_ctr->unsolvable) {
+      status = LSD_SHOT_UNSOLVABLE;
+      break;
+    }
+    ++steps;
+    par = nxt;
+  }
+  glsd_solve<<<grid, 256, 0, G->st>>>(g, corr, status == LSD_SHOT_OK_LSD ? 1 : 0);
+  if ((rc = check_launch(G))) return rc;
+  if ((rc = read_ctr(G))) return rc;
+  if (G->h_ctr->overflow) return LSD_ERR_ADMISSION;
+  if (info) {
+    info->status = status;
+    info->nu = G->h_ctr->nu;
+    info->kappa = G->h_ctr->kappa;
+    info->steps = steps;
+    info->arena_bytes_used = (int64_t)G->h_ctr->arena_top * 4;
+  }
+  return LSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
+                     const int32_t* cols, const float* channel_probs, int32_t bp_iters,
+                     size_t arena_bytes, const lsd_options* opt) {
+  if (!out) return LSD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (m < 1 || n < 1 || nnz < 1 || nnz >= INT32_MAX || !rows || !cols || !channel_probs ||
+      bp_iters < 0)
+    return LSD_ERR_INVALID_ARG;
+  lsd_options o{};
+  if (opt) o = *opt;
+  if (o.ms_scaling < 0.f) return LSD_ERR_INVALID_ARG;
+  for (int j = 0; j < n; ++j)
+    if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
+  std::vector<std::pair<int, int>> e((size_t)nnz);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (rows[k] < 0 || rows[k] >= m || cols[k] < 0 || cols[k] >= n) return LSD_ERR_INVALID_ARG;
+    e[(size_t)k] = {rows[k], cols[k]};
+  }
+  std::sort(e.begin(), e.end());
+  for (size_t k = 1; k < e.size(); ++k)
+    if (e[k] == e[k - 1]) return LSD_ERR_INVALID_ARG;
+  const int E = (int)e.size();
+  std::vector<int> chk_ptr(m + 1, 0), var_ptr(n + 1, 0), chk_var(E), var_edge(E), var_chk(E);
+  for (auto& p : e) {
+    chk_ptr[p.first + 1]++;
+    var_ptr[p.second + 1]++;
+  }
+  for (int i = 0; i < m; ++i) chk_ptr[i + 1] += chk_ptr[i];
+  for (int j = 0; j < n; ++j) var_ptr[j + 1] += var_ptr[j];
+  std::vector<int> fill(var_ptr.begin(), var_ptr.end() - 1);
+  for (int k = 0; k < E; ++k) {  // ascending (row, column): each column's list ascends in row
+    chk_var[k] = e[k].second;
+    const int slot = fill[e[k].second]++;
+    var_edge[slot] = k;
+    var_chk[slot] = e[k].first;
+  }
+
+  lsd_giant* G = new (std::nothrow) lsd_giant();
+  if (!G) return LSD_ERR_OOM;
+  G->m = m;
+  G->n = n;
+  G->E = E;
+  G->bp_iters = bp_iters;
+  G->alpha = o.ms_scaling > 0.f ? o.ms_scaling : 0.625f;
+  G->st = static_cast<cudaStream_t>(o.stream);
+  GD& g = G->g;
+  g.m = m;
+  g.n = n;
+  const size_t words = arena_bytes ? arena_bytes / 4 : ((size_t)64 << 20);  // 256 MiB
+  int rc = LSD_OK;
+  int *d_chk_ptr = nullptr, *d_chk_var = nullptr, *d_var_ptr = nullptr, *d_var_edge = nullptr,
+      *d_var_chk = nullptr;
+  float *d_prior = nullptr, *d_probs = nullptr;
+  long long* d_wfix = nullptr;
+  auto A = [&](auto** p, size_t count) {
+    if (rc == LSD_OK) rc = galloc(G, p, count);
+  };
+  A(&d_chk_ptr, m + 1);
+  A(&d_chk_var, E);
+  A(&d_var_ptr, n + 1);
+  A(&d_var_edge, E);
+  A(&d_var_chk, E);
+  A(&d_prior, n);
+  A(&d_probs, n);
+  A(&d_wfix, n);
+  A(&g.q, E);
+  A(&g.r, E);
+  A(&g.lam, n);
+  A(&g.hard, n);
+  A(&g.dlab, m);
+  A(&g.lslot, m);
+  A(&g.fst, n);
+  A(&g.front, n);
+  for (int** p : {&g.parent, &g.inv0, &g.inv1, &g.mlist, &g.chg, &g.cap, &g.nsl, &g.ncol,
+                  &g.valid, &g.grow, &g.mark, &g.extra, &g.newslots, &g.aoff, &g.newcnt,
+                  &g.boff, &g.nc_g, &g.nc_r, &g.nc_rank, &g.bucket, &g.cl_d, &g.cl_r,
+                  &g.cl_rel})
+    A(p, m);
+  A(&g.best, m);
+  A(&g.blk, m);
+  A(&g.nc_key, m);
+  A(&g.arena, words);
+  A(&g.ctr, 1);
+  g.arena_words = words;
+  if (rc == LSD_OK) {
+    cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&G->h_ctr), sizeof(GCtr));
+    if (err != cudaSuccess) rc = gfail(err);
+  }
+  if (rc == LSD_OK) {
+    cudaError_t err = cudaMemcpyAsync(d_chk_ptr, chk_ptr.data(), (m + 1) * sizeof(int),
+                                      cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_chk_var, chk_var.data(), (size_t)E * sizeof(int),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_var_ptr, var_ptr.data(), (n + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_var_edge, var_edge.data(), (size_t)E * sizeof(int),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_var_chk, var_chk.data(), (size_t)E * sizeof(int),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_probs, channel_probs, (size_t)n * sizeof(float),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess) err = launch_priors(d_probs, d_prior, d_wfix, n, G->st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(G->st);
+    if (err != cudaSuccess) rc = gfail(err);
+  }
+  if (rc == LSD_OK) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess)
+      err = cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = cudaEventCreate(&G->ev[k]);
+    if (err != cudaSuccess) rc = gfail(err);
+  }
+  g.chk_ptr = d_chk_ptr;
+  g.chk_var = d_chk_var;
+  g.var_ptr = d_var_ptr;
+  g.var_edge = d_var_edge;
+  g.var_chk = d_var_chk;
+  g.prior = d_prior;
+  if (rc != LSD_OK) {
+    lsd_giant_destroy(G);
+    return rc;
+  }
+  *out = G;
+  return LSD_OK;
+}
+
+int lsd_giant_postprocess(lsd_giant* G, const float* llr, const uint8_t* syndrome,
+                          uint8_t* correction, lsd_giant_info* info) {
+  if (!G || !llr || !syndrome || !correction) return LSD_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  cudaEventRecord(G->ev[1], G->st);
+  const int rc = run_plsd(G, llr, syndrome, correction, info);
+  if (rc) return rc;
+  cudaEventRecord(G->ev[2], G->st);
+  cudaError_t e = cudaEventSynchronize(G->ev[2]);
+  if (e != cudaSuccess) return gfail(e);
+  if (info) cudaEventElapsedTime(&info->ms_lsd, G->ev[1], G->ev[2]);
+  return LSD_OK;
+}
+
+int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
+                     float* posteriors, lsd_giant_info* info) {
+  if (!G || !syndrome || !correction) return LSD_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  const GD& g = G->g;
+  const int grid = grid_threads(G);
+  int rc;
+  cudaEventRecord(G->ev[0], G->st);
+  cudaError_t e = cudaMemsetAsync(g.ctr, 0, sizeof(GCtr), G->st);
+  if (e != cudaSuccess) return gfail(e);
+  gbp_init<<<grid, 256, 0, G->st>>>(g);
+  if ((rc = check_launch(G))) return rc;
+  for (int t = 0; t < G->bp_iters; ++t) {
+    gbp_check<<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha);
+    if ((rc = check_launch(G))) return rc;
+    gbp_var<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    gbp_syn<<<grid, 256, 0, G->st>>>(g, syndrome);
+    if ((rc = check_launch(G))) return rc;
+    gbp_decide<<<1, 1, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+  }
+  if (posteriors) {
+    e = cudaMemcpyAsync(posteriors, g.lam, (size_t)G->n * sizeof(float),
+                        cudaMemcpyDeviceToDevice, G->st);
+    if (e != cudaSuccess) return gfail(e);
+  }
+  cudaEventRecord(G->ev[1], G->st);
+  if ((rc = read_ctr(G))) return rc;
+  const int conv = G->h_ctr->bp_conv, iters = G->h_ctr->bp_iters;
+  if (conv) {
+    gcopy_hard<<<grid, 256, 0, G->st>>>(g, correction);
+    if ((rc = check_launch(G))) return rc;
+    if (info) info->status = LSD_SHOT_OK_BP;
+  } else {
+    rc = run_plsd(G, g.lam, syndrome, correction, info);
+    if (rc) return rc;
+  }
+  cudaEventRecord(G->ev[2], G->st);
+  e = cudaEventSynchronize(G->ev[2]);
+  if (e != cudaSuccess) return gfail(e);
+  if (info) {
+    info->bp_iterations = iters;
+    cudaEventElapsedTime(&info->ms_bp, G->ev[0], G->ev[1]);
+    cudaEventElapsedTime(&info->ms_lsd, G->ev[1], G->ev[2]);
+  }
+  return LSD_OK;
+}
+
+int lsd_giant_kernel_launches(const lsd_giant* G, int64_t* count) {
+  if (!G || !count) return LSD_ERR_INVALID_ARG;
+  *count = G->launches;
+  return LSD_OK;
+}
+
+int lsd_giant_destroy(lsd_giant* G) {
+  if (!G) return LSD_OK;
+  cudaStreamSynchronize(G->st);
+  for (void* p : G->allocs) cudaFree(p);
+  if (G->h_ctr) cudaFreeHost(G->h_ctr);
+  for (auto& ev : G->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete G;
+  return LSD_OK;
+}
+
+}  // extern "C"

@@ -187,6 +187,31 @@ def hgp(h: np.ndarray):
     return hx.astype(np.uint8), hz.astype(np.uint8)
 
 
+def hgp_coo(h: np.ndarray):
+    """H_X of :func:`hgp` as a COO list, for products too large to hold densely:
+    returns (m, n, rows, cols) with rows, cols int32 in row-major order."""
+    h = np.asarray(h, dtype=np.uint8)
+    r, c = h.shape
+    hi, hj = np.nonzero(h)                       # block h (x) I_c
+    t = np.arange(c)
+    rows1 = (hi[:, None] * c + t[None, :]).ravel()
+    cols1 = (hj[:, None] * c + t[None, :]).ravel()
+    ta, tb = np.nonzero(h.T)                     # block I_r (x) h^T
+    u = np.arange(r)
+    rows2 = (u[:, None] * c + ta[None, :]).ravel()
+    cols2 = (c * c + u[:, None] * r + tb[None, :]).ravel()
+    rows = np.concatenate([rows1, rows2]).astype(np.int64)
+    cols = np.concatenate([cols1, cols2]).astype(np.int64)
+    order = np.lexsort((cols, rows))
+    return r * c, c * c + r * r, rows[order].astype(np.int32), cols[order].astype(np.int32)
+
+
+def coo_syndrome(m: int, rows: np.ndarray, cols: np.ndarray, errors: np.ndarray) -> np.ndarray:
+    """s = H e (mod 2) of one error vector for H given as a COO list; uint8 [m]."""
+    w = errors.astype(np.int64)[cols]
+    return (np.bincount(rows, weights=w, minlength=m).astype(np.int64) & 1).astype(np.uint8)
+
+
 def hgp_48x64(seed: int = 2406):
     """HGP of a seeded (3,4)-regular 48x64 matrix: H_X is 3072 x 6400, row weight 7."""
     return hgp(random_regular_ldpc(48, 64, 3, 4, seed))

@@ -35,7 +35,9 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_server_wait_all", "lsd_server_get_report", "lsd_server_run_poisson",
            "lsd_server_destroy", "lsd_autotune", "lsd_last_error", "lsd_window_create",
            "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy",
-           "lsd_window_stream_reset", "lsd_window_stream_push")
+           "lsd_window_stream_reset", "lsd_window_stream_push", "lsd_giant_create",
+           "lsd_giant_decode", "lsd_giant_postprocess", "lsd_giant_kernel_launches",
+           "lsd_giant_destroy")
 
 
 class LsdError(RuntimeError):
@@ -82,6 +84,15 @@ class Stats(C.Structure):
 _lib = None
 
 
+class GiantInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("bp_iterations", C.c_int32), ("nu", C.c_int32),
+                ("kappa", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32),
+                ("arena_bytes_used", C.c_int64), ("ms_bp", C.c_float), ("ms_lsd", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 def lib():
     """Load liblsd.so (built in-tree by ``paper_2406_18655_gb300.build``)."""
     global _lib
@@ -120,6 +131,12 @@ def lib():
     L.lsd_window_decode.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
     L.lsd_window_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_window_destroy.argtypes = [P]
+    L.lsd_giant_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int64, P, P, P,
+                                    C.c_int32, C.c_size_t, C.POINTER(Options)]
+    L.lsd_giant_decode.argtypes = [P, P, P, P, C.POINTER(GiantInfo)]
+    L.lsd_giant_postprocess.argtypes = [P, P, P, P, C.POINTER(GiantInfo)]
+    L.lsd_giant_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
+    L.lsd_giant_destroy.argtypes = [P]
     L.lsd_window_stream_reset.argtypes = [P, C.c_int64]
     L.lsd_window_stream_push.argtypes = [P, P, P, P, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32)]
@@ -455,6 +472,85 @@ class WindowDecoder:
         v = C.c_int64()
         _check(lib().lsd_window_kernel_launches(self._h, C.byref(v)),
                "lsd_window_kernel_launches")
+        return v.value
+
+
+class GiantDecoder:
+    """One large shot on the whole GPU (``lsd_giant_create``): BP with a thread per check
+    and per variable, then P-LSD (Alg. 2).  ``rows``, ``cols`` are the COO list of H (no
+    dense matrix is needed); :meth:`from_dense` takes a 0/1 matrix."""
+
+    def __init__(self, m: int, n: int, rows, cols, channel_probs, bp_iters: int, *,
+                 arena_bytes: int = 0, ms_scaling: float = 0.0, stream=None):
+        import torch
+        self.m, self.n = int(m), int(n)
+        rows = np.ascontiguousarray(rows, np.int32)
+        cols = np.ascontiguousarray(cols, np.int32)
+        p = np.asarray(channel_probs, dtype=np.float32)
+        if p.ndim == 0:
+            p = np.full(self.n, float(p), np.float32)
+        p = np.ascontiguousarray(p)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt = Options()
+        opt.ms_scaling = ms_scaling
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        handle = C.c_void_p()
+        _check(lib().lsd_giant_create(C.byref(handle), self.m, self.n, rows.size,
+                                      rows.ctypes.data_as(C.c_void_p),
+                                      cols.ctypes.data_as(C.c_void_p),
+                                      p.ctypes.data_as(C.c_void_p), bp_iters, arena_bytes,
+                                      C.byref(opt)),
+               "lsd_giant_create")
+        self._h = handle
+
+    @classmethod
+    def from_dense(cls, h, channel_probs, bp_iters: int, **kw):
+        h = np.asarray(h, dtype=np.uint8)
+        r, c = np.nonzero(h)
+        return cls(h.shape[0], h.shape[1], r, c, channel_probs, bp_iters, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lsd_giant_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, syndrome, correction=None, posteriors=None):
+        """Device syndrome [m] (uint8) -> (correction [n], info dict)."""
+        import torch
+        _dev_tensor(syndrome, torch.uint8, (self.m,), "syndrome")
+        if correction is None:
+            correction = torch.empty(self.n, dtype=torch.uint8, device=syndrome.device)
+        _dev_tensor(correction, torch.uint8, (self.n,), "correction")
+        if posteriors is not None:
+            _dev_tensor(posteriors, torch.float32, (self.n,), "posteriors")
+        info = GiantInfo()
+        _check(lib().lsd_giant_decode(self._h, _ptr(syndrome), _ptr(correction),
+                                      _ptr(posteriors), C.byref(info)), "lsd_giant_decode")
+        return correction, info.as_dict()
+
+    def postprocess(self, llr, syndrome, correction=None):
+        """P-LSD on device soft information llr [n] (float32) -> (correction, info dict)."""
+        import torch
+        _dev_tensor(llr, torch.float32, (self.n,), "llr")
+        _dev_tensor(syndrome, torch.uint8, (self.m,), "syndrome")
+        if correction is None:
+            correction = torch.empty(self.n, dtype=torch.uint8, device=syndrome.device)
+        _dev_tensor(correction, torch.uint8, (self.n,), "correction")
+        info = GiantInfo()
+        _check(lib().lsd_giant_postprocess(self._h, _ptr(llr), _ptr(syndrome),
+                                           _ptr(correction), C.byref(info)),
+               "lsd_giant_postprocess")
+        return correction, info.as_dict()
+
+    def kernel_launches(self) -> int:
+        v = C.c_int64()
+        _check(lib().lsd_giant_kernel_launches(self._h, C.byref(v)), "lsd_giant_kernel_launches")
         return v.value
 
 

@@ -63,3 +63,16 @@ def test_space_time_structure():
     e[0, 5] = 1                      # data fault of round 0
     e[0, 108 + 5] = 1                # the same data fault again in round 1
     assert not np.any(I.space_time_data_residual(e, 72, 36, d))
+
+
+def test_hgp_coo_equals_the_dense_product():
+    h = I.random_regular_ldpc(12, 16, 3, 4, seed=9)
+    hx = I.hgp(h)[0]
+    m, n, rows, cols = I.hgp_coo(h)
+    assert (m, n) == hx.shape
+    dense = np.zeros((m, n), np.uint8)
+    dense[rows, cols] = 1
+    assert np.array_equal(dense, hx) and rows.size == int(hx.sum())
+    e = I.sample_errors(3, 4, np.full(n, 0.1))
+    for k in range(4):
+        assert np.array_equal(I.coo_syndrome(m, rows, cols, e[k]), I.syndromes(hx, e[k:k + 1])[0])
