@@ -444,6 +444,71 @@ def _stream_latency(win, s, d, m, n, stream):
     return res
 
 
+def giant_leg(args, stream):
+    """One giant shot on the whole GPU (grid-parallel BP + P-LSD, Alg. 2): HGP codes of
+    seeded (3,4)-regular bases, beyond the batch decoder's 65535-column limit, one shot per
+    point, latency of the whole decode; and, on the 3072 x 6400 HGP code, the same shots
+    through the batch decoder one at a time (one warp per shot in LSD)."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.lsd import Decoder, GiantDecoder
+    out = []
+    for r0, c0 in ((240, 320), (480, 640)):
+        base = I.random_regular_ldpc(r0, c0, 3, 4, seed=2406 + r0)
+        m, n, rows, cols = I.hgp_coo(base)
+        for p in (0.01, 0.03):
+            gd = GiantDecoder(m, n, rows, cols, np.full(n, p, np.float32), 100, stream=stream)
+            infos, wall = [], []
+            for seed in range(4):
+                e = I.sample_errors(args.seed + seed, 1, np.full(n, p))[0]
+                s = torch.from_numpy(I.coo_syndrome(m, rows, cols, e)).cuda()
+                gd.decode(s)  # warm-up on the same shot
+                stream.synchronize()
+                t0 = time.perf_counter()
+                corr, info = gd.decode(s)
+                wall.append((time.perf_counter() - t0) * 1e3)
+                ok = np.array_equal(I.coo_syndrome(m, rows, cols, corr.cpu().numpy()),
+                                    s.cpu().numpy())
+                info["explains_syndrome"] = bool(ok)
+                infos.append(info)
+            out.append({"code": f"HGP of ({r0}x{c0}) (3,4)-regular", "m": m, "n": n,
+                        "edges": int(rows.size), "p": p, "bp_iters": 100,
+                        "ms_per_shot": float(np.mean(wall)),
+                        "ms_bp": float(np.mean([i["ms_bp"] for i in infos])),
+                        "ms_lsd": float(np.mean([i["ms_lsd"] for i in infos])),
+                        "shots": [{k: i[k] for k in ("status", "bp_iterations", "nu", "kappa",
+                                                     "steps", "explains_syndrome")}
+                                  for i in infos]})
+            gd.close()
+    # small code: giant path vs batch path, one shot per call
+    h = I.hgp_48x64()[0]
+    n = h.shape[1]
+    cmp = []
+    for p in (0.03, 0.05):
+        probs = np.full(n, p, np.float32)
+        e = I.sample_errors(args.seed + 99, 16, probs.astype(np.float64))
+        s = torch.from_numpy(I.syndromes(h, e)).cuda()
+        gd = GiantDecoder.from_dense(h, probs, 100, stream=stream)
+        bd = Decoder(h, probs, 100, stream=stream)
+        tg, tb = [], []
+        for k in range(16):
+            for fn, acc in ((lambda: gd.decode(s[k]), tg),
+                            (lambda: bd.decode(s[k:k + 1]), tb)):
+                fn()
+                stream.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                stream.synchronize()
+                acc.append((time.perf_counter() - t0) * 1e3)
+        cmp.append({"p": p, "giant_ms_p50": float(np.median(tg)),
+                    "batch_one_shot_ms_p50": float(np.median(tb))})
+        gd.close()
+        bd.close()
+    return {"points": out, "hgp_3072x6400_one_shot": cmp,
+            "note": "latency = host wall time of one synchronous decode (BP up to 100 "
+                    "iterations, then P-LSD with one host round trip per growth step)"}
+
+
 def hgp_leg(args, stream, flush, barrier):
     """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
     {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
@@ -620,11 +685,12 @@ def run_ours(args):
                "h2d_bytes_per_step": int(args.shots * m),
                "d2h_bytes_per_step": int(args.shots * (n + 1))}
 
-    serving = p_sweep = hgp = lsd_mu = windows = None
+    serving = p_sweep = hgp = lsd_mu = windows = giant = None
     if rank == 0 and not args.no_sweeps:
         p_sweep = p_sweep_leg(args, hx, hz, stream, flush, barrier, checker)
         lsd_mu = lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker)
         windows = window_leg(args, hx, hz, stream, flush, barrier, checker)
+        giant = giant_leg(args, stream)
         hgp = hgp_leg(args, stream, flush, barrier)
     if not args.no_serving and rank == 0:
         serving = serving_leg(args)
@@ -677,6 +743,7 @@ def run_ours(args):
         "p_sweep": p_sweep,
         "lsd_mu_cs4": lsd_mu,
         "windows": windows,
+        "giant_shot": giant,
         "hgp": hgp,
         "serving": serving,
     }
