@@ -55,7 +55,7 @@ constexpr float kEmptyMinF = 1267650600228229401496703205376.0f;
 struct GCtr {
   // whole call
   int ns, nfront, unsolvable, overflow, uf_fail, too_big;
-  int bp_stop, bp_unsat, bp_iters, bp_conv;
+  int bp_stop, bp_unsat[2], bp_iters, bp_conv;
   int nu, kappa;
   int ninv[2];
   // reset every step
@@ -149,17 +149,23 @@ __global__ void __launch_bounds__(256) gbp_init(GD g) {
   }
 }
 
+// Iteration t (t >= 1).  For t >= 2 it also tests the previous iteration's hard decision
+// against s (Sec. 4.3's early exit), accumulating into bp_unsat[t & 1]; gbp_var(t) then
+// stops the shot, with the posteriors of iteration t-1 kept, when that test passed.
 __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict__ s,
-                                                  float alpha) {
+                                                  float alpha, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
+  bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
     const int k0 = g.chk_ptr[i], k1 = g.chk_ptr[i + 1];
     unsigned par = s[i] ? 1u : 0u;
+    unsigned hpar = par;
     float m1 = kEmptyMinF, m2 = kEmptyMinF;
     int am = -1;
     for (int k = k0; k < k1; ++k) {
       const float v = g.q[k];
       par ^= __float_as_uint(v) >> 31;
+      if (t >= 2) hpar ^= g.hard[g.chk_var[k]];
       const float a = fabsf(v);
       if (a < m1) {
         m2 = m1;
@@ -169,16 +175,32 @@ __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict
         m2 = a;
       }
     }
+    bad |= (hpar & 1u) != 0u;
     for (int k = k0; k < k1; ++k) {
       const float mag = __fmul_rn(alpha, k == am ? m2 : m1);
       const unsigned neg = par ^ (__float_as_uint(g.q[k]) >> 31);
       g.r[k] = neg ? -mag : mag;
     }
   }
+  if (t >= 2 && __any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0)
+    atomicOr(&g.ctr->bp_unsat[t & 1], 1);
 }
 
-__global__ void __launch_bounds__(256) gbp_var(GD g) {
+__global__ void __launch_bounds__(256) gbp_var(GD g, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
+  if (t >= 2 && *(volatile int*)&g.ctr->bp_unsat[t & 1] == 0) {
+    // iteration t-1 satisfied the syndrome: keep its posteriors and stop
+    if (gtid() == 0) {
+      g.ctr->bp_conv = 1;
+      g.ctr->bp_iters = t - 1;
+      g.ctr->bp_stop = 1;
+    }
+    return;
+  }
+  if (gtid() == 0) {
+    g.ctr->bp_unsat[(t + 1) & 1] = 0;
+    g.ctr->bp_iters = t;
+  }
   for (long long j = gtid(); j < g.n; j += gstride()) {
     const int a0 = g.var_ptr[j], a1 = g.var_ptr[j + 1];
     float L = g.prior[j];
@@ -192,7 +214,8 @@ __global__ void __launch_bounds__(256) gbp_var(GD g) {
   }
 }
 
-__global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__ s) {
+// The test after the last iteration T (slot (T+1) & 1, cleared by gbp_var(T)).
+__global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__ s, int slot) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
   bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
@@ -200,16 +223,13 @@ __global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__
     for (int k = g.chk_ptr[i]; k < g.chk_ptr[i + 1]; ++k) par ^= g.hard[g.chk_var[k]];
     bad |= (par & 1u) != 0;
   }
-  if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(&g.ctr->bp_unsat, 1);
+  if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(&g.ctr->bp_unsat[slot], 1);
 }
 
-__global__ void gbp_decide(GD g) {
+__global__ void gbp_final(GD g, int slot) {
   if (g.ctr->bp_stop) return;
-  g.ctr->bp_iters += 1;
-  const int ok = g.ctr->bp_unsat == 0;
-  g.ctr->bp_conv = ok;
-  g.ctr->bp_unsat = 0;
-  if (ok) g.ctr->bp_stop = 1;
+  g.ctr->bp_conv = g.ctr->bp_unsat[slot] == 0;
+  g.ctr->bp_stop = 1;
 }
 
 __global__ void __launch_bounds__(256) gcopy_hard(GD g, uint8_t* __restrict__ corr) {
@@ -740,8 +760,8 @@ int run_plsd(lsd_giant* G, const float* llr, const uint8_t* s, uint8_t* corr,
   gzero<<<grid, 256, 0, G->st>>>(corr, G->n);
   if ((rc = check_launch(G))) return rc;
   int status = LSD_SHOT_OK_LSD, steps = 0, par = 0;
+  if ((rc = read_ctr(G))) return rc;
   for (;;) {
-    if ((rc = read_ctr(G))) return rc;
     const GCtr& h = *G->h_ctr;
     if (h.overflow) return LSD_ERR_ADMISSION;
     if (h.uf_fail) return LSD_ERR_TIMEOUT;
@@ -962,14 +982,25 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
   if (e != cudaSuccess) return gfail(e);
   gbp_init<<<grid, 256, 0, G->st>>>(g);
   if ((rc = check_launch(G))) return rc;
-  for (int t = 0; t < G->bp_iters; ++t) {
-    gbp_check<<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha);
+  // iterations in chunks of 2, 4, 8, ... with a look at the stop flag after each, so that a
+  // shot that converges early is not followed by the remaining iterations' launches
+  bool stopped = false;
+  for (int t = 1, chunk = 2; t <= G->bp_iters && !stopped; chunk *= 2) {
+    const int t1 = std::min(G->bp_iters, t + chunk - 1);
+    for (; t <= t1; ++t) {
+      gbp_check<<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha, t);
+      if ((rc = check_launch(G))) return rc;
+      gbp_var<<<grid, 256, 0, G->st>>>(g, t);
+      if ((rc = check_launch(G))) return rc;
+    }
+    if ((rc = read_ctr(G))) return rc;
+    stopped = G->h_ctr->bp_stop != 0;
+  }
+  if (G->bp_iters > 0 && !stopped) {
+    const int slot = (G->bp_iters + 1) & 1;
+    gbp_syn<<<grid, 256, 0, G->st>>>(g, syndrome, slot);
     if ((rc = check_launch(G))) return rc;
-    gbp_var<<<grid, 256, 0, G->st>>>(g);
-    if ((rc = check_launch(G))) return rc;
-    gbp_syn<<<grid, 256, 0, G->st>>>(g, syndrome);
-    if ((rc = check_launch(G))) return rc;
-    gbp_decide<<<1, 1, 0, G->st>>>(g);
+    gbp_final<<<1, 1, 0, G->st>>>(g, slot);
     if ((rc = check_launch(G))) return rc;
   }
   if (posteriors) {
