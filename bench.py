@@ -509,6 +509,36 @@ def giant_leg(args, stream):
                     "iterations, then P-LSD with one host round trip per growth step)"}
 
 
+def hooks_leg(args, hx, hz, stream, flush, barrier, checker):
+    """BB[[144,12,12]] over d = 6 rounds with mid-round hook faults and seeded non-uniform
+    priors (504 x 2160, weight-2/3 hyperedges: the shape of a circuit-level error model),
+    BP 50 + LSD-0, 10^5 shots per point."""
+    import torch
+    from paper_2406_18655_gb300 import inputs as I
+    from paper_2406_18655_gb300.lsd import Decoder
+    m, n = hx.shape
+    d, shots = 6, 100_000
+    h, _ = I.space_time_hooks(hx, d, seed=d)
+    out = []
+    for p in (0.002, 0.004, 0.006):
+        probs = I.space_time_hooks_probs(n, m, d, p, seed=d + 1).astype(np.float32)
+        dec = Decoder(h, probs, 50, stream=stream)
+        e, s = dec.sample(args.seed + int(p * 1e4), shots)
+        corr = torch.empty((shots, h.shape[1]), dtype=torch.uint8, device="cuda")
+        status = torch.empty(shots, dtype=torch.uint8, device="cuda")
+        ms, st = _timed_decode(dec, s, corr, status, 3, stream, flush, barrier)
+        r = (e ^ corr).view(shots, d, 2 * n + m)
+        resid = ((r[:, :, :n].sum(dim=1) + r[:, :, n + m:].sum(dim=1)) % 2).to(torch.uint8)
+        fails = checker.failures(resid, torch.zeros_like(resid))
+        out.append({"p": p, "shots_per_s": shots / (np.mean(ms) / 1e3),
+                    "ler": float(fails.float().mean()), "lsd_frac": st["lsd_shots"] / shots,
+                    "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
+                    "kappa_max": st["kappa_max"]})
+        dec.close()
+    return {"code": "BB[[144,12,12]] space-time with hook faults, d = 6 (504 x 2160)",
+            "shots": shots, "bp_iters": 50, "points": out}
+
+
 def hgp_leg(args, stream, flush, barrier):
     """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
     {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
@@ -685,12 +715,13 @@ def run_ours(args):
                "h2d_bytes_per_step": int(args.shots * m),
                "d2h_bytes_per_step": int(args.shots * (n + 1))}
 
-    serving = p_sweep = hgp = lsd_mu = windows = giant = None
+    serving = p_sweep = hgp = lsd_mu = windows = giant = hooks = None
     if rank == 0 and not args.no_sweeps:
         p_sweep = p_sweep_leg(args, hx, hz, stream, flush, barrier, checker)
         lsd_mu = lsd_mu_leg(args, hx, hz, stream, flush, barrier, checker)
         windows = window_leg(args, hx, hz, stream, flush, barrier, checker)
         giant = giant_leg(args, stream)
+        hooks = hooks_leg(args, hx, hz, stream, flush, barrier, checker)
         hgp = hgp_leg(args, stream, flush, barrier)
     if not args.no_serving and rank == 0:
         serving = serving_leg(args)
@@ -744,6 +775,7 @@ def run_ours(args):
         "lsd_mu_cs4": lsd_mu,
         "windows": windows,
         "giant_shot": giant,
+        "circuit_like": hooks,
         "hgp": hgp,
         "serving": serving,
     }

@@ -236,6 +236,54 @@ def space_time(h: np.ndarray, d: int) -> np.ndarray:
     return out
 
 
+def space_time_hooks(h: np.ndarray, d: int, seed: int):
+    """Space-time matrix with mid-round data faults, a synthetic stand-in for a
+    circuit-level detector error model: weight-2 and weight-3 hyperedges across rounds.
+
+    Per round t (t = 0..d-1) the columns are [n data | m measurement | n hook]: data and
+    measurement faults as in :func:`space_time`; hook fault j of round t flips qubit j
+    between the measurements of its checks, so a seeded subset of column j's checks (at
+    least one, not all) fires in block t and the rest in block t+1.  Block d is the
+    noiseless final round.  Returns (H, split) with split[t][j] the number of checks of
+    qubit j (in ascending row order) that fire in block t.
+    """
+    h = np.asarray(h, dtype=np.uint8)
+    m, n = h.shape
+    F = 2 * n + m
+    out = np.zeros(((d + 1) * m, d * F), dtype=np.uint8)
+    eye = np.eye(m, dtype=np.uint8)
+    gen = Xoshiro256ss(seed, np.arange(d * n, dtype=np.uint64))
+    u = gen.uniform().reshape(d, n)
+    split = np.zeros((d, n), np.int64)
+    for t in range(d):
+        c0 = t * F
+        out[t * m:(t + 1) * m, c0:c0 + n] = h
+        out[t * m:(t + 1) * m, c0 + n:c0 + n + m] = eye
+        out[(t + 1) * m:(t + 2) * m, c0 + n:c0 + n + m] = eye
+        for j in range(n):
+            rows = np.nonzero(h[:, j])[0]
+            k = 1 + int(u[t, j] * (rows.size - 1)) if rows.size > 1 else 1
+            split[t, j] = k
+            out[t * m + rows[:k], c0 + n + m + j] = 1
+            out[(t + 1) * m + rows[k:], c0 + n + m + j] = 1
+    return out, split
+
+
+def space_time_hooks_probs(n: int, m: int, d: int, p: float, seed: int) -> np.ndarray:
+    """Non-uniform priors for :func:`space_time_hooks`: data p, measurement p and hook p / 2,
+    each scaled by a seeded factor in [0.25, 1.75) per column."""
+    base = np.tile(np.concatenate([np.full(n, p), np.full(m, p), np.full(n, p / 2)]), d)
+    g = Xoshiro256ss(seed, np.arange(base.size, dtype=np.uint64))
+    return base * (0.25 + 1.5 * g.uniform())
+
+
+def space_time_hooks_data_residual(residual: np.ndarray, n: int, m: int, d: int) -> np.ndarray:
+    """Net data flip per qubit of a residual of :func:`space_time_hooks`: data and hook faults
+    of every round, summed mod 2."""
+    r = residual.reshape(residual.shape[0], d, 2 * n + m)
+    return ((r[:, :, :n].sum(axis=1) + r[:, :, n + m:].sum(axis=1)) % 2).astype(np.uint8)
+
+
 def space_time_probs(n: int, m: int, d: int, p: float, q: float) -> np.ndarray:
     """Per-column fault probabilities of :func:`space_time`: p for data, q for measurement."""
     block = np.concatenate([np.full(n, p), np.full(m, q)])

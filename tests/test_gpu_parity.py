@@ -185,6 +185,29 @@ def test_decode_osd_cs_matches_oracle(L):
     assert np.array_equal(corr.cpu().numpy(), o["corrections"])
 
 
+@pytest.mark.parametrize("name,d,p,iters,order,osd_cs", [
+    ("bb72", 3, 0.01, 30, 0, None), ("bb72", 3, 0.02, 30, 6, None),
+    ("bb144", 3, 0.01, 50, 0, None), ("bb144", 6, 0.005, 50, 0, None),
+    ("bb144", 6, 0.008, 30, 12, 4)])
+def test_circuit_like_dem_with_non_uniform_priors(L, name, d, p, iters, order, osd_cs):
+    """Space-time matrices with mid-round hook faults (weight-2 and weight-3 hyperedges
+    across rounds) and seeded non-uniform priors, the shape of a circuit-level detector
+    error model; BB144 over 6 rounds (504 x 2160) takes the sparse LSD kernel."""
+    h0 = code(name)
+    m0, n0 = h0.shape
+    h, _ = I.space_time_hooks(h0, d, seed=d)
+    probs = I.space_time_hooks_probs(n0, m0, d, p, seed=d + 1).astype(np.float32)
+    e = I.sample_errors(83 + d, 3000, probs.astype(np.float64))
+    s = I.syndromes(h, e)
+    dec = L.Decoder(h, probs, iters, order, osd_cs=osd_cs)
+    corr, st = dec.decode(dev(s))
+    o = oracle.decode(h, f64(probs), s, iters, lsd_order=order, precision=1,
+                      osd_cs=-1 if osd_cs is None else osd_cs)
+    assert np.array_equal(st.cpu().numpy(), o["status"])
+    assert np.array_equal(corr.cpu().numpy(), o["corrections"])
+    assert (o["status"] == 2).sum() > 20
+
+
 def test_single_cluster_equals_osd0(L):
     h, probs, e, s = sample("bb144", 0.05, 200, seed=9)
     llr, *_ = oracle.bp(h, f64(probs), s, 20, precision=1)

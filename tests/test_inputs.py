@@ -76,3 +76,28 @@ def test_hgp_coo_equals_the_dense_product():
     e = I.sample_errors(3, 4, np.full(n, 0.1))
     for k in range(4):
         assert np.array_equal(I.coo_syndrome(m, rows, cols, e[k]), I.syndromes(hx, e[k:k + 1])[0])
+
+
+def test_space_time_hooks_structure():
+    """Hook columns split a qubit's checks between two consecutive blocks; with every hook
+    removed the matrix is the phenomenological one; a hook together with the data fault of
+    the same qubit and round fires exactly the checks moved to the next block, twice
+    (cancelling in block t)."""
+    h = I.bb72()[0]
+    m, n = h.shape
+    d = 3
+    hs, split = I.space_time_hooks(h, d, seed=5)
+    F = 2 * n + m
+    keep = np.concatenate([np.arange(t * F, t * F + n + m) for t in range(d)])
+    assert np.array_equal(hs[:, keep], I.space_time(h, d))
+    for t in range(d):
+        for j in range(n):
+            col = hs[:, t * F + n + m + j]
+            assert col.sum() == h[:, j].sum() == 3
+            assert 1 <= split[t, j] < 3
+            assert col[t * m:(t + 1) * m].sum() == split[t, j]
+            both = (col.astype(int) + hs[:, t * F + j]) % 2
+            assert both[t * m:(t + 1) * m].sum() == 3 - split[t, j]
+            assert np.array_equal(both[(t + 1) * m:(t + 2) * m], col[(t + 1) * m:(t + 2) * m])
+    p = I.space_time_hooks_probs(n, m, d, 0.01, seed=6)
+    assert p.size == d * F and p.min() >= 0.00125 and p.max() < 0.0175 and np.unique(p).size > 100
