@@ -65,11 +65,14 @@ struct GCtr {
 
 struct GD {
   int m, n;
-  const int *chk_ptr, *chk_var, *var_ptr, *var_edge, *var_chk;
+  const int *chk_ptr, *chk_var, *var_ptr, *var_chk;
   const float* prior;
-  // BP
-  float *q, *r, *lam;
-  uint8_t* hard;
+  // BP: position-major (ELL) tables padded with -1: ell_col[k * m + i] = column of the k-th
+  // edge of check i; ell_pos[k * n + j] = position (k' * m + i) of the k-th edge of column j
+  // in ascending row order.  Messages r[dc * m] live at those positions.
+  int dc, dv;
+  const int *ell_col, *ell_pos;
+  float *r, *lam;
   // per detector / per fault
   int *dlab, *lslot, *fst, *front;
   // per seed ordinal (at most m)
@@ -141,32 +144,39 @@ __device__ __forceinline__ long long gwarps() { return gstride() >> 5; }
 // ---------------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) gbp_init(GD g) {
-  const long long E = g.chk_ptr[g.m];
-  for (long long k = gtid(); k < E; k += gstride()) g.q[k] = g.prior[g.chk_var[k]];
-  for (long long j = gtid(); j < g.n; j += gstride()) {
-    g.lam[j] = g.prior[j];
-    g.hard[j] = 0;
-  }
+  const long long slots = (long long)g.dc * g.m;
+  for (long long k = gtid(); k < slots; k += gstride()) g.r[k] = 0.0f;
+  for (long long j = gtid(); j < g.n; j += gstride()) g.lam[j] = g.prior[j];
 }
 
-// Iteration t (t >= 1).  For t >= 2 it also tests the previous iteration's hard decision
-// against s (Sec. 4.3's early exit), accumulating into bp_unsat[t & 1]; gbp_var(t) then
-// stops the shot, with the posteriors of iteration t-1 kept, when that test passed.
+// Iteration t (t >= 1): q = Lam - r on every edge of a check, then the scaled min-sum
+// message.  For t >= 2 it also tests the hard decision [Lam < 0] of iteration t-1 against s
+// (Sec. 4.3's early exit; sign bits stand for "< 0": no Lam is -0), accumulating into
+// bp_unsat[t & 1]; gbp_var(t) stops the shot, keeping Lam of iteration t-1, when it passed.
+// A warp reads 32 consecutive checks' k-th edges: the column indices and messages are
+// contiguous, Lam is gathered.
+template <int DCMAX>
 __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict__ s,
                                                   float alpha, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
   bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
-    const int k0 = g.chk_ptr[i], k1 = g.chk_ptr[i + 1];
-    unsigned par = s[i] ? 1u : 0u;
-    unsigned hpar = par;
+    unsigned hp = s[i] ? 0x80000000u : 0u;  // bit 31: syndrome ^ signs of Lam
+    unsigned sx = 0u;                        // bit 31: signs of q
     float m1 = kEmptyMinF, m2 = kEmptyMinF;
-    int am = -1;
-    for (int k = k0; k < k1; ++k) {
-      const float v = g.q[k];
-      par ^= __float_as_uint(v) >> 31;
-      if (t >= 2) hpar ^= g.hard[g.chk_var[k]];
-      const float a = fabsf(v);
+    int am = -1, deg = 0;
+    unsigned qb[DCMAX];
+#pragma unroll
+    for (int k = 0; k < DCMAX; ++k) {
+      qb[k] = 0u;
+      const int j = k < g.dc ? g.ell_col[(long long)k * g.m + i] : -1;
+      if (j < 0) continue;
+      const float L = g.lam[j];
+      hp ^= __float_as_uint(L);
+      const float q = __fsub_rn(L, g.r[(long long)k * g.m + i]);
+      qb[k] = __float_as_uint(q);
+      sx ^= qb[k];
+      const float a = fabsf(q);
       if (a < m1) {
         m2 = m1;
         m1 = a;
@@ -174,18 +184,24 @@ __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict
       } else if (a < m2) {
         m2 = a;
       }
+      deg = k + 1;
     }
-    bad |= (hpar & 1u) != 0u;
-    for (int k = k0; k < k1; ++k) {
-      const float mag = __fmul_rn(alpha, k == am ? m2 : m1);
-      const unsigned neg = par ^ (__float_as_uint(g.q[k]) >> 31);
-      g.r[k] = neg ? -mag : mag;
+    bad |= (hp >> 31) != 0u;
+    const unsigned par = (s[i] ? 0x80000000u : 0u) ^ sx;
+    const float mag1 = __fmul_rn(alpha, m1), mag2 = __fmul_rn(alpha, m2);
+#pragma unroll
+    for (int k = 0; k < DCMAX; ++k) {
+      if (k >= deg) continue;
+      const float mag = k == am ? mag2 : mag1;
+      g.r[(long long)k * g.m + i] =
+          __uint_as_float(__float_as_uint(mag) | ((par ^ qb[k]) & 0x80000000u));
     }
   }
   if (t >= 2 && __any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0)
     atomicOr(&g.ctr->bp_unsat[t & 1], 1);
 }
 
+// Lam of iteration t: prior plus the incoming messages in ascending check order.
 __global__ void __launch_bounds__(256) gbp_var(GD g, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
   if (t >= 2 && *(volatile int*)&g.ctr->bp_unsat[t & 1] == 0) {
@@ -202,15 +218,13 @@ __global__ void __launch_bounds__(256) gbp_var(GD g, int t) {
     g.ctr->bp_iters = t;
   }
   for (long long j = gtid(); j < g.n; j += gstride()) {
-    const int a0 = g.var_ptr[j], a1 = g.var_ptr[j + 1];
     float L = g.prior[j];
-    for (int a = a0; a < a1; ++a) L = __fadd_rn(L, g.r[g.var_edge[a]]);
-    g.lam[j] = L;
-    for (int a = a0; a < a1; ++a) {
-      const int e = g.var_edge[a];
-      g.q[e] = __fsub_rn(L, g.r[e]);
+    for (int k = 0; k < g.dv; ++k) {
+      const int p = g.ell_pos[(long long)k * g.n + j];
+      if (p < 0) break;
+      L = __fadd_rn(L, g.r[p]);
     }
-    g.hard[j] = L < 0.0f ? 1 : 0;
+    g.lam[j] = L;
   }
 }
 
@@ -219,9 +233,13 @@ __global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__
   if (*(volatile int*)&g.ctr->bp_stop) return;
   bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
-    unsigned par = s[i] ? 1u : 0u;
-    for (int k = g.chk_ptr[i]; k < g.chk_ptr[i + 1]; ++k) par ^= g.hard[g.chk_var[k]];
-    bad |= (par & 1u) != 0;
+    unsigned hp = s[i] ? 0x80000000u : 0u;
+    for (int k = 0; k < g.dc; ++k) {
+      const int j = g.ell_col[(long long)k * g.m + i];
+      if (j < 0) break;
+      hp ^= __float_as_uint(g.lam[j]);
+    }
+    bad |= (hp >> 31) != 0u;
   }
   if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(&g.ctr->bp_unsat[slot], 1);
 }
@@ -233,7 +251,7 @@ __global__ void gbp_final(GD g, int slot) {
 }
 
 __global__ void __launch_bounds__(256) gcopy_hard(GD g, uint8_t* __restrict__ corr) {
-  for (long long j = gtid(); j < g.n; j += gstride()) corr[j] = g.hard[j];
+  for (long long j = gtid(); j < g.n; j += gstride()) corr[j] = g.lam[j] < 0.0f ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -860,6 +878,20 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
     var_edge[slot] = k;
     var_chk[slot] = e[k].first;
   }
+  int dc = 0, dv = 0;
+  for (int i = 0; i < m; ++i) dc = std::max(dc, chk_ptr[i + 1] - chk_ptr[i]);
+  for (int j = 0; j < n; ++j) dv = std::max(dv, var_ptr[j + 1] - var_ptr[j]);
+  if (dc > 32) return LSD_ERR_UNSUPPORTED;  // check degree of the BP kernel
+  std::vector<int> ell_col((size_t)dc * m, -1), ell_pos((size_t)dv * n, -1);
+  for (int i = 0; i < m; ++i)
+    for (int k = chk_ptr[i]; k < chk_ptr[i + 1]; ++k)
+      ell_col[(size_t)(k - chk_ptr[i]) * m + i] = chk_var[k];
+  for (int j = 0; j < n; ++j)
+    for (int a = var_ptr[j]; a < var_ptr[j + 1]; ++a) {
+      const int k = var_edge[a], i = var_chk[a];
+      ell_pos[(size_t)(a - var_ptr[j]) * n + j] = (k - chk_ptr[i]) * m + i;
+    }
+  if ((size_t)dc * m >= (size_t)INT32_MAX) return LSD_ERR_UNSUPPORTED;
 
   lsd_giant* G = new (std::nothrow) lsd_giant();
   if (!G) return LSD_ERR_OOM;
@@ -874,8 +906,7 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
   g.n = n;
   const size_t words = arena_bytes ? arena_bytes / 4 : ((size_t)64 << 20);  // 256 MiB
   int rc = LSD_OK;
-  int *d_chk_ptr = nullptr, *d_chk_var = nullptr, *d_var_ptr = nullptr, *d_var_edge = nullptr,
-      *d_var_chk = nullptr;
+  int *d_chk_ptr = nullptr, *d_chk_var = nullptr, *d_var_ptr = nullptr, *d_var_chk = nullptr;
   float *d_prior = nullptr, *d_probs = nullptr;
   long long* d_wfix = nullptr;
   auto A = [&](auto** p, size_t count) {
@@ -884,15 +915,15 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
   A(&d_chk_ptr, m + 1);
   A(&d_chk_var, E);
   A(&d_var_ptr, n + 1);
-  A(&d_var_edge, E);
   A(&d_var_chk, E);
   A(&d_prior, n);
   A(&d_probs, n);
   A(&d_wfix, n);
-  A(&g.q, E);
-  A(&g.r, E);
+  int *d_ell_col = nullptr, *d_ell_pos = nullptr;
+  A(&d_ell_col, (size_t)dc * m);
+  A(&d_ell_pos, (size_t)dv * n);
+  A(&g.r, (size_t)dc * m);
   A(&g.lam, n);
-  A(&g.hard, n);
   A(&g.dlab, m);
   A(&g.lslot, m);
   A(&g.fst, n);
@@ -922,10 +953,13 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
       err = cudaMemcpyAsync(d_var_ptr, var_ptr.data(), (n + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, G->st);
     if (err == cudaSuccess)
-      err = cudaMemcpyAsync(d_var_edge, var_edge.data(), (size_t)E * sizeof(int),
+      err = cudaMemcpyAsync(d_var_chk, var_chk.data(), (size_t)E * sizeof(int),
                             cudaMemcpyHostToDevice, G->st);
     if (err == cudaSuccess)
-      err = cudaMemcpyAsync(d_var_chk, var_chk.data(), (size_t)E * sizeof(int),
+      err = cudaMemcpyAsync(d_ell_col, ell_col.data(), ell_col.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, G->st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_ell_pos, ell_pos.data(), ell_pos.size() * sizeof(int),
                             cudaMemcpyHostToDevice, G->st);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(d_probs, channel_probs, (size_t)n * sizeof(float),
@@ -942,10 +976,13 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
     for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = cudaEventCreate(&G->ev[k]);
     if (err != cudaSuccess) rc = gfail(err);
   }
+  g.dc = dc;
+  g.dv = dv;
+  g.ell_col = d_ell_col;
+  g.ell_pos = d_ell_pos;
   g.chk_ptr = d_chk_ptr;
   g.chk_var = d_chk_var;
   g.var_ptr = d_var_ptr;
-  g.var_edge = d_var_edge;
   g.var_chk = d_var_chk;
   g.prior = d_prior;
   if (rc != LSD_OK) {
@@ -988,7 +1025,12 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
   for (int t = 1, chunk = 2; t <= G->bp_iters && !stopped; chunk *= 2) {
     const int t1 = std::min(G->bp_iters, t + chunk - 1);
     for (; t <= t1; ++t) {
-      gbp_check<<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha, t);
+      if (g.dc <= 8)
+        gbp_check<8><<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha, t);
+      else if (g.dc <= 16)
+        gbp_check<16><<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha, t);
+      else
+        gbp_check<32><<<grid, 256, 0, G->st>>>(g, syndrome, G->alpha, t);
       if ((rc = check_launch(G))) return rc;
       gbp_var<<<grid, 256, 0, G->st>>>(g, t);
       if ((rc = check_launch(G))) return rc;
