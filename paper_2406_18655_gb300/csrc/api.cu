@@ -34,6 +34,11 @@ struct lsd_decoder {
   // host-buffer entry point: copy streams and per-chunk events of the pipelined path
   cudaStream_t cp_in = nullptr, cp_out = nullptr;
   cudaEvent_t cev[2 * 8] = {};
+  // second compute stream and per-chunk counters: consecutive chunks decode on alternate
+  // streams, so that one chunk's BP fills the SMs that the previous chunk's LSD tail leaves
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t join = nullptr;
+  DevCounters* d_ctr_chunks = nullptr;  // [8]
   // launch shapes
   int bp_variant = -1, bp_grid = 0, bp_block = 0;
   size_t bp_smem = 0;
@@ -175,6 +180,40 @@ int fill_stats(lsd_decoder* d, int64_t shots, lsd_stats* stats, bool timed_lsd) 
 
 bool valid_lanes(int l) { return l == 0 || l == 8 || l == 16 || l == 32; }
 
+// BP + dense LSD of one chunk of a pipelined batch, on stream st with its own counters and
+// its own part of the queue (the rows of its shots).
+int decode_chunk(lsd_decoder* d, int64_t shots, const uint8_t* syn, uint8_t* corr,
+                 uint8_t* status, DevCounters* ctr, int32_t* queue, float* queue_llr,
+                 cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  BPArgs a = bp_args(d, shots, syn);
+  a.ctr = ctr;
+  a.corrections = corr;
+  a.status = status;
+  a.queue = queue;
+  a.queue_llr = queue_llr;
+  e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, st);
+  d->launches++;
+  if (e != cudaSuccess) return cuda_fail(e);
+  LSDArgs l{};
+  l.g = d->g;
+  l.count_from_ctr = 1;
+  l.queue = queue;
+  l.llr = queue_llr;
+  l.llr_by_item = 1;
+  l.syndromes = syn;
+  l.corrections = corr;
+  l.status = status;
+  l.order = d->order;
+  l.osd_cs = d->osd_cs;
+  l.single_cluster = d->opt.single_cluster;
+  l.ctr = ctr;
+  e = launch_lsd(l, d->lsd_warps, d->lsd_grid, d->lsd_smem, st);
+  d->launches++;
+  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
 // LSD launch on the decoder's queue or batch: the dense kernel, or for large matrices the
 // sparse kernel followed by its global-memory instance for the shots that spilled.
 int run_lsd(lsd_decoder* d, const LSDArgs& l, int64_t max_items) {
@@ -249,7 +288,8 @@ int lsd_destroy(lsd_decoder* d) {
   if (d->h_ctr) cudaFreeHost(d->h_ctr);
   for (auto& e : d->ev)
     if (e) cudaEventDestroy(e);
-  for (cudaStream_t c : {d->cp_in, d->cp_out})
+  if (d->join) cudaEventDestroy(d->join);
+  for (cudaStream_t c : {d->cp_in, d->cp_out, d->st2})
     if (c) {
       cudaStreamSynchronize(c);
       cudaStreamDestroy(c);
@@ -484,19 +524,42 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
     if (e == cudaSuccess && !d->cp_out) e = cudaStreamCreateWithFlags(&d->cp_out, cudaStreamNonBlocking);
     for (int i = 0; i < 2 * kMaxChunks && e == cudaSuccess; ++i)
       if (!d->cev[i]) e = cudaEventCreateWithFlags(&d->cev[i], cudaEventDisableTiming);
+    // dense LSD: two compute lanes (no per-decoder scratch beyond counters and queue rows)
+    const bool lanes2 = !d->sparse && d->lsd_ok;
+    if (lanes2) {
+      if (e == cudaSuccess && !d->st2) e = cudaStreamCreateWithFlags(&d->st2, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !d->join) e = cudaEventCreateWithFlags(&d->join, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
+    if (lanes2 && !d->d_ctr_chunks) {
+      const int rc = dev_alloc(d, reinterpret_cast<void**>(&d->d_ctr_chunks),
+                               kMaxChunks * sizeof(DevCounters));
+      if (rc) return rc;
+    }
+    if (lanes2) {
+      const int rc = ensure_workspace(d, shots);
+      if (rc) return rc;
+      // the second lane starts after everything already queued on the decoder's stream
+      e = cudaEventRecord(d->join, d->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->st2, d->join, 0);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     int64_t base = 0;
     for (int i = 0; i < chunks; ++i) {
       const int64_t cnt = shots * (i + 1) / chunks - base;
       const size_t sm = (size_t)base * d->m, sn = (size_t)base * d->n;
+      cudaStream_t cs = (lanes2 && (i & 1)) ? d->st2 : d->st;
       e = cudaMemcpyAsync(dsyn + sm, syndromes + sm, (size_t)cnt * d->m, cudaMemcpyHostToDevice,
                           d->cp_in);
       if (e == cudaSuccess) e = cudaEventRecord(d->cev[2 * i], d->cp_in);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->st, d->cev[2 * i], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, d->cev[2 * i], 0);
       if (e != cudaSuccess) return cuda_fail(e);
-      const int rc = lsd_decode_batch(d, cnt, dsyn + sm, dcor + sn, dst + base, nullptr, nullptr);
+      const int rc =
+          lanes2 ? decode_chunk(d, cnt, dsyn + sm, dcor + sn, dst + base, d->d_ctr_chunks + i,
+                                d->d_queue + base, d->d_queue_llr + sn, cs)
+                 : lsd_decode_batch(d, cnt, dsyn + sm, dcor + sn, dst + base, nullptr, nullptr);
       if (rc) return rc;
-      e = cudaEventRecord(d->cev[2 * i + 1], d->st);
+      e = cudaEventRecord(d->cev[2 * i + 1], cs);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(d->cp_out, d->cev[2 * i + 1], 0);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(corrections + sn, dcor + sn, (size_t)cnt * d->n,
@@ -509,6 +572,7 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
     }
     e = cudaStreamSynchronize(d->cp_out);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+    if (e == cudaSuccess && lanes2) e = cudaStreamSynchronize(d->st2);
     return e == cudaSuccess ? LSD_OK : cuda_fail(e);
   }
   cudaError_t e = cudaMemcpyAsync(dsyn, syndromes, (size_t)shots * d->m, cudaMemcpyHostToDevice,
