@@ -125,6 +125,19 @@ def test_giant_shot_explains_its_syndrome(L):
             assert info["nu"] > 1 and info["steps"] > 0
 
 
+def test_largest_giant_shot(L):
+    """HGP of a (3,4)-regular 480 x 640 matrix: 640000 faults, 307200 detectors, 2.15 M
+    edges, at a noise level where LSD meets thousands of clusters in one shot."""
+    base = I.random_regular_ldpc(480, 640, 3, 4, seed=2886)
+    m, n, rows, cols = I.hgp_coo(base)
+    gd = L.GiantDecoder(m, n, rows, cols, np.full(n, 0.03, np.float32), 30)
+    e = I.sample_errors(5, 1, np.full(n, 0.03))[0]
+    s = I.coo_syndrome(m, rows, cols, e)
+    corr, info = gd.decode(torch.from_numpy(s).cuda())
+    assert info["status"] == 2 and info["nu"] > 1000
+    assert np.array_equal(I.coo_syndrome(m, rows, cols, corr.cpu().numpy()), s)
+
+
 def test_unsolvable_and_small_arena(L):
     """A syndrome outside image(H) gives status 3 and a zero correction; an arena too small
     for the clusters raises LSD_ERR_ADMISSION and leaves the decoder usable."""

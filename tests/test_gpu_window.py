@@ -133,3 +133,18 @@ def test_streaming_pushes_match_batch_decode(L, d, w, c):
     assert torch.equal(corr, ref) and torch.equal(st, rst)
     with pytest.raises(L.LsdError):
         wd.stream_push(blocks[:, 0].contiguous(), corr, st)
+
+
+def test_window_decode_with_sparse_lsd_kernel(L):
+    """The windows' LSD on the sparse kernel (state sized by what a shot touches) gives the
+    same corrections as the oracle."""
+    h = code("bb144")
+    m, n = h.shape
+    d, p = 8, 0.01
+    s = _case(h, d, p, p, 1500, seed=59)
+    wd = L.WindowDecoder(h, np.full(n, p, np.float32), np.full(m, p, np.float32), d,
+                         bp_iters=30, lsd_kernel=2)
+    corr, st = wd.decode(torch.from_numpy(s).cuda())
+    o = OW.window_decode(h, _f32(p, n), _f32(p, m), d, s, bp_iters=30)
+    assert np.array_equal(corr.cpu().numpy(), o["corrections"])
+    assert np.array_equal(st.cpu().numpy(), o["status"])
