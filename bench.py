@@ -300,8 +300,53 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
             "learned_lsd_p99_ms": learned["latency_ms"]["p99"], "ler_learned": ler,
             "speed_ratio_learned_over_bp": learned["value"] / best["value"]}
     prior.close()
+    # the equal-LER protocol's second network depth: fewer message-passing rounds
+    learned["rounds_sweep"] = []
+    for rounds in (2,):
+        if rounds == args.learned_rounds:
+            continue
+        pr = Prior(dec, rounds=rounds, params=init_params(args.seed))
+        tr2 = train(dec, pr, args.train_pairs, batch=4096, seed=args.seed + 17, lr=3e-3)
+        for _ in range(max(args.warmup, 1)):
+            dec.decode_learned(pr, s_dev)
+        h2 = {}
+
+        def run2():
+            h2["c"], h2["st"] = dec.decode_learned(pr, s_dev)
+
+        ms2 = timed_steps(run2, args.steps, stream, flush, barrier)
+        ler2 = float(checker.failures(e_dev, h2["c"]).float().mean().item())
+        sig2 = float(np.sqrt(max(ler2 * (1 - ler2), 1.0 / n_shots) / n_shots))
+        learned["rounds_sweep"].append({
+            "rounds": rounds, "train_pairs": tr2["pairs"], "train_s": tr2["seconds"],
+            "value": n_shots / (float(np.mean(ms2)) / 1000.0), "unit": UNIT,
+            "p99_ms": float(np.percentile(ms2, 99)), "ler": ler2, "ler_sigma": sig2,
+            "equal_ler_bp_iters": [x["bp_iters"] for x in sweep
+                                   if abs(x["ler"] - ler2) <= 2 * np.hypot(sig2, x["ler_sigma"])]})
+        pr.close()
     dec.close()
     return learned
+
+
+def cluster_histograms(dec, s_dev, max_shots=200_000):
+    """kappa (largest cluster, columns) and nu (clusters) per LSD shot of the workload, from a
+    BP-only pass and LSD on its unconverged shots (outside the timed region)."""
+    import torch
+    s = s_dev[:max_shots]
+    post, conv, _ = dec.bp(s)
+    idx = torch.nonzero(conv == 0).flatten()
+    if idx.numel() == 0:
+        return None
+    _, _, info = dec.postprocess(post[idx].contiguous(), s[idx].contiguous())
+    info = info.cpu().numpy()
+    out = {"shots": int(s.shape[0]), "lsd_shots": int(idx.numel())}
+    for k, name in ((1, "kappa"), (0, "nu"), (2, "steps")):
+        v = info[:, k]
+        hist = np.bincount(v)
+        out[name] = {"mean": float(v.mean()), "max": int(v.max()),
+                     "p99": float(np.percentile(v, 99)),
+                     "histogram": {str(i): int(c) for i, c in enumerate(hist) if c}}
+    return out
 
 
 def _timed_decode(dec, s_dev, corr, status, steps, stream, flush, barrier):
@@ -539,6 +584,34 @@ def hooks_leg(args, hx, hz, stream, flush, barrier, checker):
             "shots": shots, "bp_iters": 50, "points": out}
 
 
+def _bp_onchip_roofline(E, n, m, shots, st):
+    """BP with its message state on chip (one CTA per HGP shot): algorithmic ops against the
+    ALU peak, and the launch's algorithmic DRAM I/O (syndromes in; corrections of converged
+    shots and LLR rows of queued ones out) as GB/s."""
+    peak, src = alu_peak()
+    s_bp = st["ms_bp"] / 1e3
+    ops = OPS_PER_EDGE_ITER * E * st["bp_iterations"]
+    io = shots * m + st["bp_converged"] * n + st["lsd_shots"] * 4 * n
+    return {"bound": "alu", "achieved_tops": ops / s_bp / 1e12, "peak_tops": peak,
+            "frac": ops / s_bp / 1e12 / peak, "peak_source": src,
+            "io_bytes": int(io), "io_gbps": io / s_bp / 1e9,
+            "note": "state on chip: HBM carries only the I/O, so the HBM fraction is not the bound"}
+
+
+def alu_peak():
+    """(Tops/s, description): FP32/INT32 lanes x the maximum SM clock of MEASURED_PEAKS.json."""
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32/INT32 lanes x {mhz:.0f} MHz"
+
+
 def hgp_leg(args, stream, flush, barrier):
     """Hypergraph product of a seeded (3,4)-regular 48 x 64 matrix: H_X 3072 x 6400, p in
     {0.02, 0.05}, BP 100 + LSD-10 (and LSD-0), 10^5 shots per point."""
@@ -548,6 +621,7 @@ def hgp_leg(args, stream, flush, barrier):
     from paper_2406_18655_gb300.lsd import Decoder
     hx, hz = I.hgp_48x64()
     n = hx.shape[1]
+    hx_sum, hx_m = int(hx.sum()), hx.shape[0]
     checker = LogicalChecker(hz)
     out = []
     for p, shots in ((0.02, args.hgp_shots), (0.05, max(1, args.hgp_shots // 20))):
@@ -566,7 +640,8 @@ def hgp_leg(args, stream, flush, barrier):
                         "lsd_frac": st["lsd_shots"] / shots, "lsd_spilled": st["lsd_spilled"],
                         "mean_bp_iters": st["bp_iterations"] / shots,
                         "kernel_ms": {"bp": st["ms_bp"], "lsd": st["ms_lsd"]},
-                        "kappa_max": st["kappa_max"], "nu_max": st["nu_max"]})
+                        "kappa_max": st["kappa_max"], "nu_max": st["nu_max"],
+                        "bp_roofline": _bp_onchip_roofline(int(hx_sum), n, hx_m, shots, st)})
             dec.close()
     return {"code": "HGP of a seeded (3,4)-regular 48x64 matrix, H_X 3072x6400, E=21504",
             "bp_iters": 100, "note": "p = 0.05 percolates: fewer shots (shots / 20)",
@@ -672,6 +747,7 @@ def run_ours(args):
             kappa_max = max(kappa_max, st["kappa_max"])
             nu_max = max(nu_max, st["nu_max"])
     launches = dec.kernel_launches() - launches0
+    clusters = cluster_histograms(dec, s_dev) if rank == 0 else None
     job = job_throughput(args.shots, sum(step_ms) / args.steps, device="cuda")
     ms_per_step = job["ms_per_step"]
     value = job["per_s"]
@@ -764,6 +840,7 @@ def run_ours(args):
         "lsd_frac": lsd_frac,
         "mean_bp_iters": iters_per_step / args.shots,
         "kappa_max": kappa_max, "nu_max": nu_max,
+        "lsd_clusters": clusters,
         "kernel_ms": {"bp_kernel": bp_ms_avg, "lsd_kernel": float(np.mean(lsd_ms))},
         "roofline": roofline,
         "e2e": e2e,
