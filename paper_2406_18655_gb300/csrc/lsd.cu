@@ -760,8 +760,10 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
   __syncwarp();
 
   // ---- init: one cluster per flipped detector ----
+  // (candidate masks are read only for cluster roots, which are seeds: each seed's lane
+  // clears its mask below; the single cluster's mask is cleared here)
   if constexpr (L::kMasks)
-    for (int w = lane; w < m * Wn; w += 32) S.cand()[w] = 0;
+    if (a.single_cluster && lane < Wn) S.cand()[lane] = 0;
   for (int j = lane; j < n; j += 32) S.flab()[j] = -1;
   for (int d = lane; d < m; d += 32) {
     S.dlab()[d] = -1;
@@ -806,6 +808,8 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
         S.inv()[k + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)d;
         if constexpr (L::kMasks) {
           uint32_t* c = S.cand() + (size_t)d * Wn;
+#pragma unroll
+          for (int w = 0; w < Wn; ++w) c[w] = 0;
           const int c1 = G.chk_ptr[d + 1];
           for (int e = G.chk_ptr[d]; e < c1; ++e) {
             const unsigned rk = S.rank()[G.chk_var[e]];
@@ -933,11 +937,14 @@ __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int gra
 
   const long long count = a.count_from_ctr ? (long long)a.ctr->lsd_count : a.count;
   LsdAcc acc;
+  // the next work item is requested while the current one is decoded (lane 0 reads the
+  // atomic's result only after the shot), hiding the atomic's round trip
+  unsigned long long pending = 0;
+  if (lane == 0) pending = atomicAdd(&a.ctr->lsd_next, 1ULL);
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&a.ctr->lsd_next, 1ULL);
-    item = __shfl_sync(kFull, item, 0);
+    const unsigned long long item = __shfl_sync(kFull, pending, 0);
     if (item >= (unsigned long long)count) break;
+    if (lane == 0) pending = atomicAdd(&a.ctr->lsd_next, 1ULL);
     const long long shot = a.queue ? (long long)a.queue[item] : (long long)item;
     const float* lsrc = a.llr + (a.llr_by_item ? (long long)item : shot) * n;
     lsd_shot<MM, NN, MU>(a, G, S, lsrc, a.syndromes + shot * m, shot, lane, acc);
