@@ -33,7 +33,8 @@ def _shots(h, p, shots, seed):
 
 
 @pytest.mark.parametrize("name,p,iters", [("hgp", 0.03, 50), ("bb144", 0.08, 30),
-                                          ("ldpc_480x960", 0.06, 20), ("rep_boundary", 0.2, 8)])
+                                          ("ldpc_480x960", 0.06, 20), ("rep_boundary", 0.2, 8),
+                                          ("irreg_37x61", 0.1, 12)])
 def test_giant_bp_matches_oracle(L, name, p, iters):
     h = code(name)
     probs, e, s = _shots(h, p, 12, seed=61)
@@ -57,7 +58,8 @@ def _rounded(n, seed):
 @pytest.mark.parametrize("name,p,soft,shots", [
     ("hgp", 0.05, "bp", 24), ("hgp", 0.03, "ties", 24), ("bb144", 0.1, "bp", 40),
     ("bb72", 0.08, "ties", 40), ("ldpc_480x960", 0.06, "bp", 30),
-    ("rep_boundary", 0.15, "ties", 40), ("st_bb72_d6", 0.03, "bp", 30)])
+    ("rep_boundary", 0.15, "ties", 40), ("st_bb72_d6", 0.03, "bp", 30),
+    ("irreg_37x61", 0.08, "ties", 40), ("irreg_37x61", 0.12, "bp", 40)])
 def test_plsd_matches_oracle_lsd(L, name, p, soft, shots):
     """P-LSD with many clusters growing, colliding and merging at once gives the serial
     algorithm's clusters and corrections."""
