@@ -55,7 +55,8 @@ constexpr float kEmptyMinF = 1267650600228229401496703205376.0f;
 struct GCtr {
   // whole call
   int ns, nfront, unsolvable, overflow, uf_fail, too_big;
-  int bp_stop, bp_unsat[2], bp_iters, bp_conv;
+  int bp_stop, bp_unsat[2], bp_iters, bp_conv, bp_fail;
+  unsigned bar_arrive;  // grid barrier of the persistent BP launch
   int nu, kappa;
   int ninv[2];
   // reset every step
@@ -156,9 +157,8 @@ __global__ void __launch_bounds__(256) gbp_init(GD g) {
 // A warp reads 32 consecutive checks' k-th edges: the column indices and messages are
 // contiguous, Lam is gathered.
 template <int DCMAX>
-__global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict__ s,
-                                                  float alpha, int t) {
-  if (*(volatile int*)&g.ctr->bp_stop) return;
+__device__ __forceinline__ void check_phase(const GD& g, const uint8_t* __restrict__ s,
+                                            float alpha, int t) {
   bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
     unsigned hp = s[i] ? 0x80000000u : 0u;  // bit 31: syndrome ^ signs of Lam
@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict
       qb[k] = 0u;
       const int j = k < g.dc ? g.ell_col[(long long)k * g.m + i] : -1;
       if (j < 0) continue;
-      const float L = g.lam[j];
+      const float L = __ldcg(&g.lam[j]);  // L2: written by other blocks
       hp ^= __float_as_uint(L);
-      const float q = __fsub_rn(L, g.r[(long long)k * g.m + i]);
+      const float q = __fsub_rn(L, __ldcg(&g.r[(long long)k * g.m + i]));
       qb[k] = __float_as_uint(q);
       sx ^= qb[k];
       const float a = fabsf(q);
@@ -201,47 +201,119 @@ __global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict
     atomicOr(&g.ctr->bp_unsat[t & 1], 1);
 }
 
-// Lam of iteration t: prior plus the incoming messages in ascending check order.
-__global__ void __launch_bounds__(256) gbp_var(GD g, int t) {
+template <int DCMAX>
+__global__ void __launch_bounds__(256) gbp_check(GD g, const uint8_t* __restrict__ s,
+                                                  float alpha, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
-  if (t >= 2 && *(volatile int*)&g.ctr->bp_unsat[t & 1] == 0) {
-    // iteration t-1 satisfied the syndrome: keep its posteriors and stop
-    if (gtid() == 0) {
-      g.ctr->bp_conv = 1;
-      g.ctr->bp_iters = t - 1;
-      g.ctr->bp_stop = 1;
-    }
-    return;
-  }
-  if (gtid() == 0) {
-    g.ctr->bp_unsat[(t + 1) & 1] = 0;
-    g.ctr->bp_iters = t;
-  }
+  check_phase<DCMAX>(g, s, alpha, t);
+}
+
+// Lam of iteration t: prior plus the incoming messages in ascending check order.
+__device__ __forceinline__ void var_phase(const GD& g) {
   for (long long j = gtid(); j < g.n; j += gstride()) {
     float L = g.prior[j];
     for (int k = 0; k < g.dv; ++k) {
       const int p = g.ell_pos[(long long)k * g.n + j];
       if (p < 0) break;
-      L = __fadd_rn(L, g.r[p]);
+      L = __fadd_rn(L, __ldcg(&g.r[p]));
     }
     g.lam[j] = L;
   }
 }
 
-// The test after the last iteration T (slot (T+1) & 1, cleared by gbp_var(T)).
-__global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__ s, int slot) {
+// Iteration t's decision before its variable half: stop (true) when iteration t-1
+// satisfied the syndrome, keeping its posteriors; else clear the next test's slot.
+__device__ __forceinline__ bool bp_converged_before(const GD& g, int t) {
+  if (t >= 2 && *(volatile int*)&g.ctr->bp_unsat[t & 1] == 0) {
+    if (gtid() == 0) {
+      g.ctr->bp_conv = 1;
+      g.ctr->bp_iters = t - 1;
+      g.ctr->bp_stop = 1;
+    }
+    return true;
+  }
+  if (gtid() == 0) {
+    g.ctr->bp_unsat[(t + 1) & 1] = 0;
+    g.ctr->bp_iters = t;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(256) gbp_var(GD g, int t) {
   if (*(volatile int*)&g.ctr->bp_stop) return;
+  if (bp_converged_before(g, t)) return;
+  var_phase(g);
+}
+
+// The test after the last iteration T (slot (T+1) & 1, cleared by iteration T).
+__device__ __forceinline__ void syn_phase(const GD& g, const uint8_t* __restrict__ s, int slot) {
   bool bad = false;
   for (long long i = gtid(); i < g.m; i += gstride()) {
     unsigned hp = s[i] ? 0x80000000u : 0u;
     for (int k = 0; k < g.dc; ++k) {
       const int j = g.ell_col[(long long)k * g.m + i];
       if (j < 0) break;
-      hp ^= __float_as_uint(g.lam[j]);
+      hp ^= __float_as_uint(__ldcg(&g.lam[j]));
     }
     bad |= (hp >> 31) != 0u;
   }
   if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(&g.ctr->bp_unsat[slot], 1);
+}
+
+__global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__ s, int slot) {
+  if (*(volatile int*)&g.ctr->bp_stop) return;
+  syn_phase(g, s, slot);
+}
+
+// Grid-wide barrier of the persistent launch (all blocks co-resident: cooperative launch).
+// The arrival counter only grows; barrier b waits for b * gridDim.x arrivals.  The wait is
+// bounded: past the limit the block flags bp_fail and every block leaves at its next
+// barrier, the host reporting LSD_ERR_TIMEOUT.
+constexpr unsigned kBarSpinLimit = 1u << 24;
+
+__device__ __forceinline__ bool grid_barrier(const GD& g, unsigned target) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&g.ctr->bar_arrive, 1u);
+    unsigned spins = 0;
+    while (*(volatile unsigned*)&g.ctr->bar_arrive < target &&
+           !*(volatile int*)&g.ctr->bp_fail) {
+      if (++spins > kBarSpinLimit) {
+        atomicOr(&g.ctr->bp_fail, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)&g.ctr->bp_fail == 0;
+}
+
+// All T iterations in one launch: check half, barrier, decision, variable half, barrier.
+template <int DCMAX>
+__global__ void __launch_bounds__(256) gbp_persistent(GD g, const uint8_t* __restrict__ s,
+                                                       float alpha, int T) {
+  unsigned target = 0;
+  const unsigned nb = gridDim.x;
+  for (int t = 1; t <= T; ++t) {
+    check_phase<DCMAX>(g, s, alpha, t);
+    target += nb;
+    if (!grid_barrier(g, target)) return;
+    if (bp_converged_before(g, t)) return;
+    var_phase(g);
+    target += nb;
+    if (!grid_barrier(g, target)) return;
+  }
+  const int slot = (T + 1) & 1;
+  syn_phase(g, s, slot);
+  target += nb;
+  if (!grid_barrier(g, target)) return;
+  if (gtid() == 0) {
+    g.ctr->bp_conv = g.ctr->bp_unsat[slot] == 0;
+    g.ctr->bp_stop = 1;
+  }
 }
 
 __global__ void gbp_final(GD g, int slot) {
@@ -719,6 +791,7 @@ struct lsd_giant {
   size_t bytes = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int64_t launches = 0;
+  int coop_grid = 0;  // blocks of the persistent BP launch (0: launch per half-iteration)
 };
 
 namespace {
@@ -974,6 +1047,18 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
     if (err == cudaSuccess)
       err = cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, dev);
     for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = cudaEventCreate(&G->ev[k]);
+    // the persistent BP launch: every block must be resident at once (cooperative launch)
+    int coop = 0, per_sm = 0;
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const void* fn = dc <= 8    ? (const void*)gbp_persistent<8>
+                     : dc <= 16 ? (const void*)gbp_persistent<16>
+                                : (const void*)gbp_persistent<32>;
+    if (err == cudaSuccess && coop)
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (err == cudaSuccess && coop && per_sm > 0) {
+      const long long need = (std::max<long long>(m, n) + 255) / 256;
+      G->coop_grid = (int)std::min<long long>(need, (long long)per_sm * G->sms);
+    }
     if (err != cudaSuccess) rc = gfail(err);
   }
   g.dc = dc;
@@ -1022,6 +1107,20 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
   // iterations in chunks of 2, 4, 8, ... with a look at the stop flag after each, so that a
   // shot that converges early is not followed by the remaining iterations' launches
   bool stopped = false;
+  if (G->bp_iters > 0 && G->coop_grid > 0) {
+    // one persistent launch for every iteration (grid barriers between the halves)
+    const uint8_t* sp = syndrome;
+    float alpha = G->alpha;
+    int T = G->bp_iters;
+    void* args[] = {(void*)&g, (void*)&sp, (void*)&alpha, (void*)&T};
+    const void* fn = g.dc <= 8    ? (const void*)gbp_persistent<8>
+                     : g.dc <= 16 ? (const void*)gbp_persistent<16>
+                                  : (const void*)gbp_persistent<32>;
+    e = cudaLaunchCooperativeKernel(fn, G->coop_grid, 256, args, 0, G->st);
+    G->launches++;
+    if (e != cudaSuccess) return gfail(e);
+    stopped = true;
+  }
   for (int t = 1, chunk = 2; t <= G->bp_iters && !stopped; chunk *= 2) {
     const int t1 = std::min(G->bp_iters, t + chunk - 1);
     for (; t <= t1; ++t) {
@@ -1052,6 +1151,7 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
   }
   cudaEventRecord(G->ev[1], G->st);
   if ((rc = read_ctr(G))) return rc;
+  if (G->h_ctr->bp_fail) return LSD_ERR_TIMEOUT;
   const int conv = G->h_ctr->bp_conv, iters = G->h_ctr->bp_iters;
   if (conv) {
     gcopy_hard<<<grid, 256, 0, G->st>>>(g, correction);
