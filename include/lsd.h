@@ -421,7 +421,9 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
 /*
  * lsd_giant_decode -- BP (min-sum, flooding, early exit on H e_hat = s, Sec. 4.3), then
  * P-LSD on the posteriors when BP does not converge.  Synchronous (one host round trip per
- * growth step).
+ * growth step).  BP runs as one cooperative launch whose blocks meet at grid barriers; a
+ * barrier that waits past its bound (about a second) makes the call return
+ * LSD_ERR_TIMEOUT.
  *   syndrome     device [m] bytes.   correction  device [n] bytes (written).
  *   posteriors   device [n] float32, nullable: the BP posteriors.
  *   info         host, nullable.

@@ -1,5 +1,6 @@
 // One giant shot decoded by the whole GPU: BP (Sec. 4.3) with one thread per check and per
-// variable, then P-LSD (App. B, Alg. 2): every invalid cluster grows in parallel, clusters
+// variable, every iteration in one cooperative launch (grid barriers between the check and
+// variable halves), then P-LSD (App. B, Alg. 2): every invalid cluster grows in parallel, clusters
 // merge through a lock-free union-find, and each cluster keeps its own on-the-fly
 // elimination (Sec. 4.2) in a block of a device arena.
 //
