@@ -436,6 +436,14 @@ int lsd_giant_decode(lsd_giant* dec, const uint8_t* syndrome, uint8_t* correctio
 int lsd_giant_postprocess(lsd_giant* dec, const float* llr, const uint8_t* syndrome,
                           uint8_t* correction, lsd_giant_info* info);
 
+/* lsd_giant_test_hold_barrier -- test facility for the timeout path (no counterpart in the
+ * paper): with hold != 0, block 0 of every following BP launch withholds its arrival at the
+ * first grid barrier, so the other blocks' bounded waits run out after limit_ns and the
+ * decode returns LSD_ERR_TIMEOUT with the device still usable; hold = 0 restores normal
+ * operation and the one-second bound.  LSD_ERR_UNSUPPORTED when the device cannot run the
+ * cooperative launch. */
+int lsd_giant_test_hold_barrier(lsd_giant* dec, int32_t hold, int64_t limit_ns);
+
 /* lsd_giant_kernel_launches -- kernels launched so far by the giant-shot decoder. */
 int lsd_giant_kernel_launches(const lsd_giant* dec, int64_t* count);
 

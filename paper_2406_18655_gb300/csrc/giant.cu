@@ -268,23 +268,29 @@ __global__ void __launch_bounds__(256) gbp_syn(GD g, const uint8_t* __restrict__
 
 // Grid-wide barrier of the persistent launch (all blocks co-resident: cooperative launch).
 // The arrival counter only grows; barrier b waits for b * gridDim.x arrivals.  The wait is
-// bounded: past the limit the block flags bp_fail and every block leaves at its next
-// barrier, the host reporting LSD_ERR_TIMEOUT.
-constexpr unsigned kBarSpinLimit = 1u << 24;
+// bounded by limit_ns of the global timer: past it the block flags bp_fail and every block
+// leaves at its next barrier, the host reporting LSD_ERR_TIMEOUT.  `arrive` false (the
+// timeout test only) withholds this block's arrival.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-__device__ __forceinline__ bool grid_barrier(const GD& g, unsigned target) {
+__device__ __forceinline__ bool grid_barrier(const GD& g, unsigned target, long long limit_ns,
+                                             bool arrive = true) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(&g.ctr->bar_arrive, 1u);
-    unsigned spins = 0;
+    if (arrive) atomicAdd(&g.ctr->bar_arrive, 1u);
+    const unsigned long long t0 = global_ns();
     while (*(volatile unsigned*)&g.ctr->bar_arrive < target &&
            !*(volatile int*)&g.ctr->bp_fail) {
-      if (++spins > kBarSpinLimit) {
+      if ((long long)(global_ns() - t0) > limit_ns) {
         atomicOr(&g.ctr->bp_fail, 1);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(64);
     }
     __threadfence();
   }
@@ -293,24 +299,26 @@ __device__ __forceinline__ bool grid_barrier(const GD& g, unsigned target) {
 }
 
 // All T iterations in one launch: check half, barrier, decision, variable half, barrier.
+// hold != 0 (the timeout test only): block 0 withholds its first arrival.
 template <int DCMAX>
 __global__ void __launch_bounds__(256) gbp_persistent(GD g, const uint8_t* __restrict__ s,
-                                                       float alpha, int T) {
+                                                       float alpha, int T, long long limit_ns,
+                                                       int hold) {
   unsigned target = 0;
   const unsigned nb = gridDim.x;
   for (int t = 1; t <= T; ++t) {
     check_phase<DCMAX>(g, s, alpha, t);
     target += nb;
-    if (!grid_barrier(g, target)) return;
+    if (!grid_barrier(g, target, limit_ns, !(hold && t == 1 && blockIdx.x == 0))) return;
     if (bp_converged_before(g, t)) return;
     var_phase(g);
     target += nb;
-    if (!grid_barrier(g, target)) return;
+    if (!grid_barrier(g, target, limit_ns)) return;
   }
   const int slot = (T + 1) & 1;
   syn_phase(g, s, slot);
   target += nb;
-  if (!grid_barrier(g, target)) return;
+  if (!grid_barrier(g, target, limit_ns)) return;
   if (gtid() == 0) {
     g.ctr->bp_conv = g.ctr->bp_unsat[slot] == 0;
     g.ctr->bp_stop = 1;
@@ -793,6 +801,8 @@ struct lsd_giant {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int coop_grid = 0;  // blocks of the persistent BP launch (0: launch per half-iteration)
+  long long bar_limit_ns = 1000000000LL;  // bound of a grid-barrier wait
+  int hold_barrier = 0;                   // timeout test: block 0 withholds an arrival
 };
 
 namespace {
@@ -1113,7 +1123,9 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
     const uint8_t* sp = syndrome;
     float alpha = G->alpha;
     int T = G->bp_iters;
-    void* args[] = {(void*)&g, (void*)&sp, (void*)&alpha, (void*)&T};
+    long long limit = G->bar_limit_ns;
+    int hold = G->hold_barrier;
+    void* args[] = {(void*)&g, (void*)&sp, (void*)&alpha, (void*)&T, (void*)&limit, (void*)&hold};
     const void* fn = g.dc <= 8    ? (const void*)gbp_persistent<8>
                      : g.dc <= 16 ? (const void*)gbp_persistent<16>
                                   : (const void*)gbp_persistent<32>;
@@ -1170,6 +1182,14 @@ int lsd_giant_decode(lsd_giant* G, const uint8_t* syndrome, uint8_t* correction,
     cudaEventElapsedTime(&info->ms_bp, G->ev[0], G->ev[1]);
     cudaEventElapsedTime(&info->ms_lsd, G->ev[1], G->ev[2]);
   }
+  return LSD_OK;
+}
+
+int lsd_giant_test_hold_barrier(lsd_giant* G, int32_t hold, int64_t limit_ns) {
+  if (!G || limit_ns < 0) return LSD_ERR_INVALID_ARG;
+  if (!G->coop_grid) return LSD_ERR_UNSUPPORTED;
+  G->hold_barrier = hold ? 1 : 0;
+  G->bar_limit_ns = hold ? (long long)limit_ns : 1000000000LL;
   return LSD_OK;
 }
 

@@ -37,7 +37,7 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy",
            "lsd_window_stream_reset", "lsd_window_stream_push", "lsd_giant_create",
            "lsd_giant_decode", "lsd_giant_postprocess", "lsd_giant_kernel_launches",
-           "lsd_giant_destroy")
+           "lsd_giant_destroy", "lsd_giant_test_hold_barrier")
 
 
 class LsdError(RuntimeError):
@@ -137,6 +137,7 @@ def lib():
     L.lsd_giant_postprocess.argtypes = [P, P, P, P, C.POINTER(GiantInfo)]
     L.lsd_giant_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_giant_destroy.argtypes = [P]
+    L.lsd_giant_test_hold_barrier.argtypes = [P, C.c_int32, C.c_int64]
     L.lsd_window_stream_reset.argtypes = [P, C.c_int64]
     L.lsd_window_stream_push.argtypes = [P, P, P, P, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32)]
@@ -552,6 +553,11 @@ class GiantDecoder:
         v = C.c_int64()
         _check(lib().lsd_giant_kernel_launches(self._h, C.byref(v)), "lsd_giant_kernel_launches")
         return v.value
+
+    def test_hold_barrier(self, hold: bool, limit_ns: int = 20_000_000):
+        """Timeout-path test facility (lsd_giant_test_hold_barrier)."""
+        _check(lib().lsd_giant_test_hold_barrier(self._h, int(hold), limit_ns),
+               "lsd_giant_test_hold_barrier")
 
 
 class Prior:

@@ -160,3 +160,22 @@ def test_unsolvable_and_small_arena(L):
     big = L.GiantDecoder.from_dense(hh, probs, 5)
     corr, info = big.decode(torch.from_numpy(s[1]).cuda())
     assert np.array_equal(corr.cpu().numpy(), o["corrections"][1])
+
+
+def test_grid_barrier_timeout_leaves_the_device_usable(L):
+    """A BP grid barrier whose wait runs out (block 0 withholds its arrival through the test
+    facility) makes the decode return LSD_ERR_TIMEOUT after its bound; the next decode, with
+    the hold lifted, gives the oracle's answer."""
+    h = code("hgp")
+    probs, e, s = _shots(h, 0.03, 2, seed=89)
+    gd = L.GiantDecoder.from_dense(h, probs, 50)
+    gd.test_hold_barrier(True, limit_ns=20_000_000)
+    with pytest.raises(L.LsdError) as err:
+        gd.decode(torch.from_numpy(s[0]).cuda())
+    assert err.value.code == L.LSD_ERR_TIMEOUT
+    gd.test_hold_barrier(False)
+    o = oracle.decode(h, f64(probs), s, 50, precision=1)
+    for k in range(2):
+        corr, info = gd.decode(torch.from_numpy(s[k]).cuda())
+        assert info["status"] == o["status"][k]
+        assert np.array_equal(corr.cpu().numpy(), o["corrections"][k])
