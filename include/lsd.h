@@ -391,8 +391,9 @@ int lsd_window_destroy(lsd_window* win);
  * decoded by BP with one thread per check and per variable, then, if BP does not converge,
  * by LSD with every cluster grown in parallel: clusters take their best candidate at once,
  * merge through a lock-free union-find, and keep their own on-the-fly elimination in
- * blocks of a device arena.  Corrections and status equal lsd_decode_batch's (LSD-0) on the
- * same shot.  Limits: a cluster spans at most 8192 detectors (LSD_ERR_UNSUPPORTED beyond);
+ * blocks of a device arena; with lsd_order = mu > 0, mu more growth steps for every cluster
+ * and the local OSD-E or OSD-CS reprocessing of LSD-mu follow.  Corrections and status equal
+ * lsd_decode_batch's on the same shot.  Limits: a cluster spans at most 8192 detectors (LSD_ERR_UNSUPPORTED beyond);
  * the arena holds every block a call allocates (LSD_ERR_ADMISSION when it runs out).
  * ------------------------------------------------------------------------------------ */
 typedef struct lsd_giant lsd_giant;
@@ -409,14 +410,16 @@ typedef struct lsd_giant_info {
 
 /*
  * lsd_giant_create -- decoder of one large check matrix.
- *   m, n, nnz, rows, cols, channel_probs, bp_iters   as lsd_create (host COO, no duplicates).
+ *   m, n, nnz, rows, cols, channel_probs, bp_iters, lsd_order   as lsd_create (host COO, no
+ *                  duplicates; lsd_order = mu of LSD-mu, App. D).
  *   arena_bytes    device bytes of the cluster arena; 0 = 256 MiB.
- *   opt            nullable; ms_scaling and stream are used, the other fields ignored.
+ *   opt            nullable; ms_scaling, osd_method, osd_cs_order and stream are used, the
+ *                  other fields ignored.
  * Device memory: about 20 (m + n) + 12 E bytes plus the arena.  Synchronizes.
  */
 int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
                      const int32_t* cols, const float* channel_probs, int32_t bp_iters,
-                     size_t arena_bytes, const lsd_options* opt);
+                     int32_t lsd_order, size_t arena_bytes, const lsd_options* opt);
 
 /*
  * lsd_giant_decode -- BP (min-sum, flooding, early exit on H e_hat = s, Sec. 4.3), then

@@ -55,7 +55,7 @@ constexpr float kEmptyMinF = 1267650600228229401496703205376.0f;
 
 struct GCtr {
   // whole call
-  int ns, nfront, unsolvable, overflow, uf_fail, too_big;
+  int ns, nfront, unsolvable, overflow, uf_fail, too_big, ndep, dep_top;
   int bp_stop, bp_unsat[2], bp_iters, bp_conv, bp_fail;
   unsigned bar_arrive;  // grid barrier of the persistent BP launch
   int nu, kappa;
@@ -87,6 +87,11 @@ struct GD {
   unsigned* arena;
   unsigned long long arena_words;
   GCtr* ctr;
+  // LSD-mu (App. D): growth steps, reprocessing (-1 OSD-E, w >= 0 OSD-CS-w), cost weights;
+  // dependent columns met by the elimination [n] and their per-root buckets
+  int order, osd_cs;
+  const long long* wfix;
+  int *dep_f, *dep_rank, *dep_bucket, *depcnt, *depoff;
 };
 
 __host__ __device__ inline size_t blk_words(int C) {
@@ -406,6 +411,7 @@ __global__ void __launch_bounds__(256) glsd_seed(GD g, const uint8_t* __restrict
     g.extra[ord] = 0;
     g.newslots[ord] = 0;
     g.newcnt[ord] = 0;
+    g.depcnt[ord] = 0;
     const Blk B = blk_at(g, (unsigned long long)off, C);
     for (size_t w = 0; w < words; ++w) B.b[w] = 0u;
     for (int p = 0; p < C; ++p) B.pcol()[p] = -1;
@@ -434,14 +440,14 @@ __global__ void __launch_bounds__(256) glsd_find(GD g, const float* __restrict__
 }
 
 // parallel_union: each invalid cluster takes its pick; collisions unite.
-__global__ void __launch_bounds__(256) glsd_union(GD g, int par) {
+__global__ void __launch_bounds__(256) glsd_union(GD g, int par, int strict) {
   const int cnt = g.ctr->ninv[par];
   const int* inv = par ? g.inv1 : g.inv0;
   for (long long t = gtid(); t < cnt; t += gstride()) {
     const int r = inv[t];
     const unsigned long long key = g.best[r];
     if (key == kNoKey) {
-      atomicOr(&g.ctr->unsolvable, 1);
+      if (strict) atomicOr(&g.ctr->unsolvable, 1);  // LSD-mu: a full cluster just stops
       continue;
     }
     const int f = (int)(key & 0xffffffffu);
@@ -649,7 +655,10 @@ __device__ void gadd_column(const GD& g, const Blk& D, int nslots, int f, int la
       p = (c * 32 + wl) * 32 + __ffs(word) - 1;
     }
   }
-  if (p < 0) return;  // dependent column: the cluster's span does not change
+  if (p < 0) {  // dependent column: the span does not change; LSD-mu lists it
+    if (g.order > 0 && lane == 0) g.dep_f[atomicAdd(&g.ctr->ndep, 1)] = f;
+    return;
+  }
   const int pw = p >> 5;
   const unsigned pb = 1u << (p & 31);
 #pragma unroll
@@ -758,6 +767,204 @@ __global__ void __launch_bounds__(256) glsd_collect(GD g, int par_next) {
       g.best[x] = kNoKey;
       inv[atomicAdd(&g.ctr->ninv[par_next], 1)] = (int)x;
     }
+  }
+}
+
+// LSD-mu: every root grows (App. D's extra steps).
+__global__ void __launch_bounds__(256) glsd_collect_all(GD g, int par) {
+  const int ns = g.ctr->ns;
+  int* inv = par ? g.inv1 : g.inv0;
+  for (long long x = gtid(); x < ns; x += gstride()) {
+    const bool root = g.parent[x] == x;
+    g.grow[x] = root ? 1 : 0;
+    if (root) {
+      g.best[x] = kNoKey;
+      inv[atomicAdd(&g.ctr->ninv[par], 1)] = (int)x;
+    }
+  }
+}
+
+// Dependent columns grouped by final root: rank in the root's bucket, bucket offsets, placement.
+__global__ void __launch_bounds__(256) glsd_dep_rank(GD g) {
+  const int nd = g.ctr->ndep;
+  for (long long k = gtid(); k < nd; k += gstride())
+    g.dep_rank[k] = atomicAdd(&g.depcnt[g.parent[g.fst[g.dep_f[k]]]], 1);
+}
+
+__global__ void __launch_bounds__(256) glsd_dep_offsets(GD g) {
+  const int ns = g.ctr->ns;
+  for (long long x = gtid(); x < ns; x += gstride())
+    if (g.parent[x] == x && g.depcnt[x] > 0) g.depoff[x] = atomicAdd(&g.ctr->dep_top, g.depcnt[x]);
+}
+
+__global__ void __launch_bounds__(256) glsd_dep_place(GD g) {
+  const int nd = g.ctr->ndep;
+  for (long long k = gtid(); k < nd; k += gstride()) {
+    const int R = g.parent[g.fst[g.dep_f[k]]];
+    g.dep_bucket[g.depoff[R] + g.dep_rank[k]] = g.dep_f[k];
+  }
+}
+
+// Cost of root block D's local solution (xsol) with the dependent columns i1, i2 of the
+// sorted list flipped (-1 none): tw vectors at tw + i * wc.
+__device__ long long gpattern_cost(const GD& g, const Blk& D, int wc, const unsigned* tw,
+                                   const int* cols, int i1, int i2) {
+  long long cost = 0;
+  for (int w = 0; w < wc; ++w) {
+    unsigned v = D.xsol()[w];
+    if (i1 >= 0) v ^= tw[(size_t)i1 * wc + w];
+    if (i2 >= 0) v ^= tw[(size_t)i2 * wc + w];
+    while (v) {
+      const int b = __ffs(v) - 1;
+      v &= v - 1;
+      cost += g.wfix[D.pcol()[w * 32 + b]];
+    }
+  }
+  if (i1 >= 0) cost += g.wfix[cols[i1]];
+  if (i2 >= 0) cost += g.wfix[cols[i2]];
+  return cost;
+}
+
+// LSD-mu reprocessing of every root with dependent columns (App. D), as the batch kernels:
+// OSD-E over the first min(mu, #dependent) in key order (ties to the smaller pattern), or
+// the combination sweep OSD-CS-w (no flip, every single, every pair among the first w; ties
+// to the earlier pattern).  A dependent column's representation tw over the pivots is
+// recomputed from the root's final rows (the pivots only grow, so it is the same unique
+// combination).  Chosen dependent columns go straight to the correction; xsol takes their tw.
+__global__ void __launch_bounds__(256) glsd_reprocess(GD g, const float* __restrict__ llr,
+                                                       uint8_t* __restrict__ corr) {
+  const int lane = threadIdx.x & 31;
+  const int ns = g.ctr->ns;
+  for (long long x = gwarp(); x < ns; x += gwarps()) {
+    if (g.parent[x] != x) continue;
+    const int cnt = g.depcnt[x];
+    if (cnt == 0) continue;
+    const Blk D = blk_of(g, (int)x);
+    const int wc = (g.nsl[x] + 31) >> 5;
+    const int* bk = g.dep_bucket + g.depoff[x];
+    long long off = 0;
+    if (lane == 0) off = arena_alloc(g, 1 + 2 * (size_t)cnt + (size_t)cnt * (1 + wc));
+    off = __shfl_sync(kFullMask, off, 0);
+    if (off < 0) continue;
+    off += off & 1;  // 8-byte alignment of the keys
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(g.arena + off);  // [cnt]
+    int* cols = reinterpret_cast<int*>(g.arena + off + 2 * (size_t)cnt);            // [cnt]
+    unsigned* tw = g.arena + off + 3 * (size_t)cnt;                                  // [cnt][wc]
+    // sort the bucket by (LLR, index) key: rank of each entry among the bucket
+    for (int u = lane; u < cnt; u += 32) {
+      const int f = bk[u];
+      const unsigned long long ku = llr_key(llr[f], f);
+      int pos = 0;
+      for (int v = 0; v < cnt; ++v) {
+        const int fv = bk[v];
+        pos += llr_key(llr[fv], fv) < ku ? 1 : 0;
+      }
+      cols[pos] = f;
+      keys[pos] = ku;
+    }
+    __syncwarp();
+    // representations over the pivots
+    for (int i = 0; i < cnt; ++i) {
+      const int f = cols[i];
+      for (int w = lane; w < wc; w += 32) {
+        unsigned t = 0u;
+        for (int q = g.var_ptr[f]; q < g.var_ptr[f + 1]; ++q) {
+          const int sl = g.lslot[g.var_chk[q]];
+          if (D.pcol()[sl] >= 0) t ^= D.T(sl)[w];
+        }
+        tw[(size_t)i * wc + w] = t;
+      }
+    }
+    __syncwarp();
+    long long bc = LLONG_MAX;
+    int b1 = -1, b2 = -1;
+    if (g.osd_cs < 0) {
+      const int nt = min(g.order, cnt);
+      int bt = 0;
+      for (int t = lane; t < (1 << nt); t += 32) {
+        long long cost = 0;
+        for (int w = 0; w < wc; ++w) {
+          unsigned v = D.xsol()[w];
+          for (int k = 0; k < nt; ++k)
+            if ((t >> k) & 1) v ^= tw[(size_t)k * wc + w];
+          while (v) {
+            const int b = __ffs(v) - 1;
+            v &= v - 1;
+            cost += g.wfix[D.pcol()[w * 32 + b]];
+          }
+        }
+        for (int k = 0; k < nt; ++k)
+          if ((t >> k) & 1) cost += g.wfix[cols[k]];
+        if (cost < bc) {
+          bc = cost;
+          bt = t;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long oc = __shfl_xor_sync(kFullMask, bc, o);
+        const int ot = __shfl_xor_sync(kFullMask, bt, o);
+        if (oc < bc || (oc == bc && ot < bt)) {
+          bc = oc;
+          bt = ot;
+        }
+      }
+      if (bt == 0) continue;
+      for (int w = lane; w < wc; w += 32) {
+        unsigned delta = 0u;
+        for (int k = 0; k < nt; ++k)
+          if ((bt >> k) & 1) delta ^= tw[(size_t)k * wc + w];
+        D.xsol()[w] ^= delta;
+      }
+      for (int k = lane; k < nt; k += 32)
+        if ((bt >> k) & 1) corr[cols[k]] = 1;
+      __syncwarp();
+      continue;
+    }
+    // combination sweep
+    const int wp = min(g.osd_cs, cnt);
+    int bcls = 3;
+    unsigned long long bkey = 0;
+    auto consider = [&](long long c, int cls, unsigned long long key, int i1, int i2) {
+      if (c < bc || (c == bc && (cls < bcls || (cls == bcls && key < bkey)))) {
+        bc = c;
+        bcls = cls;
+        bkey = key;
+        b1 = i1;
+        b2 = i2;
+      }
+    };
+    if (lane == 0) consider(gpattern_cost(g, D, wc, tw, cols, -1, -1), 0, 0, -1, -1);
+    for (int i = lane; i < cnt; i += 32)
+      consider(gpattern_cost(g, D, wc, tw, cols, i, -1), 1, keys[i], i, -1);
+    const int npairs = wp * (wp - 1) / 2;
+    for (int t = lane; t < npairs; t += 32) {
+      int i = 0, rem = t;
+      while (rem >= wp - 1 - i) {
+        rem -= wp - 1 - i;
+        ++i;
+      }
+      const int j = i + 1 + rem;
+      consider(gpattern_cost(g, D, wc, tw, cols, i, j), 2, (unsigned long long)(i * 16 + j), i, j);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long oc = __shfl_xor_sync(kFullMask, bc, o);
+      const int ocls = __shfl_xor_sync(kFullMask, bcls, o);
+      const unsigned long long okey = __shfl_xor_sync(kFullMask, bkey, o);
+      const int o1 = __shfl_xor_sync(kFullMask, b1, o);
+      const int o2 = __shfl_xor_sync(kFullMask, b2, o);
+      consider(oc, ocls, okey, o1, o2);
+    }
+    if (b1 < 0) continue;
+    for (int w = lane; w < wc; w += 32) {
+      unsigned delta = tw[(size_t)b1 * wc + w];
+      if (b2 >= 0) delta ^= tw[(size_t)b2 * wc + w];
+      D.xsol()[w] ^= delta;
+    }
+    if (lane == 0) {
+      corr[cols[b1]] = 1;
+      if (b2 >= 0) corr[cols[b2]] = 1;
+    }
+    __syncwarp();
   }
 }
 
@@ -883,7 +1090,7 @@ int run_plsd(lsd_giant* G, const float* llr, const uint8_t* s, uint8_t* corr,
     if (e != cudaSuccess) return gfail(e);
     glsd_find<<<grid, 256, 0, G->st>>>(g, llr);
     if ((rc = check_launch(G))) return rc;
-    glsd_union<<<grid, 256, 0, G->st>>>(g, par);
+    glsd_union<<<grid, 256, 0, G->st>>>(g, par, 1);
     if ((rc = check_launch(G))) return rc;
     glsd_flatten<<<grid, 256, 0, G->st>>>(g);
     if ((rc = check_launch(G))) return rc;
@@ -908,6 +1115,46 @@ int run_plsd(lsd_giant* G, const float* llr, const uint8_t* s, uint8_t* corr,
     ++steps;
     par = nxt;
   }
+  // ---- LSD-mu: mu more steps in which every cluster grows, then local reprocessing ----
+  if (status == LSD_SHOT_OK_LSD && g.order > 0) {
+    for (int e = 0; e < g.order; ++e) {
+      cudaError_t err = cudaMemsetAsync(&g.ctr->nmerged, 0, 6 * sizeof(int), G->st);
+      if (err == cudaSuccess) err = cudaMemsetAsync(&g.ctr->ninv[par], 0, sizeof(int), G->st);
+      if (err != cudaSuccess) return gfail(err);
+      glsd_collect_all<<<grid, 256, 0, G->st>>>(g, par);
+      if ((rc = check_launch(G))) return rc;
+      glsd_find<<<grid, 256, 0, G->st>>>(g, llr);
+      if ((rc = check_launch(G))) return rc;
+      glsd_union<<<grid, 256, 0, G->st>>>(g, par, 0);
+      if ((rc = check_launch(G))) return rc;
+      glsd_flatten<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      glsd_plan<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      glsd_relocate<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      glsd_absorb<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      glsd_claim<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      glsd_add<<<grid, 256, 0, G->st>>>(g);
+      if ((rc = check_launch(G))) return rc;
+      if ((rc = read_ctr(G))) return rc;
+      const GCtr& h = *G->h_ctr;
+      if (h.overflow) return LSD_ERR_ADMISSION;
+      if (h.uf_fail) return LSD_ERR_TIMEOUT;
+      if (h.too_big) return LSD_ERR_UNSUPPORTED;
+      if (h.nnew == 0 && h.nclaim == 0 && h.nmerged == 0) break;  // nothing could grow
+    }
+    glsd_dep_rank<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_dep_offsets<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_dep_place<<<grid, 256, 0, G->st>>>(g);
+    if ((rc = check_launch(G))) return rc;
+    glsd_reprocess<<<grid, 256, 0, G->st>>>(g, llr, corr);
+    if ((rc = check_launch(G))) return rc;
+  }
   glsd_solve<<<grid, 256, 0, G->st>>>(g, corr, status == LSD_SHOT_OK_LSD ? 1 : 0);
   if ((rc = check_launch(G))) return rc;
   if ((rc = read_ctr(G))) return rc;
@@ -928,7 +1175,7 @@ extern "C" {
 
 int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
                      const int32_t* cols, const float* channel_probs, int32_t bp_iters,
-                     size_t arena_bytes, const lsd_options* opt) {
+                     int32_t lsd_order, size_t arena_bytes, const lsd_options* opt) {
   if (!out) return LSD_ERR_INVALID_ARG;
   *out = nullptr;
   if (m < 1 || n < 1 || nnz < 1 || nnz >= INT32_MAX || !rows || !cols || !channel_probs ||
@@ -936,7 +1183,11 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
     return LSD_ERR_INVALID_ARG;
   lsd_options o{};
   if (opt) o = *opt;
-  if (o.ms_scaling < 0.f) return LSD_ERR_INVALID_ARG;
+  if (o.ms_scaling < 0.f || lsd_order < 0 || o.osd_method < 0 || o.osd_method > 1 ||
+      o.osd_cs_order < 0 || o.osd_cs_order > kMaxCsOrder ||
+      (o.osd_method == 0 && o.osd_cs_order != 0) ||
+      lsd_order > (o.osd_method == 1 ? kMaxCsGrowth : kMaxOrder))
+    return LSD_ERR_INVALID_ARG;
   for (int j = 0; j < n; ++j)
     if (!(channel_probs[j] > 0.f && channel_probs[j] < 1.f)) return LSD_ERR_INVALID_ARG;
   std::vector<std::pair<int, int>> e((size_t)nnz);
@@ -1020,6 +1271,11 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
   A(&g.best, m);
   A(&g.blk, m);
   A(&g.nc_key, m);
+  A(&g.dep_f, n);
+  A(&g.dep_rank, n);
+  A(&g.dep_bucket, n);
+  A(&g.depcnt, m);
+  A(&g.depoff, m);
   A(&g.arena, words);
   A(&g.ctr, 1);
   g.arena_words = words;
@@ -1074,6 +1330,9 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
   }
   g.dc = dc;
   g.dv = dv;
+  g.order = lsd_order;
+  g.osd_cs = o.osd_method == 1 ? o.osd_cs_order : -1;
+  g.wfix = d_wfix;
   g.ell_col = d_ell_col;
   g.ell_pos = d_ell_pos;
   g.chk_ptr = d_chk_ptr;

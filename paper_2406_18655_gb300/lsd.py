@@ -132,7 +132,7 @@ def lib():
     L.lsd_window_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
     L.lsd_window_destroy.argtypes = [P]
     L.lsd_giant_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int64, P, P, P,
-                                    C.c_int32, C.c_size_t, C.POINTER(Options)]
+                                    C.c_int32, C.c_int32, C.c_size_t, C.POINTER(Options)]
     L.lsd_giant_decode.argtypes = [P, P, P, P, C.POINTER(GiantInfo)]
     L.lsd_giant_postprocess.argtypes = [P, P, P, P, C.POINTER(GiantInfo)]
     L.lsd_giant_kernel_launches.argtypes = [P, C.POINTER(C.c_int64)]
@@ -481,8 +481,9 @@ class GiantDecoder:
     and per variable, then P-LSD (Alg. 2).  ``rows``, ``cols`` are the COO list of H (no
     dense matrix is needed); :meth:`from_dense` takes a 0/1 matrix."""
 
-    def __init__(self, m: int, n: int, rows, cols, channel_probs, bp_iters: int, *,
-                 arena_bytes: int = 0, ms_scaling: float = 0.0, stream=None):
+    def __init__(self, m: int, n: int, rows, cols, channel_probs, bp_iters: int,
+                 lsd_order: int = 0, *, osd_cs: int | None = None, arena_bytes: int = 0,
+                 ms_scaling: float = 0.0, stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         rows = np.ascontiguousarray(rows, np.int32)
@@ -494,21 +495,23 @@ class GiantDecoder:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt = Options()
         opt.ms_scaling = ms_scaling
+        opt.osd_method = 0 if osd_cs is None else 1
+        opt.osd_cs_order = 0 if osd_cs is None else osd_cs
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         handle = C.c_void_p()
         _check(lib().lsd_giant_create(C.byref(handle), self.m, self.n, rows.size,
                                       rows.ctypes.data_as(C.c_void_p),
                                       cols.ctypes.data_as(C.c_void_p),
-                                      p.ctypes.data_as(C.c_void_p), bp_iters, arena_bytes,
-                                      C.byref(opt)),
+                                      p.ctypes.data_as(C.c_void_p), bp_iters, lsd_order,
+                                      arena_bytes, C.byref(opt)),
                "lsd_giant_create")
         self._h = handle
 
     @classmethod
-    def from_dense(cls, h, channel_probs, bp_iters: int, **kw):
+    def from_dense(cls, h, channel_probs, bp_iters: int, lsd_order: int = 0, **kw):
         h = np.asarray(h, dtype=np.uint8)
         r, c = np.nonzero(h)
-        return cls(h.shape[0], h.shape[1], r, c, channel_probs, bp_iters, **kw)
+        return cls(h.shape[0], h.shape[1], r, c, channel_probs, bp_iters, lsd_order, **kw)
 
     def close(self):
         if getattr(self, "_h", None):

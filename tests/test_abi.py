@@ -89,7 +89,8 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lsdlib):
     assert L.lsd_window_destroy(None) == 0
     # giant-shot decoder: no edges, a bad index, a bad probability
     for r, c, pp, nnz in ((rows, cols, p, 0), (bad, cols, p, 3), (rows, cols, badp, 3)):
-        assert L.lsd_giant_create(C.byref(h), 2, 2, nnz, P(r), P(c), P(pp), 10, 0, None) == -1
+        assert L.lsd_giant_create(C.byref(h), 2, 2, nnz, P(r), P(c), P(pp), 10, 0, 0, None) == -1
+    assert L.lsd_giant_create(C.byref(h), 2, 2, 3, P(rows), P(cols), P(p), 10, 13, 0, None) == -1
     assert L.lsd_giant_destroy(None) == 0
     assert L.lsd_giant_decode(None, None, None, None, None) == -1
     assert L.lsd_window_decode(None, 1, None, None, None, None) == -1

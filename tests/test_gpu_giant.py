@@ -80,6 +80,28 @@ def test_plsd_matches_oracle_lsd(L, name, p, soft, shots):
                                                               r["steps"][k])
 
 
+@pytest.mark.parametrize("name,p,order,osd_cs,shots", [
+    ("bb144", 0.06, 6, None, 30), ("bb144", 0.08, 3, None, 30), ("bb72", 0.08, 10, None, 30),
+    ("bb144", 0.06, 14, 4, 30), ("bb144", 0.08, 29, 8, 20), ("hgp", 0.04, 10, None, 12),
+    ("hgp", 0.04, 20, 4, 12), ("ldpc_480x960", 0.05, 6, 0, 20)])
+def test_plsd_mu_matches_oracle(L, name, p, order, osd_cs, shots):
+    """LSD-mu in the giant shot: mu growth steps for every cluster, then OSD-E or OSD-CS-w per
+    cluster, as the serial algorithm (App. D)."""
+    h = code(name)
+    probs, e, s = _shots(h, p, shots, seed=97 + order)
+    llr, *_ = oracle.bp(h, f64(probs), s, 30, precision=1)
+    llr = llr.astype(np.float32)
+    r = oracle.lsd(h, s, llr.astype(np.float64), order=order, probs=f64(probs),
+                   osd_cs=-1 if osd_cs is None else osd_cs)
+    gd = L.GiantDecoder.from_dense(h, probs, 30, order, osd_cs=osd_cs)
+    for k in range(shots):
+        corr, info = gd.postprocess(torch.from_numpy(llr[k]).cuda(), torch.from_numpy(s[k]).cuda())
+        assert info["status"] == r["status"][k]
+        assert np.array_equal(corr.cpu().numpy(), r["corrections"][k])
+        assert (info["nu"], info["kappa"], info["steps"]) == (r["nu"][k], r["kappa"][k],
+                                                              r["steps"][k])
+
+
 def test_giant_decode_matches_oracle_and_batch_decoder(L):
     """End to end on the HGP code: the giant path, the batch decoder and the oracle agree."""
     h = code("hgp")
