@@ -501,8 +501,12 @@ def giant_leg(args, stream):
     for r0, c0 in ((240, 320), (480, 640)):
         base = I.random_regular_ldpc(r0, c0, 3, 4, seed=2406 + r0)
         m, n, rows, cols = I.hgp_coo(base)
-        for p in (0.01, 0.03):
-            gd = GiantDecoder(m, n, rows, cols, np.full(n, p, np.float32), 100, stream=stream)
+        variants = [(0.01, 0, None), (0.03, 0, None)]
+        if r0 == 480:
+            variants.append((0.03, 10, 4))  # LSD-10 with OSD-CS-4 on the largest shot
+        for p, order, osd_cs in variants:
+            gd = GiantDecoder(m, n, rows, cols, np.full(n, p, np.float32), 100, order,
+                              osd_cs=osd_cs, stream=stream)
             infos, wall = [], []
             for seed in range(4):
                 e = I.sample_errors(args.seed + seed, 1, np.full(n, p))[0]
@@ -517,7 +521,8 @@ def giant_leg(args, stream):
                 info["explains_syndrome"] = bool(ok)
                 infos.append(info)
             out.append({"code": f"HGP of ({r0}x{c0}) (3,4)-regular", "m": m, "n": n,
-                        "edges": int(rows.size), "p": p, "bp_iters": 100,
+                        "edges": int(rows.size), "p": p, "bp_iters": 100, "lsd_order": order,
+                        "osd": "-" if not order else ("E" if osd_cs is None else f"CS-{osd_cs}"),
                         "ms_per_shot": float(np.mean(wall)),
                         "ms_bp": float(np.mean([i["ms_bp"] for i in infos])),
                         "ms_lsd": float(np.mean([i["ms_lsd"] for i in infos])),
