@@ -58,7 +58,7 @@ struct GCtr {
   int ns, nfront, unsolvable, overflow, uf_fail, too_big, ndep, dep_top;
   int bp_stop, bp_unsat[2], bp_iters, bp_conv, bp_fail;
   unsigned bar_arrive;  // grid barrier of the persistent BP launch
-  int nu, kappa, lsd_steps;
+  int nu, kappa;
   int ninv[2];
   // reset every step
   int nmerged, nchg, nnew, nclaim, bucket_top, pad;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256) glsd_seed(GD g, const uint8_t* __restrict
 __global__ void glsd_seed_count(GD g) { g.ctr->ninv[0] = g.ctr->ns; }
 
 // find_candidate: every live candidate offers its key to the growing roots next to it.
-__device__ __forceinline__ void ph_find(const GD& g, const float* __restrict__ llr) {
+__global__ void __launch_bounds__(256) glsd_find(GD g, const float* __restrict__ llr) {
   const int nf = g.ctr->nfront;
   for (long long i = gtid(); i < nf; i += gstride()) {
     const int f = g.front[i];
@@ -439,10 +439,8 @@ __device__ __forceinline__ void ph_find(const GD& g, const float* __restrict__ l
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_find(GD g, const float* __restrict__ llr) { ph_find(g, llr); }
-
 // parallel_union: each invalid cluster takes its pick; collisions unite.
-__device__ __forceinline__ void ph_union(const GD& g, int par, int strict) {
+__global__ void __launch_bounds__(256) glsd_union(GD g, int par, int strict) {
   const int cnt = g.ctr->ninv[par];
   const int* inv = par ? g.inv1 : g.inv0;
   for (long long t = gtid(); t < cnt; t += gstride()) {
@@ -476,14 +474,10 @@ __device__ __forceinline__ void ph_union(const GD& g, int par, int strict) {
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_union(GD g, int par, int strict) { ph_union(g, par, strict); }
-
-__device__ __forceinline__ void ph_flatten(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_flatten(GD g) {
   const int ns = g.ctr->ns;
   for (long long x = gtid(); x < ns; x += gstride()) g.parent[x] = gfind(g, (int)x);
 }
-
-__global__ void __launch_bounds__(256) glsd_flatten(GD g) { ph_flatten(g); }
 
 __device__ __forceinline__ void mark_changed(const GD& g, int R) {
   if (atomicCAS(&g.mark[R], 0, 1) == 0) g.chg[atomicAdd(&g.ctr->nchg, 1)] = R;
@@ -491,7 +485,7 @@ __device__ __forceinline__ void mark_changed(const GD& g, int R) {
 
 // Offsets inside each root's grown block: absorbed clusters, then new detectors; ranks of
 // the new columns.
-__device__ __forceinline__ void ph_plan(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_plan(GD g) {
   const int nm = g.ctr->nmerged, nc = g.ctr->nclaim, nn = g.ctr->nnew;
   for (long long t = gtid(); t < (long long)nm + nc + nn; t += gstride()) {
     if (t < nm) {
@@ -513,11 +507,9 @@ __device__ __forceinline__ void ph_plan(const GD& g) {
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_plan(GD g) { ph_plan(g); }
-
 // A root that merged or outgrew its block moves to a new zeroed block (its own slots copied
 // at the same positions); every changed root reserves room for its new columns' list.
-__device__ __forceinline__ void ph_relocate(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_relocate(GD g) {
   const int lane = threadIdx.x & 31;
   const int nchg = g.ctr->nchg;
   for (long long t = gwarp(); t < nchg; t += gwarps()) {
@@ -565,8 +557,6 @@ __device__ __forceinline__ void ph_relocate(const GD& g) {
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_relocate(GD g) { ph_relocate(g); }
-
 // Word w of a bit vector `src` (sw words) shifted up by `sh` bits.
 __device__ __forceinline__ unsigned shifted_word(const unsigned* src, int sw, int sh, int w) {
   const int q = sh >> 5, b = sh & 31;
@@ -577,7 +567,7 @@ __device__ __forceinline__ unsigned shifted_word(const unsigned* src, int sw, in
 }
 
 // Absorbed clusters copied into their root's block at their offset (rows shifted).
-__device__ __forceinline__ void ph_absorb(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_absorb(GD g) {
   const int lane = threadIdx.x & 31;
   const int nm = g.ctr->nmerged;
   for (long long t = gwarp(); t < nm; t += gwarps()) {
@@ -611,11 +601,9 @@ __device__ __forceinline__ void ph_absorb(const GD& g) {
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_absorb(GD g) { ph_absorb(g); }
-
 // New detectors take their slots; faults next to them become candidates (Def. 4.3); the new
 // columns are placed in their root's list.
-__device__ __forceinline__ void ph_claim(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_claim(GD g) {
   const int nc = g.ctr->nclaim, nn = g.ctr->nnew;
   if (g.ctr->too_big || g.ctr->overflow) return;
   for (long long t = gtid(); t < (long long)nc + nn; t += gstride()) {
@@ -635,8 +623,6 @@ __device__ __forceinline__ void ph_claim(const GD& g) {
     }
   }
 }
-
-__global__ void __launch_bounds__(256) glsd_claim(GD g) { ph_claim(g); }
 
 // Adds fault f to the elimination of block D (nslots slots in use), as the batch kernels do.
 __device__ void gadd_column(const GD& g, const Blk& D, int nslots, int f, int lane) {
@@ -723,7 +709,7 @@ __device__ void gadd_column(const GD& g, const Blk& D, int nslots, int f, int la
 
 // on_the_fly_elimination of every changed root: its new columns in key order, then its
 // validity.
-__device__ __forceinline__ void ph_add(const GD& g) {
+__global__ void __launch_bounds__(256) glsd_add(GD g) {
   const int lane = threadIdx.x & 31;
   const int nchg = g.ctr->nchg;
   if (g.ctr->too_big || g.ctr->overflow) return;
@@ -771,9 +757,7 @@ __device__ __forceinline__ void ph_add(const GD& g) {
   }
 }
 
-__global__ void __launch_bounds__(256) glsd_add(GD g) { ph_add(g); }
-
-__device__ __forceinline__ void ph_collect(const GD& g, int par_next) {
+__global__ void __launch_bounds__(256) glsd_collect(GD g, int par_next) {
   const int ns = g.ctr->ns;
   int* inv = par_next ? g.inv1 : g.inv0;
   for (long long x = gtid(); x < ns; x += gstride()) {
@@ -784,60 +768,6 @@ __device__ __forceinline__ void ph_collect(const GD& g, int par_next) {
       inv[atomicAdd(&g.ctr->ninv[par_next], 1)] = (int)x;
     }
   }
-}
-
-__global__ void __launch_bounds__(256) glsd_collect(GD g, int par_next) { ph_collect(g, par_next); }
-
-// The whole LSD-0 loop (Alg. 2's while loop) in one cooperative launch: the nine phases of a
-// step separated by grid barriers, the loop's exit read by every block from the counters
-// after the last barrier of a step (so every block takes the same decision).  Counts the
-// steps that completed without an invalid cluster running out of candidates.
-__global__ void __launch_bounds__(256) glsd_persistent(GD g, const float* __restrict__ llr,
-                                                       long long limit_ns, int max_steps) {
-  volatile GCtr* c = g.ctr;
-  const unsigned nb = gridDim.x;
-  unsigned target = 0;
-  int par = 0, steps = 0;
-  for (;;) {
-    if (c->overflow || c->uf_fail || c->too_big || c->unsolvable || c->ninv[par] == 0 ||
-        steps > max_steps)
-      break;
-    const int nxt = par ^ 1;
-    if (gtid() == 0) {
-      c->nmerged = 0;
-      c->nchg = 0;
-      c->nnew = 0;
-      c->nclaim = 0;
-      c->bucket_top = 0;
-      c->ninv[nxt] = 0;
-    }
-#define GLSD_BARRIER                                   \
-  target += nb;                                        \
-  if (!grid_barrier(g, target, limit_ns)) return;
-    GLSD_BARRIER
-    ph_find(g, llr);
-    GLSD_BARRIER
-    ph_union(g, par, 1);
-    GLSD_BARRIER
-    ph_flatten(g);
-    GLSD_BARRIER
-    ph_plan(g);
-    GLSD_BARRIER
-    ph_relocate(g);
-    GLSD_BARRIER
-    ph_absorb(g);
-    GLSD_BARRIER
-    ph_claim(g);
-    GLSD_BARRIER
-    ph_add(g);
-    GLSD_BARRIER
-    ph_collect(g, nxt);
-    GLSD_BARRIER
-#undef GLSD_BARRIER
-    if (!c->unsolvable) ++steps;
-    par = nxt;
-  }
-  if (gtid() == 0) c->lsd_steps = steps;
 }
 
 // LSD-mu: every root grows (App. D's extra steps).
@@ -1078,7 +1008,6 @@ struct lsd_giant {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int coop_grid = 0;  // blocks of the persistent BP launch (0: launch per half-iteration)
-  int coop_lsd_grid = 0;  // blocks of the persistent LSD-0 launch (0: launches per step)
   long long bar_limit_ns = 1000000000LL;  // bound of a grid-barrier wait
   int hold_barrier = 0;                   // timeout test: block 0 withholds an arrival
 };
@@ -1141,32 +1070,7 @@ int run_plsd(lsd_giant* G, const float* llr, const uint8_t* s, uint8_t* corr,
   if ((rc = check_launch(G))) return rc;
   int status = LSD_SHOT_OK_LSD, steps = 0, par = 0;
   if ((rc = read_ctr(G))) return rc;
-  if (G->h_ctr->overflow) return LSD_ERR_ADMISSION;  // the seeds' blocks did not fit
-  const bool persistent = G->coop_lsd_grid > 0 && G->h_ctr->ninv[0] > 0;
-  if (persistent) {
-    // the whole LSD-0 loop in one cooperative launch
-    cudaError_t e = cudaMemsetAsync(&g.ctr->bar_arrive, 0, sizeof(unsigned), G->st);
-    if (e != cudaSuccess) return gfail(e);
-    GD ga = g;
-    const float* lp = llr;
-    long long limit = G->bar_limit_ns;
-    int max_steps = G->n;
-    void* args[] = {(void*)&ga, (void*)&lp, (void*)&limit, (void*)&max_steps};
-    e = cudaLaunchCooperativeKernel((const void*)glsd_persistent, G->coop_lsd_grid, 256, args, 0,
-                                    G->st);
-    G->launches++;
-    if (e != cudaSuccess) return gfail(e);
-    if ((rc = read_ctr(G))) return rc;
-    const GCtr& h = *G->h_ctr;
-    if (h.bp_fail) return LSD_ERR_TIMEOUT;
-    if (h.overflow) return LSD_ERR_ADMISSION;
-    if (h.uf_fail) return LSD_ERR_TIMEOUT;
-    if (h.too_big) return LSD_ERR_UNSUPPORTED;
-    steps = h.lsd_steps;
-    if (h.unsolvable || steps > G->n) status = LSD_SHOT_UNSOLVABLE;
-    // the next parity for LSD-mu's steps: collect_all resets the slot it uses
-  }
-  for (; !persistent;) {
+  for (;;) {
     const GCtr& h = *G->h_ctr;
     if (h.overflow) return LSD_ERR_ADMISSION;
     if (h.uf_fail) return LSD_ERR_TIMEOUT;
@@ -1422,11 +1326,6 @@ int lsd_giant_create(lsd_giant** out, int32_t m, int32_t n, int64_t nnz, const i
       const long long need = (std::max<long long>(m, n) + 255) / 256;
       G->coop_grid = (int)std::min<long long>(need, (long long)per_sm * G->sms);
     }
-    int per_sm_lsd = 0;
-    if (err == cudaSuccess && coop)
-      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_lsd, glsd_persistent, 256, 0);
-    if (err == cudaSuccess && coop && per_sm_lsd > 0)
-      G->coop_lsd_grid = std::min(per_sm_lsd, 4) * G->sms;
     if (err != cudaSuccess) rc = gfail(err);
   }
   g.dc = dc;
