@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one 10^6-shot launch of bp_reg_kernel<32,3,6,5,3> on this
 # workload, from a one-pass ncu capture of the full workload
 # (profiles/bp_reg_kernel_bb144_p005.md); None once the kernel changes.
-BP_TRAFFIC_BYTES = 75704832 + 152049408
+BP_TRAFFIC_BYTES = 76266752 + 152703744
 
 
 def parse():
