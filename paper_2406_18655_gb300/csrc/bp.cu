@@ -239,13 +239,12 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
   float* s_prior = reinterpret_cast<float*>(smem);
   for (int j = threadIdx.x; j < n; j += blockDim.x) s_prior[j] = a.g.prior[j];
   __syncthreads();
-  const int slots = m * bpreg::padded_dc(DC);  // message rows of odd stride
   float* r = reinterpret_cast<float*>(smem + align16((size_t)n * 4) +
-                                      (size_t)group * bp_reg_group_bytes(n, slots));
-  float* Lam = r + slots;
+                                      (size_t)group * bp_reg_group_bytes(n, E));
+  float* Lam = r + E;
   bpreg::Tables<CPL, DC, VPL, DV> T;
   bpreg::load_tables<G>(a.g, lane, T);
-  (void)E;
+  (void)m;
 
   unsigned long long my_iters = 0, my_conv = 0;
   for (;;) {
@@ -784,7 +783,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
     const int G = lanes_of(v);
     if (v >= 6) {
       gb = align16((size_t)g.n * 4);
-      grp = bp_reg_group_bytes(g.n, g.m * bpreg::padded_dc(kRegShapes[v - 6].dc));
+      grp = bp_reg_group_bytes(g.n, g.E);
     } else {
       gb = bp_graph_bytes(g.m, g.n, g.E);
       grp = bp_group_bytes(g.m, g.n, g.E);

@@ -1,10 +1,8 @@
 // Min-sum BP of one shot by a group of G lanes (G | 32) whose graph tables sit in
-// registers: lane l keeps the column indices of checks l, l + G, ... and the message slots
-// of variables l, l + G, ... (two 16-bit indices per register); r[m][DCP] and Lam[n] are the
-// shot's message state in shared memory, a check's DC messages in a row of DCP = DC | 1
-// words (an odd stride, so that the lanes' rows fall in distinct banks).  Used by
-// bp_reg_kernel.  Same operations in the same order as bp_kernel<G, 0> (the flooding
-// min-sum of Sec. 4.3).
+// registers: lane l keeps the column indices of checks l, l + G, ... and the edge slots of
+// variables l, l + G, ... (two 16-bit indices per register); r[E] and Lam[n] are the shot's
+// message state in shared memory.  Used by bp_reg_kernel and by the fused BP + LSD kernel.
+// Same operations in the same order as bp_kernel<G, 0> (the flooding min-sum of Sec. 4.3).
 #pragma once
 
 #include "lsd_internal.cuh"
@@ -13,9 +11,6 @@ namespace lsdgb {
 namespace bpreg {
 
 constexpr float kBig = 0x1p100f;  // minimum over an empty set (a degree-1 check)
-
-// Row stride of a check's messages: the degree rounded up to an odd count.
-__host__ __device__ constexpr int padded_dc(int dc) { return dc | 1; }
 
 template <int CPL, int DC, int VPL, int DV>
 struct Tables {
@@ -42,13 +37,8 @@ __device__ __forceinline__ void load_tables(const DevGraph& g, int lane,
 #pragma unroll
     for (int k = 0; k < (DV + 1) / 2; ++k) T.ve[v][k] = 0;
     if (j < g.n) {
-      constexpr int DCP = padded_dc(DC);
 #pragma unroll
-      for (int k = 0; k < DV; ++k) {
-        const int e = g.var_edge[j * DV + k];  // edge e = DC * check + position
-        const uint32_t slot = (uint32_t)((e / DC) * DCP + e % DC);
-        T.ve[v][k >> 1] |= slot << (16 * (k & 1));
-      }
+      for (int k = 0; k < DV; ++k) T.ve[v][k >> 1] |= (uint32_t)g.var_edge[j * DV + k] << (16 * (k & 1));
     }
   }
 }
@@ -61,7 +51,6 @@ __device__ __forceinline__ int shot_bp(const BPArgs& a, const Tables<CPL, DC, VP
                                        const float* s_prior, int lane, unsigned gmask,
                                        bool& conv) {
   const int m = a.g.m, n = a.g.n;
-  constexpr int DCP = padded_dc(DC);
   const float alpha = a.alpha;
   const uint8_t* sp = a.syndromes + shot * m;
   unsigned sbits = 0;
@@ -71,7 +60,7 @@ __device__ __forceinline__ int shot_bp(const BPArgs& a, const Tables<CPL, DC, VP
     if (i < m) {
       if (sp[i]) sbits |= 1u << c;
 #pragma unroll
-      for (int k = 0; k < DC; ++k) r[i * DCP + k] = 0.f;
+      for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
     }
   }
 #pragma unroll
@@ -100,7 +89,7 @@ __device__ __forceinline__ int shot_bp(const BPArgs& a, const Tables<CPL, DC, VP
       float min1 = kBig, min2 = kBig;
       float aq[DC];
       uint32_t qb[DC];
-      float* rc = r + i * DCP;
+      float* rc = r + i * DC;
 #pragma unroll
       for (int k = 0; k < DC; ++k) {
         const int j = (T.cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff;
