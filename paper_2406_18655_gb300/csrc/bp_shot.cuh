@@ -1,7 +1,7 @@
 // Min-sum BP of one shot by a group of G lanes (G | 32) whose graph tables sit in
 // registers: lane l keeps the column indices of checks l, l + G, ... and the edge slots of
 // variables l, l + G, ... (two 16-bit indices per register); r[E] and Lam[n] are the shot's
-// message state in shared memory.  Used by bp_reg_kernel and by the fused BP + LSD kernel.
+// message state in shared memory.  Used by bp_reg_kernel.
 // Same operations in the same order as bp_kernel<G, 0> (the flooding min-sum of Sec. 4.3).
 #pragma once
 
