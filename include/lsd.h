@@ -15,7 +15,14 @@
  * reliability, validated and solved by on-the-fly GF(2) elimination (Sec. 4.2), and
  * returns the union of the local solutions (Eq. 2).  BP is the pre-decoder of Sec. 4.3:
  * min-sum, flooding ("parallel") schedule, scaling alpha = 0.625.  LSD-mu (App. D) adds
- * mu growth steps per cluster followed by local exhaustive OSD of order mu.
+ * mu growth steps per cluster followed by local exhaustive OSD of order mu, or the
+ * combination sweep OSD-CS-w.
+ *
+ * Beyond batches of one matrix: (w, c) overlapping-window decoding of repeated syndrome
+ * rounds (Methods 4.3; lsd_window_*), batch or round by round; one giant shot decoded by
+ * the whole GPU with the parallel LSD of App. B (lsd_giant_*); the learned prior
+ * (lsd_prior_*) and the continuous-batching server (lsd_server_*), which have no
+ * counterpart in the paper.
  *
  * Conventions used by every entry point
  *   - Return value: LSD_OK (0) or a negative LSD_ERR_* code.  lsd_status_string()
