@@ -28,6 +28,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kNoKey = ~0ull;
 constexpr int kSpill = 4;  // internal status: retry with the large-capacity instance
+constexpr int kMaskSeeds = 1024;  // spill instance: shots with at most this many seeds use masks
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -75,6 +76,8 @@ struct SShot {
   int* slot;            // [m]
   int* fst;             // [n]
   int* front;           // [n]
+  uint32_t* cmask;      // spill instance: per seed, its clusters' candidate faults [SC][wn]
+  int wn;               // words of a candidate mask (ceil(n / 32)); 0 = no masks
   template <class T>
   __device__ __forceinline__ T* s(size_t off) const { return reinterpret_cast<T*>(sm + off); }
   template <class T>
@@ -324,9 +327,34 @@ __device__ int sparse_step(const SGraph& G, const SShot<L>& S, const float* llr,
     S.gflag()[r] = 1;
   }
   __syncwarp();
-  // find_candidate over the compacted candidate list, 4 entries per lane at a time: the
-  // dependent loads (entry, state, column, labels) of the four are issued together
-  {
+  // find_candidate.  With few growing clusters (the spill instance's late steps, one huge
+  // cluster growing alone), each scans its own candidate mask: the set bits are the free
+  // faults next to it, so only their LLRs are read.  Otherwise one pass over the compacted
+  // candidate list, 4 entries per lane at a time: the dependent loads (entry, state,
+  // column, labels) of the four are issued together.
+  if (S.wn > 0 && (long long)k * S.wn < 2LL * S.scal()[S_NFRONT]) {
+    for (int t = 0; t < k; ++t) {
+      const int r = S.inv()[t];
+      const uint32_t* cm = S.cmask + (size_t)r * S.wn;
+      unsigned long long best = kNoKey;
+      for (int w = lane; w < S.wn; w += 32) {
+        uint32_t bits = cm[w];
+        while (bits) {
+          const int f = w * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          if (S.fst[f] != -1) continue;  // already in a cluster
+          const unsigned long long key = llr_key(llr[f], f);
+          if (key < best) best = key;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, off);
+        if (o < best) best = o;
+      }
+      if (lane == 0) S.best()[r] = best;
+    }
+    __syncwarp();
+  } else {
     const int nf = S.scal()[S_NFRONT];
     const unsigned below = (1u << lane) - 1u;
     int kept = 0;
@@ -422,11 +450,26 @@ __device__ int sparse_step(const SGraph& G, const SShot<L>& S, const float* llr,
     }
     __syncwarp();
   }
-  // candidates next to the newly claimed detectors
+  // candidate masks: the absorbed clusters' masks fold into their roots
+  if (S.wn > 0 && S.scal()[S_MERGED]) {
+    const int nm = S.scal()[S_MERGED];
+    for (int i = 0; i < nm; ++i) {
+      const int x = S.mlist()[i];
+      const uint32_t* src = S.cmask + (size_t)x * S.wn;
+      uint32_t* dst = S.cmask + (size_t)S.parent()[x] * S.wn;
+      for (int w = lane; w < S.wn; w += 32) {
+        const uint32_t v = src[w];
+        if (v) atomicOr(&dst[w], v);
+      }
+    }
+    __syncwarp();
+  }
+  // candidates next to the newly claimed detectors (and, with masks, in their cluster's mask)
   {
     const int nd = S.scal()[S_DNEW];
     for (int t = lane; t < nd; t += 32) {
       const int d = S.dnew()[t];
+      uint32_t* cm = S.wn > 0 ? S.cmask + (size_t)S.dlab[d] * S.wn : nullptr;
       const int c1 = G.chk_ptr[d + 1];
       for (int e = G.chk_ptr[d]; e < c1; ++e) {
         const int f = G.chk_var[e];
@@ -434,6 +477,7 @@ __device__ int sparse_step(const SGraph& G, const SShot<L>& S, const float* llr,
           const int q = atomicAdd(&S.scal()[S_NFRONT], 1);
           S.front[q] = f;
         }
+        if (cm && S.fst[f] < 0) atomicOr(&cm[f >> 5], 1u << (f & 31));
       }
     }
   }
@@ -691,6 +735,11 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
   S.front = ws + 2 * m + n;
   S.rt = GLOBAL_RT ? reinterpret_cast<unsigned char*>(ws + 2 * m + 2 * n) : S.sm + L::sm_total;
   if (GLOBAL_RT) S.sm = S.rt + L::rt_total;
+  // the spill instance also keeps one candidate mask per seed (up to kMaskSeeds) after its
+  // other state
+  const int wn_masks = GLOBAL_RT ? (n + 31) / 32 : 0;
+  S.wn = 0;
+  S.cmask = GLOBAL_RT ? reinterpret_cast<uint32_t*>(S.sm + L::sm_total) : nullptr;
   SGraph G{a.g.chk_ptr, a.g.chk_var, a.g.var_ptr, a.g.var_chk, a.g.max_col_deg};
 
   long long count;
@@ -743,22 +792,29 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
     }
     int status = LSD_SHOT_OK_LSD, steps = 0;
     if (ns > SC || ns > CAP) status = kSpill;
+    S.wn = ns <= kMaskSeeds ? wn_masks : 0;
     if (lane == 0) {
       S.scal()[S_NSEED] = min(ns, SC);
       S.scal()[S_SLOTS] = min(ns, CAP);
     }
     __syncwarp();
     for (int w = lane; w < W; w += 32) S.sred()[w] = S.syn()[w];
-    // candidates next to the seeds
+    // candidates next to the seeds (and each seed's candidate mask)
     if (status == LSD_SHOT_OK_LSD) {
+      if (S.wn > 0) {
+        for (size_t w = lane; w < (size_t)ns * S.wn; w += 32) S.cmask[w] = 0u;
+        __syncwarp();
+      }
       for (int k = lane; k < ns; k += 32) {
         const int d = S.seed()[k];
+        uint32_t* cm = S.wn > 0 ? S.cmask + (size_t)k * S.wn : nullptr;
         for (int e = G.chk_ptr[d]; e < G.chk_ptr[d + 1]; ++e) {
           const int f = G.chk_var[e];
           if (atomicCAS(&S.fst[f], -2, -1) == -2) {
             const int q = atomicAdd(&S.scal()[S_NFRONT], 1);
             S.front[q] = f;
           }
+          if (cm) atomicOr(&cm[f >> 5], 1u << (f & 31));
         }
       }
     }
@@ -914,7 +970,8 @@ size_t sparse_scratch_ints(int m, int n, bool big, bool mu) {
   size_t s = (size_t)2 * m + (size_t)2 * n;
   if (big)
     s += (mu ? SLay<kBigCap, kBigSeeds, true>::rt_total + SLay<kBigCap, kBigSeeds, true>::sm_total
-             : SLay<kBigCap, kBigSeeds, false>::rt_total + SLay<kBigCap, kBigSeeds, false>::sm_total) / 4;
+             : SLay<kBigCap, kBigSeeds, false>::rt_total + SLay<kBigCap, kBigSeeds, false>::sm_total) / 4 +
+         (size_t)kMaskSeeds * ((n + 31) / 32);  // candidate masks
   return (s + 3) & ~(size_t)3;
 }
 
