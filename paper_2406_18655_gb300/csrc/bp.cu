@@ -445,23 +445,29 @@ __global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
   }
 }
 
-// BP for large row-regular graphs (hypergraph-product codes): one CTA of NT threads owns one
-// shot; like bp_reg_kernel, thread t keeps the column indices of checks t, t + NT, ... and the
-// edge slots of variables t, t + NT, ... in registers (two 16-bit indices per register), so
-// no graph table is read while iterating.  Columns of degree < DV are padded with the slot
-// of a message that stays zero (r[E]), added last, which leaves Lambda unchanged.  r[E + 1]
-// and Lam[n] live in shared memory.  Same operations in the same order as bp_kernel<G, 0>.
-template <int NT, int CPL, int DC, int VPL, int DV>
-__global__ void __launch_bounds__(NT, 1) bp_regcta_kernel(BPArgs a) {
+// BP for large graphs with register-resident tables: one CTA of NT threads owns one shot;
+// like bp_reg_kernel, thread t keeps the column indices of checks t, t + NT, ... and the
+// message slots of variables t, t + NT, ... in registers (two 16-bit indices per register),
+// so no graph table is read while iterating.  Messages r live in shared memory row-major
+// with DC slots per check (slot i * DC + k for the k-th edge of check i) plus a slot Z = m DC
+// that stays zero; columns of degree < DV are padded with Z, added last, which leaves Lambda
+// unchanged.  PAD: checks of degree < DC are padded with a dummy column n whose Lambda stays
+// 2^100 (kBig) and whose slots are read as zero and never written.  kBig is also where the
+// two running minima of a check start, so a padded edge changes neither minimum, sign nor
+// hard-decision parity: the update equals the unpadded one bit for bit.  Same operations in
+// the same order as bp_kernel<G, 0>.
+template <int NT, int CPL, int DC, int VPL, int DV, bool PAD, int MINB>
+__global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_shot;
   __shared__ unsigned long long s_slot;
-  const int m = a.g.m, n = a.g.n, E = a.g.E;
+  const int m = a.g.m, n = a.g.n;
+  const int Z = m * DC;
   const long long shots = a.shots_dev ? *a.shots_dev : a.shots;
   const int tid = threadIdx.x;
-  float* r = reinterpret_cast<float*>(smem);           // [E + 1], r[E] == 0
-  float* Lam = r + align16((size_t)(E + 1) * 4) / 4;   // [n]
-  float* s_prior = Lam + align16((size_t)n * 4) / 4;   // [n]
+  float* r = reinterpret_cast<float*>(smem);           // [m DC + 1], r[Z] == 0
+  float* Lam = r + align16((size_t)(Z + 1) * 4) / 4;   // [n + 1], Lam[n] == kBig
+  float* s_prior = Lam + align16((size_t)(n + 1) * 4) / 4;  // [n]
   const float alpha = a.alpha;
   uint32_t cv[CPL][(DC + 1) / 2];
 #pragma unroll
@@ -470,8 +476,14 @@ __global__ void __launch_bounds__(NT, 1) bp_regcta_kernel(BPArgs a) {
 #pragma unroll
     for (int k = 0; k < (DC + 1) / 2; ++k) cv[c][k] = 0;
     if (i < m) {
+      // row-regular graphs (PAD false): chk_ptr[i] = i DC
+      const int p0 = PAD ? a.g.chk_ptr[i] : i * DC;
+      const int deg = PAD ? a.g.chk_ptr[i + 1] - p0 : DC;
 #pragma unroll
-      for (int k = 0; k < DC; ++k) cv[c][k >> 1] |= (uint32_t)a.g.chk_var[i * DC + k] << (16 * (k & 1));
+      for (int k = 0; k < DC; ++k) {
+        const uint32_t j = k < deg ? (uint32_t)a.g.chk_var[p0 + k] : (uint32_t)n;
+        cv[c][k >> 1] |= j << (16 * (k & 1));
+      }
     }
   }
   uint32_t ve[VPL][(DV + 1) / 2];
@@ -484,13 +496,24 @@ __global__ void __launch_bounds__(NT, 1) bp_regcta_kernel(BPArgs a) {
       const int q0 = a.g.var_ptr[j], deg = a.g.var_ptr[j + 1] - q0;
 #pragma unroll
       for (int k = 0; k < DV; ++k) {
-        const uint32_t e = k < deg ? (uint32_t)a.g.var_edge[q0 + k] : (uint32_t)E;
+        uint32_t e = (uint32_t)Z;
+        if (k < deg) {
+          if constexpr (PAD) {
+            const int i = a.g.var_chk[q0 + k];
+            e = (uint32_t)(i * DC + (a.g.var_edge[q0 + k] - a.g.chk_ptr[i]));
+          } else {
+            e = (uint32_t)a.g.var_edge[q0 + k];  // = i DC + k when every row has DC edges
+          }
+        }
         ve[v][k >> 1] |= e << (16 * (k & 1));
       }
       s_prior[j] = a.g.prior[j];
     }
   }
-  if (tid == 0) r[E] = 0.f;
+  if (tid == 0) {
+    r[Z] = 0.f;
+    Lam[n] = kBig;
+  }
   unsigned long long my_iters = 0, my_conv = 0;
   for (;;) {
     if (tid == 0) s_shot = atomicAdd(&a.ctr->next_shot, 1ULL);
@@ -549,7 +572,8 @@ __global__ void __launch_bounds__(NT, 1) bp_regcta_kernel(BPArgs a) {
 #pragma unroll
           for (int k = 0; k < DC; ++k) {
             const float mag = (aq[k] == min1) ? m2 : m1;
-            rc[k] = __uint_as_float(__float_as_uint(mag) | ((sx ^ qb[k]) & 0x80000000u));
+            if (!PAD || ((cv[c][k >> 1] >> (16 * (k & 1))) & 0xffff) != (uint32_t)n)
+              rc[k] = __uint_as_float(__float_as_uint(mag) | ((sx ^ qb[k]) & 0x80000000u));
           }
         }
       }
@@ -662,27 +686,39 @@ const void* generic_fn(int v) {
     default: return (const void*)bp_kernel<32, 1>;
   }
 }
-// Shapes of bp_regcta_kernel: (NT, CPL, DC, VPL, DV); rows of degree exactly DC, columns of
-// degree at most DV.
+// Shapes of bp_regcta_kernel: (NT, CPL, DC, VPL, DV, PAD, MINB); rows of degree exactly DC
+// (PAD false) or at most DC (PAD true), columns of degree at most DV; MINB CTAs per SM bound
+// the registers a thread may take.
 struct RegCtaShape {
   int nt, cpl, dc, vpl, dv;
+  bool pad;
   const void* fn;
 };
-#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx) \
-  {NT, C, DCx, V, DVx, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx>}
+#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx, P, MB) \
+  {NT, C, DCx, V, DVx, P, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB>}
 const RegCtaShape kRegCtaShapes[] = {
-    LSD_REGCTA_SHAPE(768, 4, 7, 9, 4),   // m <= 3072, n <= 6912 (HGP of a 48 x 64 (3,4) code)
-    LSD_REGCTA_SHAPE(512, 6, 7, 13, 4),  // same graphs, fewer threads
+    LSD_REGCTA_SHAPE(768, 4, 7, 9, 4, false, 1),   // m <= 3072, n <= 6912 (HGP of a 48 x 64 (3,4) code)
+    LSD_REGCTA_SHAPE(512, 6, 7, 13, 4, false, 1),  // same graphs, fewer threads
+    // space-time matrices of BB codes: rows of degree w + 2 (and 1 in the last block),
+    // columns of degree <= 3
+    LSD_REGCTA_SHAPE(128, 3, 8, 6, 3, true, 4),  // m <= 384, n <= 768 (BB144 (3,1) windows)
+    LSD_REGCTA_SHAPE(256, 4, 8, 11, 3, true, 2),  // m <= 1024, n <= 2816 (BB144, d = 12)
+    LSD_REGCTA_SHAPE(512, 2, 8, 6, 3, true, 1),  // m <= 1024, n <= 3072
+    // ... with mid-round hook faults: rows of degree up to 17
+    LSD_REGCTA_SHAPE(256, 2, 17, 9, 3, true, 2),  // m <= 512, n <= 2304 (BB144, d = 6)
+    LSD_REGCTA_SHAPE(512, 1, 17, 5, 3, true, 1),  // m <= 512, n <= 2560
 };
 #undef LSD_REGCTA_SHAPE
 constexpr int kNumRegCtaShapes = sizeof(kRegCtaShapes) / sizeof(kRegCtaShapes[0]);
 
-size_t regcta_smem(const DevGraph& g) {
-  return align16((size_t)(g.E + 1) * 4) + 2 * align16((size_t)g.n * 4);
+size_t regcta_smem(const RegCtaShape& s, const DevGraph& g) {
+  return align16(((size_t)g.m * s.dc + 1) * 4) + align16(((size_t)g.n + 1) * 4) +
+         align16((size_t)g.n * 4);
 }
 bool regcta_fits(const RegCtaShape& s, const DevGraph& g) {
-  return g.m <= s.nt * s.cpl && g.n <= s.nt * s.vpl && g.min_row_deg == s.dc &&
-         g.max_row_deg == s.dc && g.max_col_deg <= s.dv && g.E < 65535 && g.n <= 65535;
+  const bool rows = s.pad ? g.max_row_deg <= s.dc : (g.min_row_deg == s.dc && g.max_row_deg == s.dc);
+  return rows && g.m <= s.nt * s.cpl && g.n <= s.nt * s.vpl && g.max_col_deg <= s.dv &&
+         (long)g.m * s.dc < 65535 && g.n < 65535;
 }
 
 constexpr int kCtaBase = 6 + kNumRegShapes;     // + method: one CTA per shot
@@ -742,10 +778,22 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
         }
       }
     }
+    if (v < 0 && method == 0 && kind == 0 && lanes == 0) {
+      // irregular or large graphs: one CTA per shot with register tables when a shape fits
+      // and the graph has at least one check per thread (no graph table read per edge, and
+      // a shot's latency spread over NT threads instead of one warp group)
+      for (int i = 0; i < kNumRegCtaShapes; ++i) {
+        const RegCtaShape& sh = kRegCtaShapes[i];
+        if (regcta_fits(sh, g) && g.m >= sh.nt && regcta_smem(sh, g) <= (size_t)max_smem) {
+          v = kRegCtaBase + i;
+          break;
+        }
+      }
+    }
     if (v < 0 && kind == 2) {  // register tables requested: a CTA shape, or nothing
       if (method == 0)
         for (int i = 0; i < kNumRegCtaShapes; ++i)
-          if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(g) <= (size_t)max_smem) {
+          if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(kRegCtaShapes[i], g) <= (size_t)max_smem) {
             v = kRegCtaBase + i;
             break;
           }
@@ -760,7 +808,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
         v = kCtaBase + (method ? 1 : 0);
         if (method == 0 && kind != 1)
           for (int i = 0; i < kNumRegCtaShapes; ++i)
-            if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(g) <= (size_t)max_smem) {
+            if (regcta_fits(kRegCtaShapes[i], g) && regcta_smem(kRegCtaShapes[i], g) <= (size_t)max_smem) {
               v = kRegCtaBase + i;
               break;
             }
@@ -771,7 +819,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
   int b;
   if (is_regcta(v)) {
     gb = 0;
-    grp = regcta_smem(g);
+    grp = regcta_smem(kRegCtaShapes[v - kRegCtaBase], g);
     if (grp > (size_t)max_smem) return cudaErrorInvalidValue;
     b = kRegCtaShapes[v - kRegCtaBase].nt;
   } else if (is_cta(v)) {

@@ -75,8 +75,47 @@ def test_register_kernel_available_for_bb_codes(L):
         post, conv, it = d.bp(dev(s))
         llr, hard, used, convo = oracle.bp(h, f64(probs), s, 30, precision=1)
         assert np.array_equal(post.cpu().numpy().astype(np.float64), llr)
-    with pytest.raises(L.LsdError):  # irregular column degrees: no register shape
-        L.Decoder(code("st_bb72_d6"), np.full(648, 0.01, np.float32), 30, bp_kernel=2)
+    with pytest.raises(L.LsdError):  # columns of weight 4: no register shape
+        L.Decoder(code("irreg_37x61"), np.full(61, 0.01, np.float32), 30, bp_kernel=2)
+
+
+def _irregular_rows(name):
+    """Check matrices whose rows have different degrees (space-time matrices, hook faults,
+    a window with the noiseless last block, a degree-1 boundary check)."""
+    from oracle import window as OW
+    if name == "hooks_bb144_d6":
+        return I.space_time_hooks(code("bb144"), 6, seed=6)[0]
+    if name == "hooks_bb72_d3":
+        return I.space_time_hooks(code("bb72"), 3, seed=3)[0]
+    if name == "window_bb144_final":
+        return OW.window_matrix(code("bb144"), 3, 4)
+    return code(name)
+
+
+@pytest.mark.parametrize("name,p,iters,shots", [
+    ("st_bb72_d6", 0.01, 50, 3000), ("st_bb72_d6", 0.04, 30, 2000),
+    ("st_bb144_d12", 0.004, 50, 1500), ("hooks_bb144_d6", 0.004, 50, 1500),
+    ("hooks_bb72_d3", 0.02, 30, 2000), ("window_bb144_final", 0.01, 30, 2000),
+    ("rep_boundary", 0.1, 20, 2000)])
+def test_register_cta_kernel_on_irregular_rows(L, name, p, iters, shots):
+    """One CTA per shot with register tables on rows of unequal degree (padded with a dummy
+    column that takes part in no minimum and no parity): posteriors, iteration counts and
+    convergence bit-exact, and the decode through the LSD queue equals the oracle's."""
+    h = _irregular_rows(name)
+    assert h.sum(1).min() < h.sum(1).max()
+    probs = np.full(h.shape[1], p, np.float32)
+    e = I.sample_errors(1300 + shots, shots, probs.astype(np.float64))
+    s = I.syndromes(h, e)
+    d = L.Decoder(h, probs, iters, bp_kernel=2)
+    post, conv, it = d.bp(dev(s))
+    llr, hard, used, convo = oracle.bp(h, f64(probs), s, iters, precision=1)
+    assert np.array_equal(it.cpu().numpy(), used)
+    assert np.array_equal(conv.cpu().numpy(), convo)
+    assert np.array_equal(post.cpu().numpy().astype(np.float64), llr)
+    corr, st = d.decode(dev(s))
+    o = oracle.decode(h, f64(probs), s, iters, precision=1)
+    assert np.array_equal(st.cpu().numpy(), o["status"])
+    assert np.array_equal(corr.cpu().numpy(), o["corrections"])
 
 
 def test_bp_no_early_exit_and_zero_iterations(L):
