@@ -701,7 +701,7 @@ const RegCtaShape kRegCtaShapes[] = {
     LSD_REGCTA_SHAPE(512, 6, 7, 13, 4, false, 1),  // same graphs, fewer threads
     // space-time matrices of BB codes: rows of degree w + 2 (and 1 in the last block),
     // columns of degree <= 3
-    LSD_REGCTA_SHAPE(128, 3, 8, 6, 3, true, 4),  // m <= 384, n <= 768 (BB144 (3,1) windows)
+    LSD_REGCTA_SHAPE(128, 3, 8, 6, 3, true, 6),  // m <= 384, n <= 768 (BB144 (3,1) windows)
     LSD_REGCTA_SHAPE(256, 4, 8, 11, 3, true, 2),  // m <= 1024, n <= 2816 (BB144, d = 12)
     LSD_REGCTA_SHAPE(512, 2, 8, 6, 3, true, 1),  // m <= 1024, n <= 3072
     // ... with mid-round hook faults: rows of degree up to 17
