@@ -395,3 +395,21 @@ def test_autotune_keeps_results(L):
     assert rep["ms_bp_best"] <= rep["ms_bp_first"] + 1e-6
     c1, s1 = d.decode(dev(s))
     assert torch.equal(c0, c1) and torch.equal(s0, s1)
+
+
+@pytest.mark.parametrize("name,p", [("window_bb144_final", 0.01), ("hooks_bb72_d3", 0.02)])
+def test_autotune_on_irregular_rows_keeps_results(L, name, p):
+    """On rows of unequal degree the autotuner times the generic kernels and every padded
+    register-table shape that fits; whichever it keeps decodes as the oracle does."""
+    h = _irregular_rows(name)
+    probs = np.full(h.shape[1], p, np.float32)
+    e = I.sample_errors(91, 6000, probs.astype(np.float64))
+    s = I.syndromes(h, e)
+    d = L.Decoder(h, probs, 30)
+    rep = d.autotune(dev(s))
+    assert rep["bp_candidates"] >= 4
+    assert rep["ms_bp_best"] <= rep["ms_bp_first"] + 1e-6
+    corr, st = d.decode(dev(s))
+    o = oracle.decode(h, f64(probs), s, 30, precision=1)
+    assert np.array_equal(st.cpu().numpy(), o["status"])
+    assert np.array_equal(corr.cpu().numpy(), o["corrections"])
