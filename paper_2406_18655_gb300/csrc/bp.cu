@@ -803,7 +803,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
       const int l = lanes ? lanes : 32;
       v = (l == 8 ? 0 : l == 16 ? 1 : 2) + (method ? 3 : 0);
       // a graph whose warp-group state does not fit next to the staged graph: one CTA per
-      // shot, with register tables when the graph is row-regular and a shape fits
+      // shot, with register tables when a shape fits
       if (bp_graph_bytes(g.m, g.n, g.E) + bp_group_bytes(g.m, g.n, g.E) > (size_t)max_smem) {
         v = kCtaBase + (method ? 1 : 0);
         if (method == 0 && kind != 1)
