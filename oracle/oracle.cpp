@@ -40,9 +40,9 @@
 //     r is not in the row space of H_Z (rank test).
 //
 // Parity status: every function above is pinned by tests/test_oracle_*.py
-// (brute force, tree exactness, closed forms, invariants, worked example),
-// except the FP32 mirror of sum-product, which is only checked against the
-// double mode within rounding (parity unpinned beyond that).
+// (brute force, tree exactness, closed forms, invariants, worked example); the
+// FP32 mirror of sum-product is pinned to exact tree inference within a
+// rounding bound derived from float tanh/atanh.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -1,6 +1,7 @@
 """Oracle BP pinned against exact inference on tree Tanner graphs and a closed form (no GPU).
 
-* Sum-product on a tree gives the exact posterior LLRs ln P(x_j=0|s)/P(x_j=1|s).
+* Sum-product on a tree gives the exact posterior LLRs ln P(x_j=0|s)/P(x_j=1|s), in double
+  and, within its derived rounding bound, in the FP32 mirror.
 * Min-sum with alpha = 1 on a tree gives exact min-marginal differences
   min_{x_j=1} cost(x) - min_{x_j=0} cost(x), cost(x) = sum_k lambda_k x_k.
 * One check, one iteration: the scaled min-sum message (alpha = 0.625, Sec. 4.3).
@@ -41,6 +42,25 @@ def test_sum_product_exact_on_trees(oracle_lib, seed):
     llr, hard, used, conv = oracle_lib.bp(h, p, s[None], iters=2 * n, method=1, early_exit=0)
     assert used[0] == 2 * n
     np.testing.assert_allclose(llr[0], exact, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_sum_product_fp32_mirror_exact_on_trees(oracle_lib, seed):
+    """The FP32 mirror of sum-product against exact inference on the float-rounded
+    probabilities.  Bound: each message is at most 14 tanh products and one atanh, each
+    rounded to 2^-24 relative, amplified by atanh's condition number (<= 10 for products up
+    to tanh(2) ~ 0.96) along a path of at most 14 edges, on LLRs of magnitude <= 5:
+    14 * 10 * 2^-24 * 5 ~ 4e-5; a dropped term or a flipped sign is off by 0.1 or more."""
+    h, p, s = _tree_case(seed, 8 + seed % 7)
+    n = h.shape[1]
+    p32 = p.astype(np.float32).astype(np.float64)
+    xs = _consistent(h, s)
+    w = np.exp(xs @ np.log(p32) + (1 - xs) @ np.log(1 - p32))
+    exact = np.array([np.log(w[xs[:, j] == 0].sum() / w[xs[:, j] == 1].sum()) for j in range(n)])
+    assert np.abs(exact).max() <= 5.5
+    llr, hard, used, conv = oracle_lib.bp(h, p, s[None], iters=2 * n, method=1, early_exit=0,
+                                          precision=1)
+    np.testing.assert_allclose(llr[0], exact, rtol=0, atol=5e-5)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
