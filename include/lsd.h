@@ -75,8 +75,9 @@ typedef struct lsd_options {
   int32_t single_cluster; /* 1 = LSD seeds one cluster holding every detector; it then equals OSD-0 */
   int32_t bp_lanes;       /* threads cooperating on one shot in BP: 0 = auto, else 8, 16 or 32 */
   int32_t lsd_warps;      /* warps per CTA of the LSD kernel: 0 = auto, else 1..16 */
-  int32_t bp_kernel;      /* BP kernel: 0 = auto (register tables when a shape fits, else
-                             generic), 1 = generic (graph in shared memory, or read through
+  int32_t bp_kernel;      /* BP kernel: 0 = auto (register tables when a shape fits and,
+                             for the CTA-per-shot shapes, the graph has at least as many
+                             checks as the shape has threads; else generic), 1 = generic (graph in shared memory, or read through
                              the cache by one CTA per shot for large graphs), 2 =
                              register-resident graph tables (min-sum: a warp group per shot
                              for small regular codes; a CTA per shot for larger graphs whose
