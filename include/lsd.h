@@ -77,14 +77,15 @@ typedef struct lsd_options {
   int32_t lsd_warps;      /* warps per CTA of the LSD kernel: 0 = auto, else 1..16 */
   int32_t bp_kernel;      /* BP kernel: 0 = auto (register tables when a shape fits and,
                              for the CTA-per-shot shapes, the graph has at least as many
-                             checks as the shape has threads; else generic), 1 = generic (graph in shared memory, or read through
-                             the cache by one CTA per shot for large graphs), 2 =
-                             register-resident graph tables (min-sum: a warp group per shot
-                             for small regular codes; a CTA per shot for larger graphs whose
-                             rows all have 7 edges and columns at most 4, as hypergraph
-                             products, or whose rows have at most 8 or 17 edges and columns
-                             at most 3, as space-time matrices with or without hook faults;
-                             shorter rows are padded) */
+                             checks as the shape has threads; else generic), 1 = generic
+                             (graph in shared memory, or read through the cache by one CTA
+                             per shot for large graphs), 2 = register-resident graph tables
+                             (min-sum: a warp group per shot for small regular codes; a CTA
+                             per shot for larger graphs whose rows all have 7 edges and
+                             columns at most 4, as hypergraph products, or whose rows have
+                             at most 8 or 17 edges and columns at most 3, as space-time
+                             matrices with or without hook faults; shorter rows are
+                             padded) */
   int32_t lsd_kernel;     /* LSD kernel: 0 = auto, 1 = dense (state indexed by detector and
                              fault, m <= 512, n <= 2048), 2 = sparse (state sized by what a shot
                              touches; any m, n < 65536; no single_cluster) */
