@@ -13,7 +13,11 @@ independent, so there is no collective on the data path) and the step time is th
 over ranks.  ``--impl reference`` times the CPU oracle (the only reference this project
 has) on the host cores, on a bounded sample of the same workload.
 
-Prints one JSON line on rank 0.
+Rank 0 prints one JSON line per measured leg (learned prior, p sweep, LSD-mu, windows,
+giant shot, hook faults, HGP, serving, cluster histograms), then, as the LAST line of stdout,
+one compact headline line (about 2 KB) with the metric, the value, the roofline, the CPU
+baseline, the end-to-end figure and a summary of the learned prior at equal LER.
+``--legs-out PATH`` also writes every leg to one JSON file.
 """
 from __future__ import annotations
 
@@ -38,10 +42,10 @@ UNIT = "shots/s"
 # and subtract, and the hard-decision parity (about ten integer / FP32 operations).
 OPS_PER_EDGE_ITER = 10
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one 10^6-shot launch of bp_reg_kernel<32,3,6,5,3> on this
-# workload, from a one-pass ncu capture of the full workload
-# (profiles/bp_reg_kernel_bb144_p005.md); None once the kernel changes.
-BP_TRAFFIC_BYTES = 76266752 + 152703744
+# DRAM bytes (read + write) of one 10^6-shot BP launch on this workload (BB144, p = 0.05,
+# 50 iterations), per kernel variant, from a one-pass ncu capture of the full workload;
+# a variant without a capture reports traffic null.
+BP_TRAFFIC_BYTES = {"bp_reg_kernel<32,3,6,5,3>": 76266752 + 152703744}
 
 
 def parse():
@@ -75,6 +79,7 @@ def parse():
     ap.add_argument("--serving-loads", default="1e4,1e5,1e6,1e7",
                     help="offered loads (shots/s) of the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=0.5)
+    ap.add_argument("--legs-out", default=None, help="also write every leg to this JSON file")
     return ap.parse_args()
 
 
@@ -641,7 +646,7 @@ def hgp_leg(args, stream, flush, barrier):
     hx_sum, hx_m = int(hx.sum()), hx.shape[0]
     checker = LogicalChecker(hz)
     out = []
-    for p, shots in ((0.02, args.hgp_shots), (0.05, max(1, args.hgp_shots // 20))):
+    for p, shots in ((0.02, args.hgp_shots), (0.05, args.hgp_shots)):
         probs = np.full(n, p, np.float32)
         for order in (0, 10):
             dec = Decoder(hx, probs, 100, order, stream=stream)
@@ -661,8 +666,7 @@ def hgp_leg(args, stream, flush, barrier):
                         "bp_roofline": _bp_onchip_roofline(int(hx_sum), n, hx_m, shots, st)})
             dec.close()
     return {"code": "HGP of a seeded (3,4)-regular 48x64 matrix, H_X 3072x6400, E=21504",
-            "bp_iters": 100, "note": "p = 0.05 percolates: fewer shots (shots / 20)",
-            "points": out}
+            "bp_iters": 100, "points": out}
 
 
 def serving_leg(args):
@@ -697,6 +701,37 @@ def serving_leg(args):
             "noise": "phenomenological p = q = 0.003", "bp_iters": 30, "lsd_order": 0,
             "mix": "equal", "seconds_per_load": args.serving_seconds,
             "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)", "loads": out}
+
+
+def learned_summary(learned):
+    """The learned prior's headline figures and the BP+LSD points it is compared with."""
+    if not learned:
+        return None
+    out = {"rounds": learned["rounds"], "train_pairs": learned["train_pairs"],
+           "train_s": round(learned["train_s"], 3), "value": learned["value"],
+           "p99_ms": learned["latency_ms"]["p99"], "ler": learned["ler"],
+           "ler_sigma": learned["ler_sigma"], "kernel_ms": learned["kernel_ms"]}
+    pairs = learned.get("equal_ler_pairs") or []
+    if pairs:  # the fastest BP+LSD point whose LER is within 2 sigma of the learned one's
+        best = max(pairs, key=lambda x: x["bp_lsd_shots_per_s"])
+        out["equal_ler_bp_lsd"] = {"bp_iters": best["bp_iters"], "value": best["bp_lsd_shots_per_s"],
+                                   "p99_ms": best["bp_lsd_p99_ms"], "ler": best["ler_bp"]}
+    nw = learned.get("fastest_bp_lsd_at_no_worse_ler")
+    if nw:
+        out["fastest_bp_lsd_no_worse_ler"] = {"bp_iters": nw["bp_iters"],
+                                              "value": nw["bp_lsd_shots_per_s"],
+                                              "p99_ms": nw["bp_lsd_p99_ms"], "ler": nw["ler"]}
+    return out
+
+
+def serving_summary(serving):
+    """Per offered load: completed shots/s and p50 / p99 latency in microseconds."""
+    if not serving:
+        return None
+    return {"codes": "BB72 d=6, BB144 d=12, BB288 d=18 space-time, p=q=0.003",
+            "loads": [[x["offered_rate"], round(x["shots_per_s"]), round(x["p50_us"], 1),
+                       round(x["p99_us"], 1)] for x in serving["loads"]],
+            "columns": ["offered shots/s", "completed shots/s", "p50 us", "p99 us"]}
 
 
 def run_ours(args):
@@ -824,26 +859,28 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    from paper_2406_18655_gb300.lsd import bp_variant_name
     E = int(hx.sum())
     bp_ms_avg = float(np.mean(bp_ms))
     iters_per_step = iters_sum / args.steps
+    peak, peak_src = alu_peak()
     achieved = OPS_PER_EDGE_ITER * E * iters_per_step / (bp_ms_avg / 1000.0) / 1e12
-    alu_peak = sms * 128 * sm_max_mhz * 1e6 / 1e12  # FP32/INT32 lanes x max SM clock
-    roofline = {"bound": "alu", "kernel": "bp_kernel", "achieved": achieved, "peak": alu_peak,
-                "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": BP_TRAFFIC_BYTES,
-                "peak_source": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_max_mhz:.0f} MHz "
-                               "(max SM clock of MEASURED_PEAKS.json)",
+    bp_name = bp_variant_name(tune["bp_variant"]) if tune else None
+    roofline = {"bound": "alu", "kernel": bp_name or "bp (default variant)",
+                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": BP_TRAFFIC_BYTES.get(bp_name),
+                "peak_source": peak_src + " (max SM clock of MEASURED_PEAKS.json)",
                 "ops_per_unit": f"{OPS_PER_EDGE_ITER} ops per edge-iteration, {E} edges, "
                                 f"{iters_per_step:.0f} shot-iterations per launch"}
+    legs = {"lsd_clusters": clusters, "autotune": tune, "learned": learned,
+            "p_sweep": p_sweep, "lsd_mu_cs4": lsd_mu, "windows": windows, "giant_shot": giant,
+            "circuit_like": hooks, "hgp": hgp, "serving": serving}
+    for name, leg in legs.items():
+        if leg is not None:
+            print(json.dumps({"leg": name, "result": leg}), flush=True)
+    if args.legs_out:
+        with open(args.legs_out, "w") as f:
+            json.dump(legs, f, indent=1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -852,30 +889,20 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
                        "what": "batch latency of one step (10^6 shots, device-resident)"},
-        "ler": ler,
-        "bp_converged_frac": conv_frac,
-        "lsd_frac": lsd_frac,
+        "ler": ler, "bp_converged_frac": conv_frac, "lsd_frac": lsd_frac,
         "mean_bp_iters": iters_per_step / args.shots,
-        "kappa_max": kappa_max, "nu_max": nu_max,
-        "lsd_clusters": clusters,
-        "kernel_ms": {"bp_kernel": bp_ms_avg, "lsd_kernel": float(np.mean(lsd_ms))},
+        "kernel_ms": {"bp": bp_ms_avg, "lsd": float(np.mean(lsd_ms))},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
-        "autotune": tune,
         "clocks": clk.summary(),
-        "learned": learned,
-        "p_sweep": p_sweep,
-        "lsd_mu_cs4": lsd_mu,
-        "windows": windows,
-        "giant_shot": giant,
-        "circuit_like": hooks,
-        "hgp": hgp,
-        "serving": serving,
+        "learned": learned_summary(learned),
+        "serving": serving_summary(serving),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, hx, probs.astype(np.float64), s,
                                             args.cpu_seconds)
+    sys.stderr.flush()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -219,13 +219,19 @@ int lsd_get_stats(lsd_decoder* dec, lsd_stats* stats);
  *   syndromes    device [shots][m] bytes.  corrections device [shots][n] bytes.
  *   status       device [shots] bytes, nullable.
  * Behaviour:
+ *   - Decoders whose LSD runs in the sparse kernel (more than 512 detectors or 2048 faults:
+ *     the large HGP and space-time matrices) are refused with LSD_ERR_UNSUPPORTED, since
+ *     that kernel's per-warp scratch is not part of the array; so is a decoder without LSD.
  *   - The first call on a device looks up the array's device address on that device (the
  *     current one); make that first call before any stream capture.  Later calls reuse it.
+ *     A lookup that fails returns LSD_ERR_CUDA and is retried by the next call.
  *   - Every call, on every decoder, shares the one array; each call clears the counters it
  *     needs at its start.  Calls that overlap on the GPU (different streams, decoders or
  *     threads without ordering between them) race on the array and give wrong results:
  *     order them on one stream or synchronize between them.
  *   - Asynchronous on the decoder's stream, like lsd_decode_batch.
+ *   - It keeps no statistics: lsd_get_stats goes on reporting the decoder's last
+ *     lsd_decode_batch (or similar) call, not this one.
  */
 #define LSD_STATIC_SCRATCH_BYTES ((size_t)8 << 20)
 int lsd_decode_batch_static(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
@@ -550,6 +556,11 @@ typedef struct lsd_tune_report {
 } lsd_tune_report;
 int lsd_autotune(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
                  lsd_tune_report* report);
+
+/* lsd_bp_variant_name -- the BP kernel and template shape behind a variant id of
+ * lsd_tune_report.bp_variant, e.g. "bp_reg_kernel<32,3,6,5,3>" (as it appears in profiler
+ * launch lists).  Static storage owned by the library; "" for an unknown id.  No GPU call. */
+const char* lsd_bp_variant_name(int32_t variant);
 
 /* lsd_get_priors -- copy the n float32 priors lambda_j to host memory; synchronizes. */
 int lsd_get_priors(lsd_decoder* dec, float* priors);

@@ -163,23 +163,3 @@ def loss_and_grad(h, theta, syndromes, errors, lam, rounds: int = 4, hd: int = 3
     llr, cache = forward(g, theta, syndromes, lam, rounds, hd)
     loss, dllr = loss_and_dllr(llr, errors)
     return loss, backward(g, cache, dllr, rounds, hd), llr
-
-
-def init_params(seed: int, hd: int = 32, scale2: float = 0.1):
-    """A seeded initialisation: uniform fan-in scaling, second layers scaled down, output
-    weights zero (the untrained prior returns the channel prior exactly)."""
-    rng = np.random.default_rng(seed)
-    p = {}
-    din = 2 * hd + 1
-    p["a0"] = rng.uniform(-1, 1, hd)
-    p["a1"] = rng.uniform(0, 0.5, hd)
-    p["u0"] = rng.uniform(-1, 1, hd)
-    p["u1"] = rng.uniform(-0.1, 0.1, hd)
-    for d in ("cv", "vc"):
-        p["W1_" + d] = rng.uniform(-1, 1, (hd, din)) / np.sqrt(din)
-        p["b1_" + d] = np.zeros(hd)
-        p["W2_" + d] = rng.uniform(-1, 1, (hd, hd)) / np.sqrt(hd) * scale2
-        p["b2_" + d] = np.zeros(hd)
-    p["w_o"] = np.zeros(hd)
-    p["b_o"] = np.zeros(1)
-    return flatten(p, hd)

@@ -672,6 +672,11 @@ int lsd_kernel_launches(const lsd_decoder* d, int64_t* count) {
   return LSD_OK;
 }
 
+const char* lsd_bp_variant_name(int32_t variant) {
+  const char* s = bp_variant_name(variant);
+  return s ? s : "";
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
@@ -685,26 +690,28 @@ static __device__ __align__(256) unsigned char g_static_scratch[LSD_STATIC_SCRAT
 
 constexpr int kMaxStaticDevices = 64;
 
-struct StaticScratchSlot {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
-  void* ptr = nullptr;
-};
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {};
 
-StaticScratchSlot g_static_slots[kMaxStaticDevices];
-
-// Device address of g_static_scratch on the current device (first use: the lookup).
+// Device address of g_static_scratch on the current device.  Only a successful lookup is
+// kept: a failed one (for example a first call made during stream capture) clears the
+// runtime's error state and is retried by the next call.
 int static_scratch(void** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
   if (dev < 0 || dev >= kMaxStaticDevices) return LSD_ERR_UNSUPPORTED;
-  StaticScratchSlot& slot = g_static_slots[dev];
-  std::call_once(slot.once, [&slot]() {
-    slot.err = cudaGetSymbolAddress(&slot.ptr, g_static_scratch);
-  });
-  if (slot.err != cudaSuccess || !slot.ptr) return cuda_fail(slot.err);
-  *ptr = slot.ptr;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    }
+    g_static_ptr[dev] = p;
+  }
+  *ptr = g_static_ptr[dev];
   return LSD_OK;
 }
 

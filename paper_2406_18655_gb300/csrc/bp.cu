@@ -646,9 +646,12 @@ __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
 struct RegShape {
   int G, cpl, dc, vpl, dv;
   const void* fn;
+  const char* name;
 };
 
-#define LSD_REG_SHAPE(G, C, DCx, V, DVx) {G, C, DCx, V, DVx, (const void*)bp_reg_kernel<G, C, DCx, V, DVx>}
+#define LSD_REG_SHAPE(G, C, DCx, V, DVx)                                 \
+  {G, C, DCx, V, DVx, (const void*)bp_reg_kernel<G, C, DCx, V, DVx>,     \
+   "bp_reg_kernel<" #G "," #C "," #DCx "," #V "," #DVx ">"}
 const RegShape kRegShapes[] = {
     LSD_REG_SHAPE(16, 3, 6, 5, 3),   // m <= 48,  n <= 80   (BB [[72,12,6]])
     LSD_REG_SHAPE(32, 3, 6, 5, 3),   // m <= 96,  n <= 160  (BB [[144,12,12]])
@@ -693,9 +696,11 @@ struct RegCtaShape {
   int nt, cpl, dc, vpl, dv;
   bool pad;
   const void* fn;
+  const char* name;
 };
-#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx, P, MB) \
-  {NT, C, DCx, V, DVx, P, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB>}
+#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx, P, MB)                               \
+  {NT, C, DCx, V, DVx, P, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB>, \
+   "bp_regcta_kernel<" #NT "," #C "," #DCx "," #V "," #DVx "," #P "," #MB ">"}
 const RegCtaShape kRegCtaShapes[] = {
     LSD_REGCTA_SHAPE(768, 4, 7, 9, 4, false, 1),   // m <= 3072, n <= 6912 (HGP of a 48 x 64 (3,4) code)
     LSD_REGCTA_SHAPE(512, 6, 7, 13, 4, false, 1),  // same graphs, fewer threads
@@ -738,6 +743,15 @@ const void* variant_fn(int v) {
 }  // namespace
 
 int bp_num_variants() { return kRegCtaBase + kNumRegCtaShapes; }
+
+const char* bp_variant_name(int v) {
+  static const char* const generic[6] = {"bp_kernel<8,0>", "bp_kernel<16,0>", "bp_kernel<32,0>",
+                                         "bp_kernel<8,1>", "bp_kernel<16,1>", "bp_kernel<32,1>"};
+  if (v < 0 || v >= bp_num_variants()) return nullptr;
+  if (is_regcta(v)) return kRegCtaShapes[v - kRegCtaBase].name;
+  if (is_cta(v)) return v == kCtaBase ? "bp_cta_kernel<0>" : "bp_cta_kernel<1>";
+  return v >= 6 ? kRegShapes[v - 6].name : generic[v];
+}
 
 cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
                       int* grid, int* block, size_t* smem) {

@@ -87,6 +87,7 @@ cudaError_t launch_bp(const BPArgs& a, int variant, int grid, int block, size_t 
 cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* variant,
                       int* grid, int* block, size_t* smem);
 int bp_num_variants();
+const char* bp_variant_name(int variant);  // nullptr for an unknown id
 cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaStream_t st);
 cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, int* grid,
                        size_t* smem, int* words);

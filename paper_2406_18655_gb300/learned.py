@@ -19,22 +19,25 @@ PARAM_SHAPES = [("a0", (HIDDEN,)), ("a1", (HIDDEN,)), ("u0", (HIDDEN,)), ("u1", 
                 ("w_o", (HIDDEN,)), ("b_o", (1,))]
 
 
-def init_params(seed: int, scale2: float = 0.1) -> np.ndarray:
+def init_params(seed: int, scale2: float = 0.1, hd: int = HIDDEN) -> np.ndarray:
     """Seeded initialisation: fan-in uniform first layers, second layers scaled by `scale2`,
-    zero output weights, so the untrained prior returns the channel prior exactly."""
+    zero output weights, so the untrained prior returns the channel prior exactly.
+
+    Flat, in the C ABI's parameter order, float32.  `hd` other than 32 is for small CPU
+    models only (the kernels are built for a hidden width of 32)."""
     rng = np.random.default_rng(seed)
     parts = {}
-    din = 2 * HIDDEN + 1
-    parts["a0"] = rng.uniform(-1, 1, HIDDEN)
-    parts["a1"] = rng.uniform(0, 0.5, HIDDEN)
-    parts["u0"] = rng.uniform(-1, 1, HIDDEN)
-    parts["u1"] = rng.uniform(-0.1, 0.1, HIDDEN)
+    din = 2 * hd + 1
+    parts["a0"] = rng.uniform(-1, 1, hd)
+    parts["a1"] = rng.uniform(0, 0.5, hd)
+    parts["u0"] = rng.uniform(-1, 1, hd)
+    parts["u1"] = rng.uniform(-0.1, 0.1, hd)
     for d in ("cv", "vc"):
-        parts["W1_" + d] = rng.uniform(-1, 1, (HIDDEN, din)) / np.sqrt(din)
-        parts["b1_" + d] = np.zeros(HIDDEN)
-        parts["W2_" + d] = rng.uniform(-1, 1, (HIDDEN, HIDDEN)) / np.sqrt(HIDDEN) * scale2
-        parts["b2_" + d] = np.zeros(HIDDEN)
-    parts["w_o"] = np.zeros(HIDDEN)
+        parts["W1_" + d] = rng.uniform(-1, 1, (hd, din)) / np.sqrt(din)
+        parts["b1_" + d] = np.zeros(hd)
+        parts["W2_" + d] = rng.uniform(-1, 1, (hd, hd)) / np.sqrt(hd) * scale2
+        parts["b2_" + d] = np.zeros(hd)
+    parts["w_o"] = np.zeros(hd)
     parts["b_o"] = np.zeros(1)
     return np.concatenate([parts[k].ravel() for k, _ in PARAM_SHAPES]).astype(np.float32)
 

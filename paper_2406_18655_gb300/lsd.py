@@ -37,7 +37,7 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy",
            "lsd_window_stream_reset", "lsd_window_stream_push", "lsd_giant_create",
            "lsd_giant_decode", "lsd_giant_postprocess", "lsd_giant_kernel_launches",
-           "lsd_giant_destroy", "lsd_giant_test_hold_barrier")
+           "lsd_giant_destroy", "lsd_giant_test_hold_barrier", "lsd_bp_variant_name")
 
 
 class LsdError(RuntimeError):
@@ -142,9 +142,10 @@ def lib():
     L.lsd_window_stream_push.argtypes = [P, P, P, P, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32)]
     L.lsd_status_string.argtypes = [C.c_int]
-    L.lsd_status_string.restype = C.c_char_p
+    L.lsd_bp_variant_name.argtypes = [C.c_int32]
     for name in EXPORTS:
-        getattr(L, name).restype = (C.c_char_p if name in ("lsd_status_string", "lsd_last_error")
+        getattr(L, name).restype = (C.c_char_p if name in ("lsd_status_string", "lsd_last_error",
+                                                           "lsd_bp_variant_name")
                                     else C.c_int)
     _lib = L
     return L
@@ -152,6 +153,11 @@ def lib():
 
 def status_string(code: int) -> str:
     return lib().lsd_status_string(int(code)).decode()
+
+
+def bp_variant_name(variant: int) -> str:
+    """Kernel and template shape of a BP variant id (``Decoder.autotune()['bp_variant']``)."""
+    return lib().lsd_bp_variant_name(int(variant)).decode()
 
 
 def _check(code: int, what: str):

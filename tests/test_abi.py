@@ -97,3 +97,12 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lsdlib):
     # NULL handles are rejected or ignored
     assert L.lsd_destroy(None) == 0
     assert L.lsd_decode_batch(None, 1, None, None, None, None, None) == -1
+
+
+def test_bp_variant_names(lsdlib):
+    """Variant ids of the autotuner's report name the kernel and shape that ran (host only)."""
+    names = [lsdlib.bp_variant_name(v) for v in range(64)]
+    assert names[2] == "bp_kernel<32,0>"
+    assert names[7] == "bp_reg_kernel<32,3,6,5,3>"
+    assert any(n.startswith("bp_regcta_kernel<128,3,8,6,3,true,6>") for n in names)
+    assert lsdlib.bp_variant_name(-1) == "" and names[-1] == ""

@@ -15,6 +15,7 @@ import torch
 
 import oracle.prior as P
 from paper_2406_18655_gb300 import inputs as I
+from paper_2406_18655_gb300.learned import init_params
 from tests.gpu_cases import logicals_hz, sample
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +41,7 @@ def bf16_weights(theta):
 
 def params_case(seed):
     rng = np.random.default_rng(seed)
-    pp = P.unflatten(P.init_params(seed))
+    pp = P.unflatten(init_params(seed))
     pp["w_o"] = rng.normal(0, 0.3, 32)
     pp["b_o"] = np.array([0.05])
     for d in ("cv", "vc"):
@@ -106,7 +107,7 @@ def test_training_gains_over_lsd_on_channel_priors(L):
     name, p = "bb144", 0.05
     h, probs, _, _ = sample(name, p, 1, seed=1)
     d = L.Decoder(h, probs, 50)
-    pr = L.Prior(d, rounds=4, params=P.init_params(7).astype(np.float32))
+    pr = L.Prior(d, rounds=4, params=init_params(7))
     losses = []
     batch = 2048
     for step in range(250):
@@ -129,7 +130,10 @@ def test_training_gains_over_lsd_on_channel_priors(L):
     ler_learned = chk.failures(ed, corr_l).float().mean().item()
     ler_prior = chk.failures(ed, corr_0).float().mean().item()
     ler_bp = chk.failures(ed, corr_bp).float().mean().item()
+    d4 = L.Decoder(h, probs, 4)  # BP with as many message-passing rounds as the network
+    corr_bp4, _ = d4.decode(sd)
+    ler_bp4 = chk.failures(ed, corr_bp4).float().mean().item()
     print(f"LER learned+LSD {ler_learned:.4f}  LSD on channel priors {ler_prior:.4f}  "
-          f"BP(50)+LSD {ler_bp:.4f}")
+          f"BP(4)+LSD {ler_bp4:.4f}  BP(50)+LSD {ler_bp:.4f}")
     sigma = np.sqrt(ler_prior * (1 - ler_prior) / 20000)
     assert ler_learned < ler_prior - 3 * sigma

@@ -1,8 +1,12 @@
 """Learned-prior oracle (float64 numpy) pinned by finite differences and closed forms (no GPU)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import prior as P
+from paper_2406_18655_gb300.learned import init_params
 from paper_2406_18655_gb300 import inputs as I
 
 
@@ -11,7 +15,7 @@ def _case(seed, shots=3, p=0.08):
     e = I.sample_errors(seed, shots, np.full(72, p))
     s = I.syndromes(h, e)
     lam = np.full(72, np.log((1 - p) / p))
-    theta = P.init_params(seed)
+    theta = init_params(seed).astype(np.float64)
     rng = np.random.default_rng(seed + 1)
     pp = P.unflatten(theta)
     pp["w_o"] = rng.normal(0, 0.3, 32)
@@ -84,3 +88,27 @@ def test_messages_follow_the_tanner_graph():
     # round 1) nothing else yet reaches the output
     assert set(changed.tolist()) <= set(np.nonzero(h[c])[0].tolist())
     assert len(changed) > 0
+
+
+def _golden_rounds():
+    path = os.path.join(os.path.dirname(__file__), "golden", "prior_rounds_hand.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("rounds", [1, 2])
+def test_round_update_matches_hand_derivation(case, rounds):
+    """One and two rounds of the model stated in include/lsd.h, worked out by hand with
+    hidden width 2 (tests/golden/prior_rounds_hand.json holds the derivation): pins the
+    order of the MLP input blocks, the h_v^{t+1} read of the check update, the biases, the
+    orientation of W2 and the syndrome sign."""
+    g = _golden_rounds()
+    hd = g["hd"]
+    theta = P.flatten({k: np.array(v, dtype=np.float64) for k, v in g["params"].items()}, hd)
+    c = g["cases"][case]
+    h = np.array(c["H"], np.uint8)
+    llr, _ = P.forward(P.Graph(h), theta, np.array([c["syndrome"]], np.uint8),
+                       np.array(c["lambda"], np.float64), rounds=rounds, hd=hd)
+    # dyadic values throughout: float64 is exact
+    assert np.array_equal(llr[0], np.array(c["llr"][str(rounds)], np.float64)), llr[0]

@@ -69,3 +69,33 @@ def test_static_scratch_rejects_oversized_batches(L):
     assert _call_static(L, dec, sd[:14462], corr[:14462], status[:14462]) == L.LSD_OK
     torch.cuda.synchronize()
     assert np.all(status[:14462].cpu().numpy() == L.SHOT_OK_BP)  # zero syndromes
+
+
+def test_static_scratch_padded_cta_kernel_without_status(L):
+    """A BB[[72,12,6]] space-time matrix over 6 noisy rounds (252 x 648, rows of 8 edges and
+    1 in the last block): BP runs in the register-table CTA kernel with padded rows and LSD
+    in the dense kernel.  No status buffer is passed; the corrections must still equal
+    lsd_decode_batch's, on two calls in a row."""
+    from paper_2406_18655_gb300 import inputs as I
+    hx = I.bb72()[0]
+    m0, n0 = hx.shape
+    h = I.space_time(hx, 6)
+    probs = I.space_time_probs(n0, m0, 6, 0.01, 0.01).astype(np.float32)
+    dec = L.Decoder(h, probs, 30)
+    ref = L.Decoder(h, probs, 30)
+    held = dec.workspace_bytes()
+    lsd_seen = False
+    for call, (shots, seed) in enumerate([(3000, 611), (1700, 612)]):
+        e = I.sample_errors(seed, shots, probs.astype(np.float64))
+        sd = torch.from_numpy(I.syndromes(h, e)).cuda()
+        corr = torch.full((shots, h.shape[1]), 7, dtype=torch.uint8, device="cuda")
+        rc = L.lib().lsd_decode_batch_static(dec._h, shots, C.c_void_p(sd.data_ptr()),
+                                             C.c_void_p(corr.data_ptr()), None)
+        assert rc == L.LSD_OK, f"call {call}"
+        torch.cuda.synchronize()
+        assert dec.workspace_bytes() == held
+        ref_c, ref_st = ref.decode(sd)
+        torch.cuda.synchronize()
+        assert torch.equal(corr, ref_c), f"call {call}: corrections differ"
+        lsd_seen |= bool((ref_st.cpu().numpy() == L.SHOT_OK_LSD).any())
+    assert lsd_seen  # the LSD kernel ran on the static queue
