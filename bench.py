@@ -673,34 +673,78 @@ def serving_leg(args):
     """Poisson arrivals mixing the space-time matrices of the BB [[72,12,6]], [[144,12,12]]
     and [[288,12,18]] codes (phenomenological noise p = q = 0.003 over d = 6, 12, 18 noisy
     rounds plus one noiseless round), decoded by the continuous-batching server (BP 30
-    iterations + LSD-0); p50 / p99 request latency and completed shots/s per offered load."""
+    iterations + LSD-0); p50 / p99 request latency and completed shots/s per offered load.
+    Then streams of BB[[144,12,12]] syndrome rounds (d = 12, p = q = 0.003) decoded in (3, 1)
+    windows inside the same server: per-round p50 / p99 (a window job's latency from the
+    submission of its completing block) at offered loads of stream rounds, alone and mixed
+    with the shots.  The reference point is the same three matrices decoded as plain
+    batches (65536 shots per code, device-resident)."""
     import torch
     from paper_2406_18655_gb300 import inputs as I
     from paper_2406_18655_gb300.lsd import Decoder, Server
 
-    codes, pools = [], []
+    codes, pools, batch_ms = [], [], []
     for k, (fn, d) in enumerate(((I.bb72, 6), (I.bb144, 12), (I.bb288, 18))):
         hx = fn()[0]
         h = I.space_time(hx, d)
         probs = I.space_time_probs(hx.shape[1], hx.shape[0], d, 0.003, 0.003).astype(np.float32)
-        dec = Decoder(h, probs, 1)
-        _, syn = dec.sample(args.seed + 101 + k, 8192)
-        pools.append(syn.cpu().pin_memory())
+        dec = Decoder(h, probs, 30)
+        _, syn = dec.sample(args.seed + 101 + k, 65536)
+        for _ in range(2):
+            dec.decode(syn)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            dec.decode(syn)
+        torch.cuda.synchronize()
+        batch_ms.append((time.perf_counter() - t0) / 3 * 1e3)
+        pools.append(syn[:8192].cpu().pin_memory())
         dec.close()
         codes.append((h, probs, 30, 0))
-    srv = Server(codes)
+    # batch throughput of the equal mix: 3 x 65536 shots in the summed batch times
+    mix_batch_rate = 3 * 65536 / (sum(batch_ms) / 1e3)
+    hx = I.bb144()[0]
+    m, n = hx.shape
+    d, streams = 12, 1024
+    probs = I.space_time_probs(n, m, d, 0.003, 0.003)
+    seqs = torch.from_numpy(I.syndromes(I.space_time(hx, d),
+                                        I.sample_errors(args.seed + 131, 4096, probs)))
+    wcode = dict(h=hx, p=0.003, q=0.003, rounds=d, window=3, commit=1, bp_iters=30,
+                 streams=streams)
+    srv = Server(codes, window_codes=[wcode])
     out = []
     for rate in [float(x) for x in args.serving_loads.split(",") if x]:
-        rep = srv.run_poisson(rate, args.serving_seconds, [1, 1, 1], pools, seed=args.seed + 7)
-        out.append({k: rep[k] for k in ("offered_rate", "generated", "completed", "shots_per_s",
-                                         "p50_us", "p99_us", "max_us", "mean_batch",
-                                         "admission_waits")})
+        rep = srv.run_poisson(rate, args.serving_seconds, [1, 1, 1, 0], pools + [seqs],
+                              seed=args.seed + 7)
+        pt = {k: rep[k] for k in ("offered_rate", "generated", "completed", "shots_per_s",
+                                  "p50_us", "p99_us", "max_us", "mean_batch", "admission_waits")}
+        pt["per_code_p50_p99_us"] = [[round(r["p50_us"], 1), round(r["p99_us"], 1)]
+                                     for r in (srv.code_report(c) for c in range(3))]
+        out.append(pt)
+    windows = []
+    for rate in (1e4, 1e5, 1e6):
+        for mixed in (False, True):
+            # mixed: the same round rate plus shots at a tenth of it
+            mix = [rate / 30, rate / 30, rate / 30, rate] if mixed else [0, 0, 0, rate]
+            total = sum(mix)
+            rep = srv.run_poisson(total, args.serving_seconds, mix, pools + [seqs],
+                                  seed=args.seed + 11)
+            w = srv.code_report(3)
+            windows.append({"offered_rounds_per_s": rate, "with_shots": mixed,
+                            "blocks": rep["generated"], "window_jobs": w["completed"],
+                            "rounds_per_s": w["completed"] / max(rep["seconds"], 1e-9),
+                            "p50_us": w["p50_us"], "p99_us": w["p99_us"], "max_us": w["max_us"],
+                            "refused_blocks": rep["admission_waits"]})
     srv.close()
     return {"codes": ["BB[[72,12,6]] d=6: H 252x648", "BB[[144,12,12]] d=12: H 936x2592",
                       "BB[[288,12,18]] d=18: H 2736x7776"],
             "noise": "phenomenological p = q = 0.003", "bp_iters": 30, "lsd_order": 0,
             "mix": "equal", "seconds_per_load": args.serving_seconds,
-            "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)", "loads": out}
+            "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)", "loads": out,
+            "batch_reference": {"ms_per_65536_shots": batch_ms,
+                                "mix_shots_per_s": mix_batch_rate},
+            "windows": {"code": "BB[[144,12,12]] rounds, d = 12, (3,1) windows, 1024 streams",
+                        "loads": windows}}
 
 
 def learned_summary(learned):
@@ -725,13 +769,19 @@ def learned_summary(learned):
 
 
 def serving_summary(serving):
-    """Per offered load: completed shots/s and p50 / p99 latency in microseconds."""
+    """Per offered load: completed shots/s and p50 / p99 latency in microseconds; per offered
+    round rate of the window streams: p50 / p99 per round, alone and mixed with shots."""
     if not serving:
         return None
     return {"codes": "BB72 d=6, BB144 d=12, BB288 d=18 space-time, p=q=0.003",
             "loads": [[x["offered_rate"], round(x["shots_per_s"]), round(x["p50_us"], 1),
                        round(x["p99_us"], 1)] for x in serving["loads"]],
-            "columns": ["offered shots/s", "completed shots/s", "p50 us", "p99 us"]}
+            "columns": ["offered shots/s", "completed shots/s", "p50 us", "p99 us"],
+            "batch_mix_shots_per_s": round(serving["batch_reference"]["mix_shots_per_s"]),
+            "window_rounds": [[x["offered_rounds_per_s"], int(x["with_shots"]),
+                               round(x["p50_us"], 1), round(x["p99_us"], 1)]
+                              for x in serving["windows"]["loads"]],
+            "window_columns": ["offered rounds/s", "with shots", "p50 us", "p99 us"]}
 
 
 def run_ours(args):

@@ -252,10 +252,13 @@ int lsd_decode_batch_static(lsd_decoder* dec, int64_t shots, const uint8_t* synd
  * Parameters: FP32 master copy, flat in the order a0, a1, u0, u1, W1_cv, b1_cv, W2_cv,
  * b2_cv, W1_vc, b1_vc, W2_vc, b2_vc, w_o, b_o (lsd_prior_num_params() floats).  The
  * matrix products run on the tensor cores with BF16 weights and activations and FP32
- * accumulation; node states and the loss are FP32.  The states of one shot live in one
- * CTA's shared memory: inference takes about 384 (n + m) + 64 max(n, m) + 16 KB bytes
- * (BB [[288,12,18]], 201 KB, fits); training takes more (up to m = 96, n = 192), and
- * lsd_prior_gradient / lsd_prior_train_step return LSD_ERR_UNSUPPORTED beyond that.
+ * accumulation; node states and the loss are FP32.  Inference runs on the tcgen05 tensor
+ * cores with the per-node projections held in tensor memory when H has at most 8 tiles of
+ * 128 node rows (ceil(n/128) + ceil(m/128) <= 8, e.g. BB [[144,12,12]]: 3), else on the
+ * per-node mma.sync kernel, whose states of one shot live in one CTA's shared memory (about
+ * 384 (n + m) + 64 max(n, m) + 16 KB bytes; BB [[288,12,18]], 201 KB, fits).  Training runs
+ * on the mma.sync kernels and takes more (up to m = 96, n = 192); lsd_prior_gradient /
+ * lsd_prior_train_step return LSD_ERR_UNSUPPORTED beyond that.
  * ------------------------------------------------------------------------------------ */
 #define LSD_PRIOR_HIDDEN 32
 typedef struct lsd_prior lsd_prior;
@@ -275,8 +278,16 @@ int lsd_prior_set_params(lsd_prior* prior, const float* params);
 int lsd_prior_get_params(lsd_prior* prior, float* params);
 
 /* lsd_prior_forward -- LLRs of every shot: syndromes device [shots][m] bytes, llrs device
- * [shots][n] float32.  Asynchronous. */
+ * [shots][n] float32.  Asynchronous on the mma.sync kernel; on the tensor-memory kernel it
+ * synchronizes and returns LSD_ERR_TIMEOUT if a completion wait inside the kernel ran out
+ * (after one second; the LLRs are then unspecified). */
 int lsd_prior_forward(lsd_prior* prior, int64_t shots, const uint8_t* syndromes, float* llrs);
+
+/* lsd_prior_set_kernel -- the inference kernel: 0 = automatic (the tensor-memory kernel
+ * when H fits it), 1 = the per-node mma.sync kernel, 2 = the tensor-memory kernel
+ * (LSD_ERR_UNSUPPORTED when H does not fit it).  Both compute the same model; their
+ * results differ only in rounding. */
+int lsd_prior_set_kernel(lsd_prior* prior, int32_t kernel);
 
 /*
  * lsd_prior_gradient -- loss and gradient over a batch without updating the parameters.
@@ -298,7 +309,8 @@ int lsd_prior_train_step(lsd_prior* prior, int64_t shots, const uint8_t* syndrom
  * (status 2).  Shots LSD cannot solve (status 3) are decoded again by the decoder's own
  * BP + LSD, the fallback.  Arguments as lsd_decode_batch, except that `status` is required
  * (the fallback reads it).  Synchronizes (the fallback needs the count of unsolved shots);
- * stats->bp_converged counts the shots the prior's hard decision solved.
+ * stats->bp_converged counts the shots the prior's hard decision solved.  LSD_ERR_TIMEOUT:
+ * a completion wait of the tensor-memory kernel ran out (after one second).
  */
 int lsd_decode_learned(lsd_decoder* dec, lsd_prior* prior, int64_t shots,
                        const uint8_t* syndromes, uint8_t* corrections, uint8_t* status,
@@ -475,12 +487,14 @@ int lsd_giant_destroy(lsd_giant* dec);
 
 /* ------------------------------------------------------------------------------------
  * Serving (no counterpart in the paper): continuous batching of single-shot requests over
- * several codes.  A scheduler thread keeps `slots_per_code` batches of each code in flight
- * (each slot a decoder with its own stream); a batch launches as soon as a slot is idle and
- * either max_batch requests wait or the oldest has waited max_wait_us, and only as many
- * shots as the memory budget still admits.  Request buffers are read and written by the
- * GPU directly: they must be page-locked host memory (cudaHostAlloc / cudaHostRegister) or
- * device memory, owned by the caller and valid until the request completes.
+ * several codes, and of streams of syndrome rounds decoded in overlapping windows (Methods
+ * 4.3).  A scheduler thread keeps `slots_per_code` batches of each code (each window
+ * matrix of a window code) in flight, each slot a decoder with its own stream; a batch
+ * launches as soon as a slot is idle (or, with max_wait_us > 0, once max_batch requests
+ * wait or the oldest has waited max_wait_us), and only as many shots as the memory budget
+ * still admits.  Request buffers are read and written by the GPU directly: they must be
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister) or device memory, owned by the
+ * caller and valid until the request completes.
  * ------------------------------------------------------------------------------------ */
 typedef struct lsd_server lsd_server;
 
@@ -496,7 +510,8 @@ typedef struct lsd_server_code {    /* one code served: the arguments of lsd_cre
 typedef struct lsd_server_options { /* zero = defaults */
   int32_t slots_per_code;   /* batches of one code in flight (default 3, at most 16) */
   int32_t max_batch;        /* shots per batch (default 8192) */
-  int32_t max_wait_us;      /* a partial batch launches once its oldest request waited this long (50) */
+  int32_t max_wait_us;      /* 0: an idle slot launches whatever is pending at once; > 0: a partial
+                               batch waits for max_batch requests or for its oldest to reach this age */
   int32_t use_graphs;       /* 0: each slot's batch pipeline (gather, BP, LSD, scatter) is captured
                                once as a CUDA graph and replayed per batch; -1: plain launches */
   size_t mem_budget;        /* device bytes of in-flight shots (m + 2n + 2 + 4(n+1) each); 0 = no limit */
@@ -515,22 +530,82 @@ typedef struct lsd_server_report {
 int lsd_server_create(lsd_server** out, int32_t n_codes, const lsd_server_code* codes,
                       const lsd_server_options* opt);
 
+/*
+ * Window codes: streams of repeated syndrome rounds of a code H (m x n) under
+ * phenomenological noise, d noisy rounds plus a noiseless one per sequence, decoded in
+ * (w, c) overlapping windows exactly as lsd_window_decode decodes them (Methods 4.3: the
+ * windows, their matrices and the commit rule are those of lsd_window_create).
+ */
+typedef struct lsd_server_window_code {
+  int32_t m, n;
+  int64_t nnz;
+  const int32_t* rows;      /* host COO of H (one round), as for lsd_create */
+  const int32_t* cols;
+  const float* p_data;      /* host, n data-fault probabilities */
+  const float* q_meas;      /* host, m measurement-fault probabilities */
+  int32_t rounds;           /* d >= 1: noisy rounds per sequence (d + 1 detector blocks) */
+  int32_t window, commit;   /* w >= 1, 1 <= c <= w */
+  int32_t bp_iters, lsd_order;
+  int32_t streams;          /* concurrent streams, 1 .. 2^24 */
+} lsd_server_window_code;
+
+/*
+ * lsd_server_create_with_windows -- a server of n_codes shot codes (user code ids
+ * 0 .. n_codes-1, lsd_server_submit) and n_window_codes window codes (ids n_codes ..
+ * n_codes + n_window_codes - 1, lsd_server_submit_round); n_codes + n_window_codes >= 1.
+ * Each window code holds two windows' decoders per slot (the inner window's matrix,
+ * w m x w (n+m), and the final window's), a pinned host history of 2 (d+1) m bytes per
+ * stream and m device bytes per stream (the measurement faults of its last committed round).
+ */
+int lsd_server_create_with_windows(lsd_server** out, int32_t n_codes, const lsd_server_code* codes,
+                                   int32_t n_window_codes, const lsd_server_window_code* wcodes,
+                                   const lsd_server_options* opt);
+
 /* Submits one shot: syndrome [m] bytes, correction [n] bytes and status [1] byte (both
  * nullable) in GPU-accessible memory (see above).  Thread-safe; returns at once. */
 int lsd_server_submit(lsd_server* s, int32_t code, const uint8_t* syndrome, uint8_t* correction,
                       uint8_t* status, int64_t* id);
 
+/*
+ * lsd_server_submit_round -- the next detector block of stream `stream` of window code
+ * `code`: [m] bytes of host memory (any; copied before the call returns).  Blocks 0 .. d
+ * of a stream form one sequence; after block d the stream's next block starts a new one.
+ * The block that completes a window (block t + w - 1 of the window starting at round t, or
+ * block d for the final window) makes it a request: once decoded, the corrections of the
+ * rounds the window commits -- `*rounds` rounds from `*first_round` on, [rounds][n + m]
+ * bytes, data faults then measurement faults per round -- go to `correction` and the
+ * window's LSD_SHOT_* status to `status` (both nullable, GPU-accessible as above).  A block
+ * that completes no window sets *first_round = -1, *rounds = 0 and leaves both untouched.
+ * Windows of one stream are decoded one at a time, in order; different streams batch
+ * together and with shot requests.  Returns LSD_ERR_ADMISSION (nothing stored) when block
+ * 0 of a sequence arrives while a window of the sequence two before it is still pending.
+ * Thread-safe; calls for one stream must come from one thread at a time, in round order.
+ */
+int lsd_server_submit_round(lsd_server* s, int32_t code, int32_t stream, const uint8_t* block,
+                            uint8_t* correction, uint8_t* status, int32_t* first_round,
+                            int32_t* rounds, int64_t* id);
+
 /* Blocks until every submitted request has completed. */
 int lsd_server_wait_all(lsd_server* s);
 
-/* Throughput, batching and latency since the last reset (reset != 0 clears them). */
+/* Throughput, batching and latency since the last reset (reset != 0 clears them).  For
+ * window codes a request is one window job (latency from its completing block's submission). */
 int lsd_server_get_report(lsd_server* s, lsd_server_report* report, int32_t reset);
+
+/* The same figures for one user code since the last reset (submitted, completed,
+ * shots_per_s over the server's whole reporting interval, latency percentiles). */
+int lsd_server_get_code_report(lsd_server* s, int32_t code, lsd_server_report* report);
 
 /*
  * lsd_server_run_poisson -- load test: requests arrive as a Poisson process of `rate`
- * shots/s for `seconds`; each picks code c with probability mix[c] / sum(mix) and the next
- * syndrome of pools[c] ([pool_sizes[c]][m_c] bytes, GPU-accessible, cycled); outputs are
- * discarded.  Waits for completion and fills `report` (latency from the scheduled arrival).
+ * shots/s for `seconds`; each picks code c with probability mix[c] / sum(mix) (one entry per
+ * user code, window codes included) and the next syndrome of pools[c] ([pool_sizes[c]][m_c]
+ * bytes, GPU-accessible, cycled); outputs are discarded.  For a window code an arrival is
+ * one detector block of the code's streams in turn, stream s playing the sequences s,
+ * s + S, s + 2S, ... of pools[c] ([pool_sizes[c]][(d+1) m] bytes, host memory); blocks
+ * refused for a busy history are dropped and counted in admission_waits.  Waits for
+ * completion and fills `report` (latency from the scheduled arrival); the per-code reports
+ * of the run stay readable until the next reset.
  */
 int lsd_server_run_poisson(lsd_server* s, double rate, double seconds, const double* mix,
                            const uint8_t* const* pools, const int64_t* pool_sizes, uint64_t seed,

@@ -67,7 +67,10 @@ struct lsd_prior {
   double* d_loss = nullptr;
   double* h_loss = nullptr;  // pinned
   float* d_scratch = nullptr;
+  int* d_flag = nullptr;     // set by the tensor-memory kernel when a wait runs out
   int grid_train = 0, grid_fwd = 0;
+  int grid_tc = 0;           // > 0: inference may run on the tensor-memory kernel
+  int kernel = 0;            // 0 auto, 1 per-node mma.sync kernel, 2 tensor-memory kernel
   int step = 0;
 };
 
@@ -79,6 +82,12 @@ int cuda_fail(cudaError_t e) {
   lsdgb::record_cuda_error(e);
   if (e == cudaErrorMemoryAllocation) return LSD_ERR_OOM;
   return LSD_ERR_CUDA;
+}
+
+// Inference of the prior on the tensor-memory kernel: chosen automatically when the graph
+// fits it, or on request.
+bool prior_uses_tc(const lsd_prior* p) {
+  return p->grid_tc > 0 && p->kernel != 1;
 }
 
 // Device allocation charged to the decoder (and to its memory budget).
@@ -775,7 +784,7 @@ void prior_free(lsd_prior* p) {
   if (!p) return;
   cudaStreamSynchronize(p->dec ? p->dec->st : nullptr);
   for (void* q : {(void*)p->d_params, (void*)p->d_grads, (void*)p->d_m, (void*)p->d_v,
-                  (void*)p->d_loss, (void*)p->d_scratch})
+                  (void*)p->d_loss, (void*)p->d_scratch, (void*)p->d_flag})
     if (q) cudaFree(q);
   if (p->h_loss) cudaFreeHost(p->h_loss);
   cudaGetLastError();
@@ -828,6 +837,10 @@ int lsd_prior_create(lsd_prior** out, lsd_decoder* d, int32_t rounds, const floa
     prior_free(p);
     return LSD_ERR_UNSUPPORTED;
   }
+  if (prior_tc_config(d->g, &p->grid_tc) != cudaSuccess) {
+    cudaGetLastError();
+    p->grid_tc = 0;
+  }
   // training is optional: its kernel keeps more per-shot state
   if (d->m > 96 || d->n > 192 ||
       prior_config(d->m, d->n, d->E, true, &p->grid_train) != cudaSuccess) {
@@ -839,6 +852,7 @@ int lsd_prior_create(lsd_prior** out, lsd_decoder* d, int32_t rounds, const floa
   if ((rc = prior_alloc((void**)&p->d_params, nb)) || (rc = prior_alloc((void**)&p->d_grads, nb)) ||
       (rc = prior_alloc((void**)&p->d_m, nb)) || (rc = prior_alloc((void**)&p->d_v, nb)) ||
       (rc = prior_alloc((void**)&p->d_loss, sizeof(double))) ||
+      (rc = prior_alloc((void**)&p->d_flag, sizeof(int))) ||
       (p->grid_train > 0 &&
        (rc = prior_alloc((void**)&p->d_scratch,
                          sizeof(float) * prior_scratch_floats(d->m, d->n, rounds, p->grid_train))))) {
@@ -851,6 +865,7 @@ int lsd_prior_create(lsd_prior** out, lsd_decoder* d, int32_t rounds, const floa
     return LSD_ERR_OOM;
   }
   *out = p;
+  cudaMemsetAsync(p->d_flag, 0, sizeof(int), d->st);
   if (params) return lsd_prior_set_params(p, params);
   cudaMemsetAsync(p->d_params, 0, nb, d->st);
   cudaMemsetAsync(p->d_m, 0, nb, d->st);
@@ -884,10 +899,33 @@ int lsd_prior_forward(lsd_prior* p, int64_t shots, const uint8_t* syndromes, flo
   if (shots == 0) return LSD_OK;
   if (!syndromes || !llrs) return LSD_ERR_INVALID_ARG;
   lsd_decoder* d = p->dec;
-  cudaError_t e = launch_prior(false, p->grid_fwd, d->g, p->rounds, p->d_params, shots,
-                               syndromes, nullptr, llrs, nullptr, nullptr, nullptr, d->st);
+  cudaError_t e;
+  if (prior_uses_tc(p)) {
+    e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), d->st);
+    if (e == cudaSuccess)
+      e = launch_prior_tc(p->grid_tc, d->g, p->rounds, p->d_params, shots, syndromes, llrs,
+                          nullptr, nullptr, nullptr, nullptr, nullptr, p->d_flag, d->st);
+  } else {
+    e = launch_prior(false, p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
+                     nullptr, llrs, nullptr, nullptr, nullptr, d->st);
+  }
   d->launches++;
-  return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!prior_uses_tc(p)) return LSD_OK;
+  // the tensor-memory kernel reports a completion wait that ran out (a device fault, never
+  // expected): synchronize and read its flag
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, d->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return flag ? LSD_ERR_TIMEOUT : LSD_OK;
+}
+
+int lsd_prior_set_kernel(lsd_prior* p, int32_t kernel) {
+  if (!p || kernel < 0 || kernel > 2) return LSD_ERR_INVALID_ARG;
+  if (kernel == 2 && p->grid_tc <= 0) return LSD_ERR_UNSUPPORTED;
+  p->kernel = kernel;
+  return LSD_OK;
 }
 
 int lsd_prior_gradient(lsd_prior* p, int64_t shots, const uint8_t* syndromes,
@@ -951,9 +989,14 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
   if (!st) return LSD_ERR_INVALID_ARG;
   if ((rc = reset_counters(d))) return rc;
   cudaEventRecord(d->ev[0], d->st);
-  cudaError_t e = launch_prior_decode(p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
-                                      nullptr, corrections, st, d->d_queue, d->d_queue_llr,
-                                      d->d_ctr, d->st);
+  cudaError_t e =
+      prior_uses_tc(p)
+          ? launch_prior_tc(p->grid_tc, d->g, p->rounds, p->d_params, shots, syndromes, nullptr,
+                            corrections, st, d->d_queue, d->d_queue_llr, d->d_ctr,
+                            &d->d_ctr->timeout_flag, d->st)
+          : launch_prior_decode(p->grid_fwd, d->g, p->rounds, p->d_params, shots, syndromes,
+                                nullptr, corrections, st, d->d_queue, d->d_queue_llr, d->d_ctr,
+                                d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   cudaEventRecord(d->ev[1], d->st);
@@ -980,6 +1023,7 @@ int lsd_decode_learned(lsd_decoder* d, lsd_prior* p, int64_t shots, const uint8_
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
   if (e != cudaSuccess) return cuda_fail(e);
   const DevCounters learned = *d->h_ctr;
+  if (learned.timeout_flag) return LSD_ERR_TIMEOUT;
   if (learned.unsolvable > 0) {
     std::vector<uint8_t> hs((size_t)shots);
     e = cudaMemcpy(hs.data(), st, (size_t)shots, cudaMemcpyDeviceToHost);

@@ -709,6 +709,7 @@ const RegCtaShape kRegCtaShapes[] = {
     LSD_REGCTA_SHAPE(128, 3, 8, 6, 3, true, 6),  // m <= 384, n <= 768 (BB144 (3,1) windows)
     LSD_REGCTA_SHAPE(256, 4, 8, 11, 3, true, 2),  // m <= 1024, n <= 2816 (BB144, d = 12)
     LSD_REGCTA_SHAPE(512, 2, 8, 6, 3, true, 1),  // m <= 1024, n <= 3072
+    LSD_REGCTA_SHAPE(512, 6, 8, 16, 3, true, 1),  // m <= 3072, n <= 8192 (BB288, d = 18)
     // ... with mid-round hook faults: rows of degree up to 17
     LSD_REGCTA_SHAPE(256, 2, 17, 9, 3, true, 2),  // m <= 512, n <= 2304 (BB144, d = 6)
     LSD_REGCTA_SHAPE(512, 1, 17, 5, 3, true, 1),  // m <= 512, n <= 2560

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+#include <vector>
+
 #include "../../include/lsd.h"
 
 namespace lsdgb {
@@ -127,11 +130,29 @@ cudaError_t launch_prior_decode(int grid, const DevGraph& g, int rounds, const f
                                 uint8_t* corrections, uint8_t* status, int32_t* queue,
                                 float* queue_llr, DevCounters* ctr, cudaStream_t st);
 constexpr int kPriorMaxRounds = 8;
+// Inference of the learned prior on tcgen05 tensor cores with TMEM-resident projections
+// (prior_tc.cu): graphs of at most 8 tiles of 128 node rows; same outputs as
+// launch_prior_decode; a completion wait that runs out sets *timeout_flag (nullable).
+cudaError_t prior_tc_config(const DevGraph& g, int* grid);
+cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float* params,
+                            long long shots, const uint8_t* syndromes, float* llr_out,
+                            uint8_t* corrections, uint8_t* status, int32_t* queue,
+                            float* queue_llr, DevCounters* ctr, int* timeout_flag,
+                            cudaStream_t st);
 
 // Decode whose shot count is read from device-visible memory at run time, so that one
 // captured CUDA graph serves every batch size up to max_shots (api.cu; used by the server).
 int decode_batch_counted(lsd_decoder* dec, int64_t max_shots, const long long* shots_dev,
                          const uint8_t* syndromes, uint8_t* corrections, uint8_t* status);
+
+// Decoder of one window of phenomenological rounds of H (window.cu; used by the server):
+// detector blocks 0..blocks-1 by fault rounds 0..rounds-1, [n data | m measurement] faults
+// per round with probabilities p (n) and q (m); h holds the (row, column) pairs of H.
+int window_decoder(lsd_decoder** out, int m, int n, const std::vector<std::pair<int, int>>& h,
+                   const float* p, const float* q, int rounds, int blocks, int bp_iters,
+                   int order, const lsd_options* opt);
+// First round of the final window of d rounds in (w, c) windows.
+int window_final_round(int d, int w, int c);
 
 // LSD for large matrices (lsd_sparse.cu).
 size_t sparse_scratch_ints(int m, int n, bool big, bool mu);

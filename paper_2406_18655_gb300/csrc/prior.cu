@@ -16,24 +16,17 @@
 #include <cuda_bf16.h>
 
 #include "lsd_internal.cuh"
+#include "prior_params.cuh"
 
 namespace lsdgb {
 
 namespace {
 
-constexpr int HD = 32;        // hidden width
-constexpr int DIN = 2 * HD + 1;
+using prior_params::DIN;
+using prior_params::HD;
+using prior_params::POff;
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-// offsets of the flat parameter vector
-struct POff {
-  static constexpr int a0 = 0, a1 = 32, u0 = 64, u1 = 96;
-  static constexpr int W1cv = 128, b1cv = W1cv + HD * DIN, W2cv = b1cv + HD, b2cv = W2cv + HD * HD;
-  static constexpr int W1vc = b2cv + HD, b1vc = W1vc + HD * DIN, W2vc = b1vc + HD,
-                       b2vc = W2vc + HD * HD;
-  static constexpr int wo = b2vc + HD, bo = wo + HD, total = bo + 1;
-};
 
 // ---- mma.sync helpers (PTX ISA fragment layouts for m16n8k16 .bf16) ----
 __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {

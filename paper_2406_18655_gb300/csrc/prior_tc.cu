@@ -1,0 +1,608 @@
+// Learned prior, inference on the 5th-generation tensor cores: the per-node projections of
+// every round live in tensor memory (TMEM) as FP32 accumulators, and each round's dense
+// products are tcgen05.mma instructions (BF16 operands from shared memory, FP32 accumulate)
+// issued by one thread and tracked by an mbarrier.  The paper has no learned component; the
+// model is the one defined in include/lsd.h (see prior.cu for its restatement).
+//
+// Reformulation.  The projections the gathers read are linear in the node states:
+//   P_v = [C_v | B_v] = Wv h_v,   Wv = [W1vc[:, 0:32] ; W1cv[:, 32:64]]            (64 x 32)
+//   P_c = [A_c | D_c] = Wc h_c + sigma_c ws + b1,   Wc = [W1cv[:, 0:32] ; W1vc[:, 32:64]]
+// and a round adds W2 S + deg b2 to a state, so the projections themselves advance by
+//   P_v <- P_v + Mv S_v + deg_v kv,   Mv = Wv W2cv,  kv = Wv b2cv
+//   P_c <- P_c + Mc T_c + deg_c kc,   Mc = Wc W2vc,  kc = Wc b2vc
+// (S_v = sum_c relu(A_c + B_v), T_c = sum_v relu(C_v + D_c): the gathers).  The states are
+// never formed: TMEM holds P^0 + sum_t M S^t per node row, the deg k terms are added in FP32
+// when a row is read, and the output LLR_v = lambda_v + w_o . h_v^R + b_o is tracked as
+//   y_v = lambda_v + w_o . h_v^0 + b_o + sum_t (W2cv^T w_o) . S_v^t + deg_v (w_o . b2cv).
+// The initial projections do not depend on the shot for variables (h_v^0 is a function of
+// lambda_v) and take one of two values for checks (sigma_c = +-1): both are tabulated once
+// per CTA.  Weights are rounded to BF16, Mv and Mc formed from the rounded factors in FP32
+// and rounded to BF16 once; accumulators, biases and LLRs stay FP32.
+//
+// Layout.  One CTA works on one shot at a time: variable rows 0..n-1 in vt 128-row tiles and
+// check rows 0..m-1 in ct tiles, 64 TMEM columns per tile (vt + ct <= 8).  A round:
+//   X2 (all threads, 4 per row, 8 features each): S_v from the A_c rows in shared memory and
+//       the row's own B_v; BF16 S_v into the MMA operand buffer; the LLR update
+//   MMA (one thread): P_v tiles += S tile x Mv^T (M = 128, N = 64, K = 32: two K = 16 steps)
+//   epilogue (the warps whose TMEM lane quarter holds the row): tcgen05.ld of P_v, + deg kv,
+//       BF16 C_v and B_v rows into shared memory
+//   X1, MMA on the check tiles, epilogue: the same for T_c, P_c, A_c and D_c
+// The last round stops after X2 (only the LLR needs it).  Shared-memory operands use the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices, adjacent along K
+// 128 bytes apart, adjacent along M/N 512 bytes apart (a K = 32 BF16 row block).
+#include <cuda_bf16.h>
+
+#include "lsd_internal.cuh"
+#include "prior_params.cuh"
+
+namespace lsdgb {
+
+namespace {
+
+using prior_params::DIN;
+using prior_params::HD;
+using prior_params::POff;
+
+constexpr int kTcMinWarps = 8, kTcMaxWarps = 12;
+constexpr int kTcMaxTiles = 8;  // variable + check tiles: 64 TMEM columns each, 512 in all
+
+struct TcArgs {
+  int m, n, rounds, vt, ct, tmem_cols;
+  const int32_t* chk_ptr;
+  const uint16_t* chk_var;
+  const int32_t* var_ptr;
+  const uint16_t* var_chk;
+  const float* prior;
+  const float* params;
+  long long shots;
+  const uint8_t* syndromes;
+  float* llr_out;       // [shots][n], or null: decode mode (as prior_fwd_kernel)
+  uint8_t* corrections;
+  uint8_t* status;
+  int32_t* queue;
+  float* queue_llr;
+  DevCounters* ctr;
+  int* timeout_flag;    // set when an MMA completion wait runs out (nullable)
+};
+
+struct TcLay {
+  size_t mv, mc, op, as, ds, cs, bs, p0, pc0, kv, kc, u, y0, llr, degv, degc, sig, misc, total;
+};
+
+__host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline TcLay tc_layout(int m, int n, int vt, int ct) {
+  TcLay L;
+  size_t o = 0;
+  L.mv = o; o += 4096;                                   // Mv: 64 x 32 BF16, K-major
+  L.mc = o; o += 4096;                                   // Mc
+  // S or T tiles (128 x 32 BF16 each); at set-up, Wv and Wc in FP32 (16 KB)
+  L.op = o; o += (size_t)(vt > ct ? (vt > 2 ? vt : 2) : (ct > 2 ? ct : 2)) * 8192;
+  L.as = o; o += al((size_t)m * 64, 128);                // BF16 rows [m][32] (swizzled)
+  L.ds = o; o += al((size_t)m * 64, 128);
+  L.cs = o; o += al((size_t)n * 64, 128);
+  L.bs = o; o += al((size_t)n * 64, 128);                // at set-up, with cs: h_v^0 [n][32] FP32
+  L.p0 = o; o += (size_t)n * 256;                        // FP32 [n][64]
+  L.pc0 = o; o += 512;                                   // FP32 [2][64]: sigma = +1, -1
+  L.kv = o; o += 256;
+  L.kc = o; o += 256;
+  L.u = o; o += 128;
+  L.y0 = o; o += al((size_t)n * 4, 16);
+  L.llr = o; o += al((size_t)n * 4, 16);
+  L.degv = o; o += al((size_t)n * 4, 16);
+  L.degc = o; o += al((size_t)m * 4, 16);
+  L.sig = o; o += al((size_t)m * 4, 16);
+  L.misc = o; o += 64;                                   // kappa, TMEM address, mbarrier, flags
+  L.total = o;
+  return L;
+}
+
+// ---- PTX helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading (K direction) and
+// stride (M/N direction) byte offsets in 16-byte units, the fixed version field 0b001 at
+// bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+// Byte offset of element (row r, column k) of a K-major operand with K = 32 per row block.
+__device__ __forceinline__ int koff(int r, int k) {
+  return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N = 64, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+      :: "r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(1));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the mbarrier phase with the given parity; false after about one second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = smem_u32(mbar);
+  uint32_t done = 0;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* f) {
+  uint32_t v[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* f) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};"
+      :: "r"(taddr), "r"(__float_as_uint(f[0])), "r"(__float_as_uint(f[1])),
+         "r"(__float_as_uint(f[2])), "r"(__float_as_uint(f[3])), "r"(__float_as_uint(f[4])),
+         "r"(__float_as_uint(f[5])), "r"(__float_as_uint(f[6])), "r"(__float_as_uint(f[7])),
+         "r"(__float_as_uint(f[8])), "r"(__float_as_uint(f[9])), "r"(__float_as_uint(f[10])),
+         "r"(__float_as_uint(f[11])), "r"(__float_as_uint(f[12])), "r"(__float_as_uint(f[13])),
+         "r"(__float_as_uint(f[14])), "r"(__float_as_uint(f[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ void unpack8(const uint4 v, float f[8]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+// BF16 node rows [rows][32]: the 16-byte chunk b of row r sits at chunk b ^ ((r >> 1) & 3),
+// so 32 lanes writing one row each (the epilogue) spread over all banks.
+__device__ __forceinline__ uint4* row_chunk(unsigned char* base, int r, int b) {
+  return reinterpret_cast<uint4*>(base + (size_t)r * 64 + ((b ^ ((r >> 1) & 3)) << 4));
+}
+
+// Epilogue / init of one 32-row chunk of a tile: rows r0 .. r0+31 (this lane: r0 + lane).
+// mode 0: init from the tables (variables: P0; checks: Pc0[sigma]) with tcgen05.st;
+// mode 1: read the accumulators and add `nb` deg k.  Writes the two BF16 halves (columns
+// 0-31 and 32-63) to the row arrays lo and hi, 16 columns at a time.
+__device__ __forceinline__ void tc_rows(uint32_t taddr, int r, int rows, bool check, int mode,
+                                        float nb, const float* p0, const float* pc0,
+                                        const float* k, const float* deg, const float* sig,
+                                        unsigned char* lo, unsigned char* hi) {
+  const bool ok = r < rows;
+  const float dk = ok ? nb * deg[r] : 0.f;
+  const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (size_t)(ok ? r : 0) * 64;
+#pragma unroll 1
+  for (int part = 0; part < 4; ++part) {
+    float f[16];
+    if (mode == 0) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f[i] = src[part * 16 + i];
+      tmem_st16(taddr + part * 16, f);
+    } else {
+      tmem_ld16(taddr + part * 16, f);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f[i] = fmaf(dk, k[part * 16 + i], f[i]);
+    }
+    if (ok) {
+      unsigned char* dst = part < 2 ? lo : hi;
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        *row_chunk(dst, r, (part & 1) * 2 + b) =
+            make_uint4(pack2(f[8 * b], f[8 * b + 1]), pack2(f[8 * b + 2], f[8 * b + 3]),
+                       pack2(f[8 * b + 4], f[8 * b + 5]), pack2(f[8 * b + 6], f[8 * b + 7]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int m = a.m, n = a.n, R = a.rounds, vt = a.vt, ct = a.ct;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, T = blockDim.x;
+  const int W = T >> 5;
+  const TcLay L = tc_layout(m, n, vt, ct);
+  unsigned char* mv = smem + L.mv;
+  unsigned char* mc = smem + L.mc;
+  unsigned char* op = smem + L.op;
+  unsigned char* as = smem + L.as;
+  unsigned char* ds = smem + L.ds;
+  unsigned char* cs = smem + L.cs;
+  unsigned char* bs = smem + L.bs;
+  float* p0 = reinterpret_cast<float*>(smem + L.p0);
+  float* pc0 = reinterpret_cast<float*>(smem + L.pc0);
+  float* kv = reinterpret_cast<float*>(smem + L.kv);
+  float* kc = reinterpret_cast<float*>(smem + L.kc);
+  float* u = reinterpret_cast<float*>(smem + L.u);
+  float* y0 = reinterpret_cast<float*>(smem + L.y0);
+  float* llr = reinterpret_cast<float*>(smem + L.llr);
+  float* degv = reinterpret_cast<float*>(smem + L.degv);
+  float* degc = reinterpret_cast<float*>(smem + L.degc);
+  float* sig = reinterpret_cast<float*>(smem + L.sig);
+  float* kappa = reinterpret_cast<float*>(smem + L.misc);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc + 8);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.misc + 16);
+  const float* P = a.params;
+
+  // ---- tables: Mv, Mc (BF16 operands), kv, kc, P0, Pc0, y0, u, kappa, degrees ----
+  // staging: BF16-rounded Wv and Wc (FP32) in the operand buffer, h_v^0 over cs / bs
+  float* swv = reinterpret_cast<float*>(op);
+  float* swc = swv + 64 * HD;
+  float* h0 = reinterpret_cast<float*>(cs);
+  for (int i = tid; i < 64 * HD; i += T) {
+    const int o = i >> 5, j = i & 31;
+    swv[i] = bfr(o < HD ? __ldg(P + POff::W1vc + o * DIN + j) : __ldg(P + POff::W1cv + (o - HD) * DIN + HD + j));
+    swc[i] = bfr(o < HD ? __ldg(P + POff::W1cv + o * DIN + j) : __ldg(P + POff::W1vc + (o - HD) * DIN + HD + j));
+  }
+  for (int i = tid; i < n * HD; i += T) {
+    const int v = i >> 5, j = i & 31;
+    h0[i] = fmaxf(fmaf(__ldg(a.prior + v), __ldg(P + POff::a0 + j), __ldg(P + POff::a1 + j)), 0.f);
+  }
+  __syncthreads();
+  for (int i = tid; i < 2 * 64 * HD; i += T) {
+    const bool chk = i >= 64 * HD;
+    const int o = (i >> 5) & 63, kk = i & 31;
+    const float* w = (chk ? swc : swv) + o * HD;
+    const float* w2 = P + (chk ? POff::W2vc : POff::W2cv) + kk;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < HD; ++j) acc = fmaf(w[j], bfr(__ldg(w2 + j * HD)), acc);
+    *reinterpret_cast<__nv_bfloat16*>((chk ? mc : mv) + koff(o, kk)) = __float2bfloat16_rn(acc);
+  }
+  for (int o = tid; o < 64; o += T) {
+    float a1 = 0.f, a2 = 0.f, sp = 0.f, sm = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < HD; ++j) {
+      const float v = swv[o * HD + j], c = swc[o * HD + j];
+      a1 = fmaf(v, __ldg(P + POff::b2cv + j), a1);
+      a2 = fmaf(c, __ldg(P + POff::b2vc + j), a2);
+      const float u0 = __ldg(P + POff::u0 + j), u1 = __ldg(P + POff::u1 + j);
+      sp = fmaf(c, u1 + u0, sp);  // h_c^0 = sigma u0 + u1, sigma = +1
+      sm = fmaf(c, u1 - u0, sm);  //                        sigma = -1
+    }
+    kv[o] = a1;
+    kc[o] = a2;
+    const float ws = bfr(o < HD ? __ldg(P + POff::W1cv + o * DIN + 2 * HD)
+                                : __ldg(P + POff::W1vc + (o - HD) * DIN + 2 * HD));
+    const float b1 = o < HD ? __ldg(P + POff::b1cv + o) : __ldg(P + POff::b1vc + o - HD);
+    pc0[o] = sp + ws + b1;
+    pc0[64 + o] = sm - ws + b1;
+  }
+  for (int kk = tid; kk < HD; kk += T) {
+    float acc = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < HD; ++o)
+      acc = fmaf(bfr(__ldg(P + POff::W2cv + o * HD + kk)), __ldg(P + POff::wo + o), acc);
+    u[kk] = acc;
+  }
+  if (tid == 0) {
+    float acc = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < HD; ++o) acc = fmaf(__ldg(P + POff::wo + o), __ldg(P + POff::b2cv + o), acc);
+    *kappa = acc;
+  }
+  for (int i = tid; i < n * 64; i += T) {
+    const int v = i >> 6, o = i & 63;
+    const float* w = swv + o * HD;
+    const float* h = h0 + v * HD;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < HD; ++j) acc = fmaf(w[j], h[j], acc);
+    p0[i] = acc;
+  }
+  for (int v = tid; v < n; v += T) {
+    float acc = __ldg(a.prior + v) + __ldg(P + POff::bo);
+#pragma unroll 1
+    for (int j = 0; j < HD; ++j) acc = fmaf(__ldg(P + POff::wo + j), h0[v * HD + j], acc);
+    y0[v] = acc;
+    degv[v] = (float)(__ldg(a.var_ptr + v + 1) - __ldg(a.var_ptr + v));
+  }
+  for (int c = tid; c < m; c += T) degc[c] = (float)(__ldg(a.chk_ptr + c + 1) - __ldg(a.chk_ptr + c));
+  __syncthreads();
+  {  // the staging is done: operand rows past the last node stay zero (finite)
+    const int words = (int)((L.as - L.op) / 16);
+    for (int i = tid; i < words; i += T) reinterpret_cast<uint4*>(op)[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(tmem_slot)), "r"(a.tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const float kap = *kappa;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  // warp w serves TMEM lane quarter w % 4; chunk (tile i, quarter q) of `tiles` tiles goes to
+  // warp q + 4 ((i + rot) % nq), nq = the number of warps on quarter q
+  const int q = warp & 3;
+  const int nq = (W - q + 3) >> 2;
+  const int wslot = warp >> 2;
+  auto chunks = [&](int tiles, int rows, int col0, int rot, bool check, int mode, float nb,
+                    unsigned char* lo, unsigned char* hi) {
+    for (int i = 0; i < tiles; ++i) {
+      if ((i + rot) % nq != wslot || i * 128 + q * 32 >= rows) continue;
+      const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(col0 + 64 * i);
+      tc_rows(taddr, i * 128 + q * 32 + lane, rows, check, mode, nb, p0, pc0, check ? kc : kv,
+              check ? degc : degv, sig, lo, hi);
+    }
+  };
+  // the MMA of `tiles` tiles: accumulators at column col0 + 64 i, operand tile i, weights w
+  auto mma_tiles = [&](int tiles, int col0, const unsigned char* w) -> bool {
+    if (tid == 0) {
+      fence_after();
+      for (int i = 0; i < tiles; ++i)
+        for (int j = 0; j < 2; ++j)
+          mma_bf16(tbase + (uint32_t)(col0 + 64 * i), umma_desc(smem_u32(op + 8192 * i + 256 * j)),
+                   umma_desc(smem_u32(w + 256 * j)));
+      mma_commit(mbar);
+    }
+    const bool ok = mbar_wait(mbar, phase);
+    phase ^= 1u;
+    fence_after();
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+  };
+
+  for (long long shot = blockIdx.x; shot < a.shots && !failed; shot += gridDim.x) {
+    const uint8_t* sp = a.syndromes + shot * m;
+    for (int c = tid; c < m; c += T) sig[c] = sp[c] ? -1.f : 1.f;
+    for (int v = tid; v < n; v += T) llr[v] = y0[v];
+    __syncthreads();
+    // initial accumulators and the round-0 gather sources
+    chunks(vt, n, 0, 0, false, 0, 0.f, cs, bs);
+    chunks(ct, m, 64 * vt, 1, true, 0, 0.f, as, ds);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    fence_before();
+    __syncthreads();
+    for (int t = 0; t < R; ++t) {
+      const bool last = t == R - 1;
+      // ---- X2: S_v = sum_c relu(A_c + B_v), 4 threads per row, and the LLR update ----
+      for (int base = warp * 32; base < 4 * n; base += T) {
+        const int task = base + lane, v = task >> 2, b = task & 3;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (task < 4 * n) {
+          float qv[8];
+          unpack8(*row_chunk(bs, v, b), qv);
+          const int e1 = __ldg(a.var_ptr + v + 1);
+          for (int e = __ldg(a.var_ptr + v); e < e1; ++e) {
+            float pa[8];
+            unpack8(*row_chunk(as, __ldg(a.var_chk + e), b), pa);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] += fmaxf(pa[k] + qv[k], 0.f);
+          }
+          if (!last)
+            *reinterpret_cast<uint4*>(op + koff(v, 8 * b)) =
+                make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
+        }
+        float dot = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dot = fmaf(u[8 * b + k], s[k], dot);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+        if (task < 4 * n && b == 0) llr[v] += dot + degv[v] * kap;
+      }
+      if (last) break;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (!mma_tiles(vt, 0, mv)) {
+        failed = true;
+        break;
+      }
+      chunks(vt, n, 0, 0, false, 1, (float)(t + 1), cs, bs);
+      fence_before();
+      __syncthreads();
+      // ---- X1: T_c = sum_v relu(C_v + D_c) ----
+      for (int task = tid; task < 4 * m; task += T) {
+        const int c = task >> 2, b = task & 3;
+        float qd[8], s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        unpack8(*row_chunk(ds, c, b), qd);
+        const int e1 = __ldg(a.chk_ptr + c + 1);
+        for (int e = __ldg(a.chk_ptr + c); e < e1; ++e) {
+          float pc[8];
+          unpack8(*row_chunk(cs, __ldg(a.chk_var + e), b), pc);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) s[k] += fmaxf(pc[k] + qd[k], 0.f);
+        }
+        *reinterpret_cast<uint4*>(op + koff(c, 8 * b)) =
+            make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (!mma_tiles(ct, 64 * vt, mc)) {
+        failed = true;
+        break;
+      }
+      chunks(ct, m, 64 * vt, 1, true, 1, (float)(t + 1), as, ds);
+      fence_before();
+      __syncthreads();
+    }
+    if (failed) break;
+    __syncthreads();
+    if (a.llr_out) {
+      float* lo = a.llr_out + shot * n;
+      for (int v = tid; v < n; v += T) lo[v] = llr[v];
+      __syncthreads();
+      continue;
+    }
+    // ---- decode mode: the hard decision of the LLRs, or the shot is queued for LSD ----
+    bool bad = false;
+    for (int c = tid; c < m; c += T) {
+      unsigned par = sig[c] < 0.f ? 1u : 0u;
+      const int e1 = __ldg(a.chk_ptr + c + 1);
+      for (int e = __ldg(a.chk_ptr + c); e < e1; ++e) par ^= llr[__ldg(a.chk_var + e)] < 0.f;
+      bad = bad || par;
+    }
+    if (__syncthreads_or(bad)) {
+      __shared__ unsigned long long s_slot;
+      if (tid == 0) {
+        s_slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
+        a.queue[s_slot] = (int32_t)shot;
+      }
+      __syncthreads();
+      float* lo = a.queue_llr + (long long)s_slot * n;
+      for (int v = tid; v < n; v += T) lo[v] = llr[v];
+    } else {
+      uint8_t* co = a.corrections + shot * n;
+      for (int v = tid; v < n; v += T) co[v] = llr[v] < 0.f ? 1 : 0;
+      if (tid == 0) {
+        if (a.status) a.status[shot] = LSD_SHOT_OK_BP;
+        atomicAdd(&a.ctr->bp_converged, 1ULL);
+      }
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    // the MMA that did not report is given one more bounded wait before TMEM is released
+    mbar_wait(mbar, phase ^ 1u);
+    if (tid == 0 && a.timeout_flag) atomicExch(a.timeout_flag, 1);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tbase), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+struct TcShape {
+  int vt, ct, cols, threads;
+  size_t smem;
+};
+
+// The launch shape for H (m x n with maximal degrees dv, dc), or false when the graph does
+// not fit: at most 8 tiles of 128 rows, the tables in shared memory.
+bool tc_shape(int m, int n, int dv, int dc, int max_smem, TcShape* s) {
+  s->vt = (n + 127) / 128;
+  s->ct = (m + 127) / 128;
+  if (s->vt + s->ct > kTcMaxTiles || n >= 65535 || m >= 65535) return false;
+  const int need = 64 * (s->vt + s->ct);
+  s->cols = 32;
+  while (s->cols < need) s->cols <<= 1;
+  s->smem = tc_layout(m, n, s->vt, s->ct).total;
+  // at most as many CTAs per SM as TMEM holds: pad shared memory so no more fit
+  const int per_sm = 512 / s->cols;
+  const size_t floor_smem = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1024;
+  if (s->smem < floor_smem) s->smem = floor_smem;
+  if (s->smem > (size_t)max_smem) return false;
+  // warps: the count that leaves the fewest idle task slots in the two gathers
+  double best = -1.0;
+  for (int w = kTcMinWarps; w <= kTcMaxWarps; ++w) {
+    const int T = 32 * w;
+    const double pv = (double)((4 * n + T - 1) / T) * T * dv, pc = (double)((4 * m + T - 1) / T) * T * dc;
+    const double eff = (4.0 * n * dv + 4.0 * m * dc) / (pv + pc);
+    if (eff > best + 1e-9) {
+      best = eff;
+      s->threads = T;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+cudaError_t prior_tc_config(const DevGraph& g, int* grid) {
+  int dev = 0, sms = 0, max_smem = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  TcShape s;
+  if (!tc_shape(g.m, g.n, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
+  err = allow_max_dynamic_smem((const void*)prior_tc_kernel, max_smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prior_tc_kernel, s.threads, s.smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidValue;
+  if (per_sm > 512 / s.cols) per_sm = 512 / s.cols;
+  *grid = per_sm * sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float* params,
+                            long long shots, const uint8_t* syndromes, float* llr_out,
+                            uint8_t* corrections, uint8_t* status, int32_t* queue,
+                            float* queue_llr, DevCounters* ctr, int* timeout_flag,
+                            cudaStream_t st) {
+  if (!llr_out && (!corrections || !queue || !queue_llr || !ctr)) return cudaErrorInvalidValue;
+  int dev = 0, max_smem = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  TcShape s;
+  if (!tc_shape(g.m, g.n, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.m = g.m;
+  a.n = g.n;
+  a.rounds = rounds;
+  a.vt = s.vt;
+  a.ct = s.ct;
+  a.tmem_cols = s.cols;
+  a.chk_ptr = g.chk_ptr;
+  a.chk_var = g.chk_var;
+  a.var_ptr = g.var_ptr;
+  a.var_chk = g.var_chk;
+  a.prior = g.prior;
+  a.params = params;
+  a.shots = shots;
+  a.syndromes = syndromes;
+  a.llr_out = llr_out;
+  a.corrections = corrections;
+  a.status = status;
+  a.queue = queue;
+  a.queue_llr = queue_llr;
+  a.ctr = ctr;
+  a.timeout_flag = timeout_flag;
+  const long long blocks = shots < grid ? shots : grid;
+  if (blocks <= 0) return cudaSuccess;
+  prior_tc_kernel<<<(int)blocks, s.threads, s.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace lsdgb

@@ -96,43 +96,6 @@ __global__ void __launch_bounds__(256) block_store_kernel(long long shots, int m
   }
 }
 
-// COO of a window: detector blocks 0..blocks-1, fault rounds 0..rounds-1.
-void window_coo(int m, int n, const std::vector<std::pair<int, int>>& h, int rounds, int blocks,
-                std::vector<int32_t>& rows, std::vector<int32_t>& cols) {
-  rows.clear();
-  cols.clear();
-  const int F = n + m;
-  for (int r = 0; r < rounds; ++r) {
-    for (const auto& e : h) {
-      rows.push_back(r * m + e.first);
-      cols.push_back(r * F + e.second);
-    }
-    for (int i = 0; i < m; ++i) {
-      rows.push_back(r * m + i);
-      cols.push_back(r * F + n + i);
-      if (r + 1 < blocks) {
-        rows.push_back((r + 1) * m + i);
-        cols.push_back(r * F + n + i);
-      }
-    }
-  }
-}
-
-int make_decoder(lsd_decoder** out, int m, int n, const std::vector<std::pair<int, int>>& h,
-                 const float* p, const float* q, int rounds, int blocks, int bp_iters, int order,
-                 const lsd_options* opt) {
-  std::vector<int32_t> rows, cols;
-  window_coo(m, n, h, rounds, blocks, rows, cols);
-  std::vector<float> probs;
-  probs.reserve((size_t)rounds * (n + m));
-  for (int r = 0; r < rounds; ++r) {
-    probs.insert(probs.end(), p, p + n);
-    probs.insert(probs.end(), q, q + m);
-  }
-  return lsd_create(out, blocks * m, rounds * (n + m), (int64_t)rows.size(), rows.data(),
-                    cols.data(), probs.data(), bp_iters, order, opt);
-}
-
 int ensure(lsd_window* W, int64_t shots) {
   if ((size_t)shots <= W->cap) return LSD_OK;
   cudaError_t e = cudaStreamSynchronize(W->st);
@@ -182,6 +145,53 @@ int launch_step(lsd_window* W, int64_t shots, const uint8_t* syn, int wr, int t,
 
 }  // namespace
 
+namespace lsdgb {
+
+// COO of a window: detector blocks 0..blocks-1, fault rounds 0..rounds-1.
+static void window_coo(int m, int n, const std::vector<std::pair<int, int>>& h, int rounds,
+                       int blocks, std::vector<int32_t>& rows, std::vector<int32_t>& cols) {
+  rows.clear();
+  cols.clear();
+  const int F = n + m;
+  for (int r = 0; r < rounds; ++r) {
+    for (const auto& e : h) {
+      rows.push_back(r * m + e.first);
+      cols.push_back(r * F + e.second);
+    }
+    for (int i = 0; i < m; ++i) {
+      rows.push_back(r * m + i);
+      cols.push_back(r * F + n + i);
+      if (r + 1 < blocks) {
+        rows.push_back((r + 1) * m + i);
+        cols.push_back(r * F + n + i);
+      }
+    }
+  }
+}
+
+int window_decoder(lsd_decoder** out, int m, int n, const std::vector<std::pair<int, int>>& h,
+                   const float* p, const float* q, int rounds, int blocks, int bp_iters,
+                   int order, const lsd_options* opt) {
+  std::vector<int32_t> rows, cols;
+  window_coo(m, n, h, rounds, blocks, rows, cols);
+  std::vector<float> probs;
+  probs.reserve((size_t)rounds * (n + m));
+  for (int r = 0; r < rounds; ++r) {
+    probs.insert(probs.end(), p, p + n);
+    probs.insert(probs.end(), q, q + m);
+  }
+  return lsd_create(out, blocks * m, rounds * (n + m), (int64_t)rows.size(), rows.data(),
+                    cols.data(), probs.data(), bp_iters, order, opt);
+}
+
+int window_final_round(int d, int w, int c) {
+  int t = 0;
+  while (t + w - 1 < d && t + c < d) t += c;
+  return t;
+}
+
+}  // namespace lsdgb
+
 extern "C" {
 
 int lsd_window_create(lsd_window** out, int32_t m, int32_t n, int64_t nnz, const int32_t* rows,
@@ -206,16 +216,15 @@ int lsd_window_create(lsd_window** out, int32_t m, int32_t n, int64_t nnz, const
   W->w = window;
   W->c = commit;
   W->st = opt ? static_cast<cudaStream_t>(opt->stream) : nullptr;
-  int t = 0;
-  while (t + window - 1 < rounds && t + commit < rounds) t += commit;
+  const int t = window_final_round(rounds, window, commit);
   W->t_final = t;
   W->bmax = std::max(window, rounds - t + 1);
   int rc = LSD_OK;
   if (t > 0)
-    rc = make_decoder(&W->inner, m, n, h, p_data, q_meas, window, window, bp_iters, lsd_order,
+    rc = window_decoder(&W->inner, m, n, h, p_data, q_meas, window, window, bp_iters, lsd_order,
                       opt);
   if (rc == LSD_OK)
-    rc = make_decoder(&W->fin, m, n, h, p_data, q_meas, rounds - t, rounds - t + 1, bp_iters,
+    rc = window_decoder(&W->fin, m, n, h, p_data, q_meas, rounds - t, rounds - t + 1, bp_iters,
                       lsd_order, opt);
   if (rc == LSD_OK) {
     int dev = 0;

@@ -37,7 +37,9 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_window_decode", "lsd_window_kernel_launches", "lsd_window_destroy",
            "lsd_window_stream_reset", "lsd_window_stream_push", "lsd_giant_create",
            "lsd_giant_decode", "lsd_giant_postprocess", "lsd_giant_kernel_launches",
-           "lsd_giant_destroy", "lsd_giant_test_hold_barrier", "lsd_bp_variant_name")
+           "lsd_giant_destroy", "lsd_giant_test_hold_barrier", "lsd_bp_variant_name",
+           "lsd_server_create_with_windows", "lsd_server_submit_round",
+           "lsd_server_get_code_report", "lsd_prior_set_kernel")
 
 
 class LsdError(RuntimeError):
@@ -119,6 +121,7 @@ def lib():
     L.lsd_prior_set_params.argtypes = [P, P]
     L.lsd_prior_get_params.argtypes = [P, P]
     L.lsd_prior_forward.argtypes = [P, C.c_int64, P, P]
+    L.lsd_prior_set_kernel.argtypes = [P, C.c_int32]
     L.lsd_prior_gradient.argtypes = [P, C.c_int64, P, P, C.POINTER(C.c_double), P]
     L.lsd_prior_train_step.argtypes = [P, C.c_int64, P, P, C.c_float, C.POINTER(C.c_double)]
     L.lsd_decode_learned.argtypes = [P, P, C.c_int64, P, P, P, C.POINTER(Stats)]
@@ -609,6 +612,12 @@ class Prior:
         _check(lib().lsd_prior_set_params(self._h, buf.ctypes.data_as(C.c_void_p)),
                "lsd_prior_set_params")
 
+    def set_kernel(self, kernel: str):
+        """Inference kernel: "auto", "mma_sync" (per-node kernel) or "tcgen05"
+        (tensor-memory kernel)."""
+        code = {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]
+        _check(lib().lsd_prior_set_kernel(self._h, code), "lsd_prior_set_kernel")
+
     def forward(self, syndromes):
         import torch
         d = self.decoder
@@ -644,6 +653,13 @@ class ServerCode(C.Structure):
                 ("lsd_order", C.c_int32)]
 
 
+class ServerWindowCode(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64), ("rows", C.c_void_p),
+                ("cols", C.c_void_p), ("p_data", C.c_void_p), ("q_meas", C.c_void_p),
+                ("rounds", C.c_int32), ("window", C.c_int32), ("commit", C.c_int32),
+                ("bp_iters", C.c_int32), ("lsd_order", C.c_int32), ("streams", C.c_int32)]
+
+
 class ServerOptions(C.Structure):
     _fields_ = [("slots_per_code", C.c_int32), ("max_batch", C.c_int32),
                 ("max_wait_us", C.c_int32), ("use_graphs", C.c_int32), ("mem_budget", C.c_size_t)]
@@ -671,8 +687,16 @@ def _server_lib():
         L.lsd_server_run_poisson.argtypes = [P, C.c_double, C.c_double, P, P, P, C.c_uint64,
                                              C.POINTER(ServerReport)]
         L.lsd_server_destroy.argtypes = [P]
+        L.lsd_server_create_with_windows.argtypes = [C.POINTER(P), C.c_int32, P, C.c_int32, P,
+                                                     C.POINTER(ServerOptions)]
+        L.lsd_server_submit_round.argtypes = [P, C.c_int32, C.c_int32, P, P, P,
+                                              C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_int64)]
+        L.lsd_server_get_code_report.argtypes = [P, C.c_int32, C.POINTER(ServerReport)]
         for name in ("lsd_server_create", "lsd_server_submit", "lsd_server_wait_all",
-                     "lsd_server_get_report", "lsd_server_run_poisson", "lsd_server_destroy"):
+                     "lsd_server_get_report", "lsd_server_run_poisson", "lsd_server_destroy",
+                     "lsd_server_create_with_windows", "lsd_server_submit_round",
+                     "lsd_server_get_code_report", "lsd_prior_set_kernel"):
             getattr(L, name).restype = C.c_int
         L._server_ready = True
     return L
@@ -681,15 +705,18 @@ def _server_lib():
 class Server:
     """Continuous-batching decode server over several codes (lsd_server_*).
 
-    ``codes`` is a list of (h, channel_probs, bp_iters, lsd_order).  Request buffers must be
-    pinned host tensors (``pin_memory()``) or CUDA tensors.
+    ``codes`` is a list of (h, channel_probs, bp_iters, lsd_order).  ``window_codes`` is a
+    list of dicts (h, p, q, rounds, window, commit, bp_iters, lsd_order, streams): streams of
+    syndrome rounds of h decoded in (window, commit) windows; their code ids follow the shot
+    codes'.  Request buffers must be pinned host tensors (``pin_memory()``) or CUDA tensors;
+    the blocks of ``submit_round`` may be any host tensors.
     """
 
     def __init__(self, codes, slots_per_code: int = 0, max_batch: int = 0, max_wait_us: int = 0,
-                 mem_budget: int = 0, graphs: bool = True):
+                 mem_budget: int = 0, graphs: bool = True, window_codes=()):
         L = _server_lib()
         keep = []
-        arr = (ServerCode * len(codes))()
+        arr = (ServerCode * max(1, len(codes)))()
         self.shapes = []
         for k, (h, probs, iters, order) in enumerate(codes):
             h = np.asarray(h, dtype=np.uint8)
@@ -704,10 +731,27 @@ class Server:
             arr[k] = ServerCode(h.shape[0], h.shape[1], r.size, r.ctypes.data, c.ctypes.data,
                                 p.ctypes.data, iters, order)
             self.shapes.append(h.shape)
+        warr = (ServerWindowCode * max(1, len(window_codes)))()
+        self.window_shapes = []
+        for k, wc in enumerate(window_codes):
+            h = np.asarray(wc["h"], dtype=np.uint8)
+            m, n = h.shape
+            r, c = np.nonzero(h)
+            r = np.ascontiguousarray(r, np.int32)
+            c = np.ascontiguousarray(c, np.int32)
+            pd = np.ascontiguousarray(np.broadcast_to(np.asarray(wc["p"], np.float32), (n,)))
+            qm = np.ascontiguousarray(np.broadcast_to(np.asarray(wc["q"], np.float32), (m,)))
+            keep += [r, c, pd, qm]
+            warr[k] = ServerWindowCode(m, n, r.size, r.ctypes.data, c.ctypes.data, pd.ctypes.data,
+                                       qm.ctypes.data, wc["rounds"], wc.get("window", 3),
+                                       wc.get("commit", 1), wc.get("bp_iters", 30),
+                                       wc.get("lsd_order", 0), wc["streams"])
+            self.window_shapes.append((m, n, wc["rounds"]))
         opt = ServerOptions(slots_per_code, max_batch, max_wait_us, 0 if graphs else -1, mem_budget)
         handle = C.c_void_p()
-        _check(L.lsd_server_create(C.byref(handle), len(codes), C.cast(arr, C.c_void_p),
-                                   C.byref(opt)), "lsd_server_create")
+        _check(L.lsd_server_create_with_windows(
+            C.byref(handle), len(codes), C.cast(arr, C.c_void_p), len(window_codes),
+            C.cast(warr, C.c_void_p), C.byref(opt)), "lsd_server_create_with_windows")
         self._h = handle
 
     def submit(self, code: int, syndrome, correction=None, status=None) -> int:
@@ -720,6 +764,24 @@ class Server:
             "lsd_server_submit")
         return rid.value
 
+    def submit_round(self, code: int, stream: int, block, correction=None, status=None):
+        """Next detector block (1-D uint8 host tensor or array) of a stream of a window code.
+        Returns (first_round, rounds) of the window it completes, or (-1, 0)."""
+        first, rounds, rid = C.c_int32(), C.c_int32(), C.c_int64()
+        ptr = block.data_ptr() if hasattr(block, "data_ptr") else block.ctypes.data
+        _check(_server_lib().lsd_server_submit_round(
+            self._h, code, stream, C.c_void_p(ptr),
+            None if correction is None else C.c_void_p(correction.data_ptr()),
+            None if status is None else C.c_void_p(status.data_ptr()), C.byref(first),
+            C.byref(rounds), C.byref(rid)), "lsd_server_submit_round")
+        return first.value, rounds.value
+
+    def code_report(self, code: int) -> dict:
+        r = ServerReport()
+        _check(_server_lib().lsd_server_get_code_report(self._h, code, C.byref(r)),
+               "lsd_server_get_code_report", "lsd_prior_set_kernel")
+        return r.as_dict()
+
     def wait_all(self):
         _check(_server_lib().lsd_server_wait_all(self._h), "lsd_server_wait_all")
 
@@ -730,8 +792,9 @@ class Server:
         return r.as_dict()
 
     def run_poisson(self, rate: float, seconds: float, mix, pools, seed: int = 1) -> dict:
-        """Poisson load test; pools[c] is a pinned uint8 tensor [k][m_c] of syndromes."""
-        nc = len(self.shapes)
+        """Poisson load test; pools[c] is a pinned uint8 tensor [k][m_c] of syndromes, or for
+        a window code a host tensor [k][(d+1) m] of block sequences."""
+        nc = len(self.shapes) + len(self.window_shapes)
         mixa = (C.c_double * nc)(*[float(x) for x in mix])
         ptrs = (C.c_void_p * nc)(*[C.c_void_p(t.data_ptr()) for t in pools])
         sizes = (C.c_int64 * nc)(*[int(t.shape[0]) for t in pools])

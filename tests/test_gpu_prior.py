@@ -59,22 +59,49 @@ def test_sampler_matches_host_generator(L):
     assert np.array_equal(s.cpu().numpy(), I.syndromes(h, e_host))
 
 
+@pytest.mark.parametrize("kernel", ["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("name,rounds", [("bb72", 4), ("bb144", 4), ("bb288", 4),
                                          ("irreg_37x61", 1), ("irreg_37x61", 3)])
-def test_forward_matches_oracle(L, name, rounds):
-    """The inference kernel (per-node projections) against the oracle's per-edge MLPs:
-    several 16-row tiles with a ragged last tile, irregular degrees, 1 to 4 rounds."""
+def test_forward_matches_oracle(L, name, rounds, kernel):
+    """Both inference kernels against the oracle's per-edge MLPs: the per-node mma.sync
+    kernel (16-row tiles, ragged last tile) and the tcgen05 kernel (projections in tensor
+    memory, 128-row tiles: BB[[288,12,18]] takes 3 variable and 2 check tiles), irregular
+    degrees, 1 to 4 rounds."""
     h, probs, e, s = sample(name, 0.06, 64, seed=11)
     theta = params_case(3)
     d = L.Decoder(h, probs, 10)
     pr = L.Prior(d, rounds=rounds, params=theta.astype(np.float32))
+    pr.set_kernel(kernel)
     llr = pr.forward(torch.from_numpy(s).cuda()).cpu().numpy().astype(np.float64)
     lam = np.log((1 - probs.astype(np.float64)) / probs.astype(np.float64))
     ref, _ = P.forward(P.Graph(h), theta.astype(np.float32).astype(np.float64), s, lam,
                        rounds=rounds)
     err = np.abs(llr - ref) / np.maximum(1.0, np.abs(ref))
-    print(f"forward {name} R={rounds}: max rel err {err.max():.3e}, mean {err.mean():.3e}")
+    print(f"forward {kernel} {name} R={rounds}: max rel err {err.max():.3e}, mean {err.mean():.3e}")
     assert err.max() <= 5e-3
+
+
+def test_tensor_memory_kernel_many_shots_per_cta(L):
+    """20000 BB[[144,12,12]] shots (each CTA of the persistent grid takes tens of shots, so
+    the tensor-memory state is reinitialised between shots): 64 shots spread over the batch
+    against the oracle, and every shot against the mma.sync kernel."""
+    h, probs, e, s = sample("bb144", 0.06, 20000, seed=13)
+    theta = params_case(5)
+    d = L.Decoder(h, probs, 10)
+    pr = L.Prior(d, rounds=4, params=theta.astype(np.float32))
+    sd = torch.from_numpy(s).cuda()
+    pr.set_kernel("tcgen05")
+    llr_tc = pr.forward(sd).cpu().numpy().astype(np.float64)
+    pr.set_kernel("mma_sync")
+    llr_ms = pr.forward(sd).cpu().numpy().astype(np.float64)
+    pick = np.linspace(0, 19999, 64).astype(int)
+    lam = np.log((1 - probs.astype(np.float64)) / probs.astype(np.float64))
+    ref, _ = P.forward(P.Graph(h), theta.astype(np.float32).astype(np.float64), s[pick], lam)
+    err = np.abs(llr_tc[pick] - ref) / np.maximum(1.0, np.abs(ref))
+    both = np.abs(llr_tc - llr_ms) / np.maximum(1.0, np.abs(llr_ms))
+    print(f"tcgen05 vs oracle max rel err {err.max():.3e}; vs mma.sync {both.max():.3e}")
+    assert err.max() <= 5e-3
+    assert both.max() <= 1e-2
 
 
 def test_gradient_matches_oracle(L):

@@ -146,3 +146,106 @@ def test_rejects_pageable_buffers(L, setup):
     with pytest.raises(L.LsdError):
         srv.submit(0, pageable)
     srv.close()
+
+
+def _served_windows(L, srv, code, h, seqs, streams, d, mix_with=None):
+    """Submits the block sequences `seqs` ([k][(d+1) m], k a multiple of `streams`) round by
+    round, stream s playing sequences s, s + S, ...; returns the committed corrections
+    [k][d (n+m)] and the largest window status per sequence, assembled from what each
+    completing block's request received.  `mix_with` (a callable) is invoked between rounds
+    to submit other requests."""
+    m, n = h.shape
+    F = n + m
+    k = seqs.shape[0]
+    corr = np.zeros((k, d * F), np.uint8)
+    status = np.zeros(k, np.uint8)
+    pending = []
+    for rep in range(k // streams):
+        for b in range(d + 1):
+            for s in range(streams):
+                j = rep * streams + s
+                buf = torch.zeros(d * F, dtype=torch.uint8).pin_memory()
+                st = torch.zeros(1, dtype=torch.uint8).pin_memory()
+                blk = seqs[j, b * m:(b + 1) * m].contiguous()
+                first, rounds = srv.submit_round(code, s, blk, buf, st)
+                if rounds:
+                    pending.append((j, first, rounds, buf, st))
+            if mix_with is not None:
+                mix_with()
+        srv.wait_all()  # a stream's next sequence reuses its history once these are done
+    for j, first, rounds, buf, st in pending:
+        corr[j, first * F:(first + rounds) * F] = buf.numpy()[:rounds * F]
+        status[j] = max(status[j], int(st[0]))
+    return corr, status
+
+
+@pytest.mark.parametrize("d,w,c", [(6, 3, 1), (7, 4, 2)])
+def test_served_windows_match_window_oracle(L, d, w, c):
+    """Streams of BB[[72,12,6]] syndrome rounds (p = q = 0.02) served round by round in (w, c)
+    windows: the committed corrections and statuses equal the window oracle's and
+    lsd_window_decode's, bit for bit, alone and mixed with whole-shot requests of other codes
+    submitted between the rounds."""
+    import oracle.window as OW
+    hx = I.bb72()[0]
+    m, n = hx.shape
+    p = 0.02
+    streams, k = 24, 48
+    probs = I.space_time_probs(n, m, d, p, p).astype(np.float32)
+    e = I.sample_errors(900 + d, k, probs.astype(np.float64))
+    seqs = torch.from_numpy(I.syndromes(I.space_time(hx, d), e))
+    wcode = dict(h=hx, p=p, q=p, rounds=d, window=w, commit=c, bp_iters=30, streams=streams)
+    h_st, p_st = st_code("bb144")
+    shot_pool = pool(L, h_st, p_st, 64, 77)
+    srv = L.Server([(h_st, p_st, 50, 0)], slots_per_code=3, max_batch=64, window_codes=[wcode])
+    alone = _served_windows(L, srv, 1, hx, seqs, streams, d)
+    outs = torch.zeros((64, h_st.shape[1]), dtype=torch.uint8).pin_memory()
+    sts = torch.zeros(64, dtype=torch.uint8).pin_memory()
+    cursor = [0]
+
+    def shots():  # 5 per round: (d + 1) * (k / streams) * 5 >= 64 shots in all
+        for _ in range(5):
+            j = cursor[0] % 64
+            srv.submit(0, shot_pool[j], outs[j], sts[j])
+            cursor[0] += 1
+
+    mixed = _served_windows(L, srv, 1, hx, seqs, streams, d, mix_with=shots)
+    srv.wait_all()
+    assert cursor[0] >= 64
+    np.testing.assert_array_equal(mixed[0], alone[0])
+    np.testing.assert_array_equal(mixed[1], alone[1])
+    o = OW.window_decode(hx, np.full(n, p, np.float32).astype(np.float64),
+                         np.full(m, p, np.float32).astype(np.float64), d, seqs.numpy(),
+                         w=w, c=c, bp_iters=30)
+    np.testing.assert_array_equal(alone[0], o["corrections"])
+    np.testing.assert_array_equal(alone[1], o["status"])
+    wd = L.WindowDecoder(hx, np.full(n, p, np.float32), np.full(m, p, np.float32), d, w, c,
+                         bp_iters=30)
+    c2, s2 = wd.decode(seqs.cuda())
+    np.testing.assert_array_equal(alone[0], c2.cpu().numpy())
+    # the shot requests of the mix equal the direct decode
+    dec = L.Decoder(h_st, p_st, 50)
+    c3, s3 = dec.decode(shot_pool.cuda())
+    assert torch.equal(outs, c3.cpu()) and torch.equal(sts, s3.cpu())
+    rep = srv.code_report(1)
+    assert rep["completed"] == rep["submitted"] > 0
+    srv.close()
+
+
+def test_served_windows_under_poisson_load(L):
+    """The load generator drives window streams and shots together; every window job and
+    shot completes, and per-code latency figures are reported."""
+    hx = I.bb72()[0]
+    m, n = hx.shape
+    d, p = 6, 0.003
+    probs = I.space_time_probs(n, m, d, p, p).astype(np.float32)
+    e = I.sample_errors(31, 256, probs.astype(np.float64))
+    seqs = torch.from_numpy(I.syndromes(I.space_time(hx, d), e))
+    h_st, p_st = st_code("bb72")
+    shot_pool = pool(L, h_st, p_st, 256, 78)
+    srv = L.Server([(h_st, p_st, 30, 0)], window_codes=[dict(h=hx, p=p, q=p, rounds=d,
+                                                              streams=64)])
+    rep = srv.run_poisson(2e4, 0.3, [1, 1], [shot_pool, seqs], seed=3)
+    assert rep["completed"] == rep["submitted"] > 0
+    wrep = srv.code_report(1)
+    assert wrep["completed"] > 0 and wrep["p99_us"] >= wrep["p50_us"] > 0
+    srv.close()
