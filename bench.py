@@ -240,6 +240,7 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
     if not args.no_autotune:
         dec.autotune(s_dev[: min(s_dev.shape[0], 200_000)])  # LSD warps of the learned path
     prior = Prior(dec, rounds=args.learned_rounds, params=init_params(args.seed))
+    prior_kernel = prior.kernel()
     tr = train(dec, prior, args.train_pairs, batch=4096, seed=args.seed + 17, lr=3e-3,
                log_every=500)
     for _ in range(max(args.warmup, 1)):
@@ -255,6 +256,7 @@ def learned_leg(args, hx, hz, probs, s_dev, e_dev, stream, flush, barrier, check
     ler = float(checker.failures(e_dev, holder["c"]).float().mean().item())
     sigma = float(np.sqrt(max(ler * (1 - ler), 1.0 / n_shots) / n_shots))
     learned = {"rounds": args.learned_rounds, "hidden": 32, "weights": "bf16 (fp32 master)",
+               "inference_kernel": prior_kernel,
                "train_pairs": tr["pairs"], "train_s": tr["seconds"],
                "train_pairs_per_s": tr["pairs_per_s"],
                "final_loss": tr["losses"][-1][1] if tr["losses"] else None,
@@ -751,7 +753,8 @@ def learned_summary(learned):
     """The learned prior's headline figures and the BP+LSD points it is compared with."""
     if not learned:
         return None
-    out = {"rounds": learned["rounds"], "train_pairs": learned["train_pairs"],
+    out = {"rounds": learned["rounds"], "inference_kernel": learned["inference_kernel"]["kernel"],
+           "train_pairs": learned["train_pairs"],
            "train_s": round(learned["train_s"], 3), "value": learned["value"],
            "p99_ms": learned["latency_ms"]["p99"], "ler": learned["ler"],
            "ler_sigma": learned["ler_sigma"], "kernel_ms": learned["kernel_ms"]}

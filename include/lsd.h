@@ -164,6 +164,23 @@ int lsd_decode_batch_host(lsd_decoder* dec, int64_t shots, const uint8_t* syndro
                           uint8_t* corrections, uint8_t* status, lsd_stats* stats);
 
 /*
+ * lsd_decode_batch_packed / lsd_decode_batch_host_packed -- lsd_decode_batch and
+ * lsd_decode_batch_host with bit-packed syndromes and corrections (the problem statement's
+ * s in F_2^m and e in F_2^n, Sec. 2.1, one bit each): element i of a row is bit (i & 31)
+ * of 32-bit word i >> 5, rows of W_m = ceil(m/32) and W_n = ceil(n/32) words.
+ *   syndromes    [shots][W_m] uint32 (device, or host for _host_packed); bits past m in
+ *                the last word of a row are ignored.
+ *   corrections  [shots][W_n] uint32; bits past n are written as zero.
+ *   status, stats  as for lsd_decode_batch (status: device / host respectively).
+ * The kernels read and write the packed rows themselves (no unpacking pass); results are
+ * identical to the byte-per-bit calls.  No posteriors output.
+ */
+int lsd_decode_batch_packed(lsd_decoder* dec, int64_t shots, const uint32_t* syndromes,
+                            uint32_t* corrections, uint8_t* status, lsd_stats* stats);
+int lsd_decode_batch_host_packed(lsd_decoder* dec, int64_t shots, const uint32_t* syndromes,
+                                 uint32_t* corrections, uint8_t* status, lsd_stats* stats);
+
+/*
  * lsd_bp_batch -- BP only (the pre-decoder of Sec. 4.3), for inspection and tests.
  *   syndromes   device [shots][m] bytes.
  *   posteriors  device [shots][n] float32: Lambda of the last iteration run.
@@ -288,6 +305,10 @@ int lsd_prior_forward(lsd_prior* prior, int64_t shots, const uint8_t* syndromes,
  * (LSD_ERR_UNSUPPORTED when H does not fit it).  Both compute the same model; their
  * results differ only in rounding. */
 int lsd_prior_set_kernel(lsd_prior* prior, int32_t kernel);
+
+/* lsd_prior_get_kernel -- the inference kernel in use (1 = mma.sync, 2 = tensor-memory) and
+ * the number of CTAs of its persistent grid.  No GPU call. */
+int lsd_prior_get_kernel(const lsd_prior* prior, int32_t* kernel, int32_t* grid);
 
 /*
  * lsd_prior_gradient -- loss and gradient over a batch without updating the parameters.

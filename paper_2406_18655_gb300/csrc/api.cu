@@ -17,6 +17,7 @@ using namespace lsdgb;
 struct lsd_decoder {
   int m = 0, n = 0, E = 0;
   int bp_iters = 0, order = 0, osd_cs = -1;
+  int io_packed = 0;  // set for the duration of a bit-packed decode call
   lsd_options opt{};
   float alpha = 0.625f;
   cudaStream_t st = nullptr;
@@ -159,6 +160,7 @@ BPArgs bp_args(lsd_decoder* d, int64_t shots, const uint8_t* syn) {
   a.method = d->opt.bp_method;
   a.early_exit = d->opt.no_early_exit ? 0 : 1;
   a.ctr = d->d_ctr;
+  a.packed = d->io_packed;
   return a;
 }
 
@@ -206,6 +208,7 @@ int decode_chunk(lsd_decoder* d, int64_t shots, const uint8_t* syn, uint8_t* cor
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
   LSDArgs l{};
+  l.packed = d->io_packed;
   l.g = d->g;
   l.count_from_ctr = 1;
   l.queue = queue;
@@ -482,6 +485,7 @@ int lsd_decode_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes,
   if (e != cudaSuccess) return cuda_fail(e);
   cudaEventRecord(d->ev[1], d->st);
   LSDArgs l{};
+  l.packed = d->io_packed;
   l.g = d->g;
   l.count_from_ctr = 1;
   l.queue = d->d_queue;
@@ -508,7 +512,10 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
   if (!d || shots < 0 || shots > INT32_MAX) return LSD_ERR_INVALID_ARG;
   if (shots == 0) return lsd_decode_batch(d, 0, nullptr, nullptr, nullptr, nullptr, stats);
   if (!syndromes || !corrections) return LSD_ERR_INVALID_ARG;
-  const size_t need = (size_t)shots * ((size_t)d->m + (size_t)d->n + 1);
+  // row bytes of syndromes and corrections: bytes, or 32-bit words when bit-packed
+  const size_t srow = d->io_packed ? 4 * (size_t)((d->m + 31) / 32) : (size_t)d->m;
+  const size_t crow = d->io_packed ? 4 * (size_t)((d->n + 31) / 32) : (size_t)d->n;
+  const size_t need = (size_t)shots * (srow + crow + 1);
   if (need > d->stage_cap) {
     cudaError_t e = cudaStreamSynchronize(d->st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -520,8 +527,8 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
     d->stage_cap = need;
   }
   uint8_t* dsyn = d->d_stage;
-  uint8_t* dcor = dsyn + (size_t)shots * d->m;
-  uint8_t* dst = dcor + (size_t)shots * d->n;
+  uint8_t* dcor = dsyn + (size_t)shots * srow;
+  uint8_t* dst = dcor + (size_t)shots * crow;
   // Large batches without statistics run as a pipeline of chunks: chunk i+1's syndromes
   // copy in and chunk i-1's corrections copy out (two copy streams) while chunk i decodes.
   constexpr int64_t kMinChunk = 65536;
@@ -556,22 +563,23 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
     int64_t base = 0;
     for (int i = 0; i < chunks; ++i) {
       const int64_t cnt = shots * (i + 1) / chunks - base;
-      const size_t sm = (size_t)base * d->m, sn = (size_t)base * d->n;
+      const size_t sm = (size_t)base * srow, sn = (size_t)base * crow;
+      const size_t ln = (size_t)base * d->n;  // LLR rows of the chunk's queue
       cudaStream_t cs = (lanes2 && (i & 1)) ? d->st2 : d->st;
-      e = cudaMemcpyAsync(dsyn + sm, syndromes + sm, (size_t)cnt * d->m, cudaMemcpyHostToDevice,
+      e = cudaMemcpyAsync(dsyn + sm, syndromes + sm, (size_t)cnt * srow, cudaMemcpyHostToDevice,
                           d->cp_in);
       if (e == cudaSuccess) e = cudaEventRecord(d->cev[2 * i], d->cp_in);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, d->cev[2 * i], 0);
       if (e != cudaSuccess) return cuda_fail(e);
       const int rc =
           lanes2 ? decode_chunk(d, cnt, dsyn + sm, dcor + sn, dst + base, d->d_ctr_chunks + i,
-                                d->d_queue + base, d->d_queue_llr + sn, cs)
+                                d->d_queue + base, d->d_queue_llr + ln, cs)
                  : lsd_decode_batch(d, cnt, dsyn + sm, dcor + sn, dst + base, nullptr, nullptr);
       if (rc) return rc;
       e = cudaEventRecord(d->cev[2 * i + 1], cs);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(d->cp_out, d->cev[2 * i + 1], 0);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(corrections + sn, dcor + sn, (size_t)cnt * d->n,
+        e = cudaMemcpyAsync(corrections + sn, dcor + sn, (size_t)cnt * crow,
                             cudaMemcpyDeviceToHost, d->cp_out);
       if (e == cudaSuccess && status)
         e = cudaMemcpyAsync(status + base, dst + base, (size_t)cnt, cudaMemcpyDeviceToHost,
@@ -584,18 +592,38 @@ int lsd_decode_batch_host(lsd_decoder* d, int64_t shots, const uint8_t* syndrome
     if (e == cudaSuccess && lanes2) e = cudaStreamSynchronize(d->st2);
     return e == cudaSuccess ? LSD_OK : cuda_fail(e);
   }
-  cudaError_t e = cudaMemcpyAsync(dsyn, syndromes, (size_t)shots * d->m, cudaMemcpyHostToDevice,
+  cudaError_t e = cudaMemcpyAsync(dsyn, syndromes, (size_t)shots * srow, cudaMemcpyHostToDevice,
                                   d->st);
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = lsd_decode_batch(d, shots, dsyn, dcor, dst, nullptr, nullptr);
   if (rc) return rc;
-  e = cudaMemcpyAsync(corrections, dcor, (size_t)shots * d->n, cudaMemcpyDeviceToHost, d->st);
+  e = cudaMemcpyAsync(corrections, dcor, (size_t)shots * crow, cudaMemcpyDeviceToHost, d->st);
   if (e == cudaSuccess && status)
     e = cudaMemcpyAsync(status, dst, (size_t)shots, cudaMemcpyDeviceToHost, d->st);
   if (e != cudaSuccess) return cuda_fail(e);
   if (stats) return fill_stats(d, shots, stats, true);
   e = cudaStreamSynchronize(d->st);
   return e == cudaSuccess ? LSD_OK : cuda_fail(e);
+}
+
+int lsd_decode_batch_packed(lsd_decoder* d, int64_t shots, const uint32_t* syndromes,
+                            uint32_t* corrections, uint8_t* status, lsd_stats* stats) {
+  if (!d) return LSD_ERR_INVALID_ARG;
+  d->io_packed = 1;
+  const int rc = lsd_decode_batch(d, shots, reinterpret_cast<const uint8_t*>(syndromes),
+                                  reinterpret_cast<uint8_t*>(corrections), status, nullptr, stats);
+  d->io_packed = 0;
+  return rc;
+}
+
+int lsd_decode_batch_host_packed(lsd_decoder* d, int64_t shots, const uint32_t* syndromes,
+                                 uint32_t* corrections, uint8_t* status, lsd_stats* stats) {
+  if (!d) return LSD_ERR_INVALID_ARG;
+  d->io_packed = 1;
+  const int rc = lsd_decode_batch_host(d, shots, reinterpret_cast<const uint8_t*>(syndromes),
+                                       reinterpret_cast<uint8_t*>(corrections), status, stats);
+  d->io_packed = 0;
+  return rc;
 }
 
 int lsd_bp_batch(lsd_decoder* d, int64_t shots, const uint8_t* syndromes, float* posteriors,
@@ -919,6 +947,14 @@ int lsd_prior_forward(lsd_prior* p, int64_t shots, const uint8_t* syndromes, flo
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
   if (e != cudaSuccess) return cuda_fail(e);
   return flag ? LSD_ERR_TIMEOUT : LSD_OK;
+}
+
+int lsd_prior_get_kernel(const lsd_prior* p, int32_t* kernel, int32_t* grid) {
+  if (!p || !kernel || !grid) return LSD_ERR_INVALID_ARG;
+  const bool tc = prior_uses_tc(p);
+  *kernel = tc ? 2 : 1;
+  *grid = tc ? p->grid_tc : p->grid_fwd;
+  return LSD_OK;
 }
 
 int lsd_prior_set_kernel(lsd_prior* p, int32_t kernel) {

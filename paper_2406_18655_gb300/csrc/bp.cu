@@ -96,8 +96,7 @@ __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
     if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
 
-    const uint8_t* sp = a.syndromes + shot * m;
-    for (int i = lane; i < m; i += G) syn[i] = sp[i] ? 1 : 0;
+    for (int i = lane; i < m; i += G) syn[i] = (uint8_t)syn_bit(a.syndromes, a.packed, shot, m, i);
     for (int e = lane; e < E; e += G) r[e] = 0.f;
     for (int j = lane; j < n; j += G) Lam[j] = s_prior[j];
     __syncwarp(gmask);
@@ -194,8 +193,7 @@ __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
     my_conv += (lane == 0 && conv) ? 1ull : 0ull;
     if (a.queue) {
       if (conv) {
-        uint8_t* co = a.corrections + shot * n;
-        for (int j = lane; j < n; j += G) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+        write_hard_decision(a.corrections, a.packed, shot, n, Lam, lane, G);
         if (lane == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
       } else {
         unsigned long long slot = 0;
@@ -227,7 +225,7 @@ __global__ void __launch_bounds__(256) bp_kernel(BPArgs a) {
 // are unrolled over the compile-time degrees; r[E], Lam[n] and the priors live in shared
 // memory as the exchange between the two phases.  Same operations in the same order as
 // bp_kernel<G, 0>, so the results are identical.
-template <int G, int CPL, int DC, int VPL, int DV>
+template <int G, int CPL, int DC, int VPL, int DV, bool PK>
 __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.g.m, n = a.g.n, E = a.g.E;
@@ -254,7 +252,7 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
     if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
     bool conv = false;
-    const int t = bpreg::shot_bp<G>(a, T, shot, r, Lam, s_prior, lane, gmask, conv);
+    const int t = bpreg::shot_bp<G, CPL, DC, VPL, DV, PK>(a, T, shot, r, Lam, s_prior, lane, gmask, conv);
 
     // ---- outputs (each lane writes its own variables) ----
     if (a.posteriors) {
@@ -273,11 +271,15 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
     my_conv += (lane == 0 && conv) ? 1ull : 0ull;
     if (a.queue) {
       if (conv) {
-        uint8_t* co = a.corrections + shot * n;
+        if constexpr (PK) {
+          write_packed_decision(a.corrections, shot, n, Lam, lane, G);
+        } else {
+          uint8_t* co = a.corrections + shot * n;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-          const int j = lane + G * v;
-          if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+          for (int v = 0; v < VPL; ++v) {
+            const int j = lane + G * v;
+            if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+          }
         }
         if (lane == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
       } else {
@@ -332,8 +334,7 @@ __global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
     const unsigned long long shot_u = s_shot;
     if (shot_u >= (unsigned long long)shots) break;
     const long long shot = (long long)shot_u;
-    const uint8_t* sp = a.syndromes + shot * m;
-    for (int i = tid; i < m; i += nt) syn[i] = sp[i] ? 1 : 0;
+    for (int i = tid; i < m; i += nt) syn[i] = (uint8_t)syn_bit(a.syndromes, a.packed, shot, m, i);
     for (int e = tid; e < E; e += nt) r[e] = 0.f;
     for (int j = tid; j < n; j += nt) Lam[j] = __ldg(prior + j);
     __syncthreads();
@@ -424,8 +425,7 @@ __global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
     }
     if (a.queue) {
       if (conv) {
-        uint8_t* co = a.corrections + shot * n;
-        for (int j = tid; j < n; j += nt) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+        write_hard_decision(a.corrections, a.packed, shot, n, Lam, tid, nt);
         if (tid == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
       } else {
         if (tid == 0) {
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(512) bp_cta_kernel(BPArgs a) {
 // two running minima of a check start, so a padded edge changes neither minimum, sign nor
 // hard-decision parity: the update equals the unpadded one bit for bit.  Same operations in
 // the same order as bp_kernel<G, 0>.
-template <int NT, int CPL, int DC, int VPL, int DV, bool PAD, int MINB>
+template <int NT, int CPL, int DC, int VPL, int DV, bool PAD, int MINB, bool PK>
 __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_shot;
@@ -527,7 +527,12 @@ __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
     for (int c = 0; c < CPL; ++c) {
       const int i = tid + NT * c;
       if (i < m) {
-        if (sp[i]) sbits |= 1u << c;
+        if constexpr (PK) {
+          const uint32_t* spw = reinterpret_cast<const uint32_t*>(a.syndromes) + shot * packed_words(m);
+          if ((spw[i >> 5] >> (i & 31)) & 1u) sbits |= 1u << c;
+        } else {
+          if (sp[i]) sbits |= 1u << c;
+        }
 #pragma unroll
         for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
       }
@@ -613,11 +618,15 @@ __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
     }
     if (a.queue) {
       if (conv) {
-        uint8_t* co = a.corrections + shot * n;
+        if constexpr (PK) {
+          write_packed_decision(a.corrections, shot, n, Lam, tid, NT);
+        } else {
+          uint8_t* co = a.corrections + shot * n;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-          const int j = tid + NT * v;
-          if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+          for (int v = 0; v < VPL; ++v) {
+            const int j = tid + NT * v;
+            if (j < n) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+          }
         }
         if (tid == 0 && a.status) a.status[shot] = LSD_SHOT_OK_BP;
       } else {
@@ -645,12 +654,14 @@ __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
 // Shapes of bp_reg_kernel: (G, CPL, DC, VPL, DV).
 struct RegShape {
   int G, cpl, dc, vpl, dv;
-  const void* fn;
+  const void* fn;     // byte-per-bit syndromes and corrections
+  const void* fn_pk;  // bit-packed
   const char* name;
 };
 
-#define LSD_REG_SHAPE(G, C, DCx, V, DVx)                                 \
-  {G, C, DCx, V, DVx, (const void*)bp_reg_kernel<G, C, DCx, V, DVx>,     \
+#define LSD_REG_SHAPE(G, C, DCx, V, DVx)                                      \
+  {G, C, DCx, V, DVx, (const void*)bp_reg_kernel<G, C, DCx, V, DVx, false>,   \
+   (const void*)bp_reg_kernel<G, C, DCx, V, DVx, true>,                       \
    "bp_reg_kernel<" #G "," #C "," #DCx "," #V "," #DVx ">"}
 const RegShape kRegShapes[] = {
     LSD_REG_SHAPE(16, 3, 6, 5, 3),   // m <= 48,  n <= 80   (BB [[72,12,6]])
@@ -696,10 +707,12 @@ struct RegCtaShape {
   int nt, cpl, dc, vpl, dv;
   bool pad;
   const void* fn;
+  const void* fn_pk;
   const char* name;
 };
-#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx, P, MB)                               \
-  {NT, C, DCx, V, DVx, P, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB>, \
+#define LSD_REGCTA_SHAPE(NT, C, DCx, V, DVx, P, MB)                                       \
+  {NT, C, DCx, V, DVx, P, (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB, false>, \
+   (const void*)bp_regcta_kernel<NT, C, DCx, V, DVx, P, MB, true>,                         \
    "bp_regcta_kernel<" #NT "," #C "," #DCx "," #V "," #DVx "," #P "," #MB ">"}
 const RegCtaShape kRegCtaShapes[] = {
     LSD_REGCTA_SHAPE(768, 4, 7, 9, 4, false, 1),   // m <= 3072, n <= 6912 (HGP of a 48 x 64 (3,4) code)
@@ -736,10 +749,13 @@ int lanes_of(int variant) {
   if (variant >= 6) return kRegShapes[variant - 6].G;
   return variant % 3 == 0 ? 8 : variant % 3 == 1 ? 16 : 32;
 }
-const void* variant_fn(int v) {
-  if (is_regcta(v)) return kRegCtaShapes[v - kRegCtaBase].fn;
+// The kernel of a variant; `packed`: the instance with bit-packed syndromes and corrections
+// (the generic and cache-read kernels take the layout from their arguments at run time).
+const void* variant_fn(int v, bool packed = false) {
+  if (is_regcta(v)) return packed ? kRegCtaShapes[v - kRegCtaBase].fn_pk : kRegCtaShapes[v - kRegCtaBase].fn;
   if (is_cta(v)) return v == kCtaBase ? (const void*)bp_cta_kernel<0> : (const void*)bp_cta_kernel<1>;
-  return v >= 6 ? kRegShapes[v - 6].fn : generic_fn(v);
+  if (v >= 6) return packed ? kRegShapes[v - 6].fn_pk : kRegShapes[v - 6].fn;
+  return generic_fn(v);
 }
 }  // namespace
 
@@ -860,6 +876,8 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
   *smem = gb + grp;
   const void* fn = variant_fn(v);
   err = allow_max_dynamic_smem(fn, max_smem);
+  if (err == cudaSuccess && variant_fn(v, true) != fn)
+    err = allow_max_dynamic_smem(variant_fn(v, true), max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b, *smem);
@@ -872,7 +890,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
 
 cudaError_t launch_bp(const BPArgs& a, int variant, int grid, int block, size_t smem,
                       cudaStream_t st) {
-  const void* fn = variant_fn(variant);
+  const void* fn = variant_fn(variant, a.packed != 0);
   void* args[] = {const_cast<BPArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }

@@ -45,7 +45,7 @@ __device__ __forceinline__ void load_tables(const DevGraph& g, int lane,
 
 // BP on `shot` from the channel priors; returns the iterations run and sets conv (the hard
 // decision of the final Lam satisfies the syndrome).  Lam holds the posteriors on return.
-template <int G, int CPL, int DC, int VPL, int DV>
+template <int G, int CPL, int DC, int VPL, int DV, bool PK = false>
 __device__ __forceinline__ int shot_bp(const BPArgs& a, const Tables<CPL, DC, VPL, DV>& T,
                                        long long shot, float* r, float* Lam,
                                        const float* s_prior, int lane, unsigned gmask,
@@ -58,7 +58,12 @@ __device__ __forceinline__ int shot_bp(const BPArgs& a, const Tables<CPL, DC, VP
   for (int c = 0; c < CPL; ++c) {
     const int i = lane + G * c;
     if (i < m) {
-      if (sp[i]) sbits |= 1u << c;
+      if constexpr (PK) {  // bit-packed syndromes (lsd_decode_batch_packed)
+        const uint32_t* spw = reinterpret_cast<const uint32_t*>(a.syndromes) + shot * packed_words(m);
+        if ((spw[i >> 5] >> (i & 31)) & 1u) sbits |= 1u << c;
+      } else {
+        if (sp[i]) sbits |= 1u << c;
+      }
 #pragma unroll
       for (int k = 0; k < DC; ++k) r[i * DC + k] = 0.f;
     }

@@ -698,7 +698,7 @@ __device__ __forceinline__ void lsd_flush(const LSDArgs& a, const LsdAcc& acc, i
 // LSD (Alg. 1, LSD-mu of App. D) of one shot by one warp: lsrc = the shot's soft
 // information (global or shared memory), ssrc = its syndrome; writes its correction and
 // status.
-template <int MM, int NN, bool MU>
+template <int MM, int NN, bool MU, bool PK>
 __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
                                          const Shot<Lay<MM, NN, MU>>& S, const float* lsrc,
                                          const uint8_t* ssrc, long long shot, int lane,
@@ -775,7 +775,14 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
 #pragma unroll
   for (int c = 0; c < W; ++c) {
     const int d = c * 32 + lane;
-    const unsigned bv = __ballot_sync(kFull, d < m && ssrc[d] != 0);
+    unsigned bv;
+    if constexpr (PK) {  // ssrc points at the shot's words; bits past m are ignored
+      const int base = c * 32;
+      bv = base < m ? reinterpret_cast<const uint32_t*>(ssrc)[c] : 0u;
+      if (base + 32 > m && base < m) bv &= (1u << (m - base)) - 1u;
+    } else {
+      bv = __ballot_sync(kFull, d < m && ssrc[d] != 0);
+    }
     if (lane == 0) {
       S.syn()[c] = bv;
       S.sred()[c] = bv;
@@ -884,8 +891,13 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
     }
   }
   __syncwarp();
-  uint8_t* co = a.corrections + shot * n;
-  for (int j = lane; j < n; j += 32) co[j] = cs[j];
+  if constexpr (PK) {
+    uint32_t* co = reinterpret_cast<uint32_t*>(a.corrections) + shot * packed_words(n);
+    for (int w = lane; w < packed_words(n); w += 32) co[w] = byte_word(cs, n, w);
+  } else {
+    uint8_t* co = a.corrections + shot * n;
+    for (int j = lane; j < n; j += 32) co[j] = cs[j];
+  }
   if (lane == 0) {
     if (a.status) a.status[shot] = (uint8_t)status;
     if (a.shot_info) {
@@ -901,7 +913,7 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
   __syncwarp();
 }
 
-template <int MM, int NN, bool MU>
+template <int MM, int NN, bool MU, bool PK>
 __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int graph_smem) {
   using L = Lay<MM, NN, MU>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -947,7 +959,11 @@ __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int gra
     if (lane == 0) pending = atomicAdd(&a.ctr->lsd_next, 1ULL);
     const long long shot = a.queue ? (long long)a.queue[item] : (long long)item;
     const float* lsrc = a.llr + (a.llr_by_item ? (long long)item : shot) * n;
-    lsd_shot<MM, NN, MU>(a, G, S, lsrc, a.syndromes + shot * m, shot, lane, acc);
+    const uint8_t* ssrc =
+        PK ? reinterpret_cast<const uint8_t*>(reinterpret_cast<const uint32_t*>(a.syndromes) +
+                                              shot * packed_words(m))
+           : a.syndromes + shot * m;
+    lsd_shot<MM, NN, MU, PK>(a, G, S, lsrc, ssrc, shot, lane, acc);
   }
   lsd_flush(a, acc, lane);
 }
@@ -980,10 +996,15 @@ size_t class_bytes(int c, bool mu) {
   }
 }
 
-const void* class_kernel(int c, bool mu) {
+// The kernel of a size class; `pk`: the instance with bit-packed syndromes and corrections.
+const void* class_kernel(int c, bool mu, bool pk = false) {
   switch (c) {
-#define X(i, M, N) \
-  case i: return mu ? (const void*)lsd_kernel<M, N, true> : (const void*)lsd_kernel<M, N, false>;
+#define X(i, M, N)                                                                      \
+  case i:                                                                               \
+    return pk ? (mu ? (const void*)lsd_kernel<M, N, true, true>                          \
+                    : (const void*)lsd_kernel<M, N, false, true>)                        \
+              : (mu ? (const void*)lsd_kernel<M, N, true, false>                         \
+                    : (const void*)lsd_kernel<M, N, false, false>);
     LSD_CLASS_CASES(X)
 #undef X
     default: return nullptr;
@@ -1017,6 +1038,7 @@ cudaError_t lsd_config(const DevGraph& g, int order, int warps, int* warps_out, 
   if (err != cudaSuccess) return err;
   if (w * 32 > fa.maxThreadsPerBlock) return cudaErrorInvalidValue;
   err = allow_max_dynamic_smem(fn, max_smem);
+  if (err == cudaSuccess) err = allow_max_dynamic_smem(class_kernel(c, mu, true), max_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, w * 32, *smem);
@@ -1032,7 +1054,8 @@ cudaError_t launch_lsd(const LSDArgs& a, int warps, int grid, size_t smem, cudaS
   const bool mu = a.order > 0;
   const int gs = graph_in_smem(a.g) ? 1 : 0;
   void* args[] = {const_cast<LSDArgs*>(&a), const_cast<int*>(&gs)};
-  return cudaLaunchKernel(class_kernel(c, mu), dim3(grid), dim3(warps * 32), args, smem, st);
+  return cudaLaunchKernel(class_kernel(c, mu, a.packed != 0), dim3(grid), dim3(warps * 32), args,
+                          smem, st);
 }
 
 }  // namespace lsdgb

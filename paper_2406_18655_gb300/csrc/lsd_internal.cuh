@@ -48,7 +48,8 @@ struct BPArgs {
   DevGraph g;
   long long shots;
   const long long* shots_dev; // if set, the shot count is read from here at kernel start
-  const uint8_t* syndromes;  // [shots][m]
+  const uint8_t* syndromes;  // [shots][m] bytes, or packed: [shots][ceil(m/32)] words
+  int packed;                // 1: syndromes and corrections bit-packed (see syn_bit)
   int iters;
   float alpha;
   int method;                // 0 min-sum, 1 sum-product
@@ -71,8 +72,9 @@ struct LSDArgs {
   const int32_t* queue;       // work item -> shot id; NULL = identity
   const float* llr;           // [items or shots][n]
   int llr_by_item;            // 1: LLR row = work item, 0: LLR row = shot id
-  const uint8_t* syndromes;   // [shots][m]
-  uint8_t* corrections;       // [shots][n]
+  const uint8_t* syndromes;   // [shots][m] bytes, or packed: [shots][ceil(m/32)] words
+  uint8_t* corrections;       // [shots][n] bytes, or packed: [shots][ceil(n/32)] words
+  int packed;
   uint8_t* status;            // [shots] nullable
   int32_t* shot_info;         // [shots][3] nullable
   int order;                  // LSD-mu: extra growth steps per cluster
@@ -144,6 +146,51 @@ cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float
 // captured CUDA graph serves every batch size up to max_shots (api.cu; used by the server).
 int decode_batch_counted(lsd_decoder* dec, int64_t max_shots, const long long* shots_dev,
                          const uint8_t* syndromes, uint8_t* corrections, uint8_t* status);
+
+// Bit-packed batch I/O: element i of a row of k elements is bit (i & 31) of 32-bit word
+// i >> 5 of a row of ceil(k/32) words.
+__device__ __forceinline__ int packed_words(int k) { return (k + 31) >> 5; }
+// Syndrome bit i of `shot` (bytes or packed words).
+__device__ __forceinline__ unsigned syn_bit(const uint8_t* syn, int packed, long long shot,
+                                            int m, int i) {
+  if (packed) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(syn) + shot * packed_words(m);
+    return (w[i >> 5] >> (i & 31)) & 1u;
+  }
+  return syn[shot * m + i] ? 1u : 0u;
+}
+// Hard decision [L_j < 0] of n posteriors (shared memory) into word `w` of a packed row.
+__device__ __forceinline__ uint32_t sign_word(const float* L, int n, int w) {
+  uint32_t x = 0;
+  const int j0 = w << 5, j1 = j0 + 32 < n ? j0 + 32 : n;
+  for (int j = j0; j < j1; ++j) x |= (L[j] < 0.f ? 1u : 0u) << (j - j0);
+  return x;
+}
+// Word `w` of the packed form of n bytes (0 / 1).
+__device__ __forceinline__ uint32_t byte_word(const uint8_t* b, int n, int w) {
+  uint32_t x = 0;
+  const int j0 = w << 5, j1 = j0 + 32 < n ? j0 + 32 : n;
+  for (int j = j0; j < j1; ++j) x |= (b[j] ? 1u : 0u) << (j - j0);
+  return x;
+}
+// The hard decision of a converged shot as packed words, `nt` threads from `t` (out of line:
+// the byte path of the BP kernels keeps its own register allocation).
+static __device__ __noinline__ void write_packed_decision(uint8_t* corrections, long long shot, int n,
+                                                   const float* Lam, int t, int nt) {
+  uint32_t* co = reinterpret_cast<uint32_t*>(corrections) + shot * packed_words(n);
+  for (int w = t; w < packed_words(n); w += nt) co[w] = sign_word(Lam, n, w);
+}
+// The hard decision of a converged shot: bytes or packed words, `nt` threads from `t`.
+__device__ __forceinline__ void write_hard_decision(uint8_t* corrections, int packed,
+                                                    long long shot, int n, const float* Lam,
+                                                    int t, int nt) {
+  if (packed) {
+    write_packed_decision(corrections, shot, n, Lam, t, nt);
+  } else {
+    uint8_t* co = corrections + shot * n;
+    for (int j = t; j < n; j += nt) co[j] = (Lam[j] < 0.f) ? 1 : 0;
+  }
+}
 
 // Decoder of one window of phenomenological rounds of H (window.cu; used by the server):
 // detector blocks 0..blocks-1 by fault rounds 0..rounds-1, [n data | m measurement] faults

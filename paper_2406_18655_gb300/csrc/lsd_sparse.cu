@@ -755,7 +755,10 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
     const long long qi = items ? (long long)items[item] : (long long)item;
     const long long shot = a.queue ? (long long)a.queue[qi] : qi;
     const float* llr = a.llr + (a.llr_by_item ? qi : shot) * n;
-    const uint8_t* ssrc = a.syndromes + shot * m;
+    // the shot's correction: bytes, or packed words (set bits with atomicOr: lanes share words)
+    uint8_t* co = a.packed ? nullptr : a.corrections + shot * n;
+    uint32_t* cw = a.packed ? reinterpret_cast<uint32_t*>(a.corrections) + shot * packed_words(n)
+                            : nullptr;
 
     // ---- init ----
     for (int d = lane; d < m; d += 32) {
@@ -773,7 +776,7 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
     int ns = 0;
     for (int b0 = 0; b0 < m; b0 += 32) {
       const int d = b0 + lane;
-      const bool f = d < m && ssrc[d] != 0;
+      const bool f = d < m && syn_bit(a.syndromes, a.packed, shot, m, d) != 0;
       const unsigned bal = __ballot_sync(kFull, f);
       if (f) {
         const int k = ns + __popc(bal & ((1u << lane) - 1u));
@@ -872,8 +875,10 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
         }
       }
       if (!spill) {
-        uint8_t* co = a.corrections + shot * n;
-        for (int j = lane; j < n; j += 32) co[j] = 0;
+        if (cw)
+          for (int w = lane; w < packed_words(n); w += 32) cw[w] = 0u;
+        else
+          for (int j = lane; j < n; j += 32) co[j] = 0;
         unsolv += 1;
       }
       __syncwarp();
@@ -917,16 +922,24 @@ __global__ void __launch_bounds__(128, 1) lsd_sparse_kernel(LSDArgs a, int* scra
     for (int x = lane; x < nseed; x += 32) S.mark()[x] = 0u;
 
     // ---- corrections ----
-    uint8_t* co = a.corrections + shot * n;
-    for (int j = lane; j < n; j += 32) co[j] = 0;
+    if (cw)
+      for (int w = lane; w < packed_words(n); w += 32) cw[w] = 0u;
+    else
+      for (int j = lane; j < n; j += 32) co[j] = 0;
     __syncwarp();
     if (status == LSD_SHOT_OK_LSD) {
+      auto set = [&](int j) {
+        if (cw)
+          atomicOr(cw + (j >> 5), 1u << (j & 31));
+        else
+          co[j] = 1;
+      };
       const int nsl = S.scal()[S_SLOTS];
       for (int sl = lane; sl < nsl; sl += 32)
-        if (bit_of(S.xsol(), sl)) co[S.pcol()[sl]] = 1;
+        if (bit_of(S.xsol(), sl)) set(S.pcol()[sl]);
       if constexpr (MU) {
         const int ne = S.scal()[S_EXT];
-        for (int t = lane; t < ne; t += 32) co[S.ext()[t]] = 1;
+        for (int t = lane; t < ne; t += 32) set(S.ext()[t]);
       }
     }
     __syncwarp();

@@ -32,6 +32,8 @@
 // 128 bytes apart, adjacent along M/N 512 bytes apart (a K = 32 BF16 row block).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "lsd_internal.cuh"
 #include "prior_params.cuh"
 
@@ -43,11 +45,11 @@ using prior_params::DIN;
 using prior_params::HD;
 using prior_params::POff;
 
-constexpr int kTcMinWarps = 8, kTcMaxWarps = 12;
+constexpr int kTcMinWarps = 8, kTcMaxWarps = 10;
 constexpr int kTcMaxTiles = 8;  // variable + check tiles: 64 TMEM columns each, 512 in all
 
 struct TcArgs {
-  int m, n, rounds, vt, ct, tmem_cols;
+  int m, n, E, rounds, vt, ct, tmem_cols;
   const int32_t* chk_ptr;
   const uint16_t* chk_var;
   const int32_t* var_ptr;
@@ -66,12 +68,13 @@ struct TcArgs {
 };
 
 struct TcLay {
-  size_t mv, mc, op, as, ds, cs, bs, p0, pc0, kv, kc, u, y0, llr, degv, degc, sig, misc, total;
+  size_t mv, mc, op, as, ds, cs, bs, p0, pc0, kv, kc, u, y0, llr, degv, degc, sig, vptr, cptr,
+      vadj, cadj, misc, total;
 };
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline TcLay tc_layout(int m, int n, int vt, int ct) {
+__host__ __device__ inline TcLay tc_layout(int m, int n, int E, int vt, int ct) {
   TcLay L;
   size_t o = 0;
   L.mv = o; o += 4096;                                   // Mv: 64 x 32 BF16, K-major
@@ -82,7 +85,7 @@ __host__ __device__ inline TcLay tc_layout(int m, int n, int vt, int ct) {
   L.ds = o; o += al((size_t)m * 64, 128);
   L.cs = o; o += al((size_t)n * 64, 128);
   L.bs = o; o += al((size_t)n * 64, 128);                // at set-up, with cs: h_v^0 [n][32] FP32
-  L.p0 = o; o += (size_t)n * 256;                        // FP32 [n][64]
+  L.p0 = o; o += (size_t)n * 256;                        // FP32 [64][n] (column-major)
   L.pc0 = o; o += 512;                                   // FP32 [2][64]: sigma = +1, -1
   L.kv = o; o += 256;
   L.kc = o; o += 256;
@@ -92,6 +95,10 @@ __host__ __device__ inline TcLay tc_layout(int m, int n, int vt, int ct) {
   L.degv = o; o += al((size_t)n * 4, 16);
   L.degc = o; o += al((size_t)m * 4, 16);
   L.sig = o; o += al((size_t)m * 4, 16);
+  L.vptr = o; o += al((size_t)(n + 1) * 4, 16);          // the graph: CSC / CSR row starts
+  L.cptr = o; o += al((size_t)(m + 1) * 4, 16);
+  L.vadj = o; o += al((size_t)E * 4, 16);                // per edge: row * 64 | swizzle bits
+  L.cadj = o; o += al((size_t)E * 4, 16);
   L.misc = o; o += 64;                                   // kappa, TMEM address, mbarrier, flags
   L.total = o;
   return L;
@@ -180,56 +187,87 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* f) {
       : "memory");
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* f) {
+  uint32_t v[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(v[i]);
+}
+
 __device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
-__device__ __forceinline__ void unpack8(const uint4 v, float f[8]) {
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+// acc (8 FP32 values as four f32x2 pairs) += relu(p + q) for 8 BF16 pairs: the sum and the
+// relu in one packed BF16 FMA (one rounding), the accumulation in FP32.
+__device__ __forceinline__ void relu_acc8(const uint4 p, const uint4 q, unsigned long long acc[4]) {
+  const uint32_t pw[4] = {p.x, p.y, p.z, p.w}, qw[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    f[2 * i] = __uint_as_float(w[i] << 16);
-    f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    uint32_t d;
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(pw[i]), "r"(0x3F803F80u), "r"(qw[i]));
+    unsigned long long x;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "r"(d << 16), "r"(d & 0xffff0000u));
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[i]) : "l"(x));
   }
 }
+__device__ __forceinline__ void unpack_acc8(const unsigned long long acc[4], float s[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) asm("mov.b64 {%0, %1}, %2;" : "=f"(s[2 * i]), "=f"(s[2 * i + 1]) : "l"(acc[i]));
+}
+
 // BF16 node rows [rows][32]: the 16-byte chunk b of row r sits at chunk b ^ ((r >> 1) & 3),
 // so 32 lanes writing one row each (the epilogue) spread over all banks.
 __device__ __forceinline__ uint4* row_chunk(unsigned char* base, int r, int b) {
   return reinterpret_cast<uint4*>(base + (size_t)r * 64 + ((b ^ ((r >> 1) & 3)) << 4));
 }
 
-// Epilogue / init of one 32-row chunk of a tile: rows r0 .. r0+31 (this lane: r0 + lane).
-// mode 0: init from the tables (variables: P0; checks: Pc0[sigma]) with tcgen05.st;
-// mode 1: read the accumulators and add `nb` deg k.  Writes the two BF16 halves (columns
-// 0-31 and 32-63) to the row arrays lo and hi, 16 columns at a time.
-__device__ __forceinline__ void tc_rows(uint32_t taddr, int r, int rows, bool check, int mode,
-                                        float nb, const float* p0, const float* pc0,
+// Chunk b of the row an edge entry x = row * 64 | ((row >> 1) & 3) points at (row_chunk).
+__device__ __forceinline__ uint4 edge_chunk(const unsigned char* base, uint32_t x, int b) {
+  return *reinterpret_cast<const uint4*>(base + (x & ~63u) + ((((uint32_t)b ^ x) & 3u) << 4));
+}
+
+// Epilogue / init of one half (32 columns: hf = 0 the first projection, 1 the second) of a
+// 32-row chunk of a tile: rows r0 .. r0+31 (this lane: r = r0 + lane), TMEM address taddr of
+// the chunk's column 0.  mode 0: init from the tables (variables: P0; checks: Pc0[sigma])
+// with tcgen05.st; mode 1: read the accumulators and add `nb` deg k.  Writes the BF16 row
+// half to dst (lo for hf = 0, hi for hf = 1).
+__device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int rows, bool check,
+                                        int mode, float nb, const float* p0, const float* pc0,
                                         const float* k, const float* deg, const float* sig,
-                                        unsigned char* lo, unsigned char* hi) {
+                                        unsigned char* dst) {
   const bool ok = r < rows;
-  const float dk = ok ? nb * deg[r] : 0.f;
-  const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (size_t)(ok ? r : 0) * 64;
-#pragma unroll 1
-  for (int part = 0; part < 4; ++part) {
-    float f[16];
-    if (mode == 0) {
+  float f[32];
+  if (mode == 0) {
+    // initial values: checks one of the two rows of Pc0, variables column r of P0 ([64][rows])
+    const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (ok ? r : 0);
+    const int stride = check ? 1 : rows;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = src[part * 16 + i];
-      tmem_st16(taddr + part * 16, f);
-    } else {
-      tmem_ld16(taddr + part * 16, f);
+    for (int i = 0; i < 32; ++i) f[i] = src[(hf * 32 + i) * stride];
+    tmem_st16(taddr + hf * 32, f);
+    tmem_st16(taddr + hf * 32 + 16, f + 16);
+  } else {
+    tmem_ld32(taddr + hf * 32, f);
+    const float dk = ok ? nb * deg[r] : 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = fmaf(dk, k[part * 16 + i], f[i]);
-    }
-    if (ok) {
-      unsigned char* dst = part < 2 ? lo : hi;
+    for (int i = 0; i < 32; ++i) f[i] = fmaf(dk, k[hf * 32 + i], f[i]);
+  }
+  if (ok) {
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
-        *row_chunk(dst, r, (part & 1) * 2 + b) =
-            make_uint4(pack2(f[8 * b], f[8 * b + 1]), pack2(f[8 * b + 2], f[8 * b + 3]),
-                       pack2(f[8 * b + 4], f[8 * b + 5]), pack2(f[8 * b + 6], f[8 * b + 7]));
-    }
+    for (int b = 0; b < 4; ++b)
+      *row_chunk(dst, r, b) = make_uint4(pack2(f[8 * b], f[8 * b + 1]), pack2(f[8 * b + 2], f[8 * b + 3]),
+                                         pack2(f[8 * b + 4], f[8 * b + 5]), pack2(f[8 * b + 6], f[8 * b + 7]));
   }
 }
 
@@ -238,7 +276,7 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
   const int m = a.m, n = a.n, R = a.rounds, vt = a.vt, ct = a.ct;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, T = blockDim.x;
   const int W = T >> 5;
-  const TcLay L = tc_layout(m, n, vt, ct);
+  const TcLay L = tc_layout(m, n, a.E, vt, ct);
   unsigned char* mv = smem + L.mv;
   unsigned char* mc = smem + L.mc;
   unsigned char* op = smem + L.op;
@@ -256,6 +294,10 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
   float* degv = reinterpret_cast<float*>(smem + L.degv);
   float* degc = reinterpret_cast<float*>(smem + L.degc);
   float* sig = reinterpret_cast<float*>(smem + L.sig);
+  int* vptr = reinterpret_cast<int*>(smem + L.vptr);
+  int* cptr = reinterpret_cast<int*>(smem + L.cptr);
+  uint32_t* vadj = reinterpret_cast<uint32_t*>(smem + L.vadj);
+  uint32_t* cadj = reinterpret_cast<uint32_t*>(smem + L.cadj);
   float* kappa = reinterpret_cast<float*>(smem + L.misc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc + 8);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.misc + 16);
@@ -318,14 +360,17 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
     for (int o = 0; o < HD; ++o) acc = fmaf(__ldg(P + POff::wo + o), __ldg(P + POff::b2cv + o), acc);
     *kappa = acc;
   }
-  for (int i = tid; i < n * 64; i += T) {
-    const int v = i >> 6, o = i & 63;
-    const float* w = swv + o * HD;
-    const float* h = h0 + v * HD;
-    float acc = 0.f;
+  for (int v = tid; v < n; v += T) {  // column-major [64][n]: a thread per variable
+    float h[HD];
+#pragma unroll
+    for (int j = 0; j < HD; ++j) h[j] = h0[v * HD + ((j + v) & (HD - 1))];  // rotated: no conflicts
 #pragma unroll 1
-    for (int j = 0; j < HD; ++j) acc = fmaf(w[j], h[j], acc);
-    p0[i] = acc;
+    for (int o = 0; o < 64; ++o) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < HD; ++j) acc = fmaf(swv[o * HD + ((j + v) & (HD - 1))], h[j], acc);
+      p0[o * n + v] = acc;
+    }
   }
   for (int v = tid; v < n; v += T) {
     float acc = __ldg(a.prior + v) + __ldg(P + POff::bo);
@@ -335,6 +380,13 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
     degv[v] = (float)(__ldg(a.var_ptr + v + 1) - __ldg(a.var_ptr + v));
   }
   for (int c = tid; c < m; c += T) degc[c] = (float)(__ldg(a.chk_ptr + c + 1) - __ldg(a.chk_ptr + c));
+  for (int v = tid; v <= n; v += T) vptr[v] = __ldg(a.var_ptr + v);
+  for (int c = tid; c <= m; c += T) cptr[c] = __ldg(a.chk_ptr + c);
+  for (int e = tid; e < a.E; e += T) {
+    const uint32_t c = __ldg(a.var_chk + e), v = __ldg(a.chk_var + e);
+    vadj[e] = (c << 6) | ((c >> 1) & 3u);
+    cadj[e] = (v << 6) | ((v >> 1) & 3u);
+  }
   __syncthreads();
   {  // the staging is done: operand rows past the last node stay zero (finite)
     const int words = (int)((L.as - L.op) / 16);
@@ -358,22 +410,27 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
   uint32_t phase = 0;
   bool failed = false;
 
-  // warp w serves TMEM lane quarter w % 4; chunk (tile i, quarter q) of `tiles` tiles goes to
-  // warp q + 4 ((i + rot) % nq), nq = the number of warps on quarter q
+  // warp w serves TMEM lane quarter w % 4; half hf of chunk (tile i, quarter q) goes to warp
+  // q + 4 ((2 i + hf + rot) % nq), nq = the number of warps on quarter q
   const int q = warp & 3;
   const int nq = (W - q + 3) >> 2;
   const int wslot = warp >> 2;
   auto chunks = [&](int tiles, int rows, int col0, int rot, bool check, int mode, float nb,
                     unsigned char* lo, unsigned char* hi) {
     for (int i = 0; i < tiles; ++i) {
-      if ((i + rot) % nq != wslot || i * 128 + q * 32 >= rows) continue;
+      if (i * 128 + q * 32 >= rows) continue;
       const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(col0 + 64 * i);
-      tc_rows(taddr, i * 128 + q * 32 + lane, rows, check, mode, nb, p0, pc0, check ? kc : kv,
-              check ? degc : degv, sig, lo, hi);
+      for (int hf = 0; hf < 2; ++hf) {
+        if ((2 * i + hf + rot) % nq != wslot) continue;
+        tc_half(taddr, hf, i * 128 + q * 32 + lane, rows, check, mode, nb, p0, pc0,
+                check ? kc : kv, check ? degc : degv, sig, hf ? hi : lo);
+      }
     }
   };
-  // the MMA of `tiles` tiles: accumulators at column col0 + 64 i, operand tile i, weights w
+  // the MMA of `tiles` tiles: accumulators at column col0 + 64 i, operand tile i, weights w.
+  // The issuing thread alone waits for completion; the others wait at the barrier.
   auto mma_tiles = [&](int tiles, int col0, const unsigned char* w) -> bool {
+    int ok = 1;
     if (tid == 0) {
       fence_after();
       for (int i = 0; i < tiles; ++i)
@@ -381,11 +438,12 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
           mma_bf16(tbase + (uint32_t)(col0 + 64 * i), umma_desc(smem_u32(op + 8192 * i + 256 * j)),
                    umma_desc(smem_u32(w + 256 * j)));
       mma_commit(mbar);
+      ok = mbar_wait(mbar, phase) ? 1 : 0;
     }
-    const bool ok = mbar_wait(mbar, phase);
     phase ^= 1u;
+    ok = __syncthreads_and(ok);
     fence_after();
-    return __syncthreads_and(ok ? 1 : 0) != 0;
+    return ok != 0;
   };
 
   for (long long shot = blockIdx.x; shot < a.shots && !failed; shot += gridDim.x) {
@@ -401,30 +459,36 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
     __syncthreads();
     for (int t = 0; t < R; ++t) {
       const bool last = t == R - 1;
-      // ---- X2: S_v = sum_c relu(A_c + B_v), 4 threads per row, and the LLR update ----
-      for (int base = warp * 32; base < 4 * n; base += T) {
-        const int task = base + lane, v = task >> 2, b = task & 3;
-        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (task < 4 * n) {
-          float qv[8];
-          unpack8(*row_chunk(bs, v, b), qv);
-          const int e1 = __ldg(a.var_ptr + v + 1);
-          for (int e = __ldg(a.var_ptr + v); e < e1; ++e) {
-            float pa[8];
-            unpack8(*row_chunk(as, __ldg(a.var_chk + e), b), pa);
+      // ---- X2: S_v = sum_c relu(A_c + B_v), 2 threads per row (16 features each), and the
+      // LLR update ----
+      for (int base = warp * 32; base < 2 * n; base += T) {
+        const int task = base + lane, v = task >> 1, h = task & 1;
+        float s[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) s[k] += fmaxf(pa[k] + qv[k], 0.f);
+        for (int k = 0; k < 16; ++k) s[k] = 0.f;
+        if (task < 2 * n) {
+          const uint4 q0 = *row_chunk(bs, v, 2 * h), q1 = *row_chunk(bs, v, 2 * h + 1);
+          unsigned long long acc0[4] = {0ull, 0ull, 0ull, 0ull}, acc1[4] = {0ull, 0ull, 0ull, 0ull};
+          const int e1 = vptr[v + 1];
+          for (int e = vptr[v]; e < e1; ++e) {
+            const uint32_t x = vadj[e];
+            relu_acc8(edge_chunk(as, x, 2 * h), q0, acc0);
+            relu_acc8(edge_chunk(as, x, 2 * h + 1), q1, acc1);
           }
-          if (!last)
-            *reinterpret_cast<uint4*>(op + koff(v, 8 * b)) =
+          unpack_acc8(acc0, s);
+          unpack_acc8(acc1, s + 8);
+          if (!last) {
+            *reinterpret_cast<uint4*>(op + koff(v, 16 * h)) =
                 make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
+            *reinterpret_cast<uint4*>(op + koff(v, 16 * h + 8)) =
+                make_uint4(pack2(s[8], s[9]), pack2(s[10], s[11]), pack2(s[12], s[13]), pack2(s[14], s[15]));
+          }
         }
         float dot = 0.f;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) dot = fmaf(u[8 * b + k], s[k], dot);
+        for (int k = 0; k < 16; ++k) dot = fmaf(u[16 * h + k], s[k], dot);
         dot += __shfl_xor_sync(0xffffffffu, dot, 1);
-        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
-        if (task < 4 * n && b == 0) llr[v] += dot + degv[v] * kap;
+        if (task < 2 * n && h == 0) llr[v] += dot + degv[v] * kap;
       }
       if (last) break;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -439,15 +503,12 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
       // ---- X1: T_c = sum_v relu(C_v + D_c) ----
       for (int task = tid; task < 4 * m; task += T) {
         const int c = task >> 2, b = task & 3;
-        float qd[8], s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        unpack8(*row_chunk(ds, c, b), qd);
-        const int e1 = __ldg(a.chk_ptr + c + 1);
-        for (int e = __ldg(a.chk_ptr + c); e < e1; ++e) {
-          float pc[8];
-          unpack8(*row_chunk(cs, __ldg(a.chk_var + e), b), pc);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) s[k] += fmaxf(pc[k] + qd[k], 0.f);
-        }
+        const uint4 qd = *row_chunk(ds, c, b);
+        unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+        const int e1 = cptr[c + 1];
+        for (int e = cptr[c]; e < e1; ++e) relu_acc8(edge_chunk(cs, cadj[e], b), qd, acc);
+        float s[8];
+        unpack_acc8(acc, s);
         *reinterpret_cast<uint4*>(op + koff(c, 8 * b)) =
             make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
       }
@@ -473,8 +534,8 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
     bool bad = false;
     for (int c = tid; c < m; c += T) {
       unsigned par = sig[c] < 0.f ? 1u : 0u;
-      const int e1 = __ldg(a.chk_ptr + c + 1);
-      for (int e = __ldg(a.chk_ptr + c); e < e1; ++e) par ^= llr[__ldg(a.chk_var + e)] < 0.f;
+      const int e1 = cptr[c + 1];
+      for (int e = cptr[c]; e < e1; ++e) par ^= llr[cadj[e] >> 6] < 0.f;
       bad = bad || par;
     }
     if (__syncthreads_or(bad)) {
@@ -517,14 +578,14 @@ struct TcShape {
 
 // The launch shape for H (m x n with maximal degrees dv, dc), or false when the graph does
 // not fit: at most 8 tiles of 128 rows, the tables in shared memory.
-bool tc_shape(int m, int n, int dv, int dc, int max_smem, TcShape* s) {
+bool tc_shape(int m, int n, int E, int dv, int dc, int max_smem, TcShape* s) {
   s->vt = (n + 127) / 128;
   s->ct = (m + 127) / 128;
   if (s->vt + s->ct > kTcMaxTiles || n >= 65535 || m >= 65535) return false;
   const int need = 64 * (s->vt + s->ct);
   s->cols = 32;
   while (s->cols < need) s->cols <<= 1;
-  s->smem = tc_layout(m, n, s->vt, s->ct).total;
+  s->smem = tc_layout(m, n, E, s->vt, s->ct).total;
   // at most as many CTAs per SM as TMEM holds: pad shared memory so no more fit
   const int per_sm = 512 / s->cols;
   const size_t floor_smem = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1024;
@@ -534,7 +595,8 @@ bool tc_shape(int m, int n, int dv, int dc, int max_smem, TcShape* s) {
   double best = -1.0;
   for (int w = kTcMinWarps; w <= kTcMaxWarps; ++w) {
     const int T = 32 * w;
-    const double pv = (double)((4 * n + T - 1) / T) * T * dv, pc = (double)((4 * m + T - 1) / T) * T * dc;
+    // X2: 2 tasks per variable, 16 features each; X1: 4 tasks per check, 8 features each
+    const double pv = (double)((2 * n + T - 1) / T) * T * 2 * dv, pc = (double)((4 * m + T - 1) / T) * T * dc;
     const double eff = (4.0 * n * dv + 4.0 * m * dc) / (pv + pc);
     if (eff > best + 1e-9) {
       best = eff;
@@ -553,14 +615,34 @@ cudaError_t prior_tc_config(const DevGraph& g, int* grid) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   TcShape s;
-  if (!tc_shape(g.m, g.n, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
+  if (!tc_shape(g.m, g.n, g.E, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
   err = allow_max_dynamic_smem((const void*)prior_tc_kernel, max_smem);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute((const void*)prior_tc_kernel,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prior_tc_kernel, s.threads, s.smem);
   if (err != cudaSuccess) return err;
+  // CTAs per SM from the kernel's own limits: registers (in 256-register warp units), shared
+  // memory (with the per-CTA reservation) and threads
+  cudaFuncAttributes fa{};
+  int regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0;
+  err = cudaFuncGetAttributes(&fa, (const void*)prior_tc_kernel);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (err != cudaSuccess) return err;
+  const long warp_regs = ((long)fa.numRegs * 32 + 255) / 256 * 256;
+  const long by_regs = regs_sm / (warp_regs * (s.threads / 32));
+  const long by_smem = smem_sm / ((long)s.smem + fa.sharedSizeBytes + reserved);
+  const long by_threads = threads_sm / s.threads;
+  const long own = std::min(std::min(by_regs, by_smem), by_threads);
+  if (own > per_sm) per_sm = (int)own;
   if (per_sm < 1) return cudaErrorInvalidValue;
-  if (per_sm > 512 / s.cols) per_sm = 512 / s.cols;
+  if (per_sm > 512 / s.cols) per_sm = 512 / s.cols;  // TMEM: 512 columns per SM
   *grid = per_sm * sms;
   return cudaSuccess;
 }
@@ -576,10 +658,11 @@ cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float
   if (err != cudaSuccess) return err;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   TcShape s;
-  if (!tc_shape(g.m, g.n, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
+  if (!tc_shape(g.m, g.n, g.E, g.max_col_deg, g.max_row_deg, max_smem, &s)) return cudaErrorInvalidValue;
   TcArgs a{};
   a.m = g.m;
   a.n = g.n;
+  a.E = g.E;
   a.rounds = rounds;
   a.vt = s.vt;
   a.ct = s.ct;

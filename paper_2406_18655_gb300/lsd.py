@@ -39,7 +39,8 @@ EXPORTS = ("lsd_create", "lsd_decode_batch", "lsd_decode_batch_host", "lsd_bp_ba
            "lsd_giant_decode", "lsd_giant_postprocess", "lsd_giant_kernel_launches",
            "lsd_giant_destroy", "lsd_giant_test_hold_barrier", "lsd_bp_variant_name",
            "lsd_server_create_with_windows", "lsd_server_submit_round",
-           "lsd_server_get_code_report", "lsd_prior_set_kernel")
+           "lsd_server_get_code_report", "lsd_prior_set_kernel", "lsd_prior_get_kernel",
+           "lsd_decode_batch_packed", "lsd_decode_batch_host_packed")
 
 
 class LsdError(RuntimeError):
@@ -108,6 +109,8 @@ def lib():
                              C.c_int32, C.POINTER(Options)]
     L.lsd_decode_batch.argtypes = [P, C.c_int64, P, P, P, P, C.POINTER(Stats)]
     L.lsd_decode_batch_host.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
+    L.lsd_decode_batch_packed.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
+    L.lsd_decode_batch_host_packed.argtypes = [P, C.c_int64, P, P, P, C.POINTER(Stats)]
     L.lsd_bp_batch.argtypes = [P, C.c_int64, P, P, P, P]
     L.lsd_postprocess_batch.argtypes = [P, C.c_int64, P, P, P, P, P]
     L.lsd_get_stats.argtypes = [P, C.POINTER(Stats)]
@@ -122,6 +125,7 @@ def lib():
     L.lsd_prior_get_params.argtypes = [P, P]
     L.lsd_prior_forward.argtypes = [P, C.c_int64, P, P]
     L.lsd_prior_set_kernel.argtypes = [P, C.c_int32]
+    L.lsd_prior_get_kernel.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.lsd_prior_gradient.argtypes = [P, C.c_int64, P, P, C.POINTER(C.c_double), P]
     L.lsd_prior_train_step.argtypes = [P, C.c_int64, P, P, C.c_float, C.POINTER(C.c_double)]
     L.lsd_decode_learned.argtypes = [P, P, C.c_int64, P, P, P, C.POINTER(Stats)]
@@ -156,6 +160,22 @@ def lib():
 
 def status_string(code: int) -> str:
     return lib().lsd_status_string(int(code)).decode()
+
+
+def pack_bits(rows) -> np.ndarray:
+    """[k][L] 0/1 bytes -> [k][ceil(L/32)] uint32: element i is bit i & 31 of word i >> 5."""
+    a = np.ascontiguousarray(np.asarray(rows, dtype=np.uint8))
+    k, L = a.shape
+    W = (L + 31) // 32
+    pad = np.zeros((k, 32 * W), np.uint8)
+    pad[:, :L] = a
+    return np.ascontiguousarray(np.packbits(pad, axis=1, bitorder="little")).view("<u4")
+
+
+def unpack_bits(words, L: int) -> np.ndarray:
+    """Inverse of pack_bits: [k][W] uint32 -> [k][L] 0/1 bytes."""
+    w = np.ascontiguousarray(np.asarray(words, dtype="<u4"))
+    return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, :L]
 
 
 def bp_variant_name(variant: int) -> str:
@@ -269,6 +289,54 @@ class Decoder:
                "lsd_decode_batch")
         if want_stats:
             return corrections, status, st.as_dict()
+        return corrections, status
+
+    def decode_packed(self, syndromes, corrections=None, status=None, want_stats: bool = False):
+        """BP then LSD on bit-packed device syndromes [shots][ceil(m/32)] (int32 tensor holding
+        the uint32 words).  Returns (packed corrections [shots][ceil(n/32)], status[, stats])."""
+        import torch
+        shots = syndromes.shape[0]
+        wm, wn = (self.m + 31) // 32, (self.n + 31) // 32
+        _dev_tensor(syndromes, torch.int32, (shots, wm), "syndromes")
+        dev = syndromes.device
+        if corrections is None:
+            corrections = torch.empty((shots, wn), dtype=torch.int32, device=dev)
+        if status is None:
+            status = torch.empty(shots, dtype=torch.uint8, device=dev)
+        _dev_tensor(corrections, torch.int32, (shots, wn), "corrections")
+        _dev_tensor(status, torch.uint8, (shots,), "status")
+        st = Stats() if want_stats else None
+        _check(lib().lsd_decode_batch_packed(self._h, shots, _ptr(syndromes), _ptr(corrections),
+                                             _ptr(status), C.byref(st) if st is not None else None),
+               "lsd_decode_batch_packed")
+        if want_stats:
+            return corrections, status, st.as_dict()
+        return corrections, status
+
+    def decode_host_packed(self, syndromes, corrections=None, status=None):
+        """Host-buffer packed decode: syndromes [shots][ceil(m/32)] uint32 (numpy, or CPU int32
+        tensors); returns (corrections [shots][ceil(n/32)], status)."""
+        shots = syndromes.shape[0]
+        wm, wn = (self.m + 31) // 32, (self.n + 31) // 32
+        if corrections is None:
+            corrections = np.empty((shots, wn), np.uint32)
+        if status is None:
+            status = np.empty(shots, np.uint8)
+
+        def hp(a, shape, name):
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+                    raise ValueError(f"{name} must be a contiguous CPU tensor of shape {shape}")
+                return C.c_void_p(a.data_ptr())
+            if a.dtype.itemsize != 4 and name != "status" or not a.flags.c_contiguous \
+                    or a.shape != tuple(shape):
+                raise ValueError(f"{name} must be a contiguous array of shape {shape}")
+            return a.ctypes.data_as(C.c_void_p)
+
+        _check(lib().lsd_decode_batch_host_packed(
+            self._h, shots, hp(syndromes, (shots, wm), "syndromes"),
+            hp(corrections, (shots, wn), "corrections"), hp(status, (shots,), "status"), None),
+            "lsd_decode_batch_host_packed")
         return corrections, status
 
     def decode_host(self, syndromes, corrections=None, status=None, want_stats: bool = False):
@@ -618,6 +686,12 @@ class Prior:
         code = {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]
         _check(lib().lsd_prior_set_kernel(self._h, code), "lsd_prior_set_kernel")
 
+    def kernel(self) -> dict:
+        """The inference kernel in use and its grid (CTAs)."""
+        k, g = C.c_int32(), C.c_int32()
+        _check(lib().lsd_prior_get_kernel(self._h, C.byref(k), C.byref(g)), "lsd_prior_get_kernel")
+        return {"kernel": {1: "mma_sync", 2: "tcgen05"}[k.value], "grid": g.value}
+
     def forward(self, syndromes):
         import torch
         d = self.decoder
@@ -696,7 +770,7 @@ def _server_lib():
         for name in ("lsd_server_create", "lsd_server_submit", "lsd_server_wait_all",
                      "lsd_server_get_report", "lsd_server_run_poisson", "lsd_server_destroy",
                      "lsd_server_create_with_windows", "lsd_server_submit_round",
-                     "lsd_server_get_code_report", "lsd_prior_set_kernel"):
+                     "lsd_server_get_code_report"):
             getattr(L, name).restype = C.c_int
         L._server_ready = True
     return L
@@ -779,7 +853,7 @@ class Server:
     def code_report(self, code: int) -> dict:
         r = ServerReport()
         _check(_server_lib().lsd_server_get_code_report(self._h, code, C.byref(r)),
-               "lsd_server_get_code_report", "lsd_prior_set_kernel")
+               "lsd_server_get_code_report")
         return r.as_dict()
 
     def wait_all(self):

@@ -130,17 +130,19 @@ def test_gradient_matches_oracle(L):
 
 def test_training_gains_over_lsd_on_channel_priors(L):
     """Train on device-sampled pairs at p = 0.05, then compare logical error rates on held-out
-    shots: LSD on the learned LLRs vs LSD on the channel priors alone (BP with 0 iterations)."""
+    shots: LSD on the learned LLRs against LSD on the channel priors alone (BP with 0
+    iterations) and against BP+LSD with as many message-passing rounds as the network has
+    (BP with 4 iterations, the method without the network at the same budget)."""
     name, p = "bb144", 0.05
     h, probs, _, _ = sample(name, p, 1, seed=1)
     d = L.Decoder(h, probs, 50)
     pr = L.Prior(d, rounds=4, params=init_params(7))
     losses = []
-    batch = 2048
-    for step in range(250):
+    batch, steps = 2048, 1000  # about 2 M pairs
+    for step in range(steps):
         e, s = d.sample(99, batch, first_shot=step * batch)
-        lr = 3e-3 if step < 200 else 1e-3
-        losses.append(pr.train_step(s, e, lr, want_loss=(step % 25 == 0 or step == 249)))
+        lr = 3e-3 if step < 0.8 * steps else 1e-3
+        losses.append(pr.train_step(s, e, lr, want_loss=(step % 100 == 0 or step == steps - 1)))
     losses = [x for x in losses if x is not None]
     print("training losses", [round(x, 5) for x in losses])
     assert losses[-1] < 0.9 * losses[0]
@@ -164,3 +166,14 @@ def test_training_gains_over_lsd_on_channel_priors(L):
           f"BP(4)+LSD {ler_bp4:.4f}  BP(50)+LSD {ler_bp:.4f}")
     sigma = np.sqrt(ler_prior * (1 - ler_prior) / 20000)
     assert ler_learned < ler_prior - 3 * sigma
+    sigma4 = np.sqrt(ler_bp4 * (1 - ler_bp4) / 20000)
+    assert ler_learned < ler_bp4 - 2 * sigma4
+    # the same network through the other inference kernel: the two kernels differ only in
+    # rounding, so their logical error rates on the same shots agree closely
+    kernels = {"mma_sync": None, "tcgen05": None}
+    for k in kernels:
+        pr.set_kernel(k)
+        c_k, _ = d.decode_learned(pr, sd)
+        kernels[k] = chk.failures(ed, c_k).float().mean().item()
+    print("LER by inference kernel", kernels)
+    assert abs(kernels["mma_sync"] - kernels["tcgen05"]) <= 2e-3
