@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--serving-loads", default="1e4,1e5,1e6,1e7",
                     help="offered loads (shots/s) of the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=0.5)
+    ap.add_argument("--serving-slots", type=int, default=3,
+                    help="in-flight batches per code (per window matrix) in the server")
     ap.add_argument("--legs-out", default=None, help="also write every leg to this JSON file")
     return ap.parse_args()
 
@@ -94,12 +96,8 @@ def config(args, hx):
         "workload": f"BB[[144,12,12]] H_X {hx.shape[0]}x{hx.shape[1]}, i.i.d. p={args.p}, "
                     f"{args.shots} shots/step, min-sum BP {args.iters} it (alpha 0.625, early exit)"
                     f" + LSD-{args.order}",
-        "code": "BB[[144,12,12]] (l=12, m=6, A=x^3+y+y^2, B=y^3+x+x^2)",
         "shots_per_step": args.shots,
-        "p": args.p,
-        "bp_iters": args.iters,
-        "lsd_order": args.order,
-        "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
+        "l2": "flushed between steps (256 MiB write)",
     }
 
 
@@ -174,8 +172,7 @@ def cpu_baseline(args, hx, probs, s, budget_s):
     oracle.decode(hx, probs, s[:n_s], args.iters, lsd_order=args.order, precision=1, nthreads=0)
     dt = time.perf_counter() - t0
     return {"value": n_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n_s} of the step's {args.shots} shots ({dt:.1f} s, "
-                      f"std::thread over shots, {cores} threads)"}
+            "sample": f"first {n_s} shots of the step, {dt:.1f} s, {cores} threads"}
 
 
 def run_reference(args):
@@ -633,7 +630,7 @@ def alu_peak():
         pass
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    return sms * 128 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32/INT32 lanes x {mhz:.0f} MHz"
+    return sms * 128 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 lanes x {mhz:.0f} MHz (max SM clock)"
 
 
 def hgp_leg(args, stream, flush, barrier):
@@ -713,7 +710,7 @@ def serving_leg(args):
                                         I.sample_errors(args.seed + 131, 4096, probs)))
     wcode = dict(h=hx, p=0.003, q=0.003, rounds=d, window=3, commit=1, bp_iters=30,
                  streams=streams)
-    srv = Server(codes, window_codes=[wcode])
+    srv = Server(codes, window_codes=[wcode], slots_per_code=args.serving_slots)
     out = []
     for rate in [float(x) for x in args.serving_loads.split(",") if x]:
         rep = srv.run_poisson(rate, args.serving_seconds, [1, 1, 1, 0], pools + [seqs],
@@ -722,6 +719,8 @@ def serving_leg(args):
                                   "p50_us", "p99_us", "max_us", "mean_batch", "admission_waits")}
         pt["per_code_p50_p99_us"] = [[round(r["p50_us"], 1), round(r["p99_us"], 1)]
                                      for r in (srv.code_report(c) for c in range(3))]
+        pt["p99_parts_us"] = {k: round(rep[k], 1) for k in ("p99_lag_us", "p99_queue_us",
+                                                             "p99_service_us")}
         out.append(pt)
     windows = []
     for rate in (1e4, 1e5, 1e6):
@@ -736,17 +735,34 @@ def serving_leg(args):
                             "blocks": rep["generated"], "window_jobs": w["completed"],
                             "rounds_per_s": w["completed"] / max(rep["seconds"], 1e-9),
                             "p50_us": w["p50_us"], "p99_us": w["p99_us"], "max_us": w["max_us"],
+                            "p99_parts_us": {k: round(w[k], 1) for k in
+                                             ("p99_lag_us", "p99_queue_us", "p99_service_us",
+                                              "p99_batch_gpu_us", "p99_launch_call_us")},
+                            "mean_batch": w["mean_batch"],
                             "refused_blocks": rep["admission_waits"]})
     srv.close()
     return {"codes": ["BB[[72,12,6]] d=6: H 252x648", "BB[[144,12,12]] d=12: H 936x2592",
                       "BB[[288,12,18]] d=18: H 2736x7776"],
             "noise": "phenomenological p = q = 0.003", "bp_iters": 30, "lsd_order": 0,
             "mix": "equal", "seconds_per_load": args.serving_seconds,
-            "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)", "loads": out,
+            "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)",
+            "slots_per_code": args.serving_slots, "loads": out,
             "batch_reference": {"ms_per_65536_shots": batch_ms,
                                 "mix_shots_per_s": mix_batch_rate},
             "windows": {"code": "BB[[144,12,12]] rounds, d = 12, (3,1) windows, 1024 streams",
                         "loads": windows}}
+
+
+def _sig(x, digits=5):
+    """Floats of a nested summary rounded to `digits` significant digits (keeps the headline
+    line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    return x
 
 
 def learned_summary(learned):
@@ -776,15 +792,12 @@ def serving_summary(serving):
     round rate of the window streams: p50 / p99 per round, alone and mixed with shots."""
     if not serving:
         return None
-    return {"codes": "BB72 d=6, BB144 d=12, BB288 d=18 space-time, p=q=0.003",
-            "loads": [[x["offered_rate"], round(x["shots_per_s"]), round(x["p50_us"], 1),
-                       round(x["p99_us"], 1)] for x in serving["loads"]],
-            "columns": ["offered shots/s", "completed shots/s", "p50 us", "p99 us"],
+    return {"shots": [[x["offered_rate"], round(x["shots_per_s"]), round(x["p50_us"]),
+                       round(x["p99_us"])] for x in serving["loads"]],
             "batch_mix_shots_per_s": round(serving["batch_reference"]["mix_shots_per_s"]),
-            "window_rounds": [[x["offered_rounds_per_s"], int(x["with_shots"]),
-                               round(x["p50_us"], 1), round(x["p99_us"], 1)]
-                              for x in serving["windows"]["loads"]],
-            "window_columns": ["offered rounds/s", "with shots", "p50 us", "p99 us"]}
+            "window_rounds": [[x["offered_rounds_per_s"], int(x["with_shots"]), round(x["p50_us"]),
+                               round(x["p99_us"])] for x in serving["windows"]["loads"]],
+            "cols": "offered/s, completed shots/s or with-shots flag, p50 us, p99 us"}
 
 
 def run_ours(args):
@@ -892,9 +905,30 @@ def run_ours(args):
             dec.decode_host(s_pin, c_pin, st_pin)
             t_e2e.append(time.perf_counter() - t0)
         job_e2e = job_throughput(args.shots, 1000.0 * sum(t_e2e) / args.steps, device="cuda")
-        e2e = {"value": job_e2e["per_s"], "unit": UNIT,
-               "h2d_bytes_per_step": int(args.shots * m),
-               "d2h_bytes_per_step": int(args.shots * (n + 1))}
+        e2e_bytes = {"value": job_e2e["per_s"], "unit": UNIT, "call": "lsd_decode_batch_host",
+                     "h2d_bytes_per_step": int(args.shots * m),
+                     "d2h_bytes_per_step": int(args.shots * (n + 1))}
+        # the same through the bit-packed host call (syndromes and corrections one bit each)
+        from paper_2406_18655_gb300.lsd import pack_bits
+        wm, wn = (m + 31) // 32, (n + 31) // 32
+        sw_pin = torch.from_numpy(pack_bits(s).view(np.int32)).pin_memory()
+        cw_pin = torch.empty((args.shots, wn), dtype=torch.int32).pin_memory()
+        for _ in range(max(args.warmup, 1)):
+            dec.decode_host_packed(sw_pin, cw_pin, st_pin)
+        barrier()
+        t_pk = []
+        for _ in range(args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            dec.decode_host_packed(sw_pin, cw_pin, st_pin)
+            t_pk.append(time.perf_counter() - t0)
+        job_pk = job_throughput(args.shots, 1000.0 * sum(t_pk) / args.steps, device="cuda")
+        e2e = {"value": job_pk["per_s"], "unit": UNIT, "call": "lsd_decode_batch_host_packed",
+               "h2d_bytes_per_step": int(args.shots * 4 * wm),
+               "d2h_bytes_per_step": int(args.shots * (4 * wn + 1)),
+               "bytes_call": {"value": e2e_bytes["value"],
+                              "h2d_bytes_per_step": e2e_bytes["h2d_bytes_per_step"],
+                              "d2h_bytes_per_step": e2e_bytes["d2h_bytes_per_step"]}}
 
     serving = p_sweep = hgp = lsd_mu = windows = giant = hooks = None
     if rank == 0 and not args.no_sweeps:
@@ -922,9 +956,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": bp_name or "bp (default variant)",
                 "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": BP_TRAFFIC_BYTES.get(bp_name),
-                "peak_source": peak_src + " (max SM clock of MEASURED_PEAKS.json)",
-                "ops_per_unit": f"{OPS_PER_EDGE_ITER} ops per edge-iteration, {E} edges, "
-                                f"{iters_per_step:.0f} shot-iterations per launch"}
+                "peak_source": peak_src,
+                "ops_per_unit": f"{OPS_PER_EDGE_ITER} x {E} edges x {iters_per_step:.0f} "
+                                "shot-iterations"}
     legs = {"lsd_clusters": clusters, "autotune": tune, "learned": learned,
             "p_sweep": p_sweep, "lsd_mu_cs4": lsd_mu, "windows": windows, "giant_shot": giant,
             "circuit_like": hooks, "hgp": hgp, "serving": serving}
@@ -940,17 +974,16 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config(args, hx),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                       "p99": float(np.percentile(step_ms, 99)),
-                       "what": "batch latency of one step (10^6 shots, device-resident)"},
+                       "p99": float(np.percentile(step_ms, 99))},
         "ler": ler, "bp_converged_frac": conv_frac, "lsd_frac": lsd_frac,
         "mean_bp_iters": iters_per_step / args.shots,
         "kernel_ms": {"bp": bp_ms_avg, "lsd": float(np.mean(lsd_ms))},
-        "roofline": roofline,
-        "e2e": e2e,
+        "roofline": _sig(roofline),
+        "e2e": _sig(e2e),
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "learned": learned_summary(learned),
-        "serving": serving_summary(serving),
+        "learned": _sig(learned_summary(learned)),
+        "serving": _sig(serving_summary(serving)),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, hx, probs.astype(np.float64), s,

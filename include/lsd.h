@@ -545,6 +545,11 @@ typedef struct lsd_server_report {
   double shots_per_s;       /* completed / seconds */
   double p50_us, p99_us, mean_us, max_us;  /* arrival-to-completion latency */
   double offered_rate;      /* lsd_server_run_poisson: the requested arrival rate (shots/s) */
+  /* p99 of the latency's parts: arrival to submission (the load generator's lag behind its
+   * schedule), submission to batch launch (queueing), launch to completion (service) */
+  double p99_lag_us, p99_queue_us, p99_service_us;
+  double p99_batch_gpu_us;  /* lsd_server_get_code_report: p99 of a batch's GPU time */
+  double p99_launch_call_us;  /* ... and of the host time of a batch's launch calls */
 } lsd_server_report;
 
 /* Creates the server and its decoders (each slot's workspace sized for max_batch). */
@@ -623,7 +628,9 @@ int lsd_server_get_code_report(lsd_server* s, int32_t code, lsd_server_report* r
  * user code, window codes included) and the next syndrome of pools[c] ([pool_sizes[c]][m_c]
  * bytes, GPU-accessible, cycled); outputs are discarded.  For a window code an arrival is
  * one detector block of the code's streams in turn, stream s playing the sequences s,
- * s + S, s + 2S, ... of pools[c] ([pool_sizes[c]][(d+1) m] bytes, host memory); blocks
+ * s + S, s + 2S, ... of pools[c] ([pool_sizes[c]][(d+1) m] bytes, host memory) and
+ * continuing from where the stream stands in the server (successive calls extend the same
+ * sequences); blocks
  * refused for a busy history are dropped and counted in admission_waits.  Waits for
  * completion and fills `report` (latency from the scheduled arrival); the per-code reports
  * of the run stay readable until the next reset.

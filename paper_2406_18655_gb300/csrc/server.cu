@@ -48,6 +48,8 @@ struct Request {
   int64_t id;
   int32_t stream = -1;   // window jobs: stream, first round of the window, history half
   int32_t t = 0, half = 0;
+  int64_t enqueue_ns = 0;  // when the server took it (arrival_ns may be a scheduled time)
+  int64_t launch_ns = 0;   // when its batch was launched
 };
 
 // Per-shot pointers and window-job fields of one batch (pinned host memory, read by the
@@ -137,13 +139,17 @@ struct Slot {
   lsd_decoder* dec = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr;  // recorded before the batch: its GPU time is start -> done
   uint8_t* d_syn = nullptr;
   uint8_t* d_corr = nullptr;
   uint8_t* d_status = nullptr;
   BatchDesc desc{};            // pinned
-  long long* count = nullptr;  // pinned, read by the kernels: shots of the batch
+  long long* count = nullptr;  // pinned: shots of the batch, written by the scheduler
+  long long* d_count = nullptr;  // device copy, made at the start of every batch and read by
+                                 // its kernels (one host read per batch, not one per warp)
   cudaGraphExec_t graph = nullptr;  // gather -> BP -> LSD -> scatter, captured once
   std::vector<Request> reqs;   // requests of the batch in flight
+  int64_t launch_call_ns = 0;  // host time its launch calls took
   size_t reserved = 0;         // admitted bytes
   bool busy = false;
 };
@@ -187,6 +193,12 @@ struct WindowCode {
 struct Stats {
   int64_t submitted = 0, completed = 0;
   std::vector<int64_t> latency_ns;
+  // the latency's parts: scheduled arrival to submission (a load generator's lag),
+  // submission to batch launch (queueing), launch to completion observed (service)
+  std::vector<int64_t> lag_ns, queue_ns, service_ns;
+  std::vector<int64_t> batch_gpu_ns;  // per batch: GPU time from its start to its done event
+  std::vector<int64_t> launch_call_ns;  // per batch: host time of the launch calls
+  int64_t batches = 0, batched = 0;
 };
 
 struct Report {
@@ -241,21 +253,24 @@ bool gpu_accessible(const void* p) {
 int enqueue_pipeline(Code& c, Slot& s, int max_batch) {
   const int blocks = (max_batch + 7) / 8;
   WindowCode* W = c.win;
+  cudaError_t e0 = cudaMemcpyAsync(s.d_count, s.count, sizeof(long long), cudaMemcpyHostToDevice,
+                                   s.st);
+  if (e0 != cudaSuccess) return cuda_rc(e0);
   if (W)
-    window_gather_kernel<<<blocks, 256, 0, s.st>>>(s.count, W->m, c.blocks, (W->d + 1) * W->m,
+    window_gather_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, W->m, c.blocks, (W->d + 1) * W->m,
                                                    W->hist, W->carry, s.desc.job, s.d_syn);
   else
-    gather_kernel<<<blocks, 256, 0, s.st>>>(s.count, c.m, s.desc.syn, s.d_syn);
+    gather_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, c.m, s.desc.syn, s.d_syn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_rc(e);
-  int rc = lsdgb::decode_batch_counted(s.dec, max_batch, s.count, s.d_syn, s.d_corr, s.d_status);
+  int rc = lsdgb::decode_batch_counted(s.dec, max_batch, s.d_count, s.d_syn, s.d_corr, s.d_status);
   if (rc) return rc;
   if (W)
-    window_commit_kernel<<<blocks, 256, 0, s.st>>>(s.count, W->n, W->m, c.n, c.commit, s.d_corr,
+    window_commit_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, W->n, W->m, c.n, c.commit, s.d_corr,
                                                    s.d_status, s.desc.job, W->carry,
                                                    s.desc.corr, s.desc.status);
   else
-    scatter_kernel<<<blocks, 256, 0, s.st>>>(s.count, c.n, s.d_corr, s.d_status, s.desc.corr,
+    scatter_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, c.n, s.d_corr, s.d_status, s.desc.corr,
                                              s.desc.status);
   return cuda_rc(cudaGetLastError());
 }
@@ -263,8 +278,10 @@ int enqueue_pipeline(Code& c, Slot& s, int max_batch) {
 // Launches one batch of code c on slot s (scheduler thread): one graph launch.
 int launch_batch(lsd_server* sv, Code& c, Slot& s) {
   const int b = (int)s.reqs.size();
+  const int64_t t_launch = now_ns();
   for (int k = 0; k < b; ++k) {
-    const Request& r = s.reqs[k];
+    Request& r = s.reqs[k];
+    r.launch_ns = t_launch;
     s.desc.syn[k] = r.syn;
     s.desc.corr[k] = r.corr;
     s.desc.status[k] = r.status;
@@ -273,7 +290,8 @@ int launch_batch(lsd_server* sv, Code& c, Slot& s) {
     s.desc.job[3 * k + 2] = r.half;
   }
   *s.count = b;
-  cudaError_t e;
+  cudaError_t e = cudaEventRecord(s.start, s.st);
+  if (e != cudaSuccess) return cuda_rc(e);
   if (s.graph) {
     e = cudaGraphLaunch(s.graph, s.st);
     if (e != cudaSuccess) return cuda_rc(e);
@@ -282,6 +300,7 @@ int launch_batch(lsd_server* sv, Code& c, Slot& s) {
     if (rc) return rc;
   }
   e = cudaEventRecord(s.done, s.st);
+  s.launch_call_ns = now_ns() - t_launch;
   return cuda_rc(e);
 }
 
@@ -310,12 +329,21 @@ void scheduler(lsd_server* sv) {
       for (auto& s : c.slots) {
         if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
         const int64_t t = now_ns();
+        float gpu_ms = 0.f;
+        if (cudaEventElapsedTime(&gpu_ms, s.start, s.done) != cudaSuccess) cudaGetLastError();
         {
           std::lock_guard<std::mutex> lk(sv->mu);
           Stats& cs = sv->rep.by_code[c.user];
+          cs.batch_gpu_ns.push_back((int64_t)(gpu_ms * 1e6));
+          cs.launch_call_ns.push_back(s.launch_call_ns);
+          cs.batches++;
+          cs.batched += (int64_t)s.reqs.size();
           for (auto& r : s.reqs) {
             sv->rep.latency_ns.push_back(t - r.arrival_ns);
             cs.latency_ns.push_back(t - r.arrival_ns);
+            cs.lag_ns.push_back(r.enqueue_ns - r.arrival_ns);
+            cs.queue_ns.push_back(r.launch_ns - r.enqueue_ns);
+            cs.service_ns.push_back(t - r.launch_ns);
             if (c.win) window_done(sv, *c.win, r);
           }
           sv->rep.completed += (int64_t)s.reqs.size();
@@ -402,9 +430,12 @@ void enqueue(lsd_server* sv, const Request* r, size_t count) {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->rep.submitted == 0) sv->rep.first_arrival = r[0].arrival_ns;
     sv->rep.submitted += (int64_t)count;
+    const int64_t t = now_ns();
     for (size_t k = 0; k < count; ++k) {
       sv->rep.by_code[sv->codes[r[k].code].user].submitted++;
-      push_pending(sv->codes[r[k].code], r[k]);
+      Request q = r[k];
+      q.enqueue_ns = t;
+      push_pending(sv->codes[q.code], q);
     }
   }
   sv->cv_work.notify_one();
@@ -427,7 +458,8 @@ int submit_round_locked(lsd_server* sv, int user, WindowCode& W, int stream,
   const int t = S.t_next;
   const bool final = t == W.t_final;
   if (b != (final ? W.d : t + W.w - 1)) return LSD_OK;
-  Request r{final ? W.fin : W.inner, nullptr, corr, status, arrival, id, stream, t, half};
+  Request r{final ? W.fin : W.inner, nullptr, corr, status, arrival, id, stream, t, half,
+            now_ns()};
   if (first_round) *first_round = t;
   if (rounds) *rounds = final ? W.d - t : W.c;
   S.outstanding[half]++;
@@ -465,8 +497,10 @@ void free_server(lsd_server* sv) {
       if (s.desc.status) cudaFreeHost(s.desc.status);
       if (s.desc.job) cudaFreeHost(s.desc.job);
       if (s.count) cudaFreeHost(s.count);
+      if (s.d_count) cudaFree(s.d_count);
       if (s.graph) cudaGraphExecDestroy(s.graph);
       if (s.done) cudaEventDestroy(s.done);
+      if (s.start) cudaEventDestroy(s.start);
       if (s.st) cudaStreamDestroy(s.st);
     }
   for (auto& W : sv->wins) {
@@ -482,6 +516,19 @@ int64_t percentile(std::vector<int64_t>& v, double q) {
   const size_t k = (size_t)(q * (double)(v.size() - 1) + 0.5);
   std::nth_element(v.begin(), v.begin() + k, v.end());
   return v[k];
+}
+
+// p99 of the latency parts of the given codes' requests.
+void fill_parts(const std::vector<const Stats*>& codes, lsd_server_report* out) {
+  std::vector<int64_t> lag, queue, service;
+  for (const Stats* st : codes) {
+    lag.insert(lag.end(), st->lag_ns.begin(), st->lag_ns.end());
+    queue.insert(queue.end(), st->queue_ns.begin(), st->queue_ns.end());
+    service.insert(service.end(), st->service_ns.begin(), st->service_ns.end());
+  }
+  out->p99_lag_us = (double)percentile(lag, 0.99) * 1e-3;
+  out->p99_queue_us = (double)percentile(queue, 0.99) * 1e-3;
+  out->p99_service_us = (double)percentile(service, 0.99) * 1e-3;
 }
 
 void fill_latency(std::vector<int64_t> v, lsd_server_report* out) {
@@ -510,7 +557,8 @@ int make_slots(lsd_server* sv, Code& c, MakeDec&& make_dec) {
   const size_t B = (size_t)o.max_batch;
   for (auto& s : c.slots) {
     cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.done);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.start);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_syn, B * c.m);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_corr, B * c.n);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_status, B);
@@ -519,6 +567,7 @@ int make_slots(lsd_server* sv, Code& c, MakeDec&& make_dec) {
     if (e == cudaSuccess) e = cudaHostAlloc(&s.desc.status, B * sizeof(void*), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostAlloc(&s.desc.job, B * 3 * sizeof(int32_t), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostAlloc(&s.count, sizeof(long long), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(long long));
     if (e != cudaSuccess) return cuda_rc(e);
     lsd_options dopt{};
     dopt.stream = s.st;
@@ -718,6 +767,11 @@ int lsd_server_get_report(lsd_server* sv, lsd_server_report* out, int32_t reset)
   out->seconds = r.completed ? (double)(r.last_completion - r.first_arrival) * 1e-9 : 0.0;
   out->shots_per_s = out->seconds > 0 ? (double)r.completed / out->seconds : 0.0;
   fill_latency(r.latency_ns, out);
+  {
+    std::vector<const Stats*> all;
+    for (const Stats& st : r.by_code) all.push_back(&st);
+    fill_parts(all, out);
+  }
   if (reset) {
     const size_t nc = r.by_code.size();
     r = Report{};
@@ -738,6 +792,15 @@ int lsd_server_get_code_report(lsd_server* sv, int32_t code, lsd_server_report* 
   out->seconds = r.completed ? (double)(r.last_completion - r.first_arrival) * 1e-9 : 0.0;
   out->shots_per_s = out->seconds > 0 ? (double)s.completed / out->seconds : 0.0;
   fill_latency(s.latency_ns, out);
+  fill_parts({&s}, out);
+  {
+    std::vector<int64_t> g = s.batch_gpu_ns;
+    out->p99_batch_gpu_us = (double)percentile(g, 0.99) * 1e-3;
+    std::vector<int64_t> lc = s.launch_call_ns;
+    out->p99_launch_call_us = (double)percentile(lc, 0.99) * 1e-3;
+    out->batches = s.batches;
+    out->mean_batch = s.batches ? (double)s.batched / (double)s.batches : 0.0;
+  }
   return sv->error;
 }
 
@@ -764,14 +827,8 @@ int lsd_server_run_poisson(lsd_server* sv, double rate, double seconds, const do
   std::uniform_real_distribution<double> uni(0.0, acc);
   std::vector<int64_t> cursor(nc, 0);
   // window codes: arrivals go to the streams in turn; stream s plays the pool's sequences
-  // s, s + S, s + 2S, ... block by block (the generator's own copy of each stream's place)
-  std::vector<std::vector<int64_t>> seq_of(sv->wins.size()), block_of(sv->wins.size());
-  for (size_t k = 0; k < sv->wins.size(); ++k) {
-    const size_t S = sv->wins[k].streams.size();
-    seq_of[k].resize(S);
-    block_of[k].assign(S, 0);
-    for (size_t s = 0; s < S; ++s) seq_of[k][s] = (int64_t)s;
-  }
+  // s, s + S, s + 2S, ... block by block, continuing from the stream's place in the server
+  // (its sequence count and next block), so that successive runs extend the same sequences
   std::vector<Request> burst;
   burst.reserve(4096);
   const int64_t t0 = now_ns();
@@ -799,19 +856,17 @@ int lsd_server_run_poisson(lsd_server* sv, double rate, double seconds, const do
           const int k = c - sv->n_shot;
           WindowCode& W = sv->wins[k];
           const int s = (int)(cursor[c]++ % (int64_t)W.streams.size());
-          const size_t row = (size_t)(seq_of[k][s] % pool_sizes[c]);
-          const uint8_t* blk = pools[c] + (row * (W.d + 1) + (size_t)block_of[k][s]) * W.m;
           bool formed = false;
           if (!lk.owns_lock()) lk.lock();
           ++blocks_held;
+          const Stream& S = W.streams[s];
+          const size_t row = (size_t)(((int64_t)s + (int64_t)S.seq * (int64_t)W.streams.size()) %
+                                      pool_sizes[c]);
+          const uint8_t* blk = pools[c] + (row * (W.d + 1) + (size_t)S.next_block) * W.m;
           const int rc = submit_round_locked(sv, c, W, s, blk, nullptr, nullptr,
                                              (int64_t)t_next, sv->next_id++, nullptr, nullptr,
                                              &formed);
           if (rc == LSD_OK) {
-            if (++block_of[k][s] > W.d) {
-              block_of[k][s] = 0;
-              seq_of[k][s] += (int64_t)W.streams.size();
-            }
             ++generated;
             woke = woke || formed;
           } else {

@@ -744,7 +744,10 @@ class ServerReport(C.Structure):
                 ("admission_waits", C.c_int64), ("peak_inflight_bytes", C.c_int64),
                 ("generated", C.c_int64), ("mean_batch", C.c_double), ("seconds", C.c_double),
                 ("shots_per_s", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double),
-                ("mean_us", C.c_double), ("max_us", C.c_double), ("offered_rate", C.c_double)]
+                ("mean_us", C.c_double), ("max_us", C.c_double), ("offered_rate", C.c_double),
+                ("p99_lag_us", C.c_double), ("p99_queue_us", C.c_double),
+                ("p99_service_us", C.c_double), ("p99_batch_gpu_us", C.c_double),
+                ("p99_launch_call_us", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
