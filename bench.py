@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one 10^6-shot BP launch on this workload (BB144, p = 0.05,
 # 50 iterations), per kernel variant, from a one-pass ncu capture of the full workload;
 # a variant without a capture reports traffic null.
-BP_TRAFFIC_BYTES = {"bp_reg_kernel<32,3,6,5,3>": 76266752 + 152703744}
+BP_TRAFFIC_BYTES = {"bp_reg_kernel<32,3,6,5,3>": 75725312 + 152473088}
 
 
 def parse():
