@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) bp_reg_kernel(BPArgs a) {
     if (a.queue) {
       if (conv) {
         if constexpr (PK) {
-          write_packed_decision(a.corrections, shot, n, Lam, lane, G);
+          group_packed_decision<G, VPL>(a.corrections, shot, n, Lam, lane, gmask);
         } else {
           uint8_t* co = a.corrections + shot * n;
 #pragma unroll
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(NT, MINB) bp_regcta_kernel(BPArgs a) {
     if (a.queue) {
       if (conv) {
         if constexpr (PK) {
-          write_packed_decision(a.corrections, shot, n, Lam, tid, NT);
+          cta_packed_decision<NT, VPL>(a.corrections, shot, n, Lam, tid);
         } else {
           uint8_t* co = a.corrections + shot * n;
 #pragma unroll

@@ -893,7 +893,11 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
   __syncwarp();
   if constexpr (PK) {
     uint32_t* co = reinterpret_cast<uint32_t*>(a.corrections) + shot * packed_words(n);
-    for (int w = lane; w < packed_words(n); w += 32) co[w] = byte_word(cs, n, w);
+    for (int base = 0; base < n; base += 32) {  // one ballot per word
+      const int j = base + lane;
+      const unsigned b = __ballot_sync(kFull, j < n && cs[j] != 0);
+      if (lane == 0) co[base >> 5] = b;
+    }
   } else {
     uint8_t* co = a.corrections + shot * n;
     for (int j = lane; j < n; j += 32) co[j] = cs[j];

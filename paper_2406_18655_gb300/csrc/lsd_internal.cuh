@@ -166,19 +166,55 @@ __device__ __forceinline__ uint32_t sign_word(const float* L, int n, int w) {
   for (int j = j0; j < j1; ++j) x |= (L[j] < 0.f ? 1u : 0u) << (j - j0);
   return x;
 }
-// Word `w` of the packed form of n bytes (0 / 1).
-__device__ __forceinline__ uint32_t byte_word(const uint8_t* b, int n, int w) {
-  uint32_t x = 0;
-  const int j0 = w << 5, j1 = j0 + 32 < n ? j0 + 32 : n;
-  for (int j = j0; j < j1; ++j) x |= (b[j] ? 1u : 0u) << (j - j0);
-  return x;
-}
 // The hard decision of a converged shot as packed words, `nt` threads from `t` (out of line:
 // the byte path of the BP kernels keeps its own register allocation).
 static __device__ __noinline__ void write_packed_decision(uint8_t* corrections, long long shot, int n,
                                                    const float* Lam, int t, int nt) {
   uint32_t* co = reinterpret_cast<uint32_t*>(corrections) + shot * packed_words(n);
   for (int w = t; w < packed_words(n); w += nt) co[w] = sign_word(Lam, n, w);
+}
+// G flags of a group of G lanes (G = 8, 16 or 32, aligned within its warp, every lane of the
+// group present) as the low G bits of one word, lane 0's flag in bit 0.
+template <int G>
+__device__ __forceinline__ uint32_t group_bits(bool b, unsigned gmask) {
+  const unsigned x = __ballot_sync(gmask, b);
+  if constexpr (G == 32) {
+    return x;
+  } else {
+    return (x >> ((threadIdx.x & 31) & ~(G - 1))) & ((1u << G) - 1u);
+  }
+}
+// The hard decision [Lam_j < 0] of a converged shot as packed words, written by a group of G
+// lanes in which lane `lane` owns the variables lane + G v (v < VPL, G VPL >= n): one ballot
+// per G variables, lane 0 stores each finished word.
+template <int G, int VPL>
+__device__ __forceinline__ void group_packed_decision(uint8_t* corrections, long long shot, int n,
+                                                      const float* Lam, int lane, unsigned gmask) {
+  uint32_t* co = reinterpret_cast<uint32_t*>(corrections) + shot * packed_words(n);
+  uint32_t word = 0;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int j = lane + G * v;
+    word |= group_bits<G>(j < n && Lam[j] < 0.f, gmask) << ((G * v) & 31);
+    if (((G * (v + 1)) & 31) == 0 || v == VPL - 1) {
+      if (lane == 0 && ((G * v) & ~31) < n) co[(G * v) >> 5] = word;
+      word = 0;
+    }
+  }
+}
+// The same for a CTA of NT threads (whole warps) in which thread `tid` owns the variables
+// tid + NT v: the 32 variables of a warp's ballot are exactly one word.
+template <int NT, int VPL>
+__device__ __forceinline__ void cta_packed_decision(uint8_t* corrections, long long shot, int n,
+                                                    const float* Lam, int tid) {
+  static_assert(NT % 32 == 0, "whole warps");
+  uint32_t* co = reinterpret_cast<uint32_t*>(corrections) + shot * packed_words(n);
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int j = tid + NT * v;
+    const unsigned b = __ballot_sync(0xffffffffu, j < n && Lam[j] < 0.f);
+    if ((tid & 31) == 0 && j < n) co[j >> 5] = b;
+  }
 }
 // The hard decision of a converged shot: bytes or packed words, `nt` threads from `t`.
 __device__ __forceinline__ void write_hard_decision(uint8_t* corrections, int packed,
