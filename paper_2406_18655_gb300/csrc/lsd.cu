@@ -100,8 +100,46 @@ struct Graph {
   const uint16_t* chk_var;
   const int32_t* var_ptr;
   const uint16_t* var_chk;
-  int max_col_deg;
+  int max_col_deg, max_row_deg;
+  // lanes over (pick, detector slot) pairs in the union of a growth step: lane = pl * D + ps
+  // for the largest column degree D <= 32 (ppass = 32 / D picks per pass, one slot pass);
+  // beyond 32, one pick per pass and dslots = D slots in passes of 32
+  int pl, ps, ppass, dslots;
+  // the same over (new detector, edge slot) pairs with the largest row degree: lane =
+  // dl * D + de, dpass detectors per pass, edges de, de + estep, ... of each
+  int dl, de, dpass, estep;
+  // log2 of the column degree rounded up to a power of two (column gathers of add_column)
+  int gshift;
 };
+
+__device__ __forceinline__ void set_lanes(Graph& G, int lane) {
+  const int D = max(G.max_col_deg, 1);
+  if (D <= 32) {
+    G.pl = lane / D;
+    G.ps = lane - G.pl * D;
+    G.ppass = 32 / D;
+    G.dslots = 1;
+  } else {
+    G.pl = 0;
+    G.ps = lane;
+    G.ppass = 1;
+    G.dslots = D;
+  }
+  G.gshift = 0;
+  while ((1 << G.gshift) < D) ++G.gshift;
+  const int Dr = max(G.max_row_deg, 1);
+  if (Dr <= 32) {
+    G.dl = lane / Dr;
+    G.de = lane - G.dl * Dr;
+    G.dpass = 32 / Dr;
+    G.estep = Dr;
+  } else {
+    G.dl = 0;
+    G.de = lane;
+    G.dpass = 1;
+    G.estep = 32;
+  }
+}
 
 // Accessors of one warp's shot state: one base pointer plus compile-time offsets.
 template <class L>
@@ -259,7 +297,29 @@ __device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int 
   constexpr int W = L::W;
   const int gcol = S.fat()[rk];
   uint32_t bw = 0, tw = 0;
-  if (lane < W) {
+  if ((W << G.gshift) <= 32) {
+    // lane (word wd, detector slot sl) reads one detector's contribution to one word; the
+    // 2^gshift slots of a word are XOR-reduced with shuffles and word w lands on lane w
+    const int wd = lane >> G.gshift, sl = lane & ((1 << G.gshift) - 1);
+    if (wd < W) {
+      const int q = G.var_ptr[gcol] + sl;
+      if (q < G.var_ptr[gcol + 1]) {
+        const int d = G.var_chk[q];
+        if ((d >> 5) == wd) bw = 1u << (d & 31);
+        if (S.pcol()[d] >= 0) {
+          bw ^= S.R()[d * W + wd];
+          tw = S.T()[d * W + wd];
+        }
+      }
+    }
+    for (int off = 1; off < (1 << G.gshift); off <<= 1) {
+      bw ^= __shfl_xor_sync(kFull, bw, off);
+      tw ^= __shfl_xor_sync(kFull, tw, off);
+    }
+    bw = __shfl_sync(kFull, bw, (lane << G.gshift) & 31);
+    tw = __shfl_sync(kFull, tw, (lane << G.gshift) & 31);
+    if (lane >= W) bw = tw = 0;
+  } else if (lane < W) {
     const int v1 = G.var_ptr[gcol + 1];
     for (int q = G.var_ptr[gcol]; q < v1; ++q) {
       const int d = G.var_chk[q];
@@ -391,19 +451,28 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     const unsigned bf = __ballot_sync(kFull, fresh);
     if (fresh) S.newr()[n_new + __popc(bf & below)] = (uint16_t)rk;
     n_new += __popc(bf);
-    for (int qq = 0; qq < G.max_col_deg; ++qq) {
-      const int q = q0 + qq;
-      int d = 0;
-      bool claim = false;
-      if (q < q1) {
-        d = G.var_chk[q];
-        const int o = atomicCAS(&S.dlab()[d], -1, r);
-        claim = o == -1;
-        if (!claim && o != r) uf_unite(S, r, o);
+    // the picks' detectors: lane (pick pl, slot ps) claims detector ps of pick tb + pl, so a
+    // pass covers ppass picks (the pick's owner lane passes its cluster and column range)
+    const int cnt = min(32, k - base);
+    for (int tb = 0; tb < cnt; tb += G.ppass) {
+      const int src = tb + G.pl;
+      const int rs = __shfl_sync(kFull, r, src & 31);
+      const int qs0 = __shfl_sync(kFull, q0, src & 31);
+      const int qs1 = __shfl_sync(kFull, q1, src & 31);
+      for (int so = 0; so < G.dslots; so += 32) {
+        const int q = qs0 + G.ps + so;
+        int d = 0;
+        bool claim = false;
+        if (G.pl < G.ppass && src < cnt && q < qs1) {
+          d = G.var_chk[q];
+          const int o = atomicCAS(&S.dlab()[d], -1, rs);
+          claim = o == -1;
+          if (!claim && o != rs) uf_unite(S, rs, o);
+        }
+        const unsigned bd = __ballot_sync(kFull, claim);
+        if (claim) S.dnew()[n_det + __popc(bd & below)] = (uint16_t)d;
+        n_det += __popc(bd);
       }
-      const unsigned bd = __ballot_sync(kFull, claim);
-      if (claim) S.dnew()[n_det + __popc(bd & below)] = (uint16_t)d;
-      n_det += __popc(bd);
     }
   }
   __syncwarp();
@@ -427,15 +496,19 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
       const uint32_t v = S.cand()[(size_t)x * Wn + w];
       if (v) atomicOr(&S.cand()[(size_t)S.parent()[x] * Wn + w], v);
     }
-    for (int t = lane; t < nd; t += 32) {
-      const int d = S.dnew()[t];
-      uint32_t* c = S.cand() + (size_t)S.dlab()[d] * Wn;
-      const int c1 = G.chk_ptr[d + 1];
-      for (int e = G.chk_ptr[d]; e < c1; ++e) {
-        const int f = G.chk_var[e];
-        if (S.flab()[f] < 0) {
-          const unsigned rk = S.rank()[f];
-          atomicOr(&c[rk >> 5], 1u << (rk & 31));
+    // lanes over (new detector, edge slot) pairs
+    for (int tb = 0; tb < nd; tb += G.dpass) {
+      const int t = tb + G.dl;
+      if (G.dl < G.dpass && t < nd) {
+        const int d = S.dnew()[t];
+        uint32_t* c = S.cand() + (size_t)S.dlab()[d] * Wn;
+        const int c1 = G.chk_ptr[d + 1];
+        for (int e = G.chk_ptr[d] + G.de; e < c1; e += G.estep) {
+          const int f = G.chk_var[e];
+          if (S.flab()[f] < 0) {
+            const unsigned rk = S.rank()[f];
+            atomicOr(&c[rk >> 5], 1u << (rk & 31));
+          }
         }
       }
     }
@@ -450,6 +523,15 @@ __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, b
     __syncwarp();
   }
   // ---- the step's new columns in reliability (rank) order ----
+  if (n_new <= 32) {  // lane t holds new column t; the warp minimum is taken n_new times
+    unsigned kt = lane < n_new ? (unsigned)S.newr()[lane] : kNone;
+    for (int t = 0; t < n_new; ++t) {
+      const unsigned v = __reduce_min_sync(kFull, kt);
+      if (kt == v) kt = kNone;
+      add_column<L, MU>(G, S, m, (int)v, lane);
+    }
+    return 0;
+  }
   for (int t = lane; t < n_new; t += 32) {
     const unsigned kt = S.newr()[t];
     int pos = 0;
@@ -949,6 +1031,8 @@ __global__ void __launch_bounds__(256, MU ? 3 : 4) lsd_kernel(LSDArgs a, int gra
     G.var_chk = a.g.var_chk;
     G.max_col_deg = a.g.max_col_deg;
   }
+  G.max_row_deg = a.g.max_row_deg;
+  set_lanes(G, lane);
   Shot<L> S{smem + (size_t)warp * L::total};
 
   const long long count = a.count_from_ctr ? (long long)a.ctr->lsd_count : a.count;
