@@ -293,17 +293,17 @@ __device__ int collect_roots(const LSDArgs& a, const Shot<L>& S, int m, bool onl
 
 // Adds the fault of rank `rk` to its cluster's factorization.
 template <class L, bool MU>
-__device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int lane) {
+__device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int gcol, int q0,
+                           int q1, int lane) {
   constexpr int W = L::W;
-  const int gcol = S.fat()[rk];
   uint32_t bw = 0, tw = 0;
   if ((W << G.gshift) <= 32) {
     // lane (word wd, detector slot sl) reads one detector's contribution to one word; the
     // 2^gshift slots of a word are XOR-reduced with shuffles and word w lands on lane w
     const int wd = lane >> G.gshift, sl = lane & ((1 << G.gshift) - 1);
     if (wd < W) {
-      const int q = G.var_ptr[gcol] + sl;
-      if (q < G.var_ptr[gcol + 1]) {
+      const int q = q0 + sl;
+      if (q < q1) {
         const int d = G.var_chk[q];
         if ((d >> 5) == wd) bw = 1u << (d & 31);
         if (S.pcol()[d] >= 0) {
@@ -320,8 +320,7 @@ __device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int 
     tw = __shfl_sync(kFull, tw, (lane << G.gshift) & 31);
     if (lane >= W) bw = tw = 0;
   } else if (lane < W) {
-    const int v1 = G.var_ptr[gcol + 1];
-    for (int q = G.var_ptr[gcol]; q < v1; ++q) {
+    for (int q = q0; q < q1; ++q) {
       const int d = G.var_chk[q];
       if ((d >> 5) == lane) bw ^= 1u << (d & 31);
       if (S.pcol()[d] >= 0) {
@@ -358,13 +357,41 @@ __device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int 
   }
   if (lane == 0) S.pcol()[p] = (int16_t)gcol;
   __syncwarp();
-  for (int d = lane; d < m; d += 32) {
-    if (d == p || S.pcol()[d] < 0) continue;
-    if (S.R()[d * W + pw] & pb) {
+  if constexpr (W <= 4) {
+    // back-elimination with the new pivot's words taken from the lanes that hold them and
+    // every row's test issued before the row updates
+    uint32_t rp[W], tp[W];
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        S.R()[d * W + w] ^= S.R()[p * W + w];
-        S.T()[d * W + w] ^= S.T()[p * W + w];
+    for (int w = 0; w < W; ++w) {
+      rp[w] = __shfl_sync(kFull, bw, w);
+      tp[w] = __shfl_sync(kFull, tw, w);
+    }
+    bool hit[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int d = lane + 32 * i;
+      hit[i] = d < m && d != p && S.pcol()[d] >= 0 && (S.R()[d * W + pw] & pb) != 0;
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      if (hit[i]) {
+        const int d = lane + 32 * i;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          S.R()[d * W + w] ^= rp[w];
+          S.T()[d * W + w] ^= tp[w];
+        }
+      }
+    }
+  } else {
+    for (int d = lane; d < m; d += 32) {
+      if (d == p || S.pcol()[d] < 0) continue;
+      if (S.R()[d * W + pw] & pb) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          S.R()[d * W + w] ^= S.R()[p * W + w];
+          S.T()[d * W + w] ^= S.T()[p * W + w];
+        }
       }
     }
   }
@@ -375,12 +402,147 @@ __device__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk, int 
   __syncwarp();
 }
 
+// add_column for the fault of rank rk (its column and CSC range read from shared memory).
+template <class L, bool MU>
+__device__ __forceinline__ void add_column(const Graph& G, const Shot<L>& S, int m, int rk,
+                                           int lane) {
+  const int gcol = S.fat()[rk];
+  add_column<L, MU>(G, S, m, rk, gcol, G.var_ptr[gcol], G.var_ptr[gcol + 1], lane);
+}
+
+// The growth step of lsd_step when the clusters' candidate masks are kept and at most 32
+// clusters grow: lane t carries cluster inv[t]'s pick (rank, fault, CSC range) from the
+// search through the union to the column order, instead of passing it through shared memory.
+// Same result as the general step: the merges, claims and mask updates commute.
+template <class L, bool MU>
+__device__ int lsd_step_small(const Graph& G, const Shot<L>& S, int m, int k, bool strict,
+                              int lane) {
+  constexpr int Wn = L::Wn;
+  // ---- find_candidate: the lowest set bit of the cluster's mask ----
+  int r = 0;
+  unsigned pick = kNone;
+  if (lane < k) {
+    r = S.inv()[lane];
+    const uint32_t* c = S.cand() + (size_t)r * Wn;
+    if constexpr (Wn <= 8) {
+      uint32_t v[Wn];
+#pragma unroll
+      for (int w = 0; w < Wn; ++w) v[w] = c[w];
+#pragma unroll
+      for (int w = Wn - 1; w >= 0; --w)
+        if (v[w]) pick = (unsigned)(w * 32 + __ffs(v[w]) - 1);
+    } else {
+      for (int w = 0; w < Wn; ++w) {
+        const uint32_t v = c[w];
+        if (v) {
+          pick = (unsigned)(w * 32 + __ffs(v) - 1);
+          break;
+        }
+      }
+    }
+  }
+  const bool has = pick != kNone;
+  const unsigned hb = __ballot_sync(kFull, has);
+  const unsigned all = k == 32 ? kFull : ((1u << k) - 1u);
+  const bool none = hb != all;
+  if ((strict && none) || hb == 0) return (strict && none) ? 1 : 2;
+  if (lane == 0) S.scal()[3] = 0;  // merged labels
+  __syncwarp();
+  // ---- parallel_union ----
+  const unsigned below = (1u << lane) - 1u;
+  int gcol = 0, q0 = 0, q1 = 0;
+  bool fresh = false;
+  if (has) {
+    gcol = S.fat()[pick];
+    const int old = atomicCAS(&S.flab()[gcol], -1, r);
+    fresh = old == -1;
+    if (!fresh) uf_unite(S, r, old);
+    q0 = G.var_ptr[gcol];
+    q1 = G.var_ptr[gcol + 1];
+  }
+  const unsigned bf = __ballot_sync(kFull, fresh);
+  const int n_new = __popc(bf);
+  int n_det = 0;
+  for (int tb = 0; tb < k; tb += G.ppass) {
+    const int src = tb + G.pl;
+    const int rs = __shfl_sync(kFull, r, src & 31);
+    const int qs0 = __shfl_sync(kFull, q0, src & 31);
+    const int qs1 = __shfl_sync(kFull, q1, src & 31);
+    for (int so = 0; so < G.dslots; so += 32) {
+      const int q = qs0 + G.ps + so;
+      int d = 0;
+      bool claim = false;
+      if (G.pl < G.ppass && src < k && q < qs1) {
+        d = G.var_chk[q];
+        const int o = atomicCAS(&S.dlab()[d], -1, rs);
+        claim = o == -1;
+        if (!claim && o != rs) uf_unite(S, rs, o);
+      }
+      const unsigned bd = __ballot_sync(kFull, claim);
+      if (claim) S.dnew()[n_det + __popc(bd & below)] = (uint16_t)d;
+      n_det += __popc(bd);
+    }
+  }
+  __syncwarp();
+  // ---- flatten labels to roots; only after a merge ----
+  const int merged = S.scal()[3];
+  if (merged) {
+    for (int x = lane; x < m; x += 32) {
+      const int root = uf_find(S.parent(), x);
+      S.parent()[x] = root;
+      const int l = S.dlab()[x];
+      if (l >= 0) S.dlab()[x] = uf_find(S.parent(), l);
+    }
+    __syncwarp();
+  }
+  // ---- masks: fold merged labels into their roots, add the new detectors' free faults ----
+  for (int idx = lane; idx < merged * Wn; idx += 32) {
+    const int x = S.mlist()[idx / Wn], w = idx % Wn;
+    const uint32_t v = S.cand()[(size_t)x * Wn + w];
+    if (v) atomicOr(&S.cand()[(size_t)S.parent()[x] * Wn + w], v);
+  }
+  for (int tb = 0; tb < n_det; tb += G.dpass) {
+    const int t = tb + G.dl;
+    if (G.dl < G.dpass && t < n_det) {
+      const int d = S.dnew()[t];
+      uint32_t* c = S.cand() + (size_t)S.dlab()[d] * Wn;
+      const int c1 = G.chk_ptr[d + 1];
+      for (int e = G.chk_ptr[d] + G.de; e < c1; e += G.estep) {
+        const int f = G.chk_var[e];
+        if (S.flab()[f] < 0) {
+          const unsigned rk = S.rank()[f];
+          atomicOr(&c[rk >> 5], 1u << (rk & 31));
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // the step's new faults are no longer candidates (a fresh pick's fault carries label r)
+  if (fresh) {
+    const int root = S.parent()[r];
+    atomicAnd(&S.cand()[(size_t)root * Wn + (pick >> 5)], ~(1u << (pick & 31)));
+  }
+  __syncwarp();
+  // ---- the new columns in rank order: the warp minimum of the fresh picks, n_new times ----
+  unsigned kt = fresh ? pick : kNone;
+  for (int t = 0; t < n_new; ++t) {
+    const unsigned v = __reduce_min_sync(kFull, kt);
+    const int src = __ffs(__ballot_sync(kFull, kt == v)) - 1;
+    if (kt == v) kt = kNone;
+    add_column<L, MU>(G, S, m, (int)v, __shfl_sync(kFull, gcol, src),
+                      __shfl_sync(kFull, q0, src), __shfl_sync(kFull, q1, src), lane);
+  }
+  return 0;
+}
+
 // One synchronous growth step of the k clusters listed in inv[].
 // Returns 0 if clusters grew, 1 if strict and a cluster had no candidate, 2 if none grew.
 template <class L, bool MU>
 __device__ int lsd_step(const Graph& G, const Shot<L>& S, int m, int n, int k, bool strict,
                         int lane) {
   constexpr int Wn = L::Wn;
+  if constexpr (L::kMasks)
+    if (k <= 32) return lsd_step_small<L, MU>(G, S, m, k, strict, lane);
   // ---- find_candidate: the lowest-rank candidate of every growing cluster ----
   if constexpr (L::kMasks) {
     for (int t = lane; t < k; t += 32) {
