@@ -257,6 +257,33 @@ __device__ void warp_sort(unsigned long long* keys, int lane) {
 template <class L>
 __device__ int collect_roots(const LSDArgs& a, const Shot<L>& S, int m, bool only_invalid,
                              int lane) {
+  if (only_invalid && L::W <= 4) {
+    // each invalid row marks its root in a bitmask over labels (cm, free until reprocessing);
+    // the roots are then listed in ascending order by ballots, and the mask is cleared
+    uint32_t* msk = S.cm();
+#pragma unroll
+    for (int i = 0; i < L::W; ++i) {
+      const int d = lane + 32 * i;
+      if ((S.sred()[i] >> lane) & 1u) {
+        const int root = S.dlab()[d];
+        if (root >= 0) atomicOr(&msk[root >> 5], 1u << (root & 31));
+      }
+    }
+    __syncwarp();
+    uint32_t mw[L::W];
+#pragma unroll
+    for (int i = 0; i < L::W; ++i) mw[i] = msk[i];
+    __syncwarp();
+    if (lane < L::W) msk[lane] = 0;
+    int count = 0;
+#pragma unroll
+    for (int i = 0; i < L::W; ++i) {
+      if ((mw[i] >> lane) & 1u) S.inv()[count + __popc(mw[i] & ((1u << lane) - 1u))] = (uint16_t)(lane + 32 * i);
+      count += __popc(mw[i]);
+    }
+    __syncwarp();
+    return count;
+  }
   if (only_invalid) {
     if (lane == 0) S.scal()[5] = 0;
     __syncwarp();
@@ -1031,6 +1058,7 @@ __device__ __forceinline__ void lsd_shot(const LSDArgs& a, const Graph& G,
       S.syn()[c] = bv;
       S.sred()[c] = bv;
       S.xsol()[c] = 0;
+      S.cm()[c] = 0;
     }
   }
   if (lane < 8) S.scal()[lane] = 0;
