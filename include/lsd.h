@@ -513,7 +513,8 @@ int lsd_giant_destroy(lsd_giant* dec);
  * matrix of a window code) in flight, each slot a decoder with its own stream; a batch
  * launches as soon as a slot is idle (or, with max_wait_us > 0, once max_batch requests
  * wait or the oldest has waited max_wait_us), and only as many shots as the memory budget
- * still admits.  Request buffers are read and written by the GPU directly: they must be
+ * still admits.  A request completes as soon as its own result is written back: the shots
+ * (window jobs) that BP solves right after BP, the others after their batch's LSD.  Request buffers are read and written by the GPU directly: they must be
  * page-locked host memory (cudaHostAlloc / cudaHostRegister) or device memory, owned by the
  * caller and valid until the request completes.
  * ------------------------------------------------------------------------------------ */

@@ -1225,8 +1225,8 @@ extern "C" int lsd_autotune(lsd_decoder* d, int64_t shots, const uint8_t* syndro
 // Decode with a device-side shot count (graph capture by the serving runtime).  The
 // workspace must already hold max_shots (no allocation may happen during a capture).
 // ---------------------------------------------------------------------------------------
-int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long long* shots_dev,
-                                const uint8_t* syndromes, uint8_t* corrections, uint8_t* status) {
+int lsdgb::bp_batch_counted(lsd_decoder* d, int64_t max_shots, const long long* shots_dev,
+                            const uint8_t* syndromes, uint8_t* corrections, uint8_t* status) {
   if (!d || max_shots <= 0 || !shots_dev || !syndromes || !corrections) return LSD_ERR_INVALID_ARG;
   if (!d->lsd_ok) return LSD_ERR_UNSUPPORTED;
   if ((size_t)max_shots > d->cap_shots) return LSD_ERR_ADMISSION;
@@ -1242,6 +1242,12 @@ int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long lo
   cudaError_t e = launch_bp(a, d->bp_variant, d->bp_grid, d->bp_block, d->bp_smem, d->st);
   d->launches++;
   if (e != cudaSuccess) return cuda_fail(e);
+  return LSD_OK;
+}
+
+int lsdgb::lsd_batch_counted(lsd_decoder* d, int64_t max_shots, const uint8_t* syndromes,
+                             uint8_t* corrections, uint8_t* status) {
+  if (!d || max_shots <= 0 || !syndromes || !corrections) return LSD_ERR_INVALID_ARG;
   LSDArgs l{};
   l.g = d->g;
   l.count_from_ctr = 1;
@@ -1256,4 +1262,10 @@ int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long lo
   l.single_cluster = d->opt.single_cluster;
   l.ctr = d->d_ctr;
   return run_lsd(d, l, max_shots);
+}
+
+int lsdgb::decode_batch_counted(lsd_decoder* d, int64_t max_shots, const long long* shots_dev,
+                                const uint8_t* syndromes, uint8_t* corrections, uint8_t* status) {
+  const int rc = bp_batch_counted(d, max_shots, shots_dev, syndromes, corrections, status);
+  return rc ? rc : lsd_batch_counted(d, max_shots, syndromes, corrections, status);
 }

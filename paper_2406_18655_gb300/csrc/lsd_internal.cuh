@@ -146,6 +146,12 @@ cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float
 // captured CUDA graph serves every batch size up to max_shots (api.cu; used by the server).
 int decode_batch_counted(lsd_decoder* dec, int64_t max_shots, const long long* shots_dev,
                          const uint8_t* syndromes, uint8_t* corrections, uint8_t* status);
+// Its two halves, so that work can be enqueued between them: BP (statuses of the shots BP
+// solves become LSD_SHOT_OK_BP, the others are queued), then LSD on the queued shots.
+int bp_batch_counted(lsd_decoder* dec, int64_t max_shots, const long long* shots_dev,
+                     const uint8_t* syndromes, uint8_t* corrections, uint8_t* status);
+int lsd_batch_counted(lsd_decoder* dec, int64_t max_shots, const uint8_t* syndromes,
+                      uint8_t* corrections, uint8_t* status);
 
 // Bit-packed batch I/O: element i of a row of k elements is bit (i & 31) of 32-bit word
 // i >> 5 of a row of ceil(k/32) words.

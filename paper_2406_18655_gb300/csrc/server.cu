@@ -12,10 +12,13 @@
 // stream, so a batch launches as soon as a slot is idle and the memory budget admits it,
 // while earlier batches are still on the device.  A batch is a list of request pointers
 // written to pinned memory; a gather kernel pulls the syndromes (or a window's blocks) into
-// the slot's device buffer, the decoder runs BP + LSD, and a scatter (commit) kernel writes
-// each correction and status back to its request's buffer.  Each slot's pipeline is
-// captured once as a CUDA graph.  The host does O(1) work per request (O(m) for a block,
-// which it copies into the stream's history).  Completion is detected by polling events.
+// the slot's device buffer, the decoder runs BP, a scatter (commit) kernel writes back the
+// rows BP solved, then LSD runs on the others and a second scatter writes them back.  A
+// request completes when its own row is written back: the shots BP solves do not wait for
+// the rare shot of their batch that needs a long LSD.  Each slot's pipeline is captured
+// once as two CUDA graphs (before and after the event that marks the first write-back).
+// The host does O(1) work per request (O(m) for a block, which it copies into the stream's
+// history).  Completion is detected by polling events.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -50,6 +53,7 @@ struct Request {
   int32_t t = 0, half = 0;
   int64_t enqueue_ns = 0;  // when the server took it (arrival_ns may be a scheduled time)
   int64_t launch_ns = 0;   // when its batch was launched
+  bool done = false;       // completed (a shot BP solved completes before its batch's LSD)
 };
 
 // Per-shot pointers and window-job fields of one batch (pinned host memory, read by the
@@ -88,12 +92,23 @@ __global__ void gather_kernel(const long long* count, int m, const uint8_t* cons
   warp_copy(out + (size_t)w * m, syn[w], m, lane);
 }
 
+// Which rows a scatter (commit) writes: every row, only the rows BP solved (written right
+// after BP, with every row's status also copied to the slot's early flags), or the rest.
+enum { kAllRows = 0, kBpRows = 1, kLsdRows = 2 };
+
+__device__ __forceinline__ bool row_in_phase(int phase, uint8_t st) {
+  return phase == kAllRows || ((st == LSD_SHOT_OK_BP) == (phase == kBpRows));
+}
+
 __global__ void scatter_kernel(const long long* count, int n, const uint8_t* corr,
                                const uint8_t* status, uint8_t* const* corr_out,
-                               uint8_t* const* status_out) {
+                               uint8_t* const* status_out, int phase, uint8_t* early) {
   const int lane = threadIdx.x & 31;
   const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= *count) return;
+  const uint8_t st = status[w];
+  if (phase == kBpRows && lane == 0) early[w] = st;
+  if (!row_in_phase(phase, st)) return;
   if (corr_out[w]) warp_copy(corr_out[w], corr + (size_t)w * n, n, lane);
   if (lane == 0 && status_out[w]) *status_out[w] = status[w];
 }
@@ -123,10 +138,14 @@ __global__ void window_gather_kernel(const long long* count, int m, int bn, int 
 __global__ void window_commit_kernel(const long long* count, int n, int m, int wrow, int commit,
                                      const uint8_t* corr, const uint8_t* status,
                                      const int32_t* job, uint8_t* carry,
-                                     uint8_t* const* corr_out, uint8_t* const* status_out) {
+                                     uint8_t* const* corr_out, uint8_t* const* status_out,
+                                     int phase, uint8_t* early) {
   const int lane = threadIdx.x & 31;
   const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= *count) return;
+  const uint8_t st0 = status[w];
+  if (phase == kBpRows && lane == 0) early[w] = st0;
+  if (!row_in_phase(phase, st0)) return;
   const uint8_t* row = corr + (size_t)w * wrow;
   if (corr_out[w]) warp_copy(corr_out[w], row, commit * (n + m), lane);
   const uint8_t* meas = row + (size_t)(commit - 1) * (n + m) + n;
@@ -140,6 +159,9 @@ struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
   cudaEvent_t start = nullptr;  // recorded before the batch: its GPU time is start -> done
+  cudaEvent_t bp_done = nullptr;  // recorded once the rows BP solved are written back
+  uint8_t* early = nullptr;    // pinned: every row's status after BP (read once bp_done is)
+  bool early_seen = false;     // the batch's BP-solved requests have been completed
   uint8_t* d_syn = nullptr;
   uint8_t* d_corr = nullptr;
   uint8_t* d_status = nullptr;
@@ -147,7 +169,7 @@ struct Slot {
   long long* count = nullptr;  // pinned: shots of the batch, written by the scheduler
   long long* d_count = nullptr;  // device copy, made at the start of every batch and read by
                                  // its kernels (one host read per batch, not one per warp)
-  cudaGraphExec_t graph = nullptr;  // gather -> BP -> LSD -> scatter, captured once
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // the pipeline's two parts, captured once
   std::vector<Request> reqs;   // requests of the batch in flight
   int64_t launch_call_ns = 0;  // host time its launch calls took
   size_t reserved = 0;         // admitted bytes
@@ -249,8 +271,28 @@ bool gpu_accessible(const void* p) {
          a.type == cudaMemoryTypeManaged;
 }
 
-// Enqueues the slot's pipeline for *s.count shots: gather, BP + LSD, scatter (or commit).
-int enqueue_pipeline(Code& c, Slot& s, int max_batch) {
+// The scatter (or commit) of a phase's rows of the slot's batch.
+int write_back(Code& c, Slot& s, int max_batch, int phase) {
+  const int blocks = (max_batch + 7) / 8;
+  WindowCode* W = c.win;
+  if (W)
+    window_commit_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, W->n, W->m, c.n, c.commit, s.d_corr,
+                                                   s.d_status, s.desc.job, W->carry, s.desc.corr,
+                                                   s.desc.status, phase, s.early);
+  else
+    scatter_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, c.n, s.d_corr, s.d_status, s.desc.corr,
+                                             s.desc.status, phase, s.early);
+  return cuda_rc(cudaGetLastError());
+}
+
+// The slot's pipeline for *s.count shots in two parts (one graph each): part 0 = gather,
+// BP and the scatter (or commit) of the rows BP solved; part 1 = LSD and the scatter of the
+// other rows.  The host records bp_done between them.
+int enqueue_part(Code& c, Slot& s, int max_batch, int part) {
+  if (part == 1) {
+    const int rc = lsdgb::lsd_batch_counted(s.dec, max_batch, s.d_syn, s.d_corr, s.d_status);
+    return rc ? rc : write_back(c, s, max_batch, kLsdRows);
+  }
   const int blocks = (max_batch + 7) / 8;
   WindowCode* W = c.win;
   cudaError_t e0 = cudaMemcpyAsync(s.d_count, s.count, sizeof(long long), cudaMemcpyHostToDevice,
@@ -263,16 +305,11 @@ int enqueue_pipeline(Code& c, Slot& s, int max_batch) {
     gather_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, c.m, s.desc.syn, s.d_syn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_rc(e);
-  int rc = lsdgb::decode_batch_counted(s.dec, max_batch, s.d_count, s.d_syn, s.d_corr, s.d_status);
-  if (rc) return rc;
-  if (W)
-    window_commit_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, W->n, W->m, c.n, c.commit, s.d_corr,
-                                                   s.d_status, s.desc.job, W->carry,
-                                                   s.desc.corr, s.desc.status);
-  else
-    scatter_kernel<<<blocks, 256, 0, s.st>>>(s.d_count, c.n, s.d_corr, s.d_status, s.desc.corr,
-                                             s.desc.status);
-  return cuda_rc(cudaGetLastError());
+  // statuses start at 0, so a row that BP leaves unsolved never reads as LSD_SHOT_OK_BP
+  e = cudaMemsetAsync(s.d_status, 0, (size_t)max_batch, s.st);
+  if (e != cudaSuccess) return cuda_rc(e);
+  const int rc = lsdgb::bp_batch_counted(s.dec, max_batch, s.d_count, s.d_syn, s.d_corr, s.d_status);
+  return rc ? rc : write_back(c, s, max_batch, kBpRows);
 }
 
 // Launches one batch of code c on slot s (scheduler thread): one graph launch.
@@ -290,14 +327,21 @@ int launch_batch(lsd_server* sv, Code& c, Slot& s) {
     s.desc.job[3 * k + 2] = r.half;
   }
   *s.count = b;
+  s.early_seen = false;
   cudaError_t e = cudaEventRecord(s.start, s.st);
   if (e != cudaSuccess) return cuda_rc(e);
-  if (s.graph) {
-    e = cudaGraphLaunch(s.graph, s.st);
-    if (e != cudaSuccess) return cuda_rc(e);
-  } else {
-    const int rc = enqueue_pipeline(c, s, sv->opt.max_batch);
-    if (rc) return rc;
+  for (int part = 0; part < 2; ++part) {
+    if (s.graph[part]) {
+      e = cudaGraphLaunch(s.graph[part], s.st);
+      if (e != cudaSuccess) return cuda_rc(e);
+    } else {
+      const int rc = enqueue_part(c, s, sv->opt.max_batch, part);
+      if (rc) return rc;
+    }
+    if (part == 0) {
+      e = cudaEventRecord(s.bp_done, s.st);
+      if (e != cudaSuccess) return cuda_rc(e);
+    }
   }
   e = cudaEventRecord(s.done, s.st);
   s.launch_call_ns = now_ns() - t_launch;
@@ -319,18 +363,55 @@ void window_done(lsd_server* sv, WindowCode& W, const Request& r) {
   }
 }
 
+// Records a request's completion at time t (mu held).
+void complete_request(lsd_server* sv, Code& c, Stats& cs, Request& r, int64_t t) {
+  sv->rep.latency_ns.push_back(t - r.arrival_ns);
+  cs.latency_ns.push_back(t - r.arrival_ns);
+  cs.lag_ns.push_back(r.enqueue_ns - r.arrival_ns);
+  cs.queue_ns.push_back(r.launch_ns - r.enqueue_ns);
+  cs.service_ns.push_back(t - r.launch_ns);
+  if (c.win) window_done(sv, *c.win, r);
+  sv->rep.completed++;
+  cs.completed++;
+  r.done = true;
+}
+
 void scheduler(lsd_server* sv) {
   const int64_t wait_ns = (int64_t)sv->opt.max_wait_us * 1000;
   const size_t budget = sv->opt.mem_budget;
   while (true) {
     bool progressed = false;
     // ---- completions ----
+    // A request whose shot BP solved completes once its batch's first part is done (its row
+    // is written back before bp_done); the others when the whole batch is.
     for (auto& c : sv->codes) {
       for (auto& s : c.slots) {
-        if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
+        if (!s.busy) continue;
+        if (!s.early_seen && cudaEventQuery(s.bp_done) == cudaSuccess) {
+          s.early_seen = true;
+          const int64_t t = now_ns();
+          int64_t k_done = 0;
+          {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            Stats& cs = sv->rep.by_code[c.user];
+            for (size_t k = 0; k < s.reqs.size(); ++k) {
+              if (s.early[k] != LSD_SHOT_OK_BP) continue;
+              complete_request(sv, c, cs, s.reqs[k], t);
+              ++k_done;
+            }
+            if (k_done) sv->rep.last_completion = t;
+          }
+          if (k_done) {
+            sv->outstanding -= k_done;
+            progressed = true;
+            sv->cv_done.notify_all();
+          }
+        }
+        if (cudaEventQuery(s.done) != cudaSuccess) continue;
         const int64_t t = now_ns();
         float gpu_ms = 0.f;
         if (cudaEventElapsedTime(&gpu_ms, s.start, s.done) != cudaSuccess) cudaGetLastError();
+        int64_t k_done = 0;
         {
           std::lock_guard<std::mutex> lk(sv->mu);
           Stats& cs = sv->rep.by_code[c.user];
@@ -339,18 +420,13 @@ void scheduler(lsd_server* sv) {
           cs.batches++;
           cs.batched += (int64_t)s.reqs.size();
           for (auto& r : s.reqs) {
-            sv->rep.latency_ns.push_back(t - r.arrival_ns);
-            cs.latency_ns.push_back(t - r.arrival_ns);
-            cs.lag_ns.push_back(r.enqueue_ns - r.arrival_ns);
-            cs.queue_ns.push_back(r.launch_ns - r.enqueue_ns);
-            cs.service_ns.push_back(t - r.launch_ns);
-            if (c.win) window_done(sv, *c.win, r);
+            if (r.done) continue;
+            complete_request(sv, c, cs, r, t);
+            ++k_done;
           }
-          sv->rep.completed += (int64_t)s.reqs.size();
-          cs.completed += (int64_t)s.reqs.size();
           sv->rep.last_completion = t;
         }
-        sv->outstanding -= (int64_t)s.reqs.size();
+        sv->outstanding -= k_done;
         sv->reserved -= s.reserved;
         s.reserved = 0;
         s.reqs.clear();
@@ -498,9 +574,12 @@ void free_server(lsd_server* sv) {
       if (s.desc.job) cudaFreeHost(s.desc.job);
       if (s.count) cudaFreeHost(s.count);
       if (s.d_count) cudaFree(s.d_count);
-      if (s.graph) cudaGraphExecDestroy(s.graph);
+      for (auto& gx : s.graph)
+        if (gx) cudaGraphExecDestroy(gx);
       if (s.done) cudaEventDestroy(s.done);
       if (s.start) cudaEventDestroy(s.start);
+      if (s.bp_done) cudaEventDestroy(s.bp_done);
+      if (s.early) cudaFreeHost(s.early);
       if (s.st) cudaStreamDestroy(s.st);
     }
   for (auto& W : sv->wins) {
@@ -559,6 +638,8 @@ int make_slots(lsd_server* sv, Code& c, MakeDec&& make_dec) {
     cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&s.done);
     if (e == cudaSuccess) e = cudaEventCreate(&s.start);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.bp_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s.early, B, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_syn, B * c.m);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_corr, B * c.n);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_status, B);
@@ -583,15 +664,15 @@ int make_slots(lsd_server* sv, Code& c, MakeDec&& make_dec) {
       s.desc.status[k] = nullptr;
     }
     std::memset(s.desc.job, 0, B * 3 * sizeof(int32_t));
-    if (o.use_graphs >= 0) {  // every batch is then one graph launch
+    for (int part = 0; part < 2 && o.use_graphs >= 0; ++part) {  // a batch: two graph launches
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const int rc2 = enqueue_pipeline(c, s, o.max_batch);
+        const int rc2 = enqueue_part(c, s, o.max_batch, part);
         e = cudaStreamEndCapture(s.st, &g);
         if (rc2) rc = rc2;
       }
-      if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&s.graph, g, 0);
+      if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&s.graph[part], g, 0);
       if (g) cudaGraphDestroy(g);
       if (!rc && e != cudaSuccess) rc = cuda_rc(e);
       if (rc) return rc;

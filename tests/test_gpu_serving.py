@@ -107,6 +107,28 @@ def test_graphs_equal_plain_launches(L, setup):
     assert (res[0][1] > 0).all()
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_rows_solved_by_bp_and_by_lsd_written_back(L, graphs):
+    """At a noise level where many shots of a batch need LSD, the rows BP solves (written back
+    before the batch's LSD) and the rows LSD solves (written back after it) both equal the
+    direct decode, and every request is reported complete once."""
+    h, p = st_code("bb144", p=0.008)
+    syn = pool(L, h, p, 400, 77)
+    srv = L.Server([(h, p, 30, 0)], slots_per_code=2, max_batch=64, max_wait_us=50,
+                   graphs=graphs)
+    out = torch.zeros((syn.shape[0], h.shape[1]), dtype=torch.uint8).pin_memory()
+    st = torch.zeros(syn.shape[0], dtype=torch.uint8).pin_memory()
+    for k in range(syn.shape[0]):
+        srv.submit(0, syn[k], out[k], st[k])
+    srv.wait_all()
+    rep = srv.report()
+    assert rep["completed"] == rep["submitted"] == syn.shape[0]
+    srv.close()
+    corr, st_d = L.Decoder(h, p, 30).decode(syn.cuda())
+    assert torch.equal(corr.cpu(), out) and torch.equal(st_d.cpu(), st)
+    assert (st == 1).sum() > 0 and (st == 2).sum() > 0, "both write-back phases exercised"
+
+
 def test_admission_by_memory(L, setup):
     codes, pools = setup
     h, p = codes[1]
