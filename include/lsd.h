@@ -85,7 +85,9 @@ typedef struct lsd_options {
                              columns at most 4, as hypergraph products, or whose rows have
                              at most 8 or 17 edges and columns at most 3, as space-time
                              matrices with or without hook faults; shorter rows are
-                             padded) */
+                             padded), 3 = latency: of the CTA-per-shot register shapes that
+                             fit, the one with the most threads (at least one fault per
+                             thread), for small batches such as the server's; else as 0 */
   int32_t lsd_kernel;     /* LSD kernel: 0 = auto, 1 = dense (state indexed by detector and
                              fault, m <= 512, n <= 2048), 2 = sparse (state sized by what a shot
                              touches; any m, n < 65536; no single_cluster) */

@@ -324,7 +324,7 @@ int lsd_create(lsd_decoder** out, int32_t m, int32_t n, int64_t nnz, const int32
   lsd_options o{};
   if (opt) o = *opt;
   if (o.bp_method < 0 || o.bp_method > 1 || !valid_lanes(o.bp_lanes) || o.lsd_warps < 0 ||
-      o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 2 || o.lsd_kernel < 0 ||
+      o.lsd_warps > 16 || o.bp_kernel < 0 || o.bp_kernel > 3 || o.lsd_kernel < 0 ||
       o.lsd_kernel > 2 || o.reserved || o.ms_scaling < 0.f || o.osd_method < 0 ||
       o.osd_method > 1 || o.osd_cs_order < 0 || o.osd_cs_order > kMaxCsOrder ||
       (o.osd_method == 0 && o.osd_cs_order != 0) ||

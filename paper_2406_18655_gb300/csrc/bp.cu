@@ -726,6 +726,10 @@ const RegCtaShape kRegCtaShapes[] = {
     // ... with mid-round hook faults: rows of degree up to 17
     LSD_REGCTA_SHAPE(256, 2, 17, 9, 3, true, 2),  // m <= 512, n <= 2304 (BB144, d = 6)
     LSD_REGCTA_SHAPE(512, 1, 17, 5, 3, true, 1),  // m <= 512, n <= 2560
+    // latency shapes (bp_kernel = 3, small batches): as many threads per shot as a CTA holds
+    LSD_REGCTA_SHAPE(1024, 3, 8, 8, 3, true, 1),  // m <= 3072, n <= 8192 (BB288, d = 18)
+    LSD_REGCTA_SHAPE(1024, 1, 8, 3, 3, true, 1),  // m <= 1024, n <= 3072 (BB144, d = 12)
+    LSD_REGCTA_SHAPE(512, 1, 8, 2, 3, true, 1),   // m <= 512, n <= 1024 (BB72, d = 6)
 };
 #undef LSD_REGCTA_SHAPE
 constexpr int kNumRegCtaShapes = sizeof(kRegCtaShapes) / sizeof(kRegCtaShapes[0]);
@@ -793,7 +797,17 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
       return cudaErrorInvalidValue;
     }
   } else {
-    if (method == 0 && kind != 1) {
+    if (method == 0 && kind == 3) {
+      // latency: the CTA-per-shot shape with the most threads (the first of equal size) among
+      // those with at least one fault per thread
+      for (int i = 0; i < kNumRegCtaShapes; ++i) {
+        const RegCtaShape& sh = kRegCtaShapes[i];
+        if (regcta_fits(sh, g) && g.n >= sh.nt && regcta_smem(sh, g) <= (size_t)max_smem &&
+            (v < 0 || sh.nt > kRegCtaShapes[v - kRegCtaBase].nt))
+          v = kRegCtaBase + i;
+      }
+    }
+    if (v < 0 && method == 0 && kind != 1) {
       // least work per lane first (fewer registers, shorter per-shot latency), then the
       // fewest idle lane slots
       long best_lane = -1, best_slots = -1;
@@ -809,7 +823,7 @@ cudaError_t bp_config(const DevGraph& g, int lanes, int method, int kind, int* v
         }
       }
     }
-    if (v < 0 && method == 0 && kind == 0 && lanes == 0) {
+    if (v < 0 && method == 0 && (kind == 0 || kind == 3) && lanes == 0) {
       // irregular or large graphs: one CTA per shot with register tables when a shape fits
       // and the graph has at least one check per thread (no graph table read per edge, and
       // a shot's latency spread over NT threads instead of one warp group)

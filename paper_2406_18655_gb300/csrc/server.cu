@@ -652,6 +652,7 @@ int make_slots(lsd_server* sv, Code& c, MakeDec&& make_dec) {
     if (e != cudaSuccess) return cuda_rc(e);
     lsd_options dopt{};
     dopt.stream = s.st;
+    dopt.bp_kernel = 3;  // batches are small at low load: the shortest per-shot BP latency
     int rc = make_dec(&s.dec, &dopt);
     if (!rc) rc = cuda_rc(cudaMemsetAsync(s.d_syn, 0, B * c.m, s.st));
     if (!rc) rc = lsd_decode_batch(s.dec, (int64_t)B, s.d_syn, s.d_corr, s.d_status, nullptr, nullptr);

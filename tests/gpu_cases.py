@@ -20,6 +20,8 @@ def code(name):
         h = I.space_time(I.bb72()[0], 6)
     elif name == "st_bb144_d12":
         h = I.space_time(I.bb144()[0], 12)
+    elif name == "st_bb288_d18":
+        h = I.space_time(I.bb288()[0], 18)
     elif name == "rep_boundary":
         # repetition-like code whose first check has degree 1 (min over an empty set in BP)
         n = 12

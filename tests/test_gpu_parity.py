@@ -92,21 +92,23 @@ def _irregular_rows(name):
     return code(name)
 
 
+@pytest.mark.parametrize("kernel", [2, 3])
 @pytest.mark.parametrize("name,p,iters,shots", [
     ("st_bb72_d6", 0.01, 50, 3000), ("st_bb72_d6", 0.04, 30, 2000),
     ("st_bb144_d12", 0.004, 50, 1500), ("hooks_bb144_d6", 0.004, 50, 1500),
     ("hooks_bb72_d3", 0.02, 30, 2000), ("window_bb144_final", 0.01, 30, 2000),
-    ("rep_boundary", 0.1, 20, 2000)])
-def test_register_cta_kernel_on_irregular_rows(L, name, p, iters, shots):
+    ("rep_boundary", 0.1, 20, 2000), ("st_bb288_d18", 0.004, 30, 300)])
+def test_register_cta_kernel_on_irregular_rows(L, kernel, name, p, iters, shots):
     """One CTA per shot with register tables on rows of unequal degree (padded with a dummy
     column that takes part in no minimum and no parity): posteriors, iteration counts and
-    convergence bit-exact, and the decode through the LSD queue equals the oracle's."""
+    convergence bit-exact, and the decode through the LSD queue equals the oracle's.
+    kernel 2: the throughput shapes; 3: the latency shapes (the most threads per shot)."""
     h = _irregular_rows(name)
     assert h.sum(1).min() < h.sum(1).max()
     probs = np.full(h.shape[1], p, np.float32)
     e = I.sample_errors(1300 + shots, shots, probs.astype(np.float64))
     s = I.syndromes(h, e)
-    d = L.Decoder(h, probs, iters, bp_kernel=2)
+    d = L.Decoder(h, probs, iters, bp_kernel=kernel)
     post, conv, it = d.bp(dev(s))
     llr, hard, used, convo = oracle.bp(h, f64(probs), s, iters, precision=1)
     assert np.array_equal(it.cpu().numpy(), used)
