@@ -19,8 +19,12 @@
 // per CTA.  Weights are rounded to BF16, Mv and Mc formed from the rounded factors in FP32
 // and rounded to BF16 once; accumulators, biases and LLRs stay FP32.
 //
-// Layout.  One CTA works on one shot at a time: variable rows 0..n-1 in vt 128-row tiles and
-// check rows 0..m-1 in ct tiles, 64 TMEM columns per tile (vt + ct <= 8).  A round:
+// Layout.  One CTA works on a group of S shots at a time, their node rows stacked: variable
+// row s * n8 + v (n8 = n rounded up to 8, so every shot's rows start a core-matrix row group)
+// in vt 128-row tiles and check row s * m8 + c in ct tiles, 64 TMEM columns per tile
+// (vt + ct <= 8; S is the largest group that fits, at most 8).  The weights are shared by all
+// rows, so one MMA per tile serves the whole group and each barrier and completion wait of a
+// round is paid once per group, not once per shot.  A round:
 //   X2 (all threads, 4 per row, 8 features each): S_v from the A_c rows in shared memory and
 //       the row's own B_v; BF16 S_v into the MMA operand buffer; the LLR update
 //   MMA (one thread): P_v tiles += S tile x Mv^T (M = 128, N = 64, K = 32: two K = 16 steps)
@@ -45,11 +49,14 @@ using prior_params::DIN;
 using prior_params::HD;
 using prior_params::POff;
 
-constexpr int kTcMinWarps = 8, kTcMaxWarps = 10;
+constexpr int kTcMinWarps = 8, kTcMaxWarps = 20;
 constexpr int kTcMaxTiles = 8;  // variable + check tiles: 64 TMEM columns each, 512 in all
+constexpr int kTcMaxGroup = 8;  // shots per CTA group
 
 struct TcArgs {
   int m, n, E, rounds, vt, ct, tmem_cols;
+  int S, n8, m8;            // shots per group; rows per shot, rounded up to 8
+  uint32_t inv_n8, inv_m8;  // ceil(2^32 / n8), ceil(2^32 / m8): row -> shot by one mul.hi
   const int32_t* chk_ptr;
   const uint16_t* chk_var;
   const int32_t* var_ptr;
@@ -74,27 +81,31 @@ struct TcLay {
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline TcLay tc_layout(int m, int n, int E, int vt, int ct) {
+__host__ __device__ inline int up8(int x) { return (x + 7) & ~7; }
+
+// Shared memory of a group of S shots: per-row arrays over S n8 / S m8 rows, the tables once.
+__host__ __device__ inline TcLay tc_layout(int m, int n, int E, int vt, int ct, int S) {
   TcLay L;
   size_t o = 0;
+  const size_t N = (size_t)S * up8(n), M = (size_t)S * up8(m);
   L.mv = o; o += 4096;                                   // Mv: 64 x 32 BF16, K-major
   L.mc = o; o += 4096;                                   // Mc
   // S or T tiles (128 x 32 BF16 each); at set-up, Wv and Wc in FP32 (16 KB)
   L.op = o; o += (size_t)(vt > ct ? (vt > 2 ? vt : 2) : (ct > 2 ? ct : 2)) * 8192;
-  L.as = o; o += al((size_t)m * 64, 128);                // BF16 rows [m][32] (swizzled)
-  L.ds = o; o += al((size_t)m * 64, 128);
-  L.cs = o; o += al((size_t)n * 64, 128);
-  L.bs = o; o += al((size_t)n * 64, 128);                // at set-up, with cs: h_v^0 [n][32] FP32
+  L.as = o; o += al(M * 64, 128);                        // BF16 rows [S m8][32] (swizzled)
+  L.ds = o; o += al(M * 64, 128);
+  L.cs = o; o += al(N * 64, 128);
+  L.bs = o; o += al(N * 64, 128);                        // at set-up, with cs: h_v^0 [n][32] FP32
   L.p0 = o; o += (size_t)n * 256;                        // FP32 [64][n] (column-major)
   L.pc0 = o; o += 512;                                   // FP32 [2][64]: sigma = +1, -1
   L.kv = o; o += 256;
   L.kc = o; o += 256;
   L.u = o; o += 128;
   L.y0 = o; o += al((size_t)n * 4, 16);
-  L.llr = o; o += al((size_t)n * 4, 16);
+  L.llr = o; o += al(N * 4, 16);
   L.degv = o; o += al((size_t)n * 4, 16);
   L.degc = o; o += al((size_t)m * 4, 16);
-  L.sig = o; o += al((size_t)m * 4, 16);
+  L.sig = o; o += al(M * 4, 16);
   L.vptr = o; o += al((size_t)(n + 1) * 4, 16);          // the graph: CSC / CSR row starts
   L.cptr = o; o += al((size_t)(m + 1) * 4, 16);
   L.vadj = o; o += al((size_t)E * 4, 16);                // per edge: row * 64 | swizzle bits
@@ -239,27 +250,28 @@ __device__ __forceinline__ uint4 edge_chunk(const unsigned char* base, uint32_t 
 }
 
 // Epilogue / init of one half (32 columns: hf = 0 the first projection, 1 the second) of a
-// 32-row chunk of a tile: rows r0 .. r0+31 (this lane: r = r0 + lane), TMEM address taddr of
-// the chunk's column 0.  mode 0: init from the tables (variables: P0; checks: Pc0[sigma])
-// with tcgen05.st; mode 1: read the accumulators and add `nb` deg k.  Writes the BF16 row
-// half to dst (lo for hf = 0, hi for hf = 1).
-__device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int rows, bool check,
+// 32-row chunk of a tile: rows r0 .. r0+31 (this lane: group row r = r0 + lane, node l of
+// its shot, l < 0 for a padding row), TMEM address taddr of the chunk's column 0.  mode 0:
+// init from the tables (variables: P0, [64][n]; checks: Pc0[sigma]) with tcgen05.st; mode 1:
+// read the accumulators and add `nb` deg k.  Writes the BF16 row half to dst (lo for hf = 0,
+// hi for hf = 1).
+__device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int l, int n, bool check,
                                         int mode, float nb, const float* p0, const float* pc0,
                                         const float* k, const float* deg, const float* sig,
                                         unsigned char* dst) {
-  const bool ok = r < rows;
+  const bool ok = l >= 0;
   float f[32];
   if (mode == 0) {
-    // initial values: checks one of the two rows of Pc0, variables column r of P0 ([64][rows])
-    const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (ok ? r : 0);
-    const int stride = check ? 1 : rows;
+    // initial values: checks one of the two rows of Pc0, variables column l of P0
+    const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (ok ? l : 0);
+    const int stride = check ? 1 : n;
 #pragma unroll
     for (int i = 0; i < 32; ++i) f[i] = src[(hf * 32 + i) * stride];
     tmem_st16(taddr + hf * 32, f);
     tmem_st16(taddr + hf * 32 + 16, f + 16);
   } else {
     tmem_ld32(taddr + hf * 32, f);
-    const float dk = ok ? nb * deg[r] : 0.f;
+    const float dk = ok ? nb * deg[l] : 0.f;
 #pragma unroll
     for (int i = 0; i < 32; ++i) f[i] = fmaf(dk, k[hf * 32 + i], f[i]);
   }
@@ -271,12 +283,13 @@ __device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int rows,
   }
 }
 
-__global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kTcMaxWarps * 32, 1) prior_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int m = a.m, n = a.n, R = a.rounds, vt = a.vt, ct = a.ct;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, T = blockDim.x;
   const int W = T >> 5;
-  const TcLay L = tc_layout(m, n, a.E, vt, ct);
+  const TcLay L = tc_layout(m, n, a.E, vt, ct, a.S);
+  const int S = a.S, n8 = a.n8, m8 = a.m8, NR = S * n8, MR = S * m8;  // group rows
   unsigned char* mv = smem + L.mv;
   unsigned char* mc = smem + L.mc;
   unsigned char* op = smem + L.op;
@@ -415,15 +428,23 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
   const int q = warp & 3;
   const int nq = (W - q + 3) >> 2;
   const int wslot = warp >> 2;
-  auto chunks = [&](int tiles, int rows, int col0, int rot, bool check, int mode, float nb,
+  auto chunks = [&](int tiles, int col0, int rot, bool check, int mode, float nb,
                     unsigned char* lo, unsigned char* hi) {
+    const int rows = check ? MR : NR, r8 = check ? m8 : n8, nn = check ? m : n;
+    const uint32_t inv = check ? a.inv_m8 : a.inv_n8;
     for (int i = 0; i < tiles; ++i) {
       if (i * 128 + q * 32 >= rows) continue;
       const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(col0 + 64 * i);
+      const int r = i * 128 + q * 32 + lane;
+      int l = -1;
+      if (r < rows) {
+        l = r - (int)__umulhi((uint32_t)r, inv) * r8;
+        if (l >= nn) l = -1;
+      }
       for (int hf = 0; hf < 2; ++hf) {
         if ((2 * i + hf + rot) % nq != wslot) continue;
-        tc_half(taddr, hf, i * 128 + q * 32 + lane, rows, check, mode, nb, p0, pc0,
-                check ? kc : kv, check ? degc : degv, sig, hf ? hi : lo);
+        tc_half(taddr, hf, r, l, n, check, mode, nb, p0, pc0, check ? kc : kv,
+                check ? degc : degv, sig, hf ? hi : lo);
       }
     }
   };
@@ -446,14 +467,25 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
     return ok != 0;
   };
 
-  for (long long shot = blockIdx.x; shot < a.shots && !failed; shot += gridDim.x) {
-    const uint8_t* sp = a.syndromes + shot * m;
-    for (int c = tid; c < m; c += T) sig[c] = sp[c] ? -1.f : 1.f;
-    for (int v = tid; v < n; v += T) llr[v] = y0[v];
+  __shared__ int s_bad[kTcMaxGroup];
+  __shared__ unsigned long long s_slot[kTcMaxGroup];
+  for (long long shot0 = (long long)blockIdx.x * S; shot0 < a.shots && !failed;
+       shot0 += (long long)gridDim.x * S) {
+    const int ns = (int)min((long long)S, a.shots - shot0);  // shots of this group
+    // rows of a shot past the batch, and padding rows, read an all-zero syndrome
+    for (int rr = tid; rr < MR; rr += T) {
+      const int s = (int)__umulhi((uint32_t)rr, a.inv_m8), c = rr - s * m8;
+      sig[rr] = (s < ns && c < m && a.syndromes[(shot0 + s) * m + c]) ? -1.f : 1.f;
+    }
+    for (int rr = tid; rr < NR; rr += T) {
+      const int v = rr - (int)__umulhi((uint32_t)rr, a.inv_n8) * n8;
+      llr[rr] = v < n ? y0[v] : 0.f;
+    }
+    if (tid < kTcMaxGroup) s_bad[tid] = 0;
     __syncthreads();
     // initial accumulators and the round-0 gather sources
-    chunks(vt, n, 0, 0, false, 0, 0.f, cs, bs);
-    chunks(ct, m, 64 * vt, 1, true, 0, 0.f, as, ds);
+    chunks(vt, 0, 0, false, 0, 0.f, cs, bs);
+    chunks(ct, 64 * vt, 1, true, 0, 0.f, as, ds);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     fence_before();
     __syncthreads();
@@ -461,34 +493,37 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
       const bool last = t == R - 1;
       // ---- X2: S_v = sum_c relu(A_c + B_v), 2 threads per row (16 features each), and the
       // LLR update ----
-      for (int base = warp * 32; base < 2 * n; base += T) {
-        const int task = base + lane, v = task >> 1, h = task & 1;
+      for (int base = warp * 32; base < 2 * NR; base += T) {
+        const int task = base + lane, r = task >> 1, h = task & 1;
+        const int sh = (int)__umulhi((uint32_t)r, a.inv_n8), v = r - sh * n8;
+        const bool live = task < 2 * NR && v < n;
         float s[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) s[k] = 0.f;
-        if (task < 2 * n) {
-          const uint4 q0 = *row_chunk(bs, v, 2 * h), q1 = *row_chunk(bs, v, 2 * h + 1);
+        if (live) {
+          const uint4 q0 = *row_chunk(bs, r, 2 * h), q1 = *row_chunk(bs, r, 2 * h + 1);
           unsigned long long acc0[4] = {0ull, 0ull, 0ull, 0ull}, acc1[4] = {0ull, 0ull, 0ull, 0ull};
+          const uint32_t xo = (uint32_t)(sh * m8) << 6;  // the shot's check rows
           const int e1 = vptr[v + 1];
           for (int e = vptr[v]; e < e1; ++e) {
-            const uint32_t x = vadj[e];
+            const uint32_t x = vadj[e] + xo;
             relu_acc8(edge_chunk(as, x, 2 * h), q0, acc0);
             relu_acc8(edge_chunk(as, x, 2 * h + 1), q1, acc1);
           }
           unpack_acc8(acc0, s);
           unpack_acc8(acc1, s + 8);
-          if (!last) {
-            *reinterpret_cast<uint4*>(op + koff(v, 16 * h)) =
-                make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
-            *reinterpret_cast<uint4*>(op + koff(v, 16 * h + 8)) =
-                make_uint4(pack2(s[8], s[9]), pack2(s[10], s[11]), pack2(s[12], s[13]), pack2(s[14], s[15]));
-          }
+        }
+        if (!last && task < 2 * NR) {  // padding rows of the operand are zero
+          *reinterpret_cast<uint4*>(op + koff(r, 16 * h)) =
+              make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
+          *reinterpret_cast<uint4*>(op + koff(r, 16 * h + 8)) =
+              make_uint4(pack2(s[8], s[9]), pack2(s[10], s[11]), pack2(s[12], s[13]), pack2(s[14], s[15]));
         }
         float dot = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) dot = fmaf(u[16 * h + k], s[k], dot);
         dot += __shfl_xor_sync(0xffffffffu, dot, 1);
-        if (task < 2 * n && h == 0) llr[v] += dot + degv[v] * kap;
+        if (live && h == 0) llr[r] += dot + degv[v] * kap;
       }
       if (last) break;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -497,19 +532,23 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
         failed = true;
         break;
       }
-      chunks(vt, n, 0, 0, false, 1, (float)(t + 1), cs, bs);
+      chunks(vt, 0, 0, false, 1, (float)(t + 1), cs, bs);
       fence_before();
       __syncthreads();
       // ---- X1: T_c = sum_v relu(C_v + D_c) ----
-      for (int task = tid; task < 4 * m; task += T) {
-        const int c = task >> 2, b = task & 3;
-        const uint4 qd = *row_chunk(ds, c, b);
-        unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
-        const int e1 = cptr[c + 1];
-        for (int e = cptr[c]; e < e1; ++e) relu_acc8(edge_chunk(cs, cadj[e], b), qd, acc);
-        float s[8];
-        unpack_acc8(acc, s);
-        *reinterpret_cast<uint4*>(op + koff(c, 8 * b)) =
+      for (int task = tid; task < 4 * MR; task += T) {
+        const int r = task >> 2, b = task & 3;
+        const int sh = (int)__umulhi((uint32_t)r, a.inv_m8), c = r - sh * m8;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (c < m) {
+          const uint4 qd = *row_chunk(ds, r, b);
+          unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+          const uint32_t xo = (uint32_t)(sh * n8) << 6;  // the shot's variable rows
+          const int e1 = cptr[c + 1];
+          for (int e = cptr[c]; e < e1; ++e) relu_acc8(edge_chunk(cs, cadj[e] + xo, b), qd, acc);
+          unpack_acc8(acc, s);
+        }
+        *reinterpret_cast<uint4*>(op + koff(r, 8 * b)) =
             make_uint4(pack2(s[0], s[1]), pack2(s[2], s[3]), pack2(s[4], s[5]), pack2(s[6], s[7]));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -518,42 +557,50 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
         failed = true;
         break;
       }
-      chunks(ct, m, 64 * vt, 1, true, 1, (float)(t + 1), as, ds);
+      chunks(ct, 64 * vt, 1, true, 1, (float)(t + 1), as, ds);
       fence_before();
       __syncthreads();
     }
     if (failed) break;
     __syncthreads();
     if (a.llr_out) {
-      float* lo = a.llr_out + shot * n;
-      for (int v = tid; v < n; v += T) lo[v] = llr[v];
+      for (int rr = tid; rr < NR; rr += T) {
+        const int s = (int)__umulhi((uint32_t)rr, a.inv_n8), v = rr - s * n8;
+        if (s < ns && v < n) a.llr_out[(shot0 + s) * n + v] = llr[rr];
+      }
       __syncthreads();
       continue;
     }
-    // ---- decode mode: the hard decision of the LLRs, or the shot is queued for LSD ----
-    bool bad = false;
-    for (int c = tid; c < m; c += T) {
-      unsigned par = sig[c] < 0.f ? 1u : 0u;
+    // ---- decode mode: per shot, the hard decision of the LLRs, or the shot is queued for
+    // LSD ----
+    for (int rr = tid; rr < MR; rr += T) {
+      const int s = (int)__umulhi((uint32_t)rr, a.inv_m8), c = rr - s * m8;
+      if (s >= ns || c >= m) continue;
+      unsigned par = sig[rr] < 0.f ? 1u : 0u;
+      const float* ls = llr + s * n8;
       const int e1 = cptr[c + 1];
-      for (int e = cptr[c]; e < e1; ++e) par ^= llr[cadj[e] >> 6] < 0.f;
-      bad = bad || par;
+      for (int e = cptr[c]; e < e1; ++e) par ^= ls[cadj[e] >> 6] < 0.f;
+      if (par) s_bad[s] = 1;
     }
-    if (__syncthreads_or(bad)) {
-      __shared__ unsigned long long s_slot;
-      if (tid == 0) {
-        s_slot = atomicAdd(&a.ctr->lsd_count, 1ULL);
-        a.queue[s_slot] = (int32_t)shot;
-      }
-      __syncthreads();
-      float* lo = a.queue_llr + (long long)s_slot * n;
-      for (int v = tid; v < n; v += T) lo[v] = llr[v];
-    } else {
-      uint8_t* co = a.corrections + shot * n;
-      for (int v = tid; v < n; v += T) co[v] = llr[v] < 0.f ? 1 : 0;
-      if (tid == 0) {
+    __syncthreads();
+    if (tid < ns) {
+      const long long shot = shot0 + tid;
+      if (s_bad[tid]) {
+        s_slot[tid] = atomicAdd(&a.ctr->lsd_count, 1ULL);
+        a.queue[s_slot[tid]] = (int32_t)shot;
+      } else {
         if (a.status) a.status[shot] = LSD_SHOT_OK_BP;
         atomicAdd(&a.ctr->bp_converged, 1ULL);
       }
+    }
+    __syncthreads();
+    for (int rr = tid; rr < NR; rr += T) {
+      const int s = (int)__umulhi((uint32_t)rr, a.inv_n8), v = rr - s * n8;
+      if (s >= ns || v >= n) continue;
+      if (s_bad[s])
+        a.queue_llr[(long long)s_slot[s] * n + v] = llr[rr];
+      else
+        a.corrections[(shot0 + s) * n + v] = llr[rr] < 0.f ? 1 : 0;
     }
     __syncthreads();
   }
@@ -572,34 +619,50 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 2) prior_tc_kernel(TcArgs a)
 }
 
 struct TcShape {
-  int vt, ct, cols, threads;
+  int vt, ct, cols, threads, S;
   size_t smem;
 };
 
 // The launch shape for H (m x n with maximal degrees dv, dc), or false when the graph does
-// not fit: at most 8 tiles of 128 rows, the tables in shared memory.
+// not fit: a group of S shots in at most 8 tiles of 128 rows, the tables in shared memory.
+// S is the group that keeps the most shots per SM in flight (TMEM holds 512 / cols CTAs).
 bool tc_shape(int m, int n, int E, int dv, int dc, int max_smem, TcShape* s) {
-  s->vt = (n + 127) / 128;
-  s->ct = (m + 127) / 128;
-  if (s->vt + s->ct > kTcMaxTiles || n >= 65535 || m >= 65535) return false;
-  const int need = 64 * (s->vt + s->ct);
-  s->cols = 32;
-  while (s->cols < need) s->cols <<= 1;
-  s->smem = tc_layout(m, n, E, s->vt, s->ct).total;
-  // at most as many CTAs per SM as TMEM holds: pad shared memory so no more fit
-  const int per_sm = 512 / s->cols;
-  const size_t floor_smem = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1024;
-  if (s->smem < floor_smem) s->smem = floor_smem;
-  if (s->smem > (size_t)max_smem) return false;
-  // warps: the count that leaves the fewest idle task slots in the two gathers
+  if (n >= 65535 || m >= 65535) return false;
+  int best_inflight = 0;
+  for (int S = 1; S <= kTcMaxGroup; ++S) {
+    const int vt = (S * up8(n) + 127) / 128, ct = (S * up8(m) + 127) / 128;
+    if (vt + ct > kTcMaxTiles) break;
+    int cols = 32;
+    while (cols < 64 * (vt + ct)) cols <<= 1;
+    size_t smem = tc_layout(m, n, E, vt, ct, S).total;
+    // at most as many CTAs per SM as TMEM holds: pad shared memory so no more fit
+    const int per_sm = 512 / cols;
+    const size_t floor_smem = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1024;
+    if (smem < floor_smem) smem = floor_smem;
+    if (smem > (size_t)max_smem) continue;
+    if (S * per_sm > best_inflight) {
+      best_inflight = S * per_sm;
+      s->S = S;
+      s->vt = vt;
+      s->ct = ct;
+      s->cols = cols;
+      s->smem = smem;
+    }
+  }
+  if (best_inflight == 0) return false;
+  // warps: the count that leaves the fewest idle task slots in the two gathers, the most
+  // warps among equals (with one CTA per SM up to 20 warps, else up to 10 so that the CTAs
+  // TMEM admits also fit in registers)
+  const int NR = s->S * up8(n), MR = s->S * up8(m);
+  const int max_w = s->cols == 512 ? kTcMaxWarps : 10;
   double best = -1.0;
-  for (int w = kTcMinWarps; w <= kTcMaxWarps; ++w) {
+  for (int w = kTcMinWarps; w <= max_w; ++w) {
     const int T = 32 * w;
-    // X2: 2 tasks per variable, 16 features each; X1: 4 tasks per check, 8 features each
-    const double pv = (double)((2 * n + T - 1) / T) * T * 2 * dv, pc = (double)((4 * m + T - 1) / T) * T * dc;
-    const double eff = (4.0 * n * dv + 4.0 * m * dc) / (pv + pc);
-    if (eff > best + 1e-9) {
-      best = eff;
+    // X2: 2 tasks per variable row, 16 features each; X1: 4 tasks per check row, 8 each
+    const double pv = (double)((2 * NR + T - 1) / T) * T * 2 * dv, pc = (double)((4 * MR + T - 1) / T) * T * dc;
+    const double eff = (4.0 * NR * dv + 4.0 * MR * dc) / (pv + pc);
+    if (eff > best - 1e-9) {
+      best = eff > best ? eff : best;
       s->threads = T;
     }
   }
@@ -666,6 +729,11 @@ cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float
   a.rounds = rounds;
   a.vt = s.vt;
   a.ct = s.ct;
+  a.S = s.S;
+  a.n8 = up8(g.n);
+  a.m8 = up8(g.m);
+  a.inv_n8 = (uint32_t)((0x100000000ull + a.n8 - 1) / a.n8);
+  a.inv_m8 = (uint32_t)((0x100000000ull + a.m8 - 1) / a.m8);
   a.tmem_cols = s.cols;
   a.chk_ptr = g.chk_ptr;
   a.chk_var = g.chk_var;
@@ -682,7 +750,8 @@ cudaError_t launch_prior_tc(int grid, const DevGraph& g, int rounds, const float
   a.queue_llr = queue_llr;
   a.ctr = ctr;
   a.timeout_flag = timeout_flag;
-  const long long blocks = shots < grid ? shots : grid;
+  const long long groups = (shots + s.S - 1) / s.S;
+  const long long blocks = groups < grid ? groups : grid;
   if (blocks <= 0) return cudaSuccess;
   prior_tc_kernel<<<(int)blocks, s.threads, s.smem, st>>>(a);
   return cudaGetLastError();
