@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--serving-loads", default="1e4,1e5,1e6,1e7",
                     help="offered loads (shots/s) of the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=0.5)
-    ap.add_argument("--serving-slots", type=int, default=3,
+    ap.add_argument("--serving-slots", type=int, default=2,
                     help="in-flight batches per code (per window matrix) in the server")
     ap.add_argument("--legs-out", default=None, help="also write every leg to this JSON file")
     return ap.parse_args()
