@@ -613,10 +613,29 @@ def _bp_onchip_roofline(E, n, m, shots, st):
     s_bp = st["ms_bp"] / 1e3
     ops = OPS_PER_EDGE_ITER * E * st["bp_iterations"]
     io = shots * m + st["bp_converged"] * n + st["lsd_shots"] * 4 * n
+    # a design that streams the messages reads and writes every FP32 edge message once per
+    # iteration (8 B per edge-iteration): the bytes it would move, against the measured HBM
+    # copy bandwidth, in this launch's time
+    stream_bytes = 8.0 * E * st["bp_iterations"]
+    hbm, hbm_src = hbm_peak()
     return {"bound": "alu", "achieved_tops": ops / s_bp / 1e12, "peak_tops": peak,
             "frac": ops / s_bp / 1e12 / peak, "peak_source": src,
             "io_bytes": int(io), "io_gbps": io / s_bp / 1e9,
+            "streaming_equivalent": {"bytes": stream_bytes, "gbps": stream_bytes / s_bp / 1e9,
+                                     "peak_gbps": hbm, "frac": stream_bytes / s_bp / 1e9 / hbm,
+                                     "peak_source": hbm_src,
+                                     "note": "on-chip; streaming-equivalent: 8 B per edge-iteration"},
             "note": "state on chip: HBM carries only the I/O, so the HBM fraction is not the bound"}
+
+
+def hbm_peak():
+    """(GB/s, description): the measured HBM copy bandwidth of MEASURED_PEAKS.json, else the
+    fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
 
 
 def alu_peak():
