@@ -536,8 +536,9 @@ typedef struct lsd_server_options { /* zero = defaults */
   int32_t max_batch;        /* shots per batch (default 8192) */
   int32_t max_wait_us;      /* 0: an idle slot launches whatever is pending at once; > 0: a partial
                                batch waits for max_batch requests or for its oldest to reach this age */
-  int32_t use_graphs;       /* 0: each slot's batch pipeline (gather, BP, LSD, scatter) is captured
-                               once as a CUDA graph and replayed per batch; -1: plain launches */
+  int32_t use_graphs;       /* 0: each slot's batch pipeline is captured once as two CUDA graphs
+                               (gather, BP, write-back of the rows BP solved; LSD, write-back
+                               of the rest) and replayed per batch; -1: plain launches */
   size_t mem_budget;        /* device bytes of in-flight shots (m + 2n + 2 + 4(n+1) each); 0 = no limit */
 } lsd_server_options;
 
