@@ -156,7 +156,7 @@ int lsd_decode_batch(lsd_decoder* dec, int64_t shots, const uint8_t* syndromes,
  * lsd_decode_batch_host -- lsd_decode_batch with HOST buffers: copies the syndromes to
  * the decoder's device staging buffers, decodes, copies the corrections (and status)
  * back, and synchronizes.  Pinned host memory makes the copies asynchronous DMA.  A batch
- * of at least 2 x 65536 shots with stats == NULL runs as a pipeline of up to 8 chunks on
+ * of at least 2 x 65536 shots with stats == NULL runs as a pipeline of up to 4 chunks on
  * two internal copy streams (copies of one chunk overlap the decoding of its neighbours);
  * the results are the same as one call per batch.
  *   syndromes    host, [shots][m] bytes.   corrections host, [shots][n] bytes.
