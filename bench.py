@@ -764,7 +764,7 @@ def serving_leg(args):
                       "BB[[288,12,18]] d=18: H 2736x7776"],
             "noise": "phenomenological p = q = 0.003", "bp_iters": 30, "lsd_order": 0,
             "mix": "equal", "seconds_per_load": args.serving_seconds,
-            "graphs": "one CUDA graph per slot (gather, BP, LSD, scatter)",
+            "graphs": "two CUDA graphs per slot (gather, BP, write-back of the rows BP solved; LSD, write-back of the rest); a request completes when its row is written back",
             "slots_per_code": args.serving_slots, "loads": out,
             "batch_reference": {"ms_per_65536_shots": batch_ms,
                                 "mix_shots_per_s": mix_batch_rate},
