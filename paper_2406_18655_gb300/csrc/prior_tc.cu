@@ -96,7 +96,7 @@ __host__ __device__ inline TcLay tc_layout(int m, int n, int E, int vt, int ct, 
   L.ds = o; o += al(M * 64, 128);
   L.cs = o; o += al(N * 64, 128);
   L.bs = o; o += al(N * 64, 128);                        // at set-up, with cs: h_v^0 [n][32] FP32
-  L.p0 = o; o += (size_t)n * 256;                        // FP32 [64][n] (column-major)
+  L.p0 = o; o += (size_t)n * 256;                        // FP32 [n][64], 4-float chunks rotated
   L.pc0 = o; o += 512;                                   // FP32 [2][64]: sigma = +1, -1
   L.kv = o; o += 256;
   L.kc = o; o += 256;
@@ -249,10 +249,16 @@ __device__ __forceinline__ uint4 edge_chunk(const unsigned char* base, uint32_t 
   return *reinterpret_cast<const uint4*>(base + (x & ~63u) + ((((uint32_t)b ^ x) & 3u) << 4));
 }
 
+// P0 row v (64 FP32) as 16 chunks of 4: chunk c at position (c + v) mod 16, so that 32 lanes
+// reading chunk c of consecutive rows spread over all banks.
+__host__ __device__ __forceinline__ int p0_index(int v, int o) {
+  return v * 64 + ((((o >> 2) + v) & 15) << 2) + (o & 3);
+}
+
 // Epilogue / init of one half (32 columns: hf = 0 the first projection, 1 the second) of a
 // 32-row chunk of a tile: rows r0 .. r0+31 (this lane: group row r = r0 + lane, node l of
 // its shot, l < 0 for a padding row), TMEM address taddr of the chunk's column 0.  mode 0:
-// init from the tables (variables: P0, [64][n]; checks: Pc0[sigma]) with tcgen05.st; mode 1:
+// init from the tables (variables: P0, rows of p0_index; checks: Pc0[sigma]) with tcgen05.st; mode 1:
 // read the accumulators and add `nb` deg k.  Writes the BF16 row half to dst (lo for hf = 0,
 // hi for hf = 1).
 __device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int l, int n, bool check,
@@ -262,11 +268,22 @@ __device__ __forceinline__ void tc_half(uint32_t taddr, int hf, int r, int l, in
   const bool ok = l >= 0;
   float f[32];
   if (mode == 0) {
-    // initial values: checks one of the two rows of Pc0, variables column l of P0
-    const float* src = check ? pc0 + (ok && sig[r] < 0.f ? 64 : 0) : p0 + (ok ? l : 0);
-    const int stride = check ? 1 : n;
+    // initial values: checks one of the two rows of Pc0, variables row l of P0
+    if (check) {
+      const float* src = pc0 + (ok && sig[r] < 0.f ? 64 : 0) + hf * 32;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) f[i] = src[(hf * 32 + i) * stride];
+      for (int i = 0; i < 32; ++i) f[i] = src[i];
+    } else {
+      const int v = ok ? l : 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(p0 + p0_index(v, 32 * hf + 4 * q));
+        f[4 * q] = x.x;
+        f[4 * q + 1] = x.y;
+        f[4 * q + 2] = x.z;
+        f[4 * q + 3] = x.w;
+      }
+    }
     tmem_st16(taddr + hf * 32, f);
     tmem_st16(taddr + hf * 32 + 16, f + 16);
   } else {
@@ -382,7 +399,7 @@ __global__ void __launch_bounds__(kTcMaxWarps * 32, 1) prior_tc_kernel(TcArgs a)
       float acc = 0.f;
 #pragma unroll
       for (int j = 0; j < HD; ++j) acc = fmaf(swv[o * HD + ((j + v) & (HD - 1))], h[j], acc);
-      p0[o * n + v] = acc;
+      p0[p0_index(v, o)] = acc;
     }
   }
   for (int v = tid; v < n; v += T) {
